@@ -1,0 +1,247 @@
+/*
+ * Oracle: Faddeeva function, Unno-Rachkovsky synthesis, weights and chi2.
+ * TEST INFRASTRUCTURE ONLY (see oracle.h).
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "oracle.h"
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+#define OR_C_KMS 299792.458   /* speed of light [km/s] */
+#define OR_ZEEMAN 4.6686e-13  /* e/(4 pi m c^2) in A^-1 G^-1 (textbook value) */
+
+/*
+ * Faddeeva function w(z) = exp(-z^2) erfc(-i z), z = x + i y.
+ *
+ * The paper evaluates the Voigt and Faraday-Voigt profiles H and F with a
+ * rational approximation (Section 4, Hui et al. 1978).  The oracle uses a
+ * different, published method so that it shares nothing with the GPU path:
+ * the trapezoidal rule with pole correction of Matta & Reichel (1971,
+ * Math. Comp. 25, 339) applied to
+ *     w(z) = (i z / pi) * Integral exp(-t^2) / (z^2 - t^2) dt,   Im z > 0,
+ * with step h = 0.5 on nodes t = k h, or on the shifted nodes t = (k+1/2) h
+ * when x lies within h/4 of an unshifted node (this keeps every denominator
+ * at least h/4 away from zero).  The poles at t = +-z add
+ *     2 exp(-z^2) / (1 -+ exp(-2 pi i z / h))    for Im z < pi / h.
+ * The discretisation error is of order exp(-pi^2/h^2) ~ 5e-18; 16 nodes per
+ * side leave a truncation of exp(-64).  For y < 0 the reflection
+ * w(z) = 2 exp(-z^2) - w(-z) is used (w is entire).
+ */
+static double complex faddeeva_upper(double x, double y)
+{
+    const double h = 0.5;
+    const int nk = 16;
+    const double complex z = x + I * y;
+    const double complex z2 = z * z;
+    const double q = x / h;
+    const int shifted = fabs(q - nearbyint(q)) < 0.25;
+    double complex s = 0.0;
+    for (int k = 0; k <= nk; ++k) {
+        double t, wt;
+        if (shifted) {
+            t = (k + 0.5) * h;
+            wt = 1.0;
+        } else {
+            t = k * h;
+            wt = (k == 0) ? 0.5 : 1.0;
+        }
+        s += wt * exp(-t * t) / (z2 - t * t);
+    }
+    double complex val = (2.0 * I * h / M_PI) * z * s;
+    if (y < M_PI / h) {
+        double complex e = cexp(-2.0 * I * M_PI * z / h);
+        double complex den = shifted ? (1.0 + e) : (1.0 - e);
+        val += 2.0 * cexp(-z2) / den;
+    }
+    return val;
+}
+
+void or_faddeeva(double x, double y, double *re, double *im)
+{
+    double complex w;
+    if (y >= 0.0) {
+        w = faddeeva_upper(x, y);
+    } else {
+        double complex z = x + I * y;
+        w = 2.0 * cexp(-z * z) - faddeeva_upper(-x, -y);
+    }
+    *re = creal(w);
+    *im = cimag(w);
+}
+
+/*
+ * Propagation-matrix elements at one wavelength (Section 4: K = 1 + eta0 Phi).
+ * The paper defers the elements of Phi to Landi Degl'Innocenti & Landolfi;
+ * with the effective-triplet Zeeman pattern they are, per line l with
+ * eta0_l = eta0 * r_l and phi + i psi = w(z):
+ *   eta_I = 1 + sum eta0_l/2 [phi_p sin^2 t + (phi_b + phi_r)/2 (1 + cos^2 t)]
+ *   eta_Q =     sum eta0_l/2 [phi_p - (phi_b + phi_r)/2] sin^2 t cos 2chi
+ *   eta_U =     sum eta0_l/2 [phi_p - (phi_b + phi_r)/2] sin^2 t sin 2chi
+ *   eta_V =     sum eta0_l/2 (phi_r - phi_b) cos t
+ * and rho_Q, rho_U, rho_V the same with psi.  b, p, r are the sigma_blue,
+ * pi and sigma_red components centred at v + v_B, v and v - v_B.
+ */
+static void kmatrix(const or_problem *pb, const double *p, double lam,
+                    double e[7])
+{
+    const double deg = M_PI / 180.0;
+    const double B = p[0], th = p[1] * deg, ch = p[2] * deg, vlos = p[3];
+    const double dld_mA = p[4], a = p[5], eta0 = p[6];
+    const double st = sin(th), ct = cos(th);
+    const double s2 = st * st, c2 = ct * ct;
+    const double c2x = cos(2.0 * ch), s2x = sin(2.0 * ch);
+    double etaI = 1.0, etaQ = 0.0, etaU = 0.0, etaV = 0.0;
+    double rhoQ = 0.0, rhoU = 0.0, rhoV = 0.0;
+    for (int l = 0; l < pb->n_lines; ++l) {
+        const double l0 = pb->lambda0[l];
+        const double lc = l0 * (1.0 + vlos / OR_C_KMS);
+        const double dD = dld_mA * 1e-3 * l0 / pb->lambda_dop;
+        const double v = (lam - lc) / dD;
+        const double vB = OR_ZEEMAN * pb->g[l] * l0 * l0 * B / dD;
+        double phb, psb, php, psp, phr, psr;
+        or_faddeeva(v + vB, a, &phb, &psb);
+        or_faddeeva(v, a, &php, &psp);
+        or_faddeeva(v - vB, a, &phr, &psr);
+        const double h = 0.5 * eta0 * pb->eta_ratio[l];
+        etaI += h * (php * s2 + 0.5 * (phb + phr) * (1.0 + c2));
+        etaQ += h * (php - 0.5 * (phb + phr)) * s2 * c2x;
+        etaU += h * (php - 0.5 * (phb + phr)) * s2 * s2x;
+        etaV += h * (phr - phb) * ct;
+        rhoQ += h * (psp - 0.5 * (psb + psr)) * s2 * c2x;
+        rhoU += h * (psp - 0.5 * (psb + psr)) * s2 * s2x;
+        rhoV += h * (psr - psb) * ct;
+    }
+    e[0] = etaI; e[1] = etaQ; e[2] = etaU; e[3] = etaV;
+    e[4] = rhoQ; e[5] = rhoU; e[6] = rhoV;
+}
+
+/*
+ * Milne-Eddington solution (Section 4): with S = S0 + S1 tau the emergent
+ * Stokes vector is S0 e + mu S1 K^-1 e, e = (1,0,0,0); I_c = S0 + mu S1.
+ * K^-1 e written out (Landi Degl'Innocenti closed form):
+ *   Delta = eI^2 (eI^2 - eQ^2 - eU^2 - eV^2 + rQ^2 + rU^2 + rV^2) - Pi^2,
+ *   Pi = eQ rQ + eU rU + eV rV,
+ *   I = eI (eI^2 + rQ^2 + rU^2 + rV^2) / Delta,
+ *   Q = -[eI^2 eQ + eI (eV rU - eU rV) + rQ Pi] / Delta, U, V cyclic.
+ */
+void or_synth(const or_problem *pb, const double *p, double mu, double *stokes)
+{
+    const int nl = pb->n_lambda;
+    const double S0 = p[7], S1 = p[8];
+    for (int j = 0; j < nl; ++j) {
+        double e[7];
+        kmatrix(pb, p, pb->lambda[j], e);
+        const double eI = e[0], eQ = e[1], eU = e[2], eV = e[3];
+        const double rQ = e[4], rU = e[5], rV = e[6];
+        const double Pi = eQ * rQ + eU * rU + eV * rV;
+        const double eI2 = eI * eI;
+        const double Delta =
+            eI2 * (eI2 - eQ * eQ - eU * eU - eV * eV + rQ * rQ + rU * rU + rV * rV)
+            - Pi * Pi;
+        const double f = mu * S1 / Delta;
+        stokes[0 * nl + j] = S0 + f * eI * (eI2 + rQ * rQ + rU * rU + rV * rV);
+        stokes[1 * nl + j] = -f * (eI2 * eQ + eI * (eV * rU - eU * rV) + rQ * Pi);
+        stokes[2 * nl + j] = -f * (eI2 * eU + eI * (eQ * rV - eV * rQ) + rU * Pi);
+        stokes[3 * nl + j] = -f * (eI2 * eV + eI * (eU * rQ - eQ * rU) + rV * Pi);
+    }
+}
+
+/* Same Stokes vector, solving K x = e directly (Gaussian elimination with
+ * partial pivoting) at every wavelength. */
+void or_synth_lu(const or_problem *pb, const double *p, double mu, double *stokes)
+{
+    const int nl = pb->n_lambda;
+    const double S0 = p[7], S1 = p[8];
+    for (int j = 0; j < nl; ++j) {
+        double e[7];
+        kmatrix(pb, p, pb->lambda[j], e);
+        const double eI = e[0], eQ = e[1], eU = e[2], eV = e[3];
+        const double rQ = e[4], rU = e[5], rV = e[6];
+        double K[4][5] = {
+            {eI, eQ, eU, eV, 1.0},
+            {eQ, eI, rV, -rU, 0.0},
+            {eU, -rV, eI, rQ, 0.0},
+            {eV, rU, -rQ, eI, 0.0},
+        };
+        for (int c = 0; c < 4; ++c) {
+            int piv = c;
+            for (int r = c + 1; r < 4; ++r)
+                if (fabs(K[r][c]) > fabs(K[piv][c])) piv = r;
+            if (piv != c)
+                for (int k = 0; k < 5; ++k) {
+                    double t = K[c][k]; K[c][k] = K[piv][k]; K[piv][k] = t;
+                }
+            for (int r = c + 1; r < 4; ++r) {
+                double m = K[r][c] / K[c][c];
+                for (int k = c; k < 5; ++k) K[r][k] -= m * K[c][k];
+            }
+        }
+        double x[4];
+        for (int r = 3; r >= 0; --r) {
+            double s = K[r][4];
+            for (int k = r + 1; k < 4; ++k) s -= K[r][k] * x[k];
+            x[r] = s / K[r][r];
+        }
+        stokes[0 * nl + j] = S0 + mu * S1 * x[0];
+        for (int s = 1; s < 4; ++s) stokes[s * nl + j] = mu * S1 * x[s];
+    }
+}
+
+/*
+ * Inverse-max weights (Section 4.5): w_I = 1/(I_c - I_0), w_Q = 1/max|Q|,
+ * w_U = 1/max|U|, w_V = 1/max|V|.  I_c is read as the largest observed I in
+ * the window and I_0 as the smallest (the line core).  Each denominator is
+ * floored at 1e-6 |I_c| so that a profile that is identically zero gives a
+ * large finite weight; a zero denominator (all-zero input) gives w = 0.
+ */
+void or_weights_invmax(const double *obs, int nl, double *w)
+{
+    double imax = obs[0], imin = obs[0];
+    for (int j = 1; j < nl; ++j) {
+        if (obs[j] > imax) imax = obs[j];
+        if (obs[j] < imin) imin = obs[j];
+    }
+    double d[4];
+    d[0] = imax - imin;
+    for (int s = 1; s < 4; ++s) {
+        double m = 0.0;
+        for (int j = 0; j < nl; ++j) {
+            double a = fabs(obs[s * nl + j]);
+            if (a > m) m = a;
+        }
+        d[s] = m;
+    }
+    const double fl = 1e-6 * fabs(imax);
+    for (int s = 0; s < 4; ++s) {
+        double dd = d[s] > fl ? d[s] : fl;
+        w[s] = dd > 0.0 ? 1.0 / dd : 0.0;
+    }
+}
+
+/* Eq. chisq: chi2 = (1/nu) sum_s w_s^2 sum_j (O_sj - M_sj)^2, nu = 4 N - M. */
+double or_chi2(const double *obs, const double *model, const double *w,
+               int nl, int m)
+{
+    double tot = 0.0;
+    for (int s = 0; s < 4; ++s) {
+        double ss = 0.0;
+        for (int j = 0; j < nl; ++j) {
+            double r = obs[s * nl + j] - model[s * nl + j];
+            ss += r * r;
+        }
+        tot += w[s] * w[s] * ss;
+    }
+    return tot / (double)(4 * nl - m);
+}
+
+/* w(x_i + i y_i) for n points (test convenience). */
+void or_faddeeva_batch(int n, const double *x, const double *y, double *re, double *im)
+{
+    for (int i = 0; i < n; ++i) or_faddeeva(x[i], y[i], re + i, im + i);
+}
