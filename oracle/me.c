@@ -100,9 +100,12 @@ static void kmatrix(const or_problem *pb, const double *p, double lam,
     double rhoQ = 0.0, rhoU = 0.0, rhoV = 0.0;
     for (int l = 0; l < pb->n_lines; ++l) {
         const double l0 = pb->lambda0[l];
-        const double lc = l0 * (1.0 + vlos / OR_C_KMS);
+        /* lambda - lambda_c with lambda_c = lambda0 (1 + v_LOS / c), written as
+         * (lambda - lambda0) - lambda0 v_LOS / c: the first difference is exact
+         * (Sterbenz), so v keeps full relative precision near the line core */
+        const double dl = (lam - l0) - l0 * vlos / OR_C_KMS;
         const double dD = dld_mA * 1e-3 * l0 / pb->lambda_dop;
-        const double v = (lam - lc) / dD;
+        const double v = dl / dD;
         const double vB = OR_ZEEMAN * pb->g[l] * l0 * l0 * B / dD;
         double phb, psb, php, psp, phr, psr;
         or_faddeeva(v + vB, a, &phb, &psb);
