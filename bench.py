@@ -1,0 +1,343 @@
+"""Benchmark: pixels inverted per second on the two-line 256x256 map.
+
+Workload (synthetic stand-in for a SOLIS/VSM scan): Fe I 6301.5 + 6302.5 in
+one propagation matrix, 128 wavelength points over 6301.0-6303.0 A, 65536
+pixels with truth drawn uniformly from the priors, noise 1e-3 I_c;
+population 128, 200 generations.  One step inverts the whole map with the
+FP32 GA (inverse-max fitness, Section 4.5) followed by 10 L-M iterations
+(sigma weights); the reported chi2 is the FP64 sigma-weighted chi2 (about 1
+at the truth).  The plain FP64 GA on the same map is timed on a pixel subset
+for the comparison the metric asks for.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank inverts its own map (pixel ids offset by rank), so
+per-GPU work is fixed (weak scaling); no collective touches the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import genesis_inputs as gi  # noqa: E402
+
+METRIC = "pixels inverted/s at fixed median chi2 vs plain FP64 GA"
+WORKLOAD = "two-line Fe I 6301.5+6302.5 ME inversion, 256x256 px, 128 lambda, npop 128, 200 gen, FP32 GA + 10 L-M"
+NPOP, NGEN, LM_ITERS = 128, 200, 10
+KERNELS_PER_STEP = 4  # GA evolve, FP64 chi2, L-M, FP64 chi2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--side", type=int, default=256, help="map side (pixels = side^2)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ inputs
+def make_map(api, torch, pb, side, rank, device):
+    """Truth, observed cube (GPU synthesis + seeded noise) and sigma weights."""
+    npix = side * side
+    truth = gi.draw_truth(npix, seed=rank)
+    tp = torch.tensor(truth, device=device)
+    clean = api.me_synth(pb, tp)
+    g = torch.Generator(device=device).manual_seed(1000 + rank)
+    noise = torch.randn(clean.shape, generator=g, device=device, dtype=clean.dtype)
+    sig = 1e-3 * (tp[:, 7] + tp[:, 8])
+    obs = (clean + sig.to(clean.dtype)[:, None, None] * noise).contiguous()
+    w = (1.0 / sig)[:, None].repeat(1, 4).contiguous()
+    return truth, obs, w
+
+
+def flop_model(nlines):
+    """Algorithmic FP32 flops (FMA = 2) of one synthesis + chi2, per unit:
+    Weideman evaluation, continued-fraction evaluation, per wavelength point."""
+    return {"weideman": 142.0, "cf": 49.0, "point": 24.0 * nlines + 84.0}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1208_0302_gb300 import _lib, api
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _lib.load()
+
+    spec = gi.two_line_spec()
+    pb32 = api.Problem.from_spec(spec, "f32")
+    pb64 = api.Problem.from_spec(spec, "f64")
+    side = args.side
+    npix = side * side
+    truth, obs, w = make_map(api, torch, pb32, side, rank, dev)
+    lo, hi = gi.PRIOR_LO, gi.PRIOR_HI
+    ga = api.GaSettings(npop=NPOP, ngen=NGEN, seed=rank)
+    pid0 = rank * npix
+    stream = torch.cuda.current_stream()
+
+    def step():
+        best, _ = api.ga_invert_batch(pb32, obs, lo, hi, ga, pixel_id0=pid0)
+        p, c2 = api.lm_polish(pb32, obs, best, lo, hi, iters=LM_ITERS, w=w)
+        return p, c2
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    # the dominant kernel (GA evolve + its FP64 chi2 pass) timed on its stream
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ga_ms = []
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        best, _ = api.ga_invert_batch(pb32, obs, lo, hi, ga, pixel_id0=pid0)
+        g1.record(stream)
+        p, c2 = api.lm_polish(pb32, obs, best, lo, hi, iters=LM_ITERS, w=w)
+        ga_ms.append((g0, g1))
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ga_avg = sum(a.elapsed_time(b) for a, b in ga_ms) / len(ga_ms)
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = npix * world / (ms_max / 1e3)
+    chi2_med = float(c2.median().item())
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    host_obs = obs.cpu().pin_memory()
+    host_w = w.cpu().pin_memory()
+    host_out = torch.empty((npix, 9), dtype=torch.float64).pin_memory()
+    host_chi = torch.empty(npix, dtype=torch.float64).pin_memory()
+    dobs = torch.empty_like(obs)
+    dw = torch.empty_like(w)
+    barrier()
+    h0 = time.perf_counter()
+    for _ in range(args.steps):
+        dobs.copy_(host_obs, non_blocking=True)
+        dw.copy_(host_w, non_blocking=True)
+        best, _ = api.ga_invert_batch(pb32, dobs, lo, hi, ga, pixel_id0=pid0)
+        p2, c22 = api.lm_polish(pb32, dobs, best, lo, hi, iters=LM_ITERS, w=dw)
+        host_out.copy_(p2, non_blocking=True)
+        host_chi.copy_(c22, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - h0) * 1e3 / args.steps
+    te = torch.tensor([e2e_ms], device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_val = npix * world / (float(te.item()) / 1e3)
+
+    result = None
+    if rank == 0:
+        # algorithmic flops of one GA launch from exact branch counts
+        counts = api.ga_count_evaluations(pb32, obs, lo, hi, ga, pixel_id0=pid0)
+        fm = flop_model(len(spec.lines))
+        flops = counts["weideman"] * fm["weideman"] + counts["cf"] * fm["cf"] + counts["points"] * fm["point"]
+        props = torch.cuda.get_device_properties(dev)
+        sms = props.multi_processor_count
+        max_mhz = clk.get("sm_max_mhz") or 2070.0
+        peak = sms * 128 * 2 * max_mhz * 1e6 / 1e12      # FP32 FMA lanes x 2 flops x clock
+        achieved = flops / (ga_avg / 1e3) / 1e12
+        syntheses = counts["syntheses"]
+        result = {
+            "metric": METRIC, "value": value, "unit": "pixels/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded truth from the priors, GPU ME synthesis + 1e-3 Ic Gaussian noise)",
+            "config": {"workload": WORKLOAD, "pixels_per_gpu": npix, "n_lambda": spec.n_lambda,
+                       "npop": NPOP, "ngen": NGEN, "lm_iters": LM_ITERS,
+                       "l2": "inputs larger than L2 (134 MB float32 cube); compute bound"},
+            "median_chi2": chi2_med,
+            "syntheses_per_s": syntheses / (ga_avg / 1e3),
+            "gpu_launches": KERNELS_PER_STEP * args.steps,
+            "clocks": clk,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_ga_evolve<float,2> (+ FP64 chi2 pass)",
+                         "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (derived)",
+                         "ga_ms": ga_avg, "flops_per_launch": flops,
+                         "evaluations": {k: v for k, v in counts.items() if k != "best"}},
+            "e2e": {"value": e2e_val, "unit": "pixels/s",
+                    "h2d_bytes_per_step": int(obs.numel() * obs.element_size() + w.numel() * 8),
+                    "d2h_bytes_per_step": int(npix * 9 * 8 + npix * 8)},
+        }
+        if not args.no_fp64:
+            result["fp64_plain_ga"] = fp64_comparator(api, torch, pb64, obs, w, lo, hi, rank)
+        if not args.no_cpu and world == 1:
+            result["cpu_baseline"] = cpu_baseline(spec, obs, w, lo, hi)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return result
+
+
+def fp64_comparator(api, torch, pb64, obs32, w, lo, hi, rank, n=1024):
+    """Plain FP64 GA (no polish) on the first n pixels of the same map."""
+    obs = obs32[:n].double().contiguous()
+    ga = api.GaSettings(npop=NPOP, ngen=NGEN, seed=rank)
+    api.ga_invert_batch(pb64, obs[:64].contiguous(), lo, hi, api.GaSettings(npop=NPOP, ngen=2))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    best, _ = api.ga_invert_batch(pb64, obs, lo, hi, ga, pixel_id0=rank * obs32.shape[0])
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    chi = api.me_chi2(pb64, obs, best, w=w[:n].contiguous())
+    return {"value": n / (ms / 1e3), "unit": "pixels/s", "pixels": n, "ms": ms,
+            "median_chi2": float(chi.median().item())}
+
+
+def cpu_baseline(spec, obs, w, lo, hi, n=None):
+    """The FP64 oracle (GA + L-M) on a bounded pixel sample, all host cores."""
+    import oracle
+    nth = os.cpu_count() or 1
+    n = n or max(8, 2 * nth)
+    o = obs[:n].double().cpu().numpy()
+    wn = w[:n].cpu().numpy()
+    cfg = oracle.ga_config(NPOP, NGEN, seed=0)
+    t0 = time.perf_counter()
+    r = oracle.ga_invert(spec, o, lo, hi, cfg, nthreads=nth)
+    p, c2 = oracle.lm_polish(spec, o, r["best"], lo, hi, iters=LM_ITERS, w=wn, nthreads=nth)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "pixels/s", "cores": nth, "kind": "oracle",
+            "sample": f"first {n} pixels of the map, FP64 GA (npop {NPOP}, {NGEN} gen) + {LM_ITERS} L-M",
+            "seconds": dt, "median_chi2": float(np.median(c2))}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on a bounded sample, rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import oracle
+    spec = gi.two_line_spec()
+    nth = os.cpu_count() or 1
+    n = max(4, nth)
+    truth = gi.draw_truth(n, seed=0)
+    clean = oracle.synth(spec, truth)
+    obs = clean + 1e-3 * (truth[:, 7] + truth[:, 8])[:, None, None] * gi.draw_noise(n, spec.n_lambda, 0)
+    sig = 1e-3 * (truth[:, 7] + truth[:, 8])
+    w = np.repeat((1 / sig)[:, None], 4, 1)
+    cfg = oracle.ga_config(NPOP, NGEN, seed=0)
+
+    def one():
+        r = oracle.ga_invert(spec, obs, gi.PRIOR_LO, gi.PRIOR_HI, cfg, nthreads=nth)
+        return oracle.lm_polish(spec, obs, r["best"], gi.PRIOR_LO, gi.PRIOR_HI, iters=LM_ITERS, w=w,
+                                nthreads=nth)
+
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        p, c2 = one()
+    dt = (time.perf_counter() - t0) / args.steps
+    val = n / dt
+    return {"impl": "reference", "metric": METRIC, "value": val, "unit": "pixels/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle on a pixel sample)"},
+            "cpu_baseline": {"value": val, "unit": "pixels/s", "cores": nth, "kind": "oracle",
+                             "sample": f"{n} pixels per step"},
+            "e2e": {"value": val, "unit": "pixels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "median_chi2": float(np.median(c2))}
+
+
+def main():
+    args = parse()
+    res = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if res is not None:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,255 @@
+/*
+ * genesis.h - C ABI of the GB300 (sm_103a) implementation of the GENESIS
+ * Milne-Eddington genetic-algorithm Stokes inversion of Harker & Mighell,
+ * "A GPU-Computing Approach to Solar Stokes Profile Inversion" (2012).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an int status: ME_OK (0) or a negative ME_E* code.
+ *    me_last_error() returns a thread-local message for the last failure.
+ *  - Pointers documented "dev" are device pointers on the current CUDA device;
+ *    "host" pointers are read during the call only.  The caller owns every
+ *    buffer; no entry point allocates device memory, except serve_create()
+ *    and the serve handle it returns.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device work is enqueued on it and the call returns without
+ *    synchronising; results are valid once the stream reaches that point.
+ *  - Invalid arguments are rejected on the host (ME_EINVAL) before anything
+ *    is launched; a failed launch returns ME_ECUDA.
+ *  - Parameter vectors have ME_NPAR = 9 entries in this fixed order
+ *    (Section 4, model vector p; v_LOS replaces lambda0 and S0, S1 replace
+ *    S0, beta0 with beta0 = S1/S0):
+ *       0 B [G]          1 theta inclination [deg]   2 chi azimuth [deg]
+ *       3 v_LOS [km/s]   4 Doppler width [mA] at lambda_dop_A
+ *       5 damping a      6 eta0 (line/continuum opacity ratio)
+ *       7 S0             8 S1 (source function S0 + S1 tau)
+ *  - Stokes arrays are [n][4][n_lambda] (I, Q, U, V), pixel-major, of the
+ *    problem's dtype (float for ME_F32, double for ME_F64).
+ */
+#ifndef GENESIS_H
+#define GENESIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define ME_OK 0
+#define ME_EINVAL (-1)    /* invalid argument (message in me_last_error)   */
+#define ME_ENOMEM (-2)    /* allocation failed (serve handle only)         */
+#define ME_ECUDA (-3)     /* CUDA runtime error                            */
+#define ME_EAGAIN (-4)    /* serve queue full, retry later                 */
+#define ME_EPENDING (-5)  /* serve request still running                   */
+#define ME_ETIMEOUT (-6)  /* a bounded wait gave up                        */
+#define ME_ENOTFOUND (-7) /* unknown serve ticket                          */
+
+/* ------------------------------------------------------------ limits/enums */
+#define ME_NPAR 9
+#define ME_MAX_LINES 4
+#define ME_MAX_LAMBDA 512
+#define ME_MIN_POP 32
+#define ME_MAX_POP 1024
+
+#define ME_F32 0 /* float cube, FP32 synthesis and chi2            */
+#define ME_F64 1 /* double cube, FP64 synthesis and chi2           */
+
+#define ME_W_INVMAX 0 /* Section 4.5 inverse-max weights from the data  */
+#define ME_W_USER 1   /* caller-supplied w[npix][4]                     */
+
+/*
+ * One spectral line (Table 1), treated as an effective Zeeman triplet
+ * (sigma_blue, pi, sigma_red at v + v_B, v, v - v_B, Section 4).
+ *   lambda0_A  rest wavelength [A]
+ *   g_eff      effective Lande factor; v_B = 4.6686e-13 g lambda0^2 B / dlambda_D
+ *   eta_ratio  eta0 of this line divided by the eta0 parameter (1 for the
+ *              reference line); all lines add into one propagation matrix.
+ */
+typedef struct me_line {
+    double lambda0_A;
+    double g_eff;
+    double eta_ratio;
+} me_line;
+
+/*
+ * The synthesis problem (Section 4): line list, wavelength grid and geometry.
+ *   n_lines       1..ME_MAX_LINES
+ *   n_lambda      1..ME_MAX_LAMBDA
+ *   lambda_A      HOST pointer to n_lambda wavelengths [A]; copied into the
+ *                 launch parameters, so the caller may free it after the call
+ *   lambda_dop_A  wavelength at which parameter 4 (Doppler width) is quoted;
+ *                 line l uses dlambda_D * lambda0_l / lambda_dop_A
+ *   mu            cosine of the heliocentric angle used when mu_px is NULL
+ *   dtype         ME_F32 or ME_F64: element type of obs/stokes arrays and the
+ *                 arithmetic of synthesis and chi2
+ */
+typedef struct me_problem {
+    int n_lines;
+    me_line line[ME_MAX_LINES];
+    int n_lambda;
+    const double *lambda_A;
+    double lambda_dop_A;
+    double mu;
+    int dtype;
+} me_problem;
+
+/* Parameter bounds u_j <= p_j <= v_j (Section 3, Eq. decode).  lo[5] (damping)
+ * must be >= 0 and lo[4] (Doppler width) > 0. */
+typedef struct me_bounds {
+    double lo[ME_NPAR];
+    double hi[ME_NPAR];
+} me_bounds;
+
+/*
+ * Genetic-algorithm settings (Section 3, Algorithm 1; Section 4.6).
+ *   npop         population, a multiple of 32 in [ME_MIN_POP, ME_MAX_POP]
+ *   ngen         generations (>= 0)
+ *   nsamp        restart period: every nsamp generations (t < ngen) the worst
+ *                half is replaced by new Sobol points; <= 0 disables restarts
+ *   pc           crossover probability of a pair
+ *   pmut_lsb     per-bit mutation probability of the least significant bit;
+ *                bit b (0 = MSB) uses pmut_lsb * pmut_ratio^(15 - b)
+ *   seed         Philox key (low, high 32 bits)
+ *   weight_mode  ME_W_INVMAX or ME_W_USER
+ */
+typedef struct ga_config {
+    int npop;
+    int ngen;
+    int nsamp;
+    double pc;
+    double pmut_lsb;
+    double pmut_ratio;
+    uint64_t seed;
+    int weight_mode;
+} ga_config;
+
+/* Thread-local message describing the last failed call ("" if none). */
+const char *me_last_error(void);
+
+/* ABI version of this library (major * 100 + minor). */
+int me_version(void);
+
+/*
+ * me_synth - Unno-Rachkovsky Stokes vectors of n parameter vectors
+ * (Section 4: K = 1 + eta0 Phi, Stokes = S0 e + mu S1 K^-1 e, I_c = S0 + mu S1).
+ *   params  dev double [n][ME_NPAR]
+ *   mu_px   dev double [n] or NULL (then pb->mu)
+ *   stokes  dev [n][4][n_lambda] of pb->dtype (output)
+ * n = 0 is a no-op.
+ */
+int me_synth(const me_problem *pb, const double *params, const double *mu_px, int n,
+             void *stokes, void *stream);
+
+/*
+ * me_synth_jac - analytic Jacobian d stokes / d p of the same synthesis
+ * (the derivative of Section 4's closed form, with w'(z) = -2 z w + 2i/sqrt(pi)).
+ *   stokes  dev [n][4][n_lambda] of pb->dtype, or NULL
+ *   jac     dev [n][4][n_lambda][ME_NPAR] of pb->dtype (output)
+ */
+int me_synth_jac(const me_problem *pb, const double *params, const double *mu_px, int n,
+                 void *stokes, void *jac, void *stream);
+
+/*
+ * me_synth_vjp - vector-Jacobian product grad_params = J^T grad_stokes, the
+ * adjoint used by the torch.autograd.Function wrapper.
+ *   grad_stokes  dev [n][4][n_lambda] of pb->dtype
+ *   grad_params  dev double [n][ME_NPAR] (output)
+ */
+int me_synth_vjp(const me_problem *pb, const double *params, const double *mu_px, int n,
+                 const void *grad_stokes, double *grad_params, void *stream);
+
+/*
+ * me_chi2 - Eq. chisq, chi2 = (1/nu) sum_s w_s^2 sum_j (O - M)^2 with
+ * nu = 4 n_lambda - ME_NPAR, evaluated in FP64 for each pixel's parameters.
+ *   obs   dev [npix][4][n_lambda] of pb->dtype
+ *   w     dev double [npix][4] (ME_W_USER) or NULL (inverse-max, Section 4.5)
+ *   chi2  dev double [npix] (output)
+ */
+int me_chi2(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
+            int npix, const double *params, double *chi2, void *stream);
+
+/*
+ * ga_invert_batch - Algorithm 1 per pixel, one thread block per pixel with the
+ * population resident in shared memory for all generations:
+ * Sobol initial population, then per generation binary tournament selection,
+ * one-point crossover, LSB-biased mutation, elitism and fitness evaluation
+ * (synthesis + chi2 in pb->dtype arithmetic), with worst-half Sobol restarts
+ * every nsamp generations (Section 4.6).  Philox4x32-10 counters are keyed by
+ * pixel id = pixel_id0 + i, so a pixel's result does not depend on the batch.
+ *   obs         dev [npix][4][n_lambda] of pb->dtype
+ *   w           dev double [npix][4] if cfg->weight_mode == ME_W_USER, else NULL
+ *   mu_px       dev double [npix] or NULL
+ *   best        dev double [npix][ME_NPAR]: decoded best individual (output)
+ *   chi2        dev double [npix]: FP64 re-evaluation of best (output)
+ *   best_genes  dev uint16 [npix][ME_NPAR] or NULL (output)
+ */
+int ga_invert_batch(const me_problem *pb, const void *obs, const double *w,
+                    const double *mu_px, int npix, uint64_t pixel_id0,
+                    const me_bounds *bounds, const ga_config *cfg, double *best,
+                    double *chi2, uint16_t *best_genes, void *stream);
+
+/*
+ * ga_count_evaluations - the same GA as ga_invert_batch (float cubes,
+ * npop <= 256) run by a separate instantiation that also counts work:
+ * counts dev uint64[2] receives (added to its contents) the number of
+ * syntheses (fitness evaluations) and of Faddeeva evaluations that took the
+ * interior branch; every other Faddeeva evaluation took the exterior branch.
+ * The arithmetic and the result `best` are those of ga_invert_batch; the
+ * counts turn into algorithmic flops for roofline reporting.
+ */
+int ga_count_evaluations(const me_problem *pb, const void *obs, const double *w,
+                         const double *mu_px, int npix, uint64_t pixel_id0,
+                         const me_bounds *bounds, const ga_config *cfg, double *best,
+                         unsigned long long *counts, void *stream);
+
+/*
+ * lm_polish - Levenberg-Marquardt refinement of each pixel's parameters
+ * (Levenberg 1944, Marquardt 1963): FP32 analytic Jacobian, normal equations
+ * (J^T W^2 J + lambda D) delta = J^T W^2 r reduced and solved by Cholesky in
+ * FP64, trial step with the azimuth wrapped into [0, 180) and clamped to the
+ * bounds, accepted when chi2 decreases.  iters trial steps are taken.
+ *   params_inout  dev double [npix][ME_NPAR]
+ *   chi2_out      dev double [npix]: FP64 chi2 of the final parameters
+ */
+int lm_polish(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
+              int npix, const me_bounds *bounds, int iters, double lambda0,
+              double *params_inout, double *chi2_out, void *stream);
+
+/* ------------------------------------------------ GA operator entry points
+ * The operators of ga_invert_batch run alone on caller-given populations, so
+ * that they can be checked bit for bit against a reference with injected
+ * fitness values.  nprob independent populations of npop individuals.
+ *
+ * ga_breed - one generation of selection, crossover, mutation and elitism
+ * (Algorithm 1 Select/Recombine/Mutate) at generation `gen` for pixel ids
+ * pixel_id0 + p.
+ *   genes    dev uint16 [nprob][npop][ME_NPAR]
+ *   fitness  dev double [nprob][npop] (NaN counts as +infinity)
+ *   child    dev uint16 [nprob][npop][ME_NPAR] (output)
+ *   elite    dev int [nprob] (output, may be NULL)
+ */
+int ga_breed(const uint16_t *genes, const double *fitness, int nprob, int npop,
+             uint64_t pixel_id0, int gen, const ga_config *cfg, uint16_t *child,
+             int *elite, void *stream);
+
+/*
+ * ga_restart - Section 4.6 restart: the worst npop/2 individuals (stable rank by
+ * fitness, then index) take Sobol points sobol_next + r in rank order r.
+ *   genes  dev uint16 [nprob][npop][ME_NPAR], modified in place
+ */
+int ga_restart(uint16_t *genes, const double *fitness, int nprob, int npop,
+               uint64_t sobol_next, void *stream);
+
+/* Philox4x32-10 of n counters: ctr dev uint32 [n][4], key {lo, hi}, out dev
+ * uint32 [n][4]. */
+int me_philox(const uint32_t *ctr, int n, uint64_t key, uint32_t *out, void *stream);
+
+/* Sobol points first..first+n-1 of dimensions 0..ndim-1 (ndim <= ME_NPAR + 1)
+ * as 32-bit integers: out dev uint32 [n][ndim]. */
+int me_sobol(uint64_t first, int n, int ndim, uint32_t *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GENESIS_H */

@@ -1,0 +1,273 @@
+"""Torch-facing calls of the GENESIS GB300 library.
+
+Each function marshals CUDA tensors into the C ABI of ``include/genesis.h``
+and enqueues the work on torch's current CUDA stream.  No computation of the
+method happens here; PyTorch provides device memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+NPAR = L.ME_NPAR
+F32, F64 = L.ME_F32, L.ME_F64
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _need(t, dtype, shape=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t
+
+
+class Problem:
+    """Line list, wavelength grid and precision (me_problem)."""
+
+    def __init__(self, lines, lambda_grid, lambda_dop, mu=1.0, dtype="f32"):
+        self.lines = [tuple(map(float, ln)) for ln in lines]
+        self.lam = np.ascontiguousarray(lambda_grid, dtype=np.float64)
+        self.lambda_dop = float(lambda_dop)
+        self.mu = float(mu)
+        self.dtype = {"f32": F32, "f64": F64}[dtype]
+        self.torch_dtype = torch.float32 if self.dtype == F32 else torch.float64
+        s = L.MeProblem()
+        s.n_lines = len(self.lines)
+        for i, (l0, g, r) in enumerate(self.lines):
+            s.line[i] = L.MeLine(l0, g, r)
+        s.n_lambda = len(self.lam)
+        s.lambda_A = self.lam.ctypes.data_as(C.POINTER(C.c_double))
+        s.lambda_dop_A = self.lambda_dop
+        s.mu = self.mu
+        s.dtype = self.dtype
+        self._s = s
+
+    @classmethod
+    def from_spec(cls, spec, dtype="f32"):
+        return cls(spec.lines, spec.lambda_grid, spec.lambda_dop, spec.mu, dtype)
+
+    @property
+    def n_lambda(self):
+        return len(self.lam)
+
+    def ref(self):
+        return C.byref(self._s)
+
+
+def bounds(lo, hi) -> L.MeBounds:
+    b = L.MeBounds()
+    for d in range(NPAR):
+        b.lo[d] = float(lo[d])
+        b.hi[d] = float(hi[d])
+    return b
+
+
+@dataclass
+class GaSettings:
+    npop: int = 128
+    ngen: int = 200
+    nsamp: int | None = None
+    pc: float = 0.9
+    pmut_lsb: float = 0.05
+    pmut_ratio: float = 0.7
+    seed: int = 0
+
+    def to_c(self, weight_mode: int) -> L.GaConfig:
+        nsamp = self.ngen // 4 if self.nsamp is None else self.nsamp
+        return L.GaConfig(int(self.npop), int(self.ngen), int(nsamp), float(self.pc),
+                          float(self.pmut_lsb), float(self.pmut_ratio), int(self.seed),
+                          int(weight_mode))
+
+
+def me_synth(pb: Problem, params, mu_px=None):
+    """Stokes [n, 4, n_lambda] of params [n, 9] (float64 CUDA)."""
+    n = params.shape[0]
+    _need(params, torch.float64, (n, NPAR), "params")
+    _need(mu_px, torch.float64, (n,), "mu_px")
+    out = torch.empty((n, 4, pb.n_lambda), dtype=pb.torch_dtype, device=params.device)
+    L.check(L.load().me_synth(pb.ref(), _ptr(params), _ptr(mu_px), n, _ptr(out), _stream()))
+    return out
+
+
+def me_synth_jac(pb: Problem, params, mu_px=None, want_stokes=False):
+    """Jacobian [n, 4, n_lambda, 9] (and Stokes if asked)."""
+    n = params.shape[0]
+    _need(params, torch.float64, (n, NPAR), "params")
+    _need(mu_px, torch.float64, (n,), "mu_px")
+    jac = torch.empty((n, 4, pb.n_lambda, NPAR), dtype=pb.torch_dtype, device=params.device)
+    st = torch.empty((n, 4, pb.n_lambda), dtype=pb.torch_dtype, device=params.device) if want_stokes else None
+    L.check(L.load().me_synth_jac(pb.ref(), _ptr(params), _ptr(mu_px), n, _ptr(st), _ptr(jac), _stream()))
+    return (jac, st) if want_stokes else jac
+
+
+def me_synth_vjp(pb: Problem, params, grad_stokes, mu_px=None):
+    """J^T grad_stokes -> [n, 9] float64."""
+    n = params.shape[0]
+    _need(params, torch.float64, (n, NPAR), "params")
+    _need(grad_stokes, pb.torch_dtype, (n, 4, pb.n_lambda), "grad_stokes")
+    _need(mu_px, torch.float64, (n,), "mu_px")
+    out = torch.empty((n, NPAR), dtype=torch.float64, device=params.device)
+    L.check(L.load().me_synth_vjp(pb.ref(), _ptr(params), _ptr(mu_px), n, _ptr(grad_stokes),
+                                  _ptr(out), _stream()))
+    return out
+
+
+def me_chi2(pb: Problem, obs, params, w=None, mu_px=None):
+    """FP64 chi2 [npix] of params against obs (Eq. chisq)."""
+    npix = obs.shape[0]
+    _need(obs, pb.torch_dtype, (npix, 4, pb.n_lambda), "obs")
+    _need(params, torch.float64, (npix, NPAR), "params")
+    _need(w, torch.float64, (npix, 4), "w")
+    _need(mu_px, torch.float64, (npix,), "mu_px")
+    out = torch.empty(npix, dtype=torch.float64, device=obs.device)
+    L.check(L.load().me_chi2(pb.ref(), _ptr(obs), _ptr(w), _ptr(mu_px), npix, _ptr(params),
+                             _ptr(out), _stream()))
+    return out
+
+
+def ga_invert_batch(pb: Problem, obs, lo, hi, ga: GaSettings, w=None, mu_px=None, pixel_id0=0,
+                    want_genes=False):
+    """Algorithm 1 per pixel on the GPU -> (best [npix, 9], chi2 [npix][, genes])."""
+    npix = obs.shape[0]
+    _need(obs, pb.torch_dtype, (npix, 4, pb.n_lambda), "obs")
+    _need(w, torch.float64, (npix, 4), "w")
+    _need(mu_px, torch.float64, (npix,), "mu_px")
+    dev = obs.device
+    best = torch.empty((npix, NPAR), dtype=torch.float64, device=dev)
+    chi2 = torch.empty(npix, dtype=torch.float64, device=dev)
+    genes = torch.empty((npix, NPAR), dtype=torch.int16, device=dev) if want_genes else None
+    cfg = ga.to_c(L.ME_W_USER if w is not None else L.ME_W_INVMAX)
+    b = bounds(lo, hi)
+    L.check(L.load().ga_invert_batch(pb.ref(), _ptr(obs), _ptr(w), _ptr(mu_px), npix,
+                                     int(pixel_id0), C.byref(b), C.byref(cfg), _ptr(best),
+                                     _ptr(chi2), _ptr(genes), _stream()))
+    if want_genes:
+        return best, chi2, genes
+    return best, chi2
+
+
+def ga_count_evaluations(pb: Problem, obs, lo, hi, ga: GaSettings, w=None, mu_px=None, pixel_id0=0):
+    """Work counts of one ga_invert_batch run (same arithmetic, counting build)."""
+    npix = obs.shape[0]
+    _need(obs, pb.torch_dtype, (npix, 4, pb.n_lambda), "obs")
+    _need(w, torch.float64, (npix, 4), "w")
+    _need(mu_px, torch.float64, (npix,), "mu_px")
+    best = torch.empty((npix, NPAR), dtype=torch.float64, device=obs.device)
+    counts = torch.zeros(2, dtype=torch.int64, device=obs.device)
+    cfg = ga.to_c(L.ME_W_USER if w is not None else L.ME_W_INVMAX)
+    b = bounds(lo, hi)
+    L.check(L.load().ga_count_evaluations(pb.ref(), _ptr(obs), _ptr(w), _ptr(mu_px), npix,
+                                          int(pixel_id0), C.byref(b), C.byref(cfg), _ptr(best),
+                                          _ptr(counts), _stream()))
+    c = counts.cpu().numpy()
+    syn = int(c[0])
+    points = syn * pb.n_lambda
+    evals = points * 3 * len(pb.lines)
+    return {"syntheses": syn, "points": points, "weideman": int(c[1]), "cf": evals - int(c[1]),
+            "best": best}
+
+
+def lm_polish(pb: Problem, obs, params, lo, hi, iters=10, lambda0=1e-3, w=None, mu_px=None):
+    """L-M refinement; returns (params [npix, 9], chi2 [npix]) (params updated in a copy)."""
+    npix = obs.shape[0]
+    _need(obs, pb.torch_dtype, (npix, 4, pb.n_lambda), "obs")
+    _need(params, torch.float64, (npix, NPAR), "params")
+    _need(w, torch.float64, (npix, 4), "w")
+    _need(mu_px, torch.float64, (npix,), "mu_px")
+    p = params.clone()
+    chi2 = torch.empty(npix, dtype=torch.float64, device=obs.device)
+    b = bounds(lo, hi)
+    L.check(L.load().lm_polish(pb.ref(), _ptr(obs), _ptr(w), _ptr(mu_px), npix, C.byref(b),
+                               int(iters), float(lambda0), _ptr(p), _ptr(chi2), _stream()))
+    return p, chi2
+
+
+# ---------------------------------------------------------- operator checks
+
+def _u16_to_dev(a, device):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint16).view(np.int16)).to(device)
+
+
+def _dev_to_u16(t):
+    return t.cpu().numpy().view(np.uint16)
+
+
+def ga_breed(genes_u16, fitness, pixel_id0, gen, ga: GaSettings, device="cuda"):
+    """One breeding step of nprob populations (numpy uint16 [nprob, npop, 9],
+    float64 [nprob, npop]) -> (child uint16, elite int)."""
+    g = np.ascontiguousarray(genes_u16, dtype=np.uint16)
+    nprob, npop, _ = g.shape
+    gd = _u16_to_dev(g, device)
+    fd = torch.as_tensor(np.ascontiguousarray(fitness, dtype=np.float64)).to(device)
+    child = torch.empty_like(gd)
+    elite = torch.empty(nprob, dtype=torch.int32, device=device)
+    cfg = ga.to_c(L.ME_W_INVMAX)
+    L.check(L.load().ga_breed(_ptr(gd), _ptr(fd), nprob, npop, int(pixel_id0), int(gen),
+                              C.byref(cfg), _ptr(child), _ptr(elite), _stream()))
+    return _dev_to_u16(child), elite.cpu().numpy()
+
+
+def ga_restart(genes_u16, fitness, sobol_next, device="cuda"):
+    g = np.ascontiguousarray(genes_u16, dtype=np.uint16)
+    nprob, npop, _ = g.shape
+    gd = _u16_to_dev(g, device)
+    fd = torch.as_tensor(np.ascontiguousarray(fitness, dtype=np.float64)).to(device)
+    L.check(L.load().ga_restart(_ptr(gd), _ptr(fd), nprob, npop, int(sobol_next), _stream()))
+    return _dev_to_u16(gd)
+
+
+def philox(ctr_u32, key, device="cuda"):
+    c = np.ascontiguousarray(ctr_u32, dtype=np.uint32).reshape(-1, 4)
+    cd = torch.from_numpy(c.view(np.int32)).to(device)
+    out = torch.empty_like(cd)
+    L.check(L.load().me_philox(_ptr(cd), c.shape[0], int(key), _ptr(out), _stream()))
+    return out.cpu().numpy().view(np.uint32)
+
+
+def sobol(first, n, ndim, device="cuda"):
+    out = torch.empty((n, ndim), dtype=torch.int32, device=device)
+    L.check(L.load().me_sobol(int(first), int(n), int(ndim), _ptr(out), _stream()))
+    return out.cpu().numpy().view(np.uint32)
+
+
+# ------------------------------------------------------------- autograd
+
+class MeSynthFunction(torch.autograd.Function):
+    """Stokes = me_synth(params); backward uses the analytic adjoint me_synth_vjp."""
+
+    @staticmethod
+    def forward(ctx, params, pb, mu_px):
+        ctx.pb = pb
+        ctx.save_for_backward(params, mu_px if mu_px is not None else torch.empty(0))
+        ctx.has_mu = mu_px is not None
+        return me_synth(pb, params.detach().contiguous(), mu_px)
+
+    @staticmethod
+    def backward(ctx, grad):
+        params, mu = ctx.saved_tensors
+        g = me_synth_vjp(ctx.pb, params.detach().contiguous(), grad.contiguous().to(ctx.pb.torch_dtype),
+                         mu if ctx.has_mu else None)
+        return g, None, None
+
+
+def synth_autograd(pb: Problem, params, mu_px=None):
+    return MeSynthFunction.apply(params, pb, mu_px)

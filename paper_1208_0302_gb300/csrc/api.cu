@@ -1,0 +1,466 @@
+// C-ABI entry points of libgenesis (see include/genesis.h): argument
+// validation, launch-parameter assembly and per-device table upload.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "genesis.h"
+#include "kernels.h"
+
+namespace genesis {
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(ME_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------- coefficient tables
+
+// Weideman (1994) coefficients a_0..a_N of (L^2 + t^2) exp(-t^2) in the basis
+// ((L + i t)/(L - i t))^n, i.e. the Fourier cosine coefficients of
+// f(theta) = L^2 sec^2(theta/2) exp(-L^2 tan^2(theta/2)) on (-pi, pi),
+// integrated with the (spectrally accurate) midpoint rule.
+std::vector<double> weideman_coefficients(int N, double L)
+{
+    const int K = 8192;
+    std::vector<double> a(N + 1, 0.0);
+    for (int k = 0; k < K; ++k) {
+        const double th = -M_PI + 2.0 * M_PI * (k + 0.5) / K;
+        const double t = L * std::tan(0.5 * th);
+        const double f = std::exp(-t * t) * (L * L + t * t);
+        for (int n = 0; n <= N; ++n) a[n] += f * std::cos(n * th);
+    }
+    for (int n = 0; n <= N; ++n) a[n] /= K;
+    return a;
+}
+
+// k-th convergent of the Laplace continued fraction of w(z):
+// t_{k+1} = z, t_m = z - (m/2) / t_{m+1}, w = (i/sqrt(pi)) / t_1.
+// With t_m = A_m / B_m: A_m = z A_{m+1} - (m/2) B_{m+1}, B_m = A_{m+1}, so
+// w = (i/sqrt(pi)) B_1 / A_1.  For odd k, A_1 is even and B_1 odd in z:
+// A_1 = a(u), B_1 = z b(u) with u = z^2.  Returns a (ascending in u) and b.
+void cf_coefficients(int k, std::vector<double> &a, std::vector<double> &b)
+{
+    std::vector<double> A = {0.0, 1.0};  // z
+    std::vector<double> B = {1.0};       // 1
+    for (int m = k; m >= 1; --m) {
+        std::vector<double> An(A.size() + 1, 0.0);
+        for (size_t i = 0; i < A.size(); ++i) An[i + 1] += A[i];
+        for (size_t i = 0; i < B.size(); ++i) An[i] -= 0.5 * m * B[i];
+        B = A;
+        A = An;
+    }
+    a.clear();
+    b.clear();
+    for (size_t i = 0; i < A.size(); i += 2) a.push_back(A[i]);
+    for (size_t i = 1; i < B.size(); i += 2) b.push_back(B[i]);
+}
+
+// Sobol direction numbers (Section 4.6; Sobol 1967, Bratley & Fox 1988):
+// dimension 0 is van der Corput; dimension d >= 1 takes the d-th primitive
+// polynomial over GF(2) (ordered by degree, then by integer encoding) and
+// initial numbers m_k = 2^k - 1, extended by the Sobol recurrence.
+bool gf2_primitive(unsigned poly, int deg)
+{
+    // x must have multiplicative order exactly 2^deg - 1 modulo poly
+    const unsigned period = (1u << deg) - 1u;
+    unsigned r = 1u;
+    for (unsigned e = 1; e <= period; ++e) {
+        r <<= 1;
+        if (r >> deg) r ^= poly;
+        if (r == 1u) return e == period;
+    }
+    return false;
+}
+
+void sobol_directions(uint32_t out[10][32])
+{
+    for (int k = 0; k < 32; ++k) out[0][k] = 1u << (31 - k);
+    int dim = 1;
+    for (int deg = 1; dim < 10; ++deg) {
+        for (unsigned poly = (1u << deg) | 1u; poly < (2u << deg) && dim < 10; poly += 2u) {
+            if (!gf2_primitive(poly, deg)) continue;
+            uint64_t m[33];
+            for (int k = 1; k <= deg; ++k) m[k] = (1ull << k) - 1ull;
+            for (int k = deg + 1; k <= 32; ++k) {
+                uint64_t v = m[k - deg] ^ (m[k - deg] << deg);
+                for (int i = 1; i < deg; ++i)
+                    if ((poly >> (deg - i)) & 1u) v ^= m[k - i] << i;
+                m[k] = v;
+            }
+            for (int k = 1; k <= 32; ++k) out[dim][k - 1] = (uint32_t)(m[k] << (32 - k));
+            ++dim;
+        }
+    }
+}
+
+HostTables build_tables()
+{
+    HostTables t;
+    std::memset(&t, 0, sizeof t);
+    {
+        const double L = 4.0;
+        const std::vector<double> a = weideman_coefficients(16, L);
+        for (int n = 0; n <= 16; ++n) t.fad.w32[n] = (float)a[n];
+        t.fad.L32 = (float)L;
+        std::vector<double> ca, cb;
+        cf_coefficients(3, ca, cb);
+        for (int i = 0; i < 3; ++i) t.fad.cfa32[i] = (float)ca[i];
+        for (int i = 0; i < 2; ++i) t.fad.cfb32[i] = (float)cb[i];
+    }
+    {
+        const double L = 5.0;
+        const std::vector<double> a = weideman_coefficients(36, L);
+        for (int n = 0; n <= 36; ++n) t.fad.w64[n] = a[n];
+        t.fad.L64 = L;
+        std::vector<double> ca, cb;
+        cf_coefficients(9, ca, cb);
+        for (int i = 0; i < 6; ++i) t.fad.cfa64[i] = ca[i];
+        for (int i = 0; i < 5; ++i) t.fad.cfb64[i] = cb[i];
+    }
+    sobol_directions(t.sobol);
+    return t;
+}
+
+std::mutex g_init_mu;
+bool g_dev_ready[256];
+
+int ensure_device()
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 256) return fail(ME_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_init_mu);
+    if (g_dev_ready[dev]) return ME_OK;
+    const HostTables &t = host_tables();
+    if ((e = upload_tables_ga(t)) != cudaSuccess) return cuda_fail(e, "upload tables");
+    if ((e = upload_tables_synth(t)) != cudaSuccess) return cuda_fail(e, "upload tables");
+    if ((e = upload_tables_lm(t)) != cudaSuccess) return cuda_fail(e, "upload tables");
+    g_dev_ready[dev] = true;
+    return ME_OK;
+}
+
+// ------------------------------------------------------------- validation
+int make_problem(const me_problem *pb, KProblem &k)
+{
+    if (!pb) return fail(ME_EINVAL, "problem is NULL");
+    if (pb->n_lines < 1 || pb->n_lines > ME_MAX_LINES) return fail(ME_EINVAL, "n_lines must be 1..4");
+    if (pb->n_lambda < 1 || pb->n_lambda > ME_MAX_LAMBDA)
+        return fail(ME_EINVAL, "n_lambda must be 1..ME_MAX_LAMBDA");
+    if (4 * pb->n_lambda <= ME_NPAR) return fail(ME_EINVAL, "n_lambda too small: 4 n_lambda must exceed 9");
+    if (!pb->lambda_A) return fail(ME_EINVAL, "lambda_A is NULL");
+    if (pb->dtype != ME_F32 && pb->dtype != ME_F64) return fail(ME_EINVAL, "dtype must be ME_F32 or ME_F64");
+    if (!(pb->lambda_dop_A > 0.0) || !std::isfinite(pb->lambda_dop_A))
+        return fail(ME_EINVAL, "lambda_dop_A must be positive");
+    if (!std::isfinite(pb->mu)) return fail(ME_EINVAL, "mu must be finite");
+    std::memset(&k, 0, sizeof k);
+    k.n_lines = pb->n_lines;
+    k.n_lambda = pb->n_lambda;
+    k.mu = pb->mu;
+    for (int l = 0; l < pb->n_lines; ++l) {
+        const me_line &ln = pb->line[l];
+        if (!(ln.lambda0_A > 0.0) || !std::isfinite(ln.lambda0_A) || !std::isfinite(ln.g_eff) ||
+            !std::isfinite(ln.eta_ratio))
+            return fail(ME_EINVAL, "invalid line parameters");
+        k.line[l].lam0 = ln.lambda0_A;
+        k.line[l].lam0_c = ln.lambda0_A / kSpeedOfLight;
+        k.line[l].dscale = 1e-3 * ln.lambda0_A / pb->lambda_dop_A;
+        k.line[l].zfac = kZeeman * ln.g_eff * ln.lambda0_A * ln.lambda0_A;
+        k.line[l].half_eta = 0.5 * ln.eta_ratio;
+    }
+    for (int j = 0; j < pb->n_lambda; ++j) {
+        const double v = pb->lambda_A[j];
+        if (!std::isfinite(v) || !(v > 0.0)) return fail(ME_EINVAL, "lambda_A must be finite and positive");
+        // lambda_j - lambda0_l must be exact in FP64 (Sterbenz): within a factor 2
+        for (int l = 0; l < pb->n_lines; ++l)
+            if (v > 2.0 * k.line[l].lam0 || 2.0 * v < k.line[l].lam0)
+                return fail(ME_EINVAL, "wavelength grid more than a factor 2 from a line");
+        k.lam[j] = v;
+    }
+    return ME_OK;
+}
+
+int check_bounds(const me_bounds *b)
+{
+    if (!b) return fail(ME_EINVAL, "bounds is NULL");
+    for (int d = 0; d < ME_NPAR; ++d)
+        if (!std::isfinite(b->lo[d]) || !std::isfinite(b->hi[d]) || b->lo[d] > b->hi[d])
+            return fail(ME_EINVAL, "bounds must be finite with lo <= hi");
+    if (b->lo[5] < 0.0) return fail(ME_EINVAL, "damping lower bound must be >= 0");
+    if (!(b->lo[4] > 0.0)) return fail(ME_EINVAL, "Doppler-width lower bound must be > 0");
+    return ME_OK;
+}
+
+// floor(p 2^32) compared with a uniform u32: p >= 1 -> 2^32, p <= 0 -> 0.
+uint64_t prob_threshold(double p)
+{
+    if (!(p > 0.0)) return 0;
+    if (p >= 1.0) return 1ull << 32;
+    return (uint64_t)std::floor(p * 4294967296.0);
+}
+
+int make_ga(const ga_config *cfg, const me_bounds *b, uint64_t pid0, KGa &g)
+{
+    if (!cfg) return fail(ME_EINVAL, "ga_config is NULL");
+    if (cfg->npop < ME_MIN_POP || cfg->npop > ME_MAX_POP || cfg->npop % 32)
+        return fail(ME_EINVAL, "npop must be a multiple of 32 in [32, 1024]");
+    if (cfg->ngen < 0) return fail(ME_EINVAL, "ngen must be >= 0");
+    if (!std::isfinite(cfg->pc) || !std::isfinite(cfg->pmut_lsb) || !std::isfinite(cfg->pmut_ratio) ||
+        cfg->pmut_ratio < 0.0)
+        return fail(ME_EINVAL, "invalid GA probabilities");
+    if (cfg->weight_mode != ME_W_INVMAX && cfg->weight_mode != ME_W_USER)
+        return fail(ME_EINVAL, "weight_mode must be ME_W_INVMAX or ME_W_USER");
+    std::memset(&g, 0, sizeof g);
+    g.npop = cfg->npop;
+    g.ngen = cfg->ngen;
+    g.nsamp = cfg->nsamp;
+    g.weight_mode = cfg->weight_mode;
+    g.seed = cfg->seed;
+    g.pixel_id0 = pid0;
+    g.t_cross = prob_threshold(cfg->pc);
+    for (int bit = 0; bit < 16; ++bit) {
+        double r = 1.0;
+        for (int k = 0; k < 15 - bit; ++k) r *= cfg->pmut_ratio;
+        g.t_mut[bit] = prob_threshold(cfg->pmut_lsb * r);
+    }
+    if (b) {
+        for (int d = 0; d < ME_NPAR; ++d) {
+            g.lo[d] = b->lo[d];
+            g.hi[d] = b->hi[d];
+        }
+    }
+    return ME_OK;
+}
+
+cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
+
+}  // namespace
+
+const HostTables &host_tables()
+{
+    static HostTables t = build_tables();
+    return t;
+}
+
+}  // namespace genesis
+
+using namespace genesis;
+
+extern "C" {
+
+const char *me_last_error(void) { return g_last_error.c_str(); }
+
+int me_version(void) { return 100; }
+
+int me_synth(const me_problem *pb, const double *params, const double *mu_px, int n, void *stokes,
+             void *stream)
+{
+    KProblem k;
+    int rc = make_problem(pb, k);
+    if (rc) return rc;
+    if (n < 0) return fail(ME_EINVAL, "n must be >= 0");
+    if (n == 0) return ME_OK;
+    if (!params || !stokes) return fail(ME_EINVAL, "params and stokes must be non-NULL");
+    if ((long long)n * pb->n_lambda > (1ll << 31) - 1) return fail(ME_EINVAL, "n * n_lambda too large");
+    if ((rc = ensure_device())) return rc;
+    cudaError_t e = launch_synth(k, pb->dtype, params, mu_px, n, stokes, as_stream(stream));
+    return e == cudaSuccess ? ME_OK : cuda_fail(e, "me_synth launch");
+}
+
+int me_synth_jac(const me_problem *pb, const double *params, const double *mu_px, int n,
+                 void *stokes, void *jac, void *stream)
+{
+    KProblem k;
+    int rc = make_problem(pb, k);
+    if (rc) return rc;
+    if (n < 0) return fail(ME_EINVAL, "n must be >= 0");
+    if (n == 0) return ME_OK;
+    if (!params || !jac) return fail(ME_EINVAL, "params and jac must be non-NULL");
+    if ((long long)n * pb->n_lambda > (1ll << 31) - 1) return fail(ME_EINVAL, "n * n_lambda too large");
+    if ((rc = ensure_device())) return rc;
+    cudaError_t e = launch_jac(k, pb->dtype, params, mu_px, n, stokes, jac, as_stream(stream));
+    return e == cudaSuccess ? ME_OK : cuda_fail(e, "me_synth_jac launch");
+}
+
+int me_synth_vjp(const me_problem *pb, const double *params, const double *mu_px, int n,
+                 const void *grad_stokes, double *grad_params, void *stream)
+{
+    KProblem k;
+    int rc = make_problem(pb, k);
+    if (rc) return rc;
+    if (n < 0) return fail(ME_EINVAL, "n must be >= 0");
+    if (n == 0) return ME_OK;
+    if (!params || !grad_stokes || !grad_params)
+        return fail(ME_EINVAL, "params, grad_stokes and grad_params must be non-NULL");
+    if ((rc = ensure_device())) return rc;
+    cudaError_t e = launch_vjp(k, pb->dtype, params, mu_px, n, grad_stokes, grad_params, as_stream(stream));
+    return e == cudaSuccess ? ME_OK : cuda_fail(e, "me_synth_vjp launch");
+}
+
+int me_chi2(const me_problem *pb, const void *obs, const double *w, const double *mu_px, int npix,
+            const double *params, double *chi2, void *stream)
+{
+    KProblem k;
+    int rc = make_problem(pb, k);
+    if (rc) return rc;
+    if (npix < 0) return fail(ME_EINVAL, "npix must be >= 0");
+    if (npix == 0) return ME_OK;
+    if (!obs || !params || !chi2) return fail(ME_EINVAL, "obs, params and chi2 must be non-NULL");
+    if ((rc = ensure_device())) return rc;
+    cudaError_t e = launch_chi2_f64(k, pb->dtype, obs, w, mu_px, npix, params, chi2, as_stream(stream));
+    return e == cudaSuccess ? ME_OK : cuda_fail(e, "me_chi2 launch");
+}
+
+int ga_invert_batch(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
+                    int npix, uint64_t pixel_id0, const me_bounds *bounds, const ga_config *cfg,
+                    double *best, double *chi2, uint16_t *best_genes, void *stream)
+{
+    KProblem k;
+    int rc = make_problem(pb, k);
+    if (rc) return rc;
+    if ((rc = check_bounds(bounds))) return rc;
+    KGa g;
+    if ((rc = make_ga(cfg, bounds, pixel_id0, g))) return rc;
+    if (npix < 0) return fail(ME_EINVAL, "npix must be >= 0");
+    if (npix == 0) return ME_OK;
+    if (!obs || !best || !chi2) return fail(ME_EINVAL, "obs, best and chi2 must be non-NULL");
+    if (cfg->weight_mode == ME_W_USER && !w) return fail(ME_EINVAL, "ME_W_USER needs w");
+    if (pixel_id0 + (uint64_t)npix < pixel_id0) return fail(ME_EINVAL, "pixel id range overflows");
+    // shared memory: obs + offsets + fitness + genes must fit one block
+    const size_t rs = pb->dtype == ME_F32 ? 4 : 8;
+    const size_t need = rs * (4 + pb->n_lines) * pb->n_lambda + rs * (cfg->npop + 72) + 128 +
+                        (size_t)4 * cfg->npop * ME_NPAR + 256;
+    if (need > 220 * 1024) return fail(ME_EINVAL, "population and grid exceed shared memory");
+    if ((rc = ensure_device())) return rc;
+    const KGa &gc = g;
+    cudaError_t e = launch_ga_evolve(k, gc, pb->dtype, obs, cfg->weight_mode == ME_W_USER ? w : nullptr,
+                                     mu_px, npix, best, best_genes, as_stream(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "ga_invert_batch launch");
+    e = launch_chi2_f64(k, pb->dtype, obs, cfg->weight_mode == ME_W_USER ? w : nullptr, mu_px, npix,
+                        best, chi2, as_stream(stream));
+    return e == cudaSuccess ? ME_OK : cuda_fail(e, "ga_invert_batch chi2 launch");
+}
+
+int ga_count_evaluations(const me_problem *pb, const void *obs, const double *w,
+                         const double *mu_px, int npix, uint64_t pixel_id0,
+                         const me_bounds *bounds, const ga_config *cfg, double *best,
+                         unsigned long long *counts, void *stream)
+{
+    KProblem k;
+    int rc = make_problem(pb, k);
+    if (rc) return rc;
+    if ((rc = check_bounds(bounds))) return rc;
+    KGa g;
+    if ((rc = make_ga(cfg, bounds, pixel_id0, g))) return rc;
+    if (pb->dtype != ME_F32 || cfg->npop > 256)
+        return fail(ME_EINVAL, "counting runs support float cubes with npop <= 256");
+    if (npix < 0) return fail(ME_EINVAL, "npix must be >= 0");
+    if (npix == 0) return ME_OK;
+    if (!obs || !best || !counts) return fail(ME_EINVAL, "obs, best and counts must be non-NULL");
+    if (cfg->weight_mode == ME_W_USER && !w) return fail(ME_EINVAL, "ME_W_USER needs w");
+    if ((rc = ensure_device())) return rc;
+    cudaError_t e = launch_ga_count(k, g, pb->dtype, obs, cfg->weight_mode == ME_W_USER ? w : nullptr,
+                                    mu_px, npix, best, counts, as_stream(stream));
+    return e == cudaSuccess ? ME_OK : cuda_fail(e, "ga_count_evaluations launch");
+}
+
+int lm_polish(const me_problem *pb, const void *obs, const double *w, const double *mu_px, int npix,
+              const me_bounds *bounds, int iters, double lambda0, double *params_inout,
+              double *chi2_out, void *stream)
+{
+    KProblem k;
+    int rc = make_problem(pb, k);
+    if (rc) return rc;
+    if ((rc = check_bounds(bounds))) return rc;
+    if (npix < 0 || iters < 0) return fail(ME_EINVAL, "npix and iters must be >= 0");
+    if (!(lambda0 > 0.0) || !std::isfinite(lambda0)) return fail(ME_EINVAL, "lambda0 must be positive");
+    if (npix == 0) return ME_OK;
+    if (!obs || !params_inout) return fail(ME_EINVAL, "obs and params_inout must be non-NULL");
+    if ((rc = ensure_device())) return rc;
+    KLm lm;
+    std::memset(&lm, 0, sizeof lm);
+    lm.iters = iters;
+    lm.lambda0 = lambda0;
+    for (int d = 0; d < ME_NPAR; ++d) {
+        lm.lo[d] = bounds->lo[d];
+        lm.hi[d] = bounds->hi[d];
+    }
+    cudaError_t e = launch_lm(k, lm, pb->dtype, obs, w, mu_px, npix, params_inout, as_stream(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "lm_polish launch");
+    if (chi2_out) {
+        e = launch_chi2_f64(k, pb->dtype, obs, w, mu_px, npix, params_inout, chi2_out, as_stream(stream));
+        if (e != cudaSuccess) return cuda_fail(e, "lm_polish chi2 launch");
+    }
+    return ME_OK;
+}
+
+int ga_breed(const uint16_t *genes, const double *fitness, int nprob, int npop, uint64_t pixel_id0,
+             int gen, const ga_config *cfg, uint16_t *child, int *elite, void *stream)
+{
+    KGa g;
+    ga_config c = cfg ? *cfg : ga_config{};
+    if (!cfg) return fail(ME_EINVAL, "ga_config is NULL");
+    c.npop = npop;
+    int rc = make_ga(&c, nullptr, pixel_id0, g);
+    if (rc) return rc;
+    if (nprob < 0) return fail(ME_EINVAL, "nprob must be >= 0");
+    if (nprob == 0) return ME_OK;
+    if (!genes || !fitness || !child) return fail(ME_EINVAL, "genes, fitness and child must be non-NULL");
+    if ((rc = ensure_device())) return rc;
+    cudaError_t e = launch_ga_breed(g, genes, fitness, nprob, gen, child, elite, as_stream(stream));
+    return e == cudaSuccess ? ME_OK : cuda_fail(e, "ga_breed launch");
+}
+
+int ga_restart(uint16_t *genes, const double *fitness, int nprob, int npop, uint64_t sobol_next,
+               void *stream)
+{
+    if (npop < ME_MIN_POP || npop > ME_MAX_POP || npop % 32)
+        return fail(ME_EINVAL, "npop must be a multiple of 32 in [32, 1024]");
+    if (nprob < 0) return fail(ME_EINVAL, "nprob must be >= 0");
+    if (nprob == 0) return ME_OK;
+    if (!genes || !fitness) return fail(ME_EINVAL, "genes and fitness must be non-NULL");
+    if (sobol_next + (uint64_t)npop > (1ull << 32)) return fail(ME_EINVAL, "Sobol index beyond 2^32");
+    int rc = ensure_device();
+    if (rc) return rc;
+    cudaError_t e = launch_ga_restart(npop, genes, fitness, nprob, sobol_next, as_stream(stream));
+    return e == cudaSuccess ? ME_OK : cuda_fail(e, "ga_restart launch");
+}
+
+int me_philox(const uint32_t *ctr, int n, uint64_t key, uint32_t *out, void *stream)
+{
+    if (n < 0) return fail(ME_EINVAL, "n must be >= 0");
+    if (n == 0) return ME_OK;
+    if (!ctr || !out) return fail(ME_EINVAL, "ctr and out must be non-NULL");
+    int rc = ensure_device();
+    if (rc) return rc;
+    cudaError_t e = launch_philox(ctr, n, key, out, as_stream(stream));
+    return e == cudaSuccess ? ME_OK : cuda_fail(e, "me_philox launch");
+}
+
+int me_sobol(uint64_t first, int n, int ndim, uint32_t *out, void *stream)
+{
+    if (n < 0 || ndim < 1 || ndim > 10) return fail(ME_EINVAL, "need n >= 0 and 1 <= ndim <= 10");
+    if (n == 0) return ME_OK;
+    if (!out) return fail(ME_EINVAL, "out must be non-NULL");
+    if (first + (uint64_t)n > (1ull << 32)) return fail(ME_EINVAL, "Sobol index beyond 2^32");
+    if ((long long)n * ndim > (1ll << 31) - 1) return fail(ME_EINVAL, "n * ndim too large");
+    int rc = ensure_device();
+    if (rc) return rc;
+    cudaError_t e = launch_sobol(first, n, ndim, out, as_stream(stream));
+    return e == cudaSuccess ? ME_OK : cuda_fail(e, "me_sobol launch");
+}
+
+}  // extern "C"

@@ -1,0 +1,507 @@
+// Fused genetic-algorithm inversion kernel for sm_103a (Section 3, Algorithm 1;
+// Section 4.6), plus the operator-only kernels used to verify it.
+//
+// One thread block per pixel, one thread per individual.  The pixel's
+// observed Stokes profiles, its wavelength offsets, the population's uint16
+// genotypes (double-buffered) and fitness stay in shared memory for all
+// generations; no host round trip happens between generations.  Each thread
+// walks the wavelength grid for its own individual, so every lane of a warp
+// reads the same shared-memory word (broadcast) and the chi2 sum needs no
+// cross-thread reduction.
+#include "kernels.h"
+#include "rng_device.cuh"
+
+namespace genesis {
+
+cudaError_t upload_tables_ga(const HostTables &t)
+{
+    cudaError_t e = cudaMemcpyToSymbol(c_fad, &t.fad, sizeof(FaddeevaTables));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(c_sobol, t.sobol, sizeof(t.sobol));
+}
+
+namespace {
+
+template <class R> __device__ __forceinline__ R clean_fit(R f)
+{
+    return f == f ? f : R(INFINITY);  // NaN ranks as +infinity
+}
+
+// Kahan-compensated accumulation of r^2.
+template <class R> __device__ __forceinline__ void kahan_sq(R &s, R &c, R r)
+{
+    const R y = r * r - c;
+    const R t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+template <class R> struct GaDecode;
+template <> struct GaDecode<float> {
+    // FP32 GA: p = lo + g (hi - lo) / 65535, scale precomputed on the host
+    static __device__ __forceinline__ float get(const KGa &ga, const float *lo32,
+                                                const float *sc32, int d, uint16_t g)
+    {
+        return fmaf((float)g, sc32[d], lo32[d]);
+    }
+};
+template <> struct GaDecode<double> {
+    static __device__ __forceinline__ double get(const KGa &ga, const float *, const float *,
+                                                 int d, uint16_t g)
+    {
+        return decode64(g, ga.lo[d], ga.hi[d]);
+    }
+};
+
+// Eq. chisq for one individual, FP32 (or FP64) synthesis over the whole grid.
+template <class R, int NL, bool COUNT>
+__device__ __forceinline__ R fitness(const KProblem &pb, int nlines, int nl, const R *p, R mu,
+                                     const R *s_obs, const R *s_doff, const R *he,
+                                     const R *s_w2, R inv_nu, unsigned long long &ninterior)
+{
+    const Geo<R> geo = make_geo<R, NL>(pb, nlines, p, mu);
+    R sI = 0, sQ = 0, sU = 0, sV = 0, cI = 0, cQ = 0, cU = 0, cV = 0;
+    for (int j = 0; j < nl; ++j) {
+        R doff[ME_MAX_LINES];
+#pragma unroll
+        for (int l = 0; l < (NL > 0 ? NL : ME_MAX_LINES); ++l)
+            doff[l] = (l < (NL > 0 ? NL : nlines)) ? s_doff[l * nl + j] : R(0);
+        const Stokes4<R> s = me_point<R, NL>(geo, doff, he, nlines);
+        if (COUNT) ninterior += count_interior<R, NL>(geo, doff, nlines);
+        kahan_sq(sI, cI, s_obs[j] - s.I);
+        kahan_sq(sQ, cQ, s_obs[nl + j] - s.Q);
+        kahan_sq(sU, cU, s_obs[2 * nl + j] - s.U);
+        kahan_sq(sV, cV, s_obs[3 * nl + j] - s.V);
+    }
+    return (s_w2[0] * sI + s_w2[1] * sQ + s_w2[2] * sU + s_w2[3] * sV) * inv_nu;
+}
+
+// argmin over the block's fitness, ties to the lowest index.  Every thread
+// gets the result.  Uses one __syncthreads().
+template <class R>
+__device__ __forceinline__ int block_argmin(const R *s_fit, R *s_wmin, int *s_widx)
+{
+    const int k = threadIdx.x, lane = k & 31, warp = k >> 5, nw = blockDim.x >> 5;
+    R v = s_fit[k];
+    int idx = k;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const R ov = __shfl_down_sync(0xffffffffu, v, off);
+        const int oi = __shfl_down_sync(0xffffffffu, idx, off);
+        if (ov < v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+    }
+    if (lane == 0) { s_wmin[warp] = v; s_widx[warp] = idx; }
+    __syncthreads();
+    R bv = s_wmin[0];
+    int bi = s_widx[0];
+    for (int w = 1; w < nw; ++w) {
+        const R ov = s_wmin[w];
+        const int oi = s_widx[w];
+        if (ov < bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    return bi;
+}
+
+// Stable rank of individual k in (fitness, index) order.
+template <class R> __device__ __forceinline__ int stable_rank(const R *s_fit, int npop, int k)
+{
+    const R fk = s_fit[k];
+    int r = 0;
+    for (int j = 0; j < npop; ++j) {
+        const R fj = s_fit[j];
+        r += (fj < fk || (fj == fk && j < k)) ? 1 : 0;
+    }
+    return r;
+}
+
+// Select (binary tournament), recombine (one-point crossover with lane k^1),
+// mutate (per-bit, LSB-biased) and elitism for child slot k.  Must be called
+// by all lanes of full warps (npop is a multiple of 32).
+template <class R>
+__device__ __forceinline__ void breed_one(const KGa &ga, uint64_t pid, int t, int k, int npop,
+                                          const R *s_fit, const uint16_t *s_cur, int elite,
+                                          uint16_t g[ME_NPAR])
+{
+    const U4 u = ga_random(ga.seed, pid, t, (uint32_t)k, kPurposeSelect);
+    const int i = (int)(((uint64_t)u.x * (uint64_t)npop) >> 32);
+    const int j = (i + 1 + (int)(((uint64_t)u.y * (uint64_t)(npop - 1)) >> 32)) % npop;
+    const R fi = s_fit[i], fj = s_fit[j];
+    const int win = (fj < fi || (fj == fi && j < i)) ? j : i;
+#pragma unroll
+    for (int d = 0; d < ME_NPAR; ++d) g[d] = s_cur[win * ME_NPAR + d];
+
+    const U4 uc = ga_random(ga.seed, pid, t, (uint32_t)(k >> 1), kPurposeCross);
+    const bool cross = (uint64_t)uc.x < ga.t_cross;
+    const int c = 1 + (int)(((uint64_t)uc.y * (uint64_t)(16 * ME_NPAR - 1)) >> 32);
+#pragma unroll
+    for (int d = 0; d < ME_NPAR; ++d) {
+        const uint32_t pg = __shfl_xor_sync(0xffffffffu, (uint32_t)g[d], 1);
+        if (cross) {
+            const int b0 = 16 * d;  // MSB-first string bits [b0, b0 + 16)
+            if (b0 >= c) {
+                g[d] = (uint16_t)pg;
+            } else if (b0 + 16 > c) {
+                const uint32_t mask = (1u << (16 - (c - b0))) - 1u;  // bits at or after the cut
+                g[d] = (uint16_t)(((uint32_t)g[d] & ~mask) | (pg & mask));
+            }
+        }
+    }
+
+#pragma unroll
+    for (int grp = 0; grp < (16 * ME_NPAR + 3) / 4; ++grp) {
+        const U4 um = ga_random(ga.seed, pid, t, (uint32_t)k, kPurposeMutate + (uint32_t)grp);
+        const uint32_t uu[4] = {um.x, um.y, um.z, um.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int bit = 4 * grp + e;
+            if (bit < 16 * ME_NPAR) {
+                const int b = bit & 15;
+                if ((uint64_t)uu[e] < ga.t_mut[b]) g[bit >> 4] ^= (uint16_t)(1u << (15 - b));
+            }
+        }
+    }
+    if (k == 0) {
+#pragma unroll
+        for (int d = 0; d < ME_NPAR; ++d) g[d] = s_cur[elite * ME_NPAR + d];
+    }
+}
+
+struct GaSmem {
+    // byte offsets into dynamic shared memory
+    int obs, doff, fit, wmin, widx, w2, he, genes, total;
+};
+
+template <class R>
+__host__ __device__ __forceinline__ GaSmem ga_smem_layout(int nl, int nlines, int npop)
+{
+    GaSmem L;
+    int o = 0;
+    auto take = [&](int bytes, int align) {
+        o = (o + align - 1) / align * align;
+        const int at = o;
+        o += bytes;
+        return at;
+    };
+    L.obs = take(4 * nl * (int)sizeof(R), 16);
+    L.doff = take(nlines * nl * (int)sizeof(R), 16);
+    L.fit = take(npop * (int)sizeof(R), 16);
+    L.wmin = take(32 * (int)sizeof(R), 16);
+    L.widx = take(32 * 4, 16);
+    L.w2 = take(4 * (int)sizeof(R), 16);
+    L.he = take(4 * (int)sizeof(R), 16);
+    L.genes = take(2 * npop * ME_NPAR * 2, 16);
+    L.total = (o + 15) / 16 * 16;
+    return L;
+}
+
+// Section 4.5 inverse-max weights of the staged pixel (warp 0), written as w^2.
+template <class R>
+__device__ __forceinline__ void weights_invmax_w2(const R *s_obs, int nl, R *s_w2)
+{
+    const int lane = threadIdx.x & 31;
+    R imax = -R(INFINITY), imin = R(INFINITY), mq = 0, mu = 0, mv = 0;
+    for (int j = lane; j < nl; j += 32) {
+        const R I = s_obs[j];
+        imax = I > imax ? I : imax;
+        imin = I < imin ? I : imin;
+        const R aq = fabs(s_obs[nl + j]), au = fabs(s_obs[2 * nl + j]), av = fabs(s_obs[3 * nl + j]);
+        mq = aq > mq ? aq : mq;
+        mu = au > mu ? au : mu;
+        mv = av > mv ? av : mv;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        R o = __shfl_xor_sync(0xffffffffu, imax, off); imax = o > imax ? o : imax;
+        o = __shfl_xor_sync(0xffffffffu, imin, off); imin = o < imin ? o : imin;
+        o = __shfl_xor_sync(0xffffffffu, mq, off); mq = o > mq ? o : mq;
+        o = __shfl_xor_sync(0xffffffffu, mu, off); mu = o > mu ? o : mu;
+        o = __shfl_xor_sync(0xffffffffu, mv, off); mv = o > mv ? o : mv;
+    }
+    if (lane == 0) {
+        const R d[4] = {imax - imin, mq, mu, mv};
+        const R fl = R(1e-6) * fabs(imax);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const R dd = d[s] > fl ? d[s] : fl;
+            const R w = dd > R(0) ? R(1) / dd : R(0);
+            s_w2[s] = w * w;
+        }
+    }
+}
+
+template <class R, int NL, int MAXT, bool COUNT>
+__global__ void __launch_bounds__(MAXT)
+k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
+            const R *__restrict__ obs, const double *__restrict__ w_user,
+            const double *__restrict__ mu_px, int npix, double *__restrict__ best,
+            uint16_t *__restrict__ best_genes, unsigned long long *__restrict__ counts)
+{
+    unsigned long long nfit = 0, ninterior = 0;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nl = pb.n_lambda;
+    const int nlines = NL > 0 ? NL : pb.n_lines;
+    const int npop = ga.npop;
+    const int k = threadIdx.x;
+    const GaSmem L = ga_smem_layout<R>(nl, nlines, npop);
+    R *s_obs = (R *)(smem + L.obs);
+    R *s_doff = (R *)(smem + L.doff);
+    R *s_fit = (R *)(smem + L.fit);
+    R *s_wmin = (R *)(smem + L.wmin);
+    int *s_widx = (int *)(smem + L.widx);
+    R *s_w2 = (R *)(smem + L.w2);
+    R *s_he = (R *)(smem + L.he);
+    uint16_t *s_genes = (uint16_t *)(smem + L.genes);
+
+    // per-launch constants
+    float lo32[ME_NPAR], sc32[ME_NPAR];
+#pragma unroll
+    for (int d = 0; d < ME_NPAR; ++d) {
+        lo32[d] = (float)ga.lo[d];
+        sc32[d] = (float)((ga.hi[d] - ga.lo[d]) / 65535.0);
+    }
+    const R inv_nu = R(1) / R(4 * nl - ME_NPAR);
+    if (k < 4) s_he[k] = k < nlines ? R(pb.line[k].half_eta) : R(0);
+    for (int i = k; i < nlines * nl; i += blockDim.x) {
+        const int l = i / nl, j = i - l * nl;
+        s_doff[i] = R(pb.lam[j] - pb.line[l].lam0);  // exact difference, then rounded
+    }
+
+    for (int pix = blockIdx.x; pix < npix; pix += gridDim.x) {
+        // a1: stage the pixel's Stokes profiles (16-byte vector loads when aligned)
+        const R *o = obs + (size_t)pix * 4 * nl;
+        const int nbytes = 4 * nl * (int)sizeof(R);
+        if ((nbytes & 15) == 0 && (((uintptr_t)o) & 15) == 0) {
+            const float4 *o4 = (const float4 *)o;
+            float4 *d4 = (float4 *)s_obs;
+            for (int i = k; i < nbytes / 16; i += blockDim.x) d4[i] = __ldg(o4 + i);
+        } else {
+            for (int i = k; i < 4 * nl; i += blockDim.x) s_obs[i] = o[i];
+        }
+        __syncthreads();
+        // a2: weights
+        if (ga.weight_mode == ME_W_USER) {
+            if (k < 4) {
+                const double wv = w_user[(size_t)pix * 4 + k];
+                s_w2[k] = R(wv * wv);
+            }
+        } else if (k < 32) {
+            weights_invmax_w2<R>(s_obs, nl, s_w2);
+        }
+        __syncthreads();
+        R he[ME_MAX_LINES];
+#pragma unroll
+        for (int l = 0; l < ME_MAX_LINES; ++l) he[l] = s_he[l];
+        const R mu = mu_px ? R(mu_px[pix]) : R(pb.mu);
+        const uint64_t pid = ga.pixel_id0 + (uint64_t)pix;
+
+        // a3 + a4: Sobol points 1..npop, decode, evaluate
+        uint16_t g[ME_NPAR];
+        R p[ME_NPAR];
+#pragma unroll
+        for (int d = 0; d < ME_NPAR; ++d) {
+            g[d] = (uint16_t)(sobol_point((uint64_t)(k + 1), d) >> 16);
+            p[d] = GaDecode<R>::get(ga, lo32, sc32, d, g[d]);
+        }
+        int cur = 0;
+#pragma unroll
+        for (int d = 0; d < ME_NPAR; ++d) s_genes[k * ME_NPAR + d] = g[d];
+        s_fit[k] = clean_fit(fitness<R, NL, COUNT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior));
+        if (COUNT) ++nfit;
+        uint64_t sobol_next = (uint64_t)npop + 1;
+
+        for (int t = 1; t <= ga.ngen; ++t) {
+            __syncthreads();  // fitness and genes of generation t-1 complete
+            const int elite = block_argmin<R>(s_fit, s_wmin, s_widx);  // a9
+            const uint16_t *s_cur = s_genes + cur * npop * ME_NPAR;
+            uint16_t *s_nxt = s_genes + (cur ^ 1) * npop * ME_NPAR;
+            breed_one<R>(ga, pid, t, k, npop, s_fit, s_cur, elite, g);  // a10-a12
+            __syncthreads();  // every tournament has read s_fit
+#pragma unroll
+            for (int d = 0; d < ME_NPAR; ++d) {
+                s_nxt[k * ME_NPAR + d] = g[d];
+                p[d] = GaDecode<R>::get(ga, lo32, sc32, d, g[d]);
+            }
+            cur ^= 1;
+            s_fit[k] = clean_fit(fitness<R, NL, COUNT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior));
+            if (COUNT) ++nfit;
+            // a13: worst-half Sobol restart
+            if (ga.nsamp > 0 && t % ga.nsamp == 0 && t < ga.ngen) {
+                __syncthreads();
+                const int rank = stable_rank<R>(s_fit, npop, k);
+                __syncthreads();
+                if (rank >= npop / 2) {
+                    const uint64_t n = sobol_next + (uint64_t)(rank - npop / 2);
+                    uint16_t *s_c = s_genes + cur * npop * ME_NPAR;
+#pragma unroll
+                    for (int d = 0; d < ME_NPAR; ++d) {
+                        g[d] = (uint16_t)(sobol_point(n, d) >> 16);
+                        s_c[k * ME_NPAR + d] = g[d];
+                        p[d] = GaDecode<R>::get(ga, lo32, sc32, d, g[d]);
+                    }
+                    s_fit[k] = clean_fit(
+                        fitness<R, NL, COUNT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior));
+                    if (COUNT) ++nfit;
+                }
+                sobol_next += (uint64_t)(npop / 2);
+            }
+        }
+        __syncthreads();
+        const int b = block_argmin<R>(s_fit, s_wmin, s_widx);
+        // a14: decoded best individual (its FP64 chi2 is a separate pass)
+        if (k < ME_NPAR) {
+            const uint16_t gb = s_genes[cur * npop * ME_NPAR + b * ME_NPAR + k];
+            best[(size_t)pix * ME_NPAR + k] = decode64(gb, ga.lo[k], ga.hi[k]);
+            if (best_genes) best_genes[(size_t)pix * ME_NPAR + k] = gb;
+        }
+        __syncthreads();  // shared memory is reused by the next pixel
+    }
+    if (COUNT) {
+        atomicAdd(counts + 0, nfit);
+        atomicAdd(counts + 1, ninterior);
+    }
+}
+
+// ------------------------------------------------- operator-only kernels
+__global__ void k_ga_breed(const __grid_constant__ KGa ga, const uint16_t *__restrict__ genes,
+                           const double *__restrict__ fit, int gen, uint16_t *__restrict__ child,
+                           int *__restrict__ elite_out)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int npop = ga.npop, k = threadIdx.x, prob = blockIdx.x;
+    double *s_fit = (double *)smem;
+    double *s_wmin = s_fit + npop;
+    int *s_widx = (int *)(s_wmin + 32);
+    uint16_t *s_cur = (uint16_t *)(s_widx + 32);
+    const size_t base = (size_t)prob * npop;
+    s_fit[k] = clean_fit(fit[base + k]);
+#pragma unroll
+    for (int d = 0; d < ME_NPAR; ++d) s_cur[k * ME_NPAR + d] = genes[(base + k) * ME_NPAR + d];
+    __syncthreads();
+    const int elite = block_argmin<double>(s_fit, s_wmin, s_widx);
+    uint16_t g[ME_NPAR];
+    breed_one<double>(ga, ga.pixel_id0 + (uint64_t)prob, gen, k, npop, s_fit, s_cur, elite, g);
+#pragma unroll
+    for (int d = 0; d < ME_NPAR; ++d) child[(base + k) * ME_NPAR + d] = g[d];
+    if (k == 0 && elite_out) elite_out[prob] = elite;
+}
+
+__global__ void k_ga_restart(int npop, uint16_t *__restrict__ genes, const double *__restrict__ fit,
+                             uint64_t sobol_next)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *s_fit = (double *)smem;
+    const int k = threadIdx.x, prob = blockIdx.x;
+    const size_t base = (size_t)prob * npop;
+    s_fit[k] = clean_fit(fit[base + k]);
+    __syncthreads();
+    const int rank = stable_rank<double>(s_fit, npop, k);
+    if (rank >= npop / 2) {
+        const uint64_t n = sobol_next + (uint64_t)(rank - npop / 2);
+#pragma unroll
+        for (int d = 0; d < ME_NPAR; ++d)
+            genes[(base + k) * ME_NPAR + d] = (uint16_t)(sobol_point(n, d) >> 16);
+    }
+}
+
+__global__ void k_philox(const uint32_t *__restrict__ ctr, int n, uint64_t key, uint32_t *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    U4 c = {ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+    const U4 r = philox4x32_10(c, (uint32_t)key, (uint32_t)(key >> 32));
+    out[4 * i] = r.x;
+    out[4 * i + 1] = r.y;
+    out[4 * i + 2] = r.z;
+    out[4 * i + 3] = r.w;
+}
+
+__global__ void k_sobol(uint64_t first, int n, int ndim, uint32_t *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * ndim) return;
+    const int pt = i / ndim, d = i - pt * ndim;
+    out[i] = sobol_point(first + (uint64_t)pt, d);
+}
+
+template <class R, int NL, int MAXT, bool COUNT = false>
+cudaError_t launch_evolve_t(const KProblem &pb, const KGa &ga, const void *obs, const double *w,
+                            const double *mu_px, int npix, double *best, uint16_t *best_genes,
+                            cudaStream_t st, unsigned long long *counts = nullptr)
+{
+    const int nlines = NL > 0 ? NL : pb.n_lines;
+    const GaSmem L = ga_smem_layout<R>(pb.n_lambda, nlines, ga.npop);
+    auto kern = k_ga_evolve<R, NL, MAXT, COUNT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+    if (e != cudaSuccess) return e;
+    kern<<<npix, ga.npop, L.total, st>>>(pb, ga, (const R *)obs, w, mu_px, npix, best, best_genes, counts);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_ga_evolve(const KProblem &pb, const KGa &ga, int dtype, const void *obs,
+                             const double *w, const double *mu_px, int npix, double *best,
+                             uint16_t *best_genes, cudaStream_t st)
+{
+    if (npix <= 0) return cudaSuccess;
+    if (dtype == ME_F32) {
+        if (ga.npop <= 256) {
+            if (pb.n_lines == 1)
+                return launch_evolve_t<float, 1, 256>(pb, ga, obs, w, mu_px, npix, best, best_genes, st);
+            if (pb.n_lines == 2)
+                return launch_evolve_t<float, 2, 256>(pb, ga, obs, w, mu_px, npix, best, best_genes, st);
+            return launch_evolve_t<float, 0, 256>(pb, ga, obs, w, mu_px, npix, best, best_genes, st);
+        }
+        return launch_evolve_t<float, 0, 1024>(pb, ga, obs, w, mu_px, npix, best, best_genes, st);
+    }
+    if (ga.npop <= 256)
+        return launch_evolve_t<double, 0, 256>(pb, ga, obs, w, mu_px, npix, best, best_genes, st);
+    return launch_evolve_t<double, 0, 1024>(pb, ga, obs, w, mu_px, npix, best, best_genes, st);
+}
+
+cudaError_t launch_ga_count(const KProblem &pb, const KGa &ga, int dtype, const void *obs,
+                            const double *w, const double *mu_px, int npix, double *best,
+                            unsigned long long *counts, cudaStream_t st)
+{
+    if (npix <= 0) return cudaSuccess;
+    if (dtype == ME_F32 && ga.npop <= 256) {
+        if (pb.n_lines == 2)
+            return launch_evolve_t<float, 2, 256, true>(pb, ga, obs, w, mu_px, npix, best, nullptr, st, counts);
+        return launch_evolve_t<float, 0, 256, true>(pb, ga, obs, w, mu_px, npix, best, nullptr, st, counts);
+    }
+    return cudaErrorNotSupported;
+}
+
+cudaError_t launch_ga_breed(const KGa &ga, const uint16_t *genes, const double *fit, int nprob,
+                            int gen, uint16_t *child, int *elite, cudaStream_t st)
+{
+    if (nprob <= 0) return cudaSuccess;
+    const int smem = ga.npop * 8 + 32 * 8 + 32 * 4 + ga.npop * ME_NPAR * 2;
+    k_ga_breed<<<nprob, ga.npop, smem, st>>>(ga, genes, fit, gen, child, elite);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ga_restart(int npop, uint16_t *genes, const double *fit, int nprob,
+                              uint64_t sobol_next, cudaStream_t st)
+{
+    if (nprob <= 0) return cudaSuccess;
+    k_ga_restart<<<nprob, npop, npop * 8, st>>>(npop, genes, fit, sobol_next);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t *ctr, int n, uint64_t key, uint32_t *out, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_philox<<<(n + 127) / 128, 128, 0, st>>>(ctr, n, key, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sobol(uint64_t first, int n, int ndim, uint32_t *out, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int tot = n * ndim;
+    k_sobol<<<(tot + 127) / 128, 128, 0, st>>>(first, n, ndim, out);
+    return cudaGetLastError();
+}
+
+}  // namespace genesis

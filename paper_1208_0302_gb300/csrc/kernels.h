@@ -1,0 +1,76 @@
+// Internal launch interface between the C-ABI layer and the kernel units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "me_device.cuh"
+
+namespace genesis {
+
+// GA launch parameters (Section 3 operators, Section 4.6 restarts).
+struct KGa {
+    int npop, ngen, nsamp, weight_mode;
+    uint64_t seed, pixel_id0;
+    uint64_t t_cross;       // crossover iff u32 < t_cross
+    uint64_t t_mut[16];     // flip bit b (0 = MSB) iff u32 < t_mut[b]
+    double lo[ME_NPAR], hi[ME_NPAR];
+};
+
+struct KLm {
+    int iters;
+    double lambda0;
+    double lo[ME_NPAR], hi[ME_NPAR];
+};
+
+// Coefficient tables, computed once on the host.
+struct HostTables {
+    FaddeevaTables fad;
+    uint32_t sobol[10][32];
+};
+const HostTables &host_tables();
+
+// Per translation unit: copy the tables into that unit's __constant__ copy
+// on the current device.
+cudaError_t upload_tables_ga(const HostTables &t);
+cudaError_t upload_tables_synth(const HostTables &t);
+cudaError_t upload_tables_lm(const HostTables &t);
+
+// ga_kernels.cu
+cudaError_t launch_ga_evolve(const KProblem &pb, const KGa &ga, int dtype, const void *obs,
+                             const double *w, const double *mu_px, int npix, double *best,
+                             uint16_t *best_genes, cudaStream_t st);
+cudaError_t launch_ga_count(const KProblem &pb, const KGa &ga, int dtype, const void *obs,
+                            const double *w, const double *mu_px, int npix, double *best,
+                            unsigned long long *counts, cudaStream_t st);
+cudaError_t launch_ga_breed(const KGa &ga, const uint16_t *genes, const double *fit, int nprob,
+                            int gen, uint16_t *child, int *elite, cudaStream_t st);
+cudaError_t launch_ga_restart(int npop, uint16_t *genes, const double *fit, int nprob,
+                              uint64_t sobol_next, cudaStream_t st);
+cudaError_t launch_philox(const uint32_t *ctr, int n, uint64_t key, uint32_t *out, cudaStream_t st);
+cudaError_t launch_sobol(uint64_t first, int n, int ndim, uint32_t *out, cudaStream_t st);
+
+// synth_kernels.cu
+cudaError_t launch_synth(const KProblem &pb, int dtype, const double *params, const double *mu_px,
+                         int n, void *stokes, cudaStream_t st);
+cudaError_t launch_jac(const KProblem &pb, int dtype, const double *params, const double *mu_px,
+                       int n, void *stokes, void *jac, cudaStream_t st);
+cudaError_t launch_vjp(const KProblem &pb, int dtype, const double *params, const double *mu_px,
+                       int n, const void *grad_stokes, double *grad_params, cudaStream_t st);
+cudaError_t launch_chi2_f64(const KProblem &pb, int dtype, const void *obs, const double *w,
+                            const double *mu_px, int npix, const double *params, double *chi2,
+                            cudaStream_t st);
+
+// lm_kernels.cu
+cudaError_t launch_lm(const KProblem &pb, const KLm &lm, int dtype, const void *obs,
+                      const double *w, const double *mu_px, int npix, double *params,
+                      cudaStream_t st);
+
+// Decode of Eq. decode in FP64 without contraction, the same expression the
+// reference evaluation uses: lo + (hi - lo) * (g / 65535).
+__device__ __forceinline__ double decode64(uint16_t g, double lo, double hi)
+{
+    return __dadd_rn(lo, __dmul_rn(__dsub_rn(hi, lo), __ddiv_rn((double)g, 65535.0)));
+}
+
+}  // namespace genesis

@@ -1,0 +1,307 @@
+// Levenberg-Marquardt polish kernel (sm_103a).
+//
+// One warp per pixel, lanes over wavelengths.  Per iteration: analytic
+// Jacobian in the problem's precision (FP32 for float cubes), per-lane partial
+// sums of J^T W^2 J and J^T W^2 r, a warp reduction in FP64, the damped
+// Cholesky solve in FP64 (lane 0, in shared memory), and a trial synthesis
+// whose chi2 decides acceptance (Levenberg 1944, Marquardt 1963).
+#include "kernels.h"
+#include "me_jac.cuh"
+#include "rng_device.cuh"
+
+namespace genesis {
+
+cudaError_t upload_tables_lm(const HostTables &t)
+{
+    return cudaMemcpyToSymbol(c_fad, &t.fad, sizeof(FaddeevaTables));
+}
+
+namespace {
+
+constexpr int kLmWarps = 4;
+constexpr int kNT = ME_NPAR * (ME_NPAR + 1) / 2;  // packed lower triangle
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+template <class R> __device__ __forceinline__ void kahan_sq(R &s, R &c, R r)
+{
+    const R y = r * r - c;
+    const R t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// chi2 (Eq. chisq) of parameters p: synthesis in R, per-lane compensated sums,
+// warp sum in FP64.  Every lane returns the same value.
+template <class R, class RO, int NL>
+__device__ double lm_chi2(const KProblem &pb, int nlines, int nl, const double *p, double mu,
+                          const RO *o, const R *s_doff, const R *he, const double *w2)
+{
+    R pr[ME_NPAR];
+#pragma unroll
+    for (int d = 0; d < ME_NPAR; ++d) pr[d] = R(p[d]);
+    const Geo<R> g = make_geo<R, NL>(pb, nlines, pr, R(mu));
+    R s[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
+    for (int j = threadIdx.x & 31; j < nl; j += 32) {
+        R doff[ME_MAX_LINES];
+#pragma unroll
+        for (int l = 0; l < ME_MAX_LINES; ++l) doff[l] = l < nlines ? s_doff[l * nl + j] : R(0);
+        const Stokes4<R> m = me_point<R, NL>(g, doff, he, nlines);
+        kahan_sq(s[0], c[0], R(o[j]) - m.I);
+        kahan_sq(s[1], c[1], R(o[nl + j]) - m.Q);
+        kahan_sq(s[2], c[2], R(o[2 * nl + j]) - m.U);
+        kahan_sq(s[3], c[3], R(o[3 * nl + j]) - m.V);
+    }
+    double tot = 0.0;
+#pragma unroll
+    for (int st = 0; st < 4; ++st) tot += w2[st] * warp_sum((double)s[st]);
+    return tot / (double)(4 * nl - ME_NPAR);
+}
+
+// Solve (A + lam D) x = g by Cholesky (row-major 9x9 in N), D = diag(max(A_jj,
+// 1e-12 max A_kk)).  Returns false if a pivot is not positive.
+__device__ bool damped_cholesky(const double *A, const double *g, double lam, double *N, double *x)
+{
+    double dmax = 0.0;
+    for (int a = 0; a < ME_NPAR; ++a) dmax = fmax(dmax, A[a * ME_NPAR + a]);
+    for (int a = 0; a < ME_NPAR * ME_NPAR; ++a) N[a] = A[a];
+    for (int a = 0; a < ME_NPAR; ++a) {
+        const double d = A[a * ME_NPAR + a] > 1e-12 * dmax ? A[a * ME_NPAR + a] : 1e-12 * dmax;
+        N[a * ME_NPAR + a] += lam * d;
+    }
+    for (int j = 0; j < ME_NPAR; ++j) {
+        double d = N[j * ME_NPAR + j];
+        for (int k = 0; k < j; ++k) d -= N[j * ME_NPAR + k] * N[j * ME_NPAR + k];
+        if (!(d > 0.0)) return false;
+        const double ljj = sqrt(d);
+        N[j * ME_NPAR + j] = ljj;
+        for (int i = j + 1; i < ME_NPAR; ++i) {
+            double s = N[i * ME_NPAR + j];
+            for (int k = 0; k < j; ++k) s -= N[i * ME_NPAR + k] * N[j * ME_NPAR + k];
+            N[i * ME_NPAR + j] = s / ljj;
+        }
+    }
+    for (int i = 0; i < ME_NPAR; ++i) {
+        double s = g[i];
+        for (int k = 0; k < i; ++k) s -= N[i * ME_NPAR + k] * x[k];
+        x[i] = s / N[i * ME_NPAR + i];
+    }
+    for (int i = ME_NPAR - 1; i >= 0; --i) {
+        double s = x[i];
+        for (int k = i + 1; k < ME_NPAR; ++k) s -= N[k * ME_NPAR + i] * x[k];
+        x[i] = s / N[i * ME_NPAR + i];
+    }
+    return true;
+}
+
+struct LmWarpSmem {
+    double A[ME_NPAR * ME_NPAR];
+    double N[ME_NPAR * ME_NPAR];
+    double g[ME_NPAR];
+    double x[ME_NPAR];
+    double w2[4];
+    double lam;
+    int ok;
+};
+
+template <class R, class RO, int NL>
+__global__ void __launch_bounds__(kLmWarps * 32)
+k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const RO *__restrict__ obs,
+     const double *__restrict__ w_user, const double *__restrict__ mu_px, int npix,
+     double *__restrict__ params)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    LmWarpSmem *s_w = (LmWarpSmem *)smem;
+    R *s_he = (R *)(smem + sizeof(LmWarpSmem) * kLmWarps);
+    R *s_doff = s_he + ME_MAX_LINES;
+    const int nl = pb.n_lambda, nlines = NL > 0 ? NL : pb.n_lines;
+    for (int i = threadIdx.x; i < nlines * nl; i += blockDim.x) {
+        const int l = i / nl, j = i - l * nl;
+        s_doff[i] = R(pb.lam[j] - pb.line[l].lam0);
+    }
+    if (threadIdx.x < ME_MAX_LINES)
+        s_he[threadIdx.x] = threadIdx.x < nlines ? R(pb.line[threadIdx.x].half_eta) : R(0);
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int pix = blockIdx.x * kLmWarps + warp;
+    if (pix >= npix) return;
+    LmWarpSmem &W = s_w[warp];
+    const RO *o = obs + (size_t)pix * 4 * nl;
+    R he[ME_MAX_LINES];
+#pragma unroll
+    for (int l = 0; l < ME_MAX_LINES; ++l) he[l] = s_he[l];
+
+    // weights (Section 4.5 inverse-max in FP64, or the caller's)
+    if (w_user) {
+        if (lane < 4) {
+            const double w = w_user[(size_t)pix * 4 + lane];
+            W.w2[lane] = w * w;
+        }
+    } else {
+        double imax = -INFINITY, imin = INFINITY, mq = 0, mu = 0, mv = 0;
+        for (int j = lane; j < nl; j += 32) {
+            const double I = (double)o[j];
+            imax = fmax(imax, I);
+            imin = fmin(imin, I);
+            mq = fmax(mq, fabs((double)o[nl + j]));
+            mu = fmax(mu, fabs((double)o[2 * nl + j]));
+            mv = fmax(mv, fabs((double)o[3 * nl + j]));
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            imax = fmax(imax, __shfl_xor_sync(0xffffffffu, imax, off));
+            imin = fmin(imin, __shfl_xor_sync(0xffffffffu, imin, off));
+            mq = fmax(mq, __shfl_xor_sync(0xffffffffu, mq, off));
+            mu = fmax(mu, __shfl_xor_sync(0xffffffffu, mu, off));
+            mv = fmax(mv, __shfl_xor_sync(0xffffffffu, mv, off));
+        }
+        if (lane == 0) {
+            const double d[4] = {imax - imin, mq, mu, mv};
+            const double fl = 1e-6 * fabs(imax);
+            for (int s = 0; s < 4; ++s) {
+                const double dd = d[s] > fl ? d[s] : fl;
+                const double w = dd > 0.0 ? 1.0 / dd : 0.0;
+                W.w2[s] = w * w;
+            }
+        }
+    }
+    __syncwarp();
+    double w2[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) w2[s] = W.w2[s];
+    R w2r[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) w2r[s] = R(w2[s]);
+
+    const double mu = mu_px ? mu_px[pix] : pb.mu;
+    double p[ME_NPAR];
+#pragma unroll
+    for (int d = 0; d < ME_NPAR; ++d) p[d] = params[(size_t)pix * ME_NPAR + d];
+    double chi2 = lm_chi2<R, RO, NL>(pb, nlines, nl, p, mu, o, s_doff, he, w2);
+    double lam = lm.lambda0;
+    bool need = true;
+    for (int it = 0; it < lm.iters; ++it) {
+        if (need) {
+            R pr[ME_NPAR];
+#pragma unroll
+            for (int d = 0; d < ME_NPAR; ++d) pr[d] = R(p[d]);
+            const GeoJ<R> G = make_geoj<R, NL>(pb, nlines, pr, R(mu));
+            R Aacc[kNT], gacc[ME_NPAR];
+#pragma unroll
+            for (int a = 0; a < kNT; ++a) Aacc[a] = R(0);
+#pragma unroll
+            for (int a = 0; a < ME_NPAR; ++a) gacc[a] = R(0);
+            for (int j = lane; j < nl; j += 32) {
+                R doff[ME_MAX_LINES];
+#pragma unroll
+                for (int l = 0; l < ME_MAX_LINES; ++l) doff[l] = l < nlines ? s_doff[l * nl + j] : R(0);
+                Stokes4<R> m;
+                R J[4][ME_NPAR];
+                me_point_jac<R, NL>(G, doff, he, nlines, m, J);
+                const R r[4] = {R(o[j]) - m.I, R(o[nl + j]) - m.Q, R(o[2 * nl + j]) - m.U,
+                                R(o[3 * nl + j]) - m.V};
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    int t = 0;
+#pragma unroll
+                    for (int a = 0; a < ME_NPAR; ++a) {
+                        const R wa = w2r[s] * J[s][a];
+                        gacc[a] += wa * r[s];
+#pragma unroll
+                        for (int b = 0; b <= a; ++b) Aacc[t++] += wa * J[s][b];
+                    }
+                }
+            }
+            int t = 0;
+#pragma unroll
+            for (int a = 0; a < ME_NPAR; ++a) {
+                const double gv = warp_sum((double)gacc[a]);
+                if (lane == 0) W.g[a] = gv;
+#pragma unroll
+                for (int b = 0; b <= a; ++b) {
+                    const double v = warp_sum((double)Aacc[t++]);
+                    if (lane == 0) { W.A[a * ME_NPAR + b] = v; W.A[b * ME_NPAR + a] = v; }
+                }
+            }
+            need = false;
+            __syncwarp();
+        }
+        if (lane == 0) {
+            bool ok = false;
+            for (int tries = 0; tries < 30 && !ok; ++tries) {
+                ok = damped_cholesky(W.A, W.g, lam, W.N, W.x);
+                if (!ok) lam *= 10.0;
+            }
+            W.ok = ok ? 1 : 0;
+            W.lam = lam;
+        }
+        __syncwarp();
+        lam = W.lam;
+        if (!W.ok) break;
+        double q[ME_NPAR];
+#pragma unroll
+        for (int d = 0; d < ME_NPAR; ++d) q[d] = p[d] + W.x[d];
+        {
+            double c = fmod(q[2], 180.0);
+            if (c < 0.0) c += 180.0;
+            if (c >= 180.0) c -= 180.0;
+            q[2] = c;
+        }
+#pragma unroll
+        for (int d = 0; d < ME_NPAR; ++d) q[d] = fmin(fmax(q[d], lm.lo[d]), lm.hi[d]);
+        const double c2 = lm_chi2<R, RO, NL>(pb, nlines, nl, q, mu, o, s_doff, he, w2);
+        __syncwarp();
+        if (c2 < chi2) {
+#pragma unroll
+            for (int d = 0; d < ME_NPAR; ++d) p[d] = q[d];
+            chi2 = c2;
+            lam /= 10.0;
+            need = true;
+        } else {
+            lam *= 10.0;
+        }
+    }
+    if (lane < ME_NPAR) {
+        double v = p[0];
+#pragma unroll
+        for (int d = 1; d < ME_NPAR; ++d) v = (lane == d) ? p[d] : v;
+        params[(size_t)pix * ME_NPAR + lane] = v;
+    }
+}
+
+template <class R, class RO, int NL>
+cudaError_t lm_t(const KProblem &pb, const KLm &lm, const void *obs, const double *w,
+                 const double *mu_px, int npix, double *params, cudaStream_t st)
+{
+    const int nlines = NL > 0 ? NL : pb.n_lines;
+    const size_t smem = sizeof(LmWarpSmem) * kLmWarps + sizeof(R) * (ME_MAX_LINES + (size_t)nlines * pb.n_lambda);
+    auto kern = k_lm<R, RO, NL>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(npix + kLmWarps - 1) / kLmWarps, kLmWarps * 32, smem, st>>>(pb, lm, (const RO *)obs, w, mu_px,
+                                                                      npix, params);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_lm(const KProblem &pb, const KLm &lm, int dtype, const void *obs,
+                      const double *w, const double *mu_px, int npix, double *params,
+                      cudaStream_t st)
+{
+    if (npix <= 0 || lm.iters <= 0) return cudaSuccess;
+    if (dtype == ME_F32) {
+        if (pb.n_lines == 1) return lm_t<float, float, 1>(pb, lm, obs, w, mu_px, npix, params, st);
+        if (pb.n_lines == 2) return lm_t<float, float, 2>(pb, lm, obs, w, mu_px, npix, params, st);
+        return lm_t<float, float, 0>(pb, lm, obs, w, mu_px, npix, params, st);
+    }
+    return lm_t<double, double, 0>(pb, lm, obs, w, mu_px, npix, params, st);
+}
+
+}  // namespace genesis

@@ -1,0 +1,269 @@
+// Device-side Milne-Eddington synthesis for sm_103a.
+//
+// Section 4 of Harker & Mighell (2012): K = 1 + eta0 Phi, the emergent Stokes
+// vector S0 e + mu S1 K^-1 e, with Voigt / Faraday-Voigt profiles for the
+// sigma_b, pi and sigma_r components of every line.  All templates take the
+// arithmetic type R (float or double).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "genesis.h"
+
+namespace genesis {
+
+constexpr double kSpeedOfLight = 299792.458;  // km/s
+constexpr double kZeeman = 4.6686e-13;        // A^-1 G^-1 (e / 4 pi m c^2)
+constexpr double kDeg = 3.14159265358979323846 / 180.0;
+
+// ------------------------------------------------------------ launch params
+struct KLine {
+    double lam0;       // rest wavelength [A]
+    double lam0_c;     // lambda0 / c [A per km/s]
+    double dscale;     // 1e-3 lambda0 / lambda_dop: Doppler width [A] per mA of param 4
+    double zfac;       // 4.6686e-13 g lambda0^2 [A / G]
+    double half_eta;   // eta_ratio / 2
+};
+
+// Everything a synthesis needs, passed by value in the kernel parameters
+// (about 4.3 KB, within the 32 KB parameter space of sm_70+).
+struct KProblem {
+    int n_lines;
+    int n_lambda;
+    double mu;
+    KLine line[ME_MAX_LINES];
+    double lam[ME_MAX_LAMBDA];  // wavelength grid [A]
+};
+
+// Faddeeva coefficient tables (filled per device at library initialisation).
+struct FaddeevaTables {
+    float w32[17];     // Weideman a_1..a_16 (index n = 1..16), N = 16
+    float L32;
+    float cfa32[3];    // continued fraction k = 3: denominator a(u) coefficients (u^0..u^2)
+    float cfb32[2];    // numerator b(u) (u^0..u^1), w = i/sqrt(pi) z b(u) / a(u)
+    double w64[37];    // Weideman N = 36
+    double L64;
+    double cfa64[6];   // k = 9: a(u) degree 5
+    double cfb64[5];   // b(u) degree 4
+};
+
+// Each translation unit holds its own copy; genesis::upload_tables() fills all.
+static __constant__ FaddeevaTables c_fad;
+
+template <class R> struct FadCfg;
+template <> struct FadCfg<float> {
+    static constexpr int N = 16;
+    static constexpr int NA = 3, NB = 2;
+    static constexpr float R2 = 36.0f;  // |z|^2 above which the continued fraction is used
+};
+template <> struct FadCfg<double> {
+    static constexpr int N = 36;
+    static constexpr int NA = 6, NB = 5;
+    static constexpr double R2 = 64.0;
+};
+
+template <class R> struct C2 { R x, y; };
+
+// MUFU reciprocal (relative error < 2^-23), one instruction.
+__device__ __forceinline__ float fast_rcp(float v)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ double fast_rcp(double v) { return 1.0 / v; }
+
+template <class R> __device__ __forceinline__ R weid(int n);
+template <> __device__ __forceinline__ float weid<float>(int n) { return c_fad.w32[n]; }
+template <> __device__ __forceinline__ double weid<double>(int n) { return c_fad.w64[n]; }
+template <class R> __device__ __forceinline__ R weidL();
+template <> __device__ __forceinline__ float weidL<float>() { return c_fad.L32; }
+template <> __device__ __forceinline__ double weidL<double>() { return c_fad.L64; }
+template <class R> __device__ __forceinline__ R cfa(int n);
+template <> __device__ __forceinline__ float cfa<float>(int n) { return c_fad.cfa32[n]; }
+template <> __device__ __forceinline__ double cfa<double>(int n) { return c_fad.cfa64[n]; }
+template <class R> __device__ __forceinline__ R cfb(int n);
+template <> __device__ __forceinline__ float cfb<float>(int n) { return c_fad.cfb32[n]; }
+template <> __device__ __forceinline__ double cfb<double>(int n) { return c_fad.cfb64[n]; }
+
+// w(z) = exp(-z^2) erfc(-i z) for z = x + i y, y >= 0.
+//
+// Interior |z| <= R: Weideman's (1994) rational series
+//     w(z) = 2 p(Z) / (L - i z)^2 + (1/sqrt(pi)) / (L - i z),
+//     Z = (L + i z) / (L - i z),  p(Z) = sum_{n=1}^{N} a_n Z^{n-1},
+// with a_n the Fourier coefficients of (L^2 + t^2) exp(-t^2) under
+// t = L tan(theta/2) (computed on the host from that integral).
+// Exterior |z| > R: the k-th convergent of the Laplace continued fraction
+//     w(z) = (i/sqrt(pi)) / (z - (1/2)/(z - 1/(z - (3/2)/(z - ...)))),
+// written as a ratio of polynomials in u = z^2.  Both branches need one
+// reciprocal.  Absolute error: FP32 ~1e-7 (N = 16, k = 3, R = 6), FP64 ~2e-15
+// (N = 36, k = 9, R = 8).
+template <class R>
+__device__ __forceinline__ C2<R> faddeeva(R x, R y)
+{
+    const R r2 = x * x + y * y;
+    C2<R> w;
+    if (r2 > FadCfg<R>::R2) {
+        const R ux = x * x - y * y, uy = R(2) * x * y;
+        R ax = cfa<R>(FadCfg<R>::NA - 1), ay = R(0);
+#pragma unroll
+        for (int n = FadCfg<R>::NA - 2; n >= 0; --n) {
+            const R tx = ax * ux - ay * uy + cfa<R>(n);
+            ay = ax * uy + ay * ux;
+            ax = tx;
+        }
+        R bx = cfb<R>(FadCfg<R>::NB - 1), by = R(0);
+#pragma unroll
+        for (int n = FadCfg<R>::NB - 2; n >= 0; --n) {
+            const R tx = bx * ux - by * uy + cfb<R>(n);
+            by = bx * uy + by * ux;
+            bx = tx;
+        }
+        // num = z b(u); w = (i/sqrt(pi)) num / a(u)
+        const R nx = x * bx - y * by, ny = x * by + y * bx;
+        const R inv = fast_rcp(ax * ax + ay * ay);
+        const R qx = (nx * ax + ny * ay) * inv, qy = (ny * ax - nx * ay) * inv;
+        const R s = R(0.56418958354775628695);  // 1/sqrt(pi)
+        w.x = -qy * s;
+        w.y = qx * s;
+    } else {
+        const R L = weidL<R>();
+        // d = L - i z = (L + y) - i x;  r = 1/d
+        const R dx = L + y, dy = -x;
+        const R inv = fast_rcp(dx * dx + dy * dy);
+        const R rx = dx * inv, ry = -dy * inv;
+        // Z = (L + i z) r = ((L - y) + i x) r
+        const R mx = L - y, my = x;
+        const R Zx = mx * rx - my * ry, Zy = mx * ry + my * rx;
+        R px = weid<R>(FadCfg<R>::N), py = R(0);
+#pragma unroll
+        for (int n = FadCfg<R>::N - 1; n >= 1; --n) {
+            const R tx = px * Zx - py * Zy + weid<R>(n);
+            py = px * Zy + py * Zx;
+            px = tx;
+        }
+        const R r2x = rx * rx - ry * ry, r2y = R(2) * rx * ry;
+        const R s = R(0.56418958354775628695);
+        w.x = R(2) * (px * r2x - py * r2y) + rx * s;
+        w.y = R(2) * (px * r2y + py * r2x) + ry * s;
+    }
+    return w;
+}
+
+// ------------------------------------------------------ per-model geometry
+template <class R> struct Geo {
+    R a;                // damping
+    R kIp, kIs;         // eta0 sin^2 t, eta0 (1 + cos^2 t)/2
+    R kQ, kU, kV;       // eta0 sin^2 t cos 2chi, eta0 sin^2 t sin 2chi, eta0 cos t
+    R S0, muS1;
+    R shift[ME_MAX_LINES];  // lambda0 v_LOS / c [A]
+    R invD[ME_MAX_LINES];   // 1 / Doppler width [1/A]
+    R vB[ME_MAX_LINES];     // Zeeman splitting in Doppler units
+};
+
+__device__ __forceinline__ void sincos_deg(float d, float *s, float *c)
+{
+    sincospif(d * (1.0f / 180.0f), s, c);
+}
+__device__ __forceinline__ void sincos_deg(double d, double *s, double *c)
+{
+    sincospi(d * (1.0 / 180.0), s, c);
+}
+
+// Geometry of one parameter vector p (Section 4 model vector), in R.
+template <class R, int NL>
+__device__ __forceinline__ Geo<R> make_geo(const KProblem &pb, int nlines, const R *p, R mu)
+{
+    Geo<R> g;
+    R st, ct, s2c, c2c;
+    sincos_deg(p[1], &st, &ct);
+    sincos_deg(R(2) * p[2], &s2c, &c2c);
+    const R eta0 = p[6];
+    const R s2 = st * st;
+    g.a = p[5];
+    g.kIp = eta0 * s2;
+    g.kIs = eta0 * R(0.5) * (R(1) + ct * ct);
+    g.kQ = eta0 * s2 * c2c;
+    g.kU = eta0 * s2 * s2c;
+    g.kV = eta0 * ct;
+    g.S0 = p[7];
+    g.muS1 = mu * p[8];
+    const int nl = NL > 0 ? NL : nlines;
+#pragma unroll
+    for (int l = 0; l < (NL > 0 ? NL : ME_MAX_LINES); ++l) {
+        if (l < nl) {
+            const KLine &ln = pb.line[l];
+            g.shift[l] = R(ln.lam0_c) * p[3];
+            g.invD[l] = R(1) / (p[4] * R(ln.dscale));
+            g.vB[l] = R(ln.zfac) * p[0] * g.invD[l];
+        }
+    }
+    return g;
+}
+
+template <class R> struct Stokes4 { R I, Q, U, V; };
+
+// Stokes vector at one wavelength.  doff[l] = lambda_j - lambda0_l (exact in
+// FP64, rounded to R), half_eta[l] = eta_ratio_l / 2.
+template <class R, int NL>
+__device__ __forceinline__ Stokes4<R> me_point(const Geo<R> &g, const R *doff, const R *half_eta,
+                                               int nlines)
+{
+    R P = 0, Sg = 0, T = 0, Dd = 0, Ti = 0, Di = 0;
+    const int nl = NL > 0 ? NL : nlines;
+#pragma unroll
+    for (int l = 0; l < (NL > 0 ? NL : ME_MAX_LINES); ++l) {
+        if (l < nl) {
+            const R v = (doff[l] - g.shift[l]) * g.invD[l];
+            const C2<R> wb = faddeeva<R>(v + g.vB[l], g.a);
+            const C2<R> wp = faddeeva<R>(v, g.a);
+            const C2<R> wr = faddeeva<R>(v - g.vB[l], g.a);
+            const R q = half_eta[l];
+            const R sx = wb.x + wr.x, sy = wb.y + wr.y;
+            P += q * wp.x;
+            Sg += q * sx;
+            T += q * (wp.x - R(0.5) * sx);
+            Ti += q * (wp.y - R(0.5) * sy);
+            Dd += q * (wr.x - wb.x);
+            Di += q * (wr.y - wb.y);
+        }
+    }
+    const R eI = R(1) + g.kIp * P + g.kIs * Sg;
+    const R eQ = g.kQ * T, eU = g.kU * T, eV = g.kV * Dd;
+    const R rQ = g.kQ * Ti, rU = g.kU * Ti, rV = g.kV * Di;
+    const R eI2 = eI * eI;
+    const R rho2 = rQ * rQ + rU * rU + rV * rV;
+    const R Pi = eQ * rQ + eU * rU + eV * rV;
+    const R Delta = eI2 * (eI2 - eQ * eQ - eU * eU - eV * eV + rho2) - Pi * Pi;
+    const R f = g.muS1 * fast_rcp(Delta);
+    Stokes4<R> s;
+    s.I = g.S0 + f * eI * (eI2 + rho2);
+    s.Q = -f * (eI2 * eQ + eI * (eV * rU - eU * rV) + rQ * Pi);
+    s.U = -f * (eI2 * eU + eI * (eQ * rV - eV * rQ) + rU * Pi);
+    s.V = -f * (eI2 * eV + eI * (eU * rQ - eQ * rU) + rV * Pi);
+    return s;
+}
+
+// Number of Faddeeva evaluations at one wavelength that take the interior
+// (Weideman) branch; the same test as faddeeva().  Used only by the counting
+// instantiation of the GA kernel, to turn branch counts into flops.
+template <class R, int NL>
+__device__ __forceinline__ unsigned count_interior(const Geo<R> &g, const R *doff, int nlines)
+{
+    unsigned c = 0;
+    const int nl = NL > 0 ? NL : nlines;
+#pragma unroll
+    for (int l = 0; l < (NL > 0 ? NL : ME_MAX_LINES); ++l) {
+        if (l < nl) {
+            const R v = (doff[l] - g.shift[l]) * g.invD[l];
+            const R xs[3] = {v + g.vB[l], v, v - g.vB[l]};
+#pragma unroll
+            for (int c3 = 0; c3 < 3; ++c3)
+                c += (xs[c3] * xs[c3] + g.a * g.a > FadCfg<R>::R2) ? 0u : 1u;
+        }
+    }
+    return c;
+}
+
+}  // namespace genesis

@@ -1,0 +1,231 @@
+// Analytic Jacobian of the Milne-Eddington Stokes vector (sm_103a).
+//
+// Differentiates Section 4's solution S0 e + mu S1 K^-1 e through the closed
+// form of K^-1 e, the propagation-matrix elements and the Faddeeva profiles,
+// using w'(z) = -2 z w(z) + 2 i / sqrt(pi) and dw/da = i w'(z).
+#pragma once
+
+#include "me_device.cuh"
+
+namespace genesis {
+
+template <class R> struct GeoJ {
+    Geo<R> g;
+    R eta0, invDpar;                 // eta0, 1 / (param 4)
+    R uIp, uIs, uQ, uU, uV;          // kIp..kV per unit eta0
+    R dIp_th, dIs_th, dQ_th, dU_th, dV_th;  // d k / d theta [per deg]
+    R dQ_ch, dU_ch;                         // d k / d chi [per deg]
+    R mu;
+    R kv[ME_MAX_LINES];              // d x / d v_LOS = -kv (lambda0 / c / Doppler width)
+    R kB[ME_MAX_LINES];              // d v_B / d B
+};
+
+template <class R, int NL>
+__device__ __forceinline__ GeoJ<R> make_geoj(const KProblem &pb, int nlines, const R *p, R mu)
+{
+    GeoJ<R> G;
+    G.g = make_geo<R, NL>(pb, nlines, p, mu);
+    R st, ct, s2c, c2c;
+    sincos_deg(p[1], &st, &ct);
+    sincos_deg(R(2) * p[2], &s2c, &c2c);
+    const R eta0 = p[6], s2 = st * st, kd = R(kDeg);
+    G.eta0 = eta0;
+    G.invDpar = R(1) / p[4];
+    G.uIp = s2;
+    G.uIs = R(0.5) * (R(1) + ct * ct);
+    G.uQ = s2 * c2c;
+    G.uU = s2 * s2c;
+    G.uV = ct;
+    const R ds2 = R(2) * st * ct * kd;    // d sin^2 / d theta
+    G.dIp_th = eta0 * ds2;
+    G.dIs_th = -eta0 * st * ct * kd;
+    G.dQ_th = eta0 * ds2 * c2c;
+    G.dU_th = eta0 * ds2 * s2c;
+    G.dV_th = -eta0 * st * kd;
+    G.dQ_ch = -eta0 * s2 * R(2) * s2c * kd;
+    G.dU_ch = eta0 * s2 * R(2) * c2c * kd;
+    G.mu = mu;
+    const int nl = NL > 0 ? NL : nlines;
+#pragma unroll
+    for (int l = 0; l < (NL > 0 ? NL : ME_MAX_LINES); ++l) {
+        if (l < nl) {
+            G.kv[l] = R(pb.line[l].lam0_c) * G.g.invD[l];
+            G.kB[l] = R(pb.line[l].zfac) * G.g.invD[l];
+        }
+    }
+    return G;
+}
+
+// Profile sums per unit eta0 and their derivatives along B, v_LOS, D, a.
+template <class R> struct Sums {
+    R P, Sg, T, Ti, Dd, Di;
+    R dP[4], dSg[4], dT[4], dTi[4], dDd[4], dDi[4];
+};
+
+// Stokes vector and J[s][k] = d Stokes_s / d p_k at one wavelength.
+template <class R, int NL>
+__device__ __forceinline__ void me_point_jac(const GeoJ<R> &G, const R *doff, const R *half_eta,
+                                             int nlines, Stokes4<R> &out, R J[4][ME_NPAR])
+{
+    const Geo<R> &g = G.g;
+    Sums<R> S;
+    S.P = S.Sg = S.T = S.Ti = S.Dd = S.Di = R(0);
+#pragma unroll
+    for (int d = 0; d < 4; ++d) S.dP[d] = S.dSg[d] = S.dT[d] = S.dTi[d] = S.dDd[d] = S.dDi[d] = R(0);
+    const R two_isp = R(1.12837916709551257390);  // 2 / sqrt(pi)
+    const int nl = NL > 0 ? NL : nlines;
+#pragma unroll
+    for (int l = 0; l < (NL > 0 ? NL : ME_MAX_LINES); ++l) {
+        if (l < nl) {
+            const R v = (doff[l] - g.shift[l]) * g.invD[l];
+            const R q = half_eta[l];
+            const R xs[3] = {v + g.vB[l], v, v - g.vB[l]};  // blue, pi, red
+            C2<R> w[3], wd[3][4];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                w[c] = faddeeva<R>(xs[c], g.a);
+                // w' = -2 z w + 2i/sqrt(pi)
+                const R dx = R(-2) * (xs[c] * w[c].x - g.a * w[c].y);
+                const R dy = R(-2) * (xs[c] * w[c].y + g.a * w[c].x) + two_isp;
+                const R sB = c == 0 ? G.kB[l] : (c == 2 ? -G.kB[l] : R(0));
+                const R sv = -G.kv[l];
+                const R sD = -xs[c] * G.invDpar;
+                wd[c][0] = {dx * sB, dy * sB};   // d/dB
+                wd[c][1] = {dx * sv, dy * sv};   // d/dv_LOS
+                wd[c][2] = {dx * sD, dy * sD};   // d/dD
+                wd[c][3] = {-dy, dx};            // d/da = i w'
+            }
+            const R sx = w[0].x + w[2].x, sy = w[0].y + w[2].y;
+            S.P += q * w[1].x;
+            S.Sg += q * sx;
+            S.T += q * (w[1].x - R(0.5) * sx);
+            S.Ti += q * (w[1].y - R(0.5) * sy);
+            S.Dd += q * (w[2].x - w[0].x);
+            S.Di += q * (w[2].y - w[0].y);
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                const R bx = wd[0][d].x + wd[2][d].x, by = wd[0][d].y + wd[2][d].y;
+                S.dP[d] += q * wd[1][d].x;
+                S.dSg[d] += q * bx;
+                S.dT[d] += q * (wd[1][d].x - R(0.5) * bx);
+                S.dTi[d] += q * (wd[1][d].y - R(0.5) * by);
+                S.dDd[d] += q * (wd[2][d].x - wd[0][d].x);
+                S.dDi[d] += q * (wd[2][d].y - wd[0][d].y);
+            }
+        }
+    }
+    // propagation-matrix elements e = (eI, eQ, eU, eV, rQ, rU, rV)
+    const R eI = R(1) + g.kIp * S.P + g.kIs * S.Sg;
+    const R eQ = g.kQ * S.T, eU = g.kU * S.T, eV = g.kV * S.Dd;
+    const R rQ = g.kQ * S.Ti, rU = g.kU * S.Ti, rV = g.kV * S.Di;
+    const R eI2 = eI * eI;
+    const R rho2 = rQ * rQ + rU * rU + rV * rV;
+    const R E2 = eQ * eQ + eU * eU + eV * eV;
+    const R Pi = eQ * rQ + eU * rU + eV * rV;
+    const R Delta = eI2 * (eI2 - E2 + rho2) - Pi * Pi;
+    const R iD = R(1) / Delta;
+    const R f = g.muS1 * iD;
+    const R nI = eI * (eI2 + rho2);
+    const R nQ = eI2 * eQ + eI * (eV * rU - eU * rV) + rQ * Pi;
+    const R nU = eI2 * eU + eI * (eQ * rV - eV * rQ) + rU * Pi;
+    const R nV = eI2 * eV + eI * (eU * rQ - eQ * rU) + rV * Pi;
+    out.I = g.S0 + f * nI;
+    out.Q = -f * nQ;
+    out.U = -f * nU;
+    out.V = -f * nV;
+
+    // d Delta / d e
+    const R dDe[7] = {R(2) * eI * (R(2) * eI2 - E2 + rho2),
+                      R(-2) * (eI2 * eQ + Pi * rQ), R(-2) * (eI2 * eU + Pi * rU),
+                      R(-2) * (eI2 * eV + Pi * rV),
+                      R(2) * (eI2 * rQ - Pi * eQ), R(2) * (eI2 * rU - Pi * eU),
+                      R(2) * (eI2 * rV - Pi * eV)};
+    // d n_s / d e
+    const R dnI[7] = {R(3) * eI2 + rho2, R(0), R(0), R(0), R(2) * eI * rQ, R(2) * eI * rU,
+                      R(2) * eI * rV};
+    const R dnQ[7] = {R(2) * eI * eQ + eV * rU - eU * rV, eI2 + rQ * rQ, -eI * rV + rQ * rU,
+                      eI * rU + rQ * rV, Pi + rQ * eQ, eI * eV + rQ * eU, -eI * eU + rQ * eV};
+    const R dnU[7] = {R(2) * eI * eU + eQ * rV - eV * rQ, eI * rV + rU * rQ, eI2 + rU * rU,
+                      -eI * rQ + rU * rV, -eI * eV + rU * eQ, Pi + rU * eU, eI * eQ + rU * eV};
+    const R dnV[7] = {R(2) * eI * eV + eU * rQ - eQ * rU, -eI * rU + rV * rQ, eI * rQ + rV * rU,
+                      eI2 + rV * rV, eI * eU + rV * eQ, -eI * eQ + rV * eU, Pi + rV * eV};
+    // G[s][e] = d Stokes_s / d e
+    R Gm[4][7];
+    const R xI = nI * iD, xQ = nQ * iD, xU = nU * iD, xV = nV * iD;
+#pragma unroll
+    for (int e = 0; e < 7; ++e) {
+        Gm[0][e] = f * (dnI[e] - xI * dDe[e]);
+        Gm[1][e] = -f * (dnQ[e] - xQ * dDe[e]);
+        Gm[2][e] = -f * (dnU[e] - xU * dDe[e]);
+        Gm[3][e] = -f * (dnV[e] - xV * dDe[e]);
+    }
+    // E[e] = d e / d p_k for k = 0..6, then J = G E
+    const int dirs[4] = {0, 3, 4, 5};  // B, v_LOS, D, a
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        R E[7];
+        E[0] = g.kIp * S.dP[d] + g.kIs * S.dSg[d];
+        E[1] = g.kQ * S.dT[d];
+        E[2] = g.kU * S.dT[d];
+        E[3] = g.kV * S.dDd[d];
+        E[4] = g.kQ * S.dTi[d];
+        E[5] = g.kU * S.dTi[d];
+        E[6] = g.kV * S.dDi[d];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            R acc = R(0);
+#pragma unroll
+            for (int e = 0; e < 7; ++e) acc += Gm[s][e] * E[e];
+            J[s][dirs[d]] = acc;
+        }
+    }
+    {   // theta
+        R E[7];
+        E[0] = G.dIp_th * S.P + G.dIs_th * S.Sg;
+        E[1] = G.dQ_th * S.T;
+        E[2] = G.dU_th * S.T;
+        E[3] = G.dV_th * S.Dd;
+        E[4] = G.dQ_th * S.Ti;
+        E[5] = G.dU_th * S.Ti;
+        E[6] = G.dV_th * S.Di;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            R acc = R(0);
+#pragma unroll
+            for (int e = 0; e < 7; ++e) acc += Gm[s][e] * E[e];
+            J[s][1] = acc;
+        }
+    }
+    {   // chi: only eQ, eU, rQ, rU depend on it
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+            J[s][2] = Gm[s][1] * G.dQ_ch * S.T + Gm[s][2] * G.dU_ch * S.T +
+                      Gm[s][4] * G.dQ_ch * S.Ti + Gm[s][5] * G.dU_ch * S.Ti;
+    }
+    {   // eta0
+        R E[7];
+        E[0] = G.uIp * S.P + G.uIs * S.Sg;
+        E[1] = G.uQ * S.T;
+        E[2] = G.uU * S.T;
+        E[3] = G.uV * S.Dd;
+        E[4] = G.uQ * S.Ti;
+        E[5] = G.uU * S.Ti;
+        E[6] = G.uV * S.Di;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            R acc = R(0);
+#pragma unroll
+            for (int e = 0; e < 7; ++e) acc += Gm[s][e] * E[e];
+            J[s][6] = acc;
+        }
+    }
+    // source function: d/dS0 = e, d/dS1 = mu K^-1 e
+    J[0][7] = R(1);
+    J[1][7] = J[2][7] = J[3][7] = R(0);
+    J[0][8] = G.mu * xI;
+    J[1][8] = -G.mu * xQ;
+    J[2][8] = -G.mu * xU;
+    J[3][8] = -G.mu * xV;
+}
+
+}  // namespace genesis

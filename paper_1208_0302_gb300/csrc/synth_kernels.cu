@@ -1,0 +1,331 @@
+// Stokes synthesis, Jacobian, adjoint and FP64 chi-square kernels (sm_103a).
+#include "kernels.h"
+#include "me_jac.cuh"
+#include "rng_device.cuh"
+
+namespace genesis {
+
+cudaError_t upload_tables_synth(const HostTables &t)
+{
+    return cudaMemcpyToSymbol(c_fad, &t.fad, sizeof(FaddeevaTables));
+}
+
+namespace {
+
+constexpr int kSynthBlock = 128;
+
+// Fill s_doff[l * nl + j] = lambda_j - lambda0_l for all lines (exact in FP64,
+// rounded to R) and s_he[l] = eta_ratio_l / 2.
+template <class R>
+__device__ __forceinline__ void stage_offsets(const KProblem &pb, int nlines, R *s_doff, R *s_he)
+{
+    const int nl = pb.n_lambda;
+    for (int i = threadIdx.x; i < nlines * nl; i += blockDim.x) {
+        const int l = i / nl, j = i - l * nl;
+        s_doff[i] = R(pb.lam[j] - pb.line[l].lam0);
+    }
+    if (threadIdx.x < ME_MAX_LINES)
+        s_he[threadIdx.x] = threadIdx.x < nlines ? R(pb.line[threadIdx.x].half_eta) : R(0);
+}
+
+// One thread per (model, wavelength).
+template <class R, int NL>
+__global__ void __launch_bounds__(kSynthBlock)
+k_synth(const __grid_constant__ KProblem pb, const double *__restrict__ params,
+        const double *__restrict__ mu_px, int n, R *__restrict__ stokes)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nl = pb.n_lambda, nlines = NL > 0 ? NL : pb.n_lines;
+    R *s_he = (R *)smem;
+    R *s_doff = s_he + ME_MAX_LINES;
+    stage_offsets<R>(pb, nlines, s_doff, s_he);
+    __syncthreads();
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n * nl) return;
+    const int m = (int)(i / nl), j = (int)(i - (long long)m * nl);
+    R p[ME_NPAR];
+#pragma unroll
+    for (int d = 0; d < ME_NPAR; ++d) p[d] = R(params[(size_t)m * ME_NPAR + d]);
+    const R mu = mu_px ? R(mu_px[m]) : R(pb.mu);
+    const Geo<R> g = make_geo<R, NL>(pb, nlines, p, mu);
+    R doff[ME_MAX_LINES], he[ME_MAX_LINES];
+#pragma unroll
+    for (int l = 0; l < ME_MAX_LINES; ++l) {
+        doff[l] = l < nlines ? s_doff[l * nl + j] : R(0);
+        he[l] = s_he[l];
+    }
+    const Stokes4<R> s = me_point<R, NL>(g, doff, he, nlines);
+    R *o = stokes + (size_t)m * 4 * nl;
+    o[j] = s.I;
+    o[nl + j] = s.Q;
+    o[2 * nl + j] = s.U;
+    o[3 * nl + j] = s.V;
+}
+
+template <class R, int NL>
+__global__ void __launch_bounds__(kSynthBlock)
+k_jac(const __grid_constant__ KProblem pb, const double *__restrict__ params,
+      const double *__restrict__ mu_px, int n, R *__restrict__ stokes, R *__restrict__ jac)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nl = pb.n_lambda, nlines = NL > 0 ? NL : pb.n_lines;
+    R *s_he = (R *)smem;
+    R *s_doff = s_he + ME_MAX_LINES;
+    stage_offsets<R>(pb, nlines, s_doff, s_he);
+    __syncthreads();
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n * nl) return;
+    const int m = (int)(i / nl), j = (int)(i - (long long)m * nl);
+    R p[ME_NPAR];
+#pragma unroll
+    for (int d = 0; d < ME_NPAR; ++d) p[d] = R(params[(size_t)m * ME_NPAR + d]);
+    const R mu = mu_px ? R(mu_px[m]) : R(pb.mu);
+    const GeoJ<R> G = make_geoj<R, NL>(pb, nlines, p, mu);
+    R doff[ME_MAX_LINES], he[ME_MAX_LINES];
+#pragma unroll
+    for (int l = 0; l < ME_MAX_LINES; ++l) {
+        doff[l] = l < nlines ? s_doff[l * nl + j] : R(0);
+        he[l] = s_he[l];
+    }
+    Stokes4<R> s;
+    R J[4][ME_NPAR];
+    me_point_jac<R, NL>(G, doff, he, nlines, s, J);
+    if (stokes) {
+        R *o = stokes + (size_t)m * 4 * nl;
+        o[j] = s.I;
+        o[nl + j] = s.Q;
+        o[2 * nl + j] = s.U;
+        o[3 * nl + j] = s.V;
+    }
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+        R *o = jac + (((size_t)m * 4 + st) * nl + j) * ME_NPAR;
+#pragma unroll
+        for (int k = 0; k < ME_NPAR; ++k) o[k] = J[st][k];
+    }
+}
+
+// One warp per model: grad_params[m] = sum_{s, j} J[s][j][:] * grad_stokes[m][s][j].
+template <class R, int NL>
+__global__ void __launch_bounds__(kSynthBlock)
+k_vjp(const __grid_constant__ KProblem pb, const double *__restrict__ params,
+      const double *__restrict__ mu_px, int n, const R *__restrict__ gs, double *__restrict__ gp)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nl = pb.n_lambda, nlines = NL > 0 ? NL : pb.n_lines;
+    R *s_he = (R *)smem;
+    R *s_doff = s_he + ME_MAX_LINES;
+    stage_offsets<R>(pb, nlines, s_doff, s_he);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int m = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (m >= n) return;
+    R p[ME_NPAR];
+#pragma unroll
+    for (int d = 0; d < ME_NPAR; ++d) p[d] = R(params[(size_t)m * ME_NPAR + d]);
+    const R mu = mu_px ? R(mu_px[m]) : R(pb.mu);
+    const GeoJ<R> G = make_geoj<R, NL>(pb, nlines, p, mu);
+    R he[ME_MAX_LINES];
+#pragma unroll
+    for (int l = 0; l < ME_MAX_LINES; ++l) he[l] = s_he[l];
+    R acc[ME_NPAR];
+#pragma unroll
+    for (int k = 0; k < ME_NPAR; ++k) acc[k] = R(0);
+    const R *g = gs + (size_t)m * 4 * nl;
+    for (int j = lane; j < nl; j += 32) {
+        R doff[ME_MAX_LINES];
+#pragma unroll
+        for (int l = 0; l < ME_MAX_LINES; ++l) doff[l] = l < nlines ? s_doff[l * nl + j] : R(0);
+        Stokes4<R> s;
+        R J[4][ME_NPAR];
+        me_point_jac<R, NL>(G, doff, he, nlines, s, J);
+#pragma unroll
+        for (int st = 0; st < 4; ++st) {
+            const R gv = g[st * nl + j];
+#pragma unroll
+            for (int k = 0; k < ME_NPAR; ++k) acc[k] += J[st][k] * gv;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < ME_NPAR; ++k) {
+        double v = (double)acc[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) gp[(size_t)m * ME_NPAR + k] = v;
+    }
+}
+
+// FP64 chi-square (Eq. chisq) of given parameters, one block per pixel,
+// threads over wavelengths.  Inverse-max weights (Section 4.5) are formed in
+// FP64 from the observed values when w is NULL.
+template <class RO>
+__global__ void __launch_bounds__(kSynthBlock)
+k_chi2_f64(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
+           const double *__restrict__ w_user, const double *__restrict__ mu_px, int npix,
+           const double *__restrict__ params, double *__restrict__ chi2)
+{
+    __shared__ double s_red[kSynthBlock / 32][4];
+    __shared__ double s_w2[4];
+    const int nl = pb.n_lambda, nlines = pb.n_lines;
+    const int pix = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const RO *o = obs + (size_t)pix * 4 * nl;
+    if (w_user) {
+        if (threadIdx.x < 4) {
+            const double w = w_user[(size_t)pix * 4 + threadIdx.x];
+            s_w2[threadIdx.x] = w * w;
+        }
+    } else if (warp == 0) {
+        double imax = -INFINITY, imin = INFINITY, mq = 0, mu = 0, mv = 0;
+        for (int j = lane; j < nl; j += 32) {
+            const double I = (double)o[j];
+            imax = fmax(imax, I);
+            imin = fmin(imin, I);
+            mq = fmax(mq, fabs((double)o[nl + j]));
+            mu = fmax(mu, fabs((double)o[2 * nl + j]));
+            mv = fmax(mv, fabs((double)o[3 * nl + j]));
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            imax = fmax(imax, __shfl_xor_sync(0xffffffffu, imax, off));
+            imin = fmin(imin, __shfl_xor_sync(0xffffffffu, imin, off));
+            mq = fmax(mq, __shfl_xor_sync(0xffffffffu, mq, off));
+            mu = fmax(mu, __shfl_xor_sync(0xffffffffu, mu, off));
+            mv = fmax(mv, __shfl_xor_sync(0xffffffffu, mv, off));
+        }
+        if (lane == 0) {
+            const double d[4] = {imax - imin, mq, mu, mv};
+            const double fl = 1e-6 * fabs(imax);
+            for (int s = 0; s < 4; ++s) {
+                const double dd = d[s] > fl ? d[s] : fl;
+                const double w = dd > 0.0 ? 1.0 / dd : 0.0;
+                s_w2[s] = w * w;
+            }
+        }
+    }
+    double p[ME_NPAR];
+#pragma unroll
+    for (int d = 0; d < ME_NPAR; ++d) p[d] = params[(size_t)pix * ME_NPAR + d];
+    const double mu = mu_px ? mu_px[pix] : pb.mu;
+    const Geo<double> g = make_geo<double, 0>(pb, nlines, p, mu);
+    double he[ME_MAX_LINES];
+#pragma unroll
+    for (int l = 0; l < ME_MAX_LINES; ++l) he[l] = l < nlines ? pb.line[l].half_eta : 0.0;
+    double ss[4] = {0, 0, 0, 0};
+    for (int j = threadIdx.x; j < nl; j += blockDim.x) {
+        double doff[ME_MAX_LINES];
+#pragma unroll
+        for (int l = 0; l < ME_MAX_LINES; ++l) doff[l] = l < nlines ? pb.lam[j] - pb.line[l].lam0 : 0.0;
+        const Stokes4<double> s = me_point<double, 0>(g, doff, he, nlines);
+        const double r0 = (double)o[j] - s.I, r1 = (double)o[nl + j] - s.Q;
+        const double r2 = (double)o[2 * nl + j] - s.U, r3 = (double)o[3 * nl + j] - s.V;
+        ss[0] += r0 * r0;
+        ss[1] += r1 * r1;
+        ss[2] += r2 * r2;
+        ss[3] += r3 * r3;
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) ss[s] += __shfl_xor_sync(0xffffffffu, ss[s], off);
+    }
+    if (lane == 0)
+        for (int s = 0; s < 4; ++s) s_red[warp][s] = ss[s];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int s = 0; s < 4; ++s) {
+            double a = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += s_red[w][s];
+            tot += s_w2[s] * a;
+        }
+        chi2[pix] = tot / (double)(4 * nl - ME_NPAR);
+    }
+}
+
+template <class R> size_t offsets_smem(const KProblem &pb)
+{
+    return sizeof(R) * (ME_MAX_LINES + (size_t)pb.n_lines * pb.n_lambda);
+}
+
+template <class R, int NL>
+cudaError_t synth_t(const KProblem &pb, const double *params, const double *mu_px, int n,
+                    void *stokes, cudaStream_t st)
+{
+    const long long tot = (long long)n * pb.n_lambda;
+    const int blocks = (int)((tot + kSynthBlock - 1) / kSynthBlock);
+    k_synth<R, NL><<<blocks, kSynthBlock, offsets_smem<R>(pb), st>>>(pb, params, mu_px, n, (R *)stokes);
+    return cudaGetLastError();
+}
+
+template <class R, int NL>
+cudaError_t jac_t(const KProblem &pb, const double *params, const double *mu_px, int n,
+                  void *stokes, void *jac, cudaStream_t st)
+{
+    const long long tot = (long long)n * pb.n_lambda;
+    const int blocks = (int)((tot + kSynthBlock - 1) / kSynthBlock);
+    k_jac<R, NL><<<blocks, kSynthBlock, offsets_smem<R>(pb), st>>>(pb, params, mu_px, n, (R *)stokes,
+                                                                  (R *)jac);
+    return cudaGetLastError();
+}
+
+template <class R, int NL>
+cudaError_t vjp_t(const KProblem &pb, const double *params, const double *mu_px, int n,
+                  const void *gs, double *gp, cudaStream_t st)
+{
+    const int per = kSynthBlock / 32;
+    k_vjp<R, NL><<<(n + per - 1) / per, kSynthBlock, offsets_smem<R>(pb), st>>>(pb, params, mu_px, n,
+                                                                               (const R *)gs, gp);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_synth(const KProblem &pb, int dtype, const double *params, const double *mu_px,
+                         int n, void *stokes, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    if (dtype == ME_F32) {
+        if (pb.n_lines == 1) return synth_t<float, 1>(pb, params, mu_px, n, stokes, st);
+        if (pb.n_lines == 2) return synth_t<float, 2>(pb, params, mu_px, n, stokes, st);
+        return synth_t<float, 0>(pb, params, mu_px, n, stokes, st);
+    }
+    return synth_t<double, 0>(pb, params, mu_px, n, stokes, st);
+}
+
+cudaError_t launch_jac(const KProblem &pb, int dtype, const double *params, const double *mu_px,
+                       int n, void *stokes, void *jac, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    if (dtype == ME_F32) {
+        if (pb.n_lines == 1) return jac_t<float, 1>(pb, params, mu_px, n, stokes, jac, st);
+        if (pb.n_lines == 2) return jac_t<float, 2>(pb, params, mu_px, n, stokes, jac, st);
+        return jac_t<float, 0>(pb, params, mu_px, n, stokes, jac, st);
+    }
+    return jac_t<double, 0>(pb, params, mu_px, n, stokes, jac, st);
+}
+
+cudaError_t launch_vjp(const KProblem &pb, int dtype, const double *params, const double *mu_px,
+                       int n, const void *gs, double *gp, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    if (dtype == ME_F32) {
+        if (pb.n_lines == 1) return vjp_t<float, 1>(pb, params, mu_px, n, gs, gp, st);
+        if (pb.n_lines == 2) return vjp_t<float, 2>(pb, params, mu_px, n, gs, gp, st);
+        return vjp_t<float, 0>(pb, params, mu_px, n, gs, gp, st);
+    }
+    return vjp_t<double, 0>(pb, params, mu_px, n, gs, gp, st);
+}
+
+cudaError_t launch_chi2_f64(const KProblem &pb, int dtype, const void *obs, const double *w,
+                            const double *mu_px, int npix, const double *params, double *chi2,
+                            cudaStream_t st)
+{
+    if (npix <= 0) return cudaSuccess;
+    if (dtype == ME_F32)
+        k_chi2_f64<float><<<npix, kSynthBlock, 0, st>>>(pb, (const float *)obs, w, mu_px, npix, params, chi2);
+    else
+        k_chi2_f64<double><<<npix, kSynthBlock, 0, st>>>(pb, (const double *)obs, w, mu_px, npix, params, chi2);
+    return cudaGetLastError();
+}
+
+}  // namespace genesis

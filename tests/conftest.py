@@ -17,3 +17,30 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+def _cuda_ok():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def pytest_collection_modifyitems(config, items):
+    if _cuda_ok():
+        return
+    skip = pytest.mark.skip(reason="needs a CUDA GPU")
+    for it in items:
+        if "gpu" in it.keywords:
+            it.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    """The CUDA-side API, with the library built (fails loudly if it cannot be)."""
+    import torch
+    from paper_1208_0302_gb300 import _lib, api
+    _lib.load()
+    torch.cuda.init()
+    return api

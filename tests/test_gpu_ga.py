@@ -1,0 +1,150 @@
+"""GPU genetic algorithm against the oracle.
+
+Operators are compared bit for bit on injected fitness values; whole runs are
+compared bit for bit in FP64 mode on every pixel whose oracle decisions are
+separated by more than the FP64 evaluation error, and in FP32 mode on short
+runs whose decisions are separated by more than the FP32 evaluation error.
+"""
+import numpy as np
+import pytest
+import torch
+
+import genesis_inputs as gi
+from gpu_helpers import make_obs
+
+pytestmark = pytest.mark.gpu
+M = 9
+
+
+def test_philox_bit_exact(gpu, orc):
+    rng = np.random.default_rng(11)
+    ctr = rng.integers(0, 2 ** 32, (1000, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    for key in [0, 0xDEADBEEFCAFEF00D, 2 ** 64 - 1]:
+        got = gpu.philox(ctr, key)
+        kk = np.array([key & 0xFFFFFFFF, key >> 32], dtype=np.uint32)
+        for i in range(0, 1000, 7):
+            assert np.array_equal(got[i], orc.philox(ctr[i], kk))
+
+
+def test_sobol_bit_exact(gpu, orc):
+    got = gpu.sobol(0, 4097, 10)
+    for n in list(range(0, 300)) + [1023, 1024, 4095, 4096]:
+        for d in range(10):
+            assert got[n, d] == orc.sobol_u32(n, d), (n, d)
+    got = gpu.sobol(123456, 10, 10)
+    for n in range(10):
+        for d in range(10):
+            assert got[n, d] == orc.sobol_u32(123456 + n, d)
+
+
+@pytest.mark.parametrize("npop", [32, 64, 128, 1024])
+@pytest.mark.parametrize("pc,plsb", [(0.9, 0.05), (1.0, 0.5), (0.0, 0.0)])
+def test_breed_bit_exact(gpu, orc, npop, pc, plsb):
+    rng = np.random.default_rng(npop + int(pc * 10))
+    nprob = 6
+    genes = rng.integers(0, 65536, (nprob, npop, M)).astype(np.uint16)
+    fit = rng.random((nprob, npop))
+    fit[0, 3] = np.nan                  # NaN ranks as +inf
+    fit[1, :] = 0.5                     # all tied
+    fit[2, ::2] = fit[2, 1::2]          # pairwise ties
+    fit[3, 5] = np.inf
+    ga = gpu.GaSettings(npop=npop, pc=pc, pmut_lsb=plsb, pmut_ratio=0.7, seed=0x1234_5678_9ABC)
+    cfg = orc.ga_config(npop, 10, pc=pc, pmut_lsb=plsb, pmut_ratio=0.7, seed=0x1234_5678_9ABC)
+    for gen in [1, 2, 77]:
+        child, elite = gpu.ga_breed(genes, fit, 1000, gen, ga)
+        for p in range(nprob):
+            ref, e = orc.ga_breed(genes[p], fit[p], 1000 + p, gen, cfg)
+            assert e == elite[p]
+            assert np.array_equal(child[p], ref), (p, gen)
+
+
+@pytest.mark.parametrize("npop", [32, 128, 256])
+def test_restart_bit_exact(gpu, orc, npop):
+    rng = np.random.default_rng(npop)
+    genes = rng.integers(0, 65536, (4, npop, M)).astype(np.uint16)
+    fit = rng.random((4, npop))
+    fit[1, :10] = fit[1, 10:20]
+    fit[2, 7] = np.nan
+    got = gpu.ga_restart(genes, fit, 4000)
+    for p in range(4):
+        ref, _ = orc.ga_restart(genes[p], fit[p], 4000)
+        assert np.array_equal(got[p], ref)
+
+
+def _ga_compare(gpu, orc, spec, dtype, npix, npop, ngen, margin_min, seed, pid0=0, frac_min=0.9):
+    truth, obs = make_obs(orc, spec, npix, seed)
+    if dtype == "f32":
+        obs = obs.astype(np.float32).astype(np.float64)   # the oracle sees the cube the GPU sees
+    cfg = orc.ga_config(npop, ngen, seed=seed)
+    ref = orc.ga_invert(spec, obs, gi.PRIOR_LO, gi.PRIOR_HI, cfg, pixel_id0=pid0, want_margin=True)
+    pb = gpu.Problem.from_spec(spec, dtype)
+    ob = torch.tensor(obs, device="cuda", dtype=pb.torch_dtype)
+    best, chi2, genes = gpu.ga_invert_batch(pb, ob, gi.PRIOR_LO, gi.PRIOR_HI,
+                                            gpu.GaSettings(npop=npop, ngen=ngen, seed=seed),
+                                            pixel_id0=pid0, want_genes=True)
+    genes = genes.cpu().numpy().view(np.uint16)
+    best = best.cpu().numpy()
+    chi2 = chi2.cpu().numpy()
+    safe = ref["margin"] > margin_min
+    assert safe.mean() >= frac_min, safe.mean()
+    same = (genes == ref["genes"]).all(1)
+    assert same[safe].all(), np.nonzero(safe & ~same)[0][:10]
+    assert np.array_equal(best[safe], ref["best"][safe])
+    assert np.max(np.abs(chi2[safe] - ref["chi2"][safe]) / ref["chi2"][safe]) < 1e-12
+    # every pixel: output inside the bounds and chi2 consistent with best
+    assert np.all(best >= gi.PRIOR_LO) and np.all(best <= gi.PRIOR_HI)
+    return ref, best, chi2, genes
+
+
+def test_ga_fp64_single_line_matches_oracle(gpu, orc):
+    """16x16 px, one line, 64 points, population 64, 100 generations, FP64."""
+    wl = gi.workload("c1")
+    _ga_compare(gpu, orc, wl.spec, "f64", wl.npix, 64, 100, 1e-10, seed=0)
+
+
+def test_ga_fp64_two_line_matches_oracle(gpu, orc):
+    """Two-line setup (128 points, population 128), ragged pixel count."""
+    _ga_compare(gpu, orc, gi.two_line_spec(), "f64", 37, 128, 24, 1e-10, seed=2, pid0=65000)
+
+
+def test_ga_fp32_short_runs_match_oracle(gpu, orc):
+    """FP32 evaluation: decisions separated by > 1e-4 relative are exact."""
+    _ga_compare(gpu, orc, gi.two_line_spec(), "f32", 64, 64, 0, 1e-4, seed=3, frac_min=0.7)
+    _ga_compare(gpu, orc, gi.two_line_spec(), "f32", 64, 64, 2, 1e-4, seed=4, frac_min=0.3)
+
+
+def test_ga_batch_invariance_and_consistency(gpu, orc):
+    """A pixel's result depends only on (obs, pixel id, seed), not on the batch."""
+    spec = gi.two_line_spec()
+    truth, obs = make_obs(orc, spec, 300, seed=5)
+    pb = gpu.Problem.from_spec(spec, "f32")
+    ob = torch.tensor(obs, device="cuda", dtype=torch.float32)
+    ga = gpu.GaSettings(npop=128, ngen=30, seed=9)
+    best, chi2 = gpu.ga_invert_batch(pb, ob, gi.PRIOR_LO, gi.PRIOR_HI, ga, pixel_id0=1000)
+    b2, c2 = gpu.ga_invert_batch(pb, ob[100:133].contiguous(), gi.PRIOR_LO, gi.PRIOR_HI, ga,
+                                 pixel_id0=1100)
+    assert torch.equal(best[100:133], b2) and torch.equal(chi2[100:133], c2)
+    again = gpu.me_chi2(pb, ob, best)
+    assert torch.equal(again, chi2)
+
+
+def test_ga_zero_pixels_and_user_weights(gpu, orc):
+    spec = gi.two_line_spec()
+    pb = gpu.Problem.from_spec(spec, "f32")
+    ob = torch.zeros((0, 4, 128), device="cuda")
+    best, chi2 = gpu.ga_invert_batch(pb, ob, gi.PRIOR_LO, gi.PRIOR_HI, gpu.GaSettings(npop=32, ngen=3))
+    assert best.shape == (0, 9)
+    truth, obs = make_obs(orc, spec, 16, seed=6)
+    sig = 1e-3 * (truth[:, 7] + truth[:, 8])
+    w = np.repeat((1 / sig)[:, None], 4, 1)
+    ob = torch.tensor(obs, device="cuda", dtype=torch.float64)
+    pb = gpu.Problem.from_spec(spec, "f64")
+    best, chi2, genes = gpu.ga_invert_batch(pb, ob, gi.PRIOR_LO, gi.PRIOR_HI,
+                                            gpu.GaSettings(npop=64, ngen=10, seed=1),
+                                            w=torch.tensor(w, device="cuda"), want_genes=True)
+    ref = orc.ga_invert(spec, obs, gi.PRIOR_LO, gi.PRIOR_HI, orc.ga_config(64, 10, seed=1), w=w,
+                        want_margin=True)
+    safe = ref["margin"] > 1e-10
+    assert (genes.cpu().numpy().view(np.uint16)[safe] == ref["genes"][safe]).all()

@@ -1,0 +1,63 @@
+"""GPU Levenberg-Marquardt polish against the oracle's and the truth."""
+import numpy as np
+import pytest
+import torch
+
+import genesis_inputs as gi
+from gpu_helpers import make_obs
+
+pytestmark = pytest.mark.gpu
+
+
+def test_lm_recovers_noiseless_truth(gpu, orc):
+    spec = gi.two_line_spec()
+    truth = gi.draw_truth(64, seed=20)
+    truth[:, 0] = np.maximum(truth[:, 0], 300.0)      # well-determined field
+    truth[:, 5] = np.clip(truth[:, 5], 0.05, 0.45)
+    truth[:, 1] = np.clip(truth[:, 1], 15.0, 165.0)
+    _, obs = make_obs(orc, spec, 64, 20, noise=False, truth=truth)
+    start = truth * (1 + 0.003 * np.random.default_rng(1).standard_normal(truth.shape))
+    start = np.clip(start, gi.PRIOR_LO, gi.PRIOR_HI)
+    w = np.full((64, 4), 1e3)
+    for dtype, tol in [("f32", 2e-3), ("f64", 1e-7)]:
+        pb = gpu.Problem.from_spec(spec, dtype)
+        ob = torch.tensor(obs, device="cuda", dtype=pb.torch_dtype)
+        p, c2 = gpu.lm_polish(pb, ob, torch.tensor(start, device="cuda"), gi.PRIOR_LO, gi.PRIOR_HI,
+                              iters=30, w=torch.tensor(w, device="cuda"))
+        p = p.cpu().numpy()
+        err = np.abs(p - truth) / (gi.PRIOR_HI - gi.PRIOR_LO)
+        assert np.median(err) < tol * 0.1 and np.quantile(err, 0.9) < tol, (dtype, np.quantile(err, 0.9))
+
+
+def test_lm_matches_oracle_polish(gpu, orc):
+    """From the same starting vectors the GPU and the oracle reach the same chi2."""
+    spec = gi.two_line_spec()
+    truth, obs = make_obs(orc, spec, 48, seed=21)
+    start = np.clip(truth * (1 + 0.02 * np.random.default_rng(2).standard_normal(truth.shape)),
+                    gi.PRIOR_LO, gi.PRIOR_HI)
+    p_ref, c_ref = orc.lm_polish(spec, obs, start, gi.PRIOR_LO, gi.PRIOR_HI, iters=10)
+    pb = gpu.Problem.from_spec(spec, "f64")
+    p, c2 = gpu.lm_polish(pb, torch.tensor(obs, device="cuda"), torch.tensor(start, device="cuda"),
+                          gi.PRIOR_LO, gi.PRIOR_HI, iters=10)
+    c2 = c2.cpu().numpy()
+    # both descend from the same start; they land within 1% of each other
+    assert np.median(np.abs(c2 - c_ref) / c_ref) < 1e-3
+    assert np.quantile(np.abs(c2 - c_ref) / c_ref, 0.9) < 1e-2
+    c0 = np.array([orc.chi2(obs[i], orc.synth(spec, start[i])[0], orc.weights_invmax(obs[i]))
+                   for i in range(48)])
+    assert np.all(c2 <= c0 * (1 + 1e-12))
+
+
+def test_lm_fp32_never_worse_and_in_bounds(gpu, orc):
+    spec = gi.two_line_spec()
+    truth, obs = make_obs(orc, spec, 128, seed=22)
+    start = gi.draw_params_uniform(128, seed=23)
+    pb = gpu.Problem.from_spec(spec, "f32")
+    ob = torch.tensor(obs, device="cuda", dtype=torch.float32)
+    st = torch.tensor(start, device="cuda")
+    c0 = gpu.me_chi2(pb, ob, st)
+    p, c2 = gpu.lm_polish(pb, ob, st, gi.PRIOR_LO, gi.PRIOR_HI, iters=10)
+    assert torch.all(c2 <= c0 * (1 + 1e-5))
+    pn = p.cpu().numpy()
+    assert np.all(pn >= gi.PRIOR_LO) and np.all(pn <= gi.PRIOR_HI)
+    assert np.all((pn[:, 2] >= 0) & (pn[:, 2] < 180.0 + 1e-12))
