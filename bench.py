@@ -120,9 +120,12 @@ def make_map(api, torch, pb, side, rank, device):
 
 
 def flop_model(nlines):
-    """Algorithmic FP32 flops (FMA = 2) of one synthesis + chi2, per unit:
-    Weideman evaluation, continued-fraction evaluation, per wavelength point."""
-    return {"weideman": 142.0, "cf": 49.0, "point": 24.0 * nlines + 84.0}
+    """Algorithmic FP32 flops (FMA = 2, reciprocal = 1) of one synthesis + chi2,
+    counted from the source of faddeeva() and me_point(), per unit: interior
+    (Weideman N = 16) evaluation, exterior (continued fraction) evaluation, and
+    per wavelength point (24 per line for the profile sums, 64 for K and its
+    closed-form inverse, 24 for the Kahan chi2 of four Stokes residuals)."""
+    return {"weideman": 135.0, "cf": 41.0, "point": 24.0 * nlines + 88.0}
 
 
 def run_ours(args):

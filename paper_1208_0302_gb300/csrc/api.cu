@@ -46,28 +46,6 @@ std::vector<double> weideman_coefficients(int N, double L)
     return a;
 }
 
-// k-th convergent of the Laplace continued fraction of w(z):
-// t_{k+1} = z, t_m = z - (m/2) / t_{m+1}, w = (i/sqrt(pi)) / t_1.
-// With t_m = A_m / B_m: A_m = z A_{m+1} - (m/2) B_{m+1}, B_m = A_{m+1}, so
-// w = (i/sqrt(pi)) B_1 / A_1.  For odd k, A_1 is even and B_1 odd in z:
-// A_1 = a(u), B_1 = z b(u) with u = z^2.  Returns a (ascending in u) and b.
-void cf_coefficients(int k, std::vector<double> &a, std::vector<double> &b)
-{
-    std::vector<double> A = {0.0, 1.0};  // z
-    std::vector<double> B = {1.0};       // 1
-    for (int m = k; m >= 1; --m) {
-        std::vector<double> An(A.size() + 1, 0.0);
-        for (size_t i = 0; i < A.size(); ++i) An[i + 1] += A[i];
-        for (size_t i = 0; i < B.size(); ++i) An[i] -= 0.5 * m * B[i];
-        B = A;
-        A = An;
-    }
-    a.clear();
-    b.clear();
-    for (size_t i = 0; i < A.size(); i += 2) a.push_back(A[i]);
-    for (size_t i = 1; i < B.size(); i += 2) b.push_back(B[i]);
-}
-
 // Sobol direction numbers (Section 4.6; Sobol 1967, Bratley & Fox 1988):
 // dimension 0 is van der Corput; dimension d >= 1 takes the d-th primitive
 // polynomial over GF(2) (ordered by degree, then by integer encoding) and
@@ -115,20 +93,12 @@ HostTables build_tables()
         const std::vector<double> a = weideman_coefficients(16, L);
         for (int n = 0; n <= 16; ++n) t.fad.w32[n] = (float)a[n];
         t.fad.L32 = (float)L;
-        std::vector<double> ca, cb;
-        cf_coefficients(3, ca, cb);
-        for (int i = 0; i < 3; ++i) t.fad.cfa32[i] = (float)ca[i];
-        for (int i = 0; i < 2; ++i) t.fad.cfb32[i] = (float)cb[i];
     }
     {
         const double L = 5.0;
         const std::vector<double> a = weideman_coefficients(36, L);
         for (int n = 0; n <= 36; ++n) t.fad.w64[n] = a[n];
         t.fad.L64 = L;
-        std::vector<double> ca, cb;
-        cf_coefficients(9, ca, cb);
-        for (int i = 0; i < 6; ++i) t.fad.cfa64[i] = ca[i];
-        for (int i = 0; i < 5; ++i) t.fad.cfb64[i] = cb[i];
     }
     sobol_directions(t.sobol);
     return t;

@@ -36,6 +36,18 @@ template <class R> __device__ __forceinline__ void kahan_sq(R &s, R &c, R r)
     s = t;
 }
 
+// Four consecutive R values of a 16-byte aligned shared-memory row.
+__device__ __forceinline__ void load4(const float *p, float v[4])
+{
+    const float4 q = *(const float4 *)p;
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void load4(const double *p, double v[4])
+{
+    const double2 a = *(const double2 *)p, b = *(const double2 *)(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
 template <class R> struct GaDecode;
 template <> struct GaDecode<float> {
     // FP32 GA: p = lo + g (hi - lo) / 65535, scale precomputed on the host
@@ -54,6 +66,8 @@ template <> struct GaDecode<double> {
 };
 
 // Eq. chisq for one individual, FP32 (or FP64) synthesis over the whole grid.
+// s_obs rows are (I, Q, U, V) of one wavelength; s_doff rows hold
+// lambda_j - lambda0_l for l = 0..3: one vector load each per wavelength.
 template <class R, int NL, bool COUNT>
 __device__ __forceinline__ R fitness(const KProblem &pb, int nlines, int nl, const R *p, R mu,
                                      const R *s_obs, const R *s_doff, const R *he,
@@ -62,16 +76,15 @@ __device__ __forceinline__ R fitness(const KProblem &pb, int nlines, int nl, con
     const Geo<R> geo = make_geo<R, NL>(pb, nlines, p, mu);
     R sI = 0, sQ = 0, sU = 0, sV = 0, cI = 0, cQ = 0, cU = 0, cV = 0;
     for (int j = 0; j < nl; ++j) {
-        R doff[ME_MAX_LINES];
-#pragma unroll
-        for (int l = 0; l < (NL > 0 ? NL : ME_MAX_LINES); ++l)
-            doff[l] = (l < (NL > 0 ? NL : nlines)) ? s_doff[l * nl + j] : R(0);
+        R doff[4], ob[4];
+        load4(s_doff + 4 * j, doff);
+        load4(s_obs + 4 * j, ob);
         const Stokes4<R> s = me_point<R, NL>(geo, doff, he, nlines);
         if (COUNT) ninterior += count_interior<R, NL>(geo, doff, nlines);
-        kahan_sq(sI, cI, s_obs[j] - s.I);
-        kahan_sq(sQ, cQ, s_obs[nl + j] - s.Q);
-        kahan_sq(sU, cU, s_obs[2 * nl + j] - s.U);
-        kahan_sq(sV, cV, s_obs[3 * nl + j] - s.V);
+        kahan_sq(sI, cI, ob[0] - s.I);
+        kahan_sq(sQ, cQ, ob[1] - s.Q);
+        kahan_sq(sU, cU, ob[2] - s.U);
+        kahan_sq(sV, cV, ob[3] - s.V);
     }
     return (s_w2[0] * sI + s_w2[1] * sQ + s_w2[2] * sU + s_w2[3] * sV) * inv_nu;
 }
@@ -120,7 +133,7 @@ template <class R> __device__ __forceinline__ int stable_rank(const R *s_fit, in
 template <class R>
 __device__ __forceinline__ void breed_one(const KGa &ga, uint64_t pid, int t, int k, int npop,
                                           const R *s_fit, const uint16_t *s_cur, int elite,
-                                          uint16_t g[ME_NPAR])
+                                          uint16_t *s_row, uint16_t g[ME_NPAR])
 {
     const U4 u = ga_random(ga.seed, pid, t, (uint32_t)k, kPurposeSelect);
     const int i = (int)(((uint64_t)u.x * (uint64_t)npop) >> 32);
@@ -147,19 +160,27 @@ __device__ __forceinline__ void breed_one(const KGa &ga, uint64_t pid, int t, in
         }
     }
 
+    // Mutation word by word through this slot's shared-memory row (a rolled
+    // loop keeps the code small): bits 16d..16d+15 use Philox calls 4d..4d+3.
 #pragma unroll
-    for (int grp = 0; grp < (16 * ME_NPAR + 3) / 4; ++grp) {
-        const U4 um = ga_random(ga.seed, pid, t, (uint32_t)k, kPurposeMutate + (uint32_t)grp);
-        const uint32_t uu[4] = {um.x, um.y, um.z, um.w};
+    for (int d = 0; d < ME_NPAR; ++d) s_row[d] = g[d];
+#pragma unroll 1
+    for (int d = 0; d < ME_NPAR; ++d) {
+        uint32_t word = s_row[d];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int bit = 4 * grp + e;
-            if (bit < 16 * ME_NPAR) {
-                const int b = bit & 15;
-                if ((uint64_t)uu[e] < ga.t_mut[b]) g[bit >> 4] ^= (uint16_t)(1u << (15 - b));
+        for (int q = 0; q < 4; ++q) {
+            const U4 um = ga_random(ga.seed, pid, t, (uint32_t)k, kPurposeMutate + (uint32_t)(4 * d + q));
+            const uint32_t uu[4] = {um.x, um.y, um.z, um.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int b = 4 * q + e;  // bit within the word, 0 = MSB
+                if ((uint64_t)uu[e] < ga.t_mut[b]) word ^= 1u << (15 - b);
             }
         }
+        s_row[d] = (uint16_t)word;
     }
+#pragma unroll
+    for (int d = 0; d < ME_NPAR; ++d) g[d] = s_row[d];
     if (k == 0) {
 #pragma unroll
         for (int d = 0; d < ME_NPAR; ++d) g[d] = s_cur[elite * ME_NPAR + d];
@@ -183,7 +204,7 @@ __host__ __device__ __forceinline__ GaSmem ga_smem_layout(int nl, int nlines, in
         return at;
     };
     L.obs = take(4 * nl * (int)sizeof(R), 16);
-    L.doff = take(nlines * nl * (int)sizeof(R), 16);
+    L.doff = take(4 * nl * (int)sizeof(R), 16);
     L.fit = take(npop * (int)sizeof(R), 16);
     L.wmin = take(32 * (int)sizeof(R), 16);
     L.widx = take(32 * 4, 16);
@@ -201,10 +222,10 @@ __device__ __forceinline__ void weights_invmax_w2(const R *s_obs, int nl, R *s_w
     const int lane = threadIdx.x & 31;
     R imax = -R(INFINITY), imin = R(INFINITY), mq = 0, mu = 0, mv = 0;
     for (int j = lane; j < nl; j += 32) {
-        const R I = s_obs[j];
+        const R I = s_obs[4 * j];
         imax = I > imax ? I : imax;
         imin = I < imin ? I : imin;
-        const R aq = fabs(s_obs[nl + j]), au = fabs(s_obs[2 * nl + j]), av = fabs(s_obs[3 * nl + j]);
+        const R aq = fabs(s_obs[4 * j + 1]), au = fabs(s_obs[4 * j + 2]), av = fabs(s_obs[4 * j + 3]);
         mq = aq > mq ? aq : mq;
         mu = au > mu ? au : mu;
         mv = av > mv ? av : mv;
@@ -229,8 +250,16 @@ __device__ __forceinline__ void weights_invmax_w2(const R *s_obs, int nl, R *s_w
     }
 }
 
+// Register budget of the FP32 npop <= 256 instantiations: MAXT * GENESIS_GA_MINB
+// threads must fit an SM's 64K registers, which caps registers per thread
+// (more resident warps hide the FP32 pipe latency).  FP64 instantiations are
+// bound by the FP64 units and keep the compiler's register choice.
+#ifndef GENESIS_GA_MINB
+#define GENESIS_GA_MINB 3
+#endif
+
 template <class R, int NL, int MAXT, bool COUNT>
-__global__ void __launch_bounds__(MAXT)
+__global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(R) == 4) ? GENESIS_GA_MINB : 1)
 k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
             const R *__restrict__ obs, const double *__restrict__ w_user,
             const double *__restrict__ mu_px, int npix, double *__restrict__ best,
@@ -261,21 +290,37 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
     }
     const R inv_nu = R(1) / R(4 * nl - ME_NPAR);
     if (k < 4) s_he[k] = k < nlines ? R(pb.line[k].half_eta) : R(0);
-    for (int i = k; i < nlines * nl; i += blockDim.x) {
-        const int l = i / nl, j = i - l * nl;
-        s_doff[i] = R(pb.lam[j] - pb.line[l].lam0);  // exact difference, then rounded
+    for (int i = k; i < 4 * nl; i += blockDim.x) {
+        const int j = i >> 2, l = i & 3;
+        // exact difference in FP64, then rounded
+        s_doff[i] = l < nlines ? R(pb.lam[j] - pb.line[l].lam0) : R(0);
     }
 
     for (int pix = blockIdx.x; pix < npix; pix += gridDim.x) {
-        // a1: stage the pixel's Stokes profiles (16-byte vector loads when aligned)
+        // a1: stage the pixel's Stokes profiles, [4][nl] in HBM -> [nl][4] rows in
+        // shared memory (16-byte vector loads when a vector stays in one row)
         const R *o = obs + (size_t)pix * 4 * nl;
-        const int nbytes = 4 * nl * (int)sizeof(R);
-        if ((nbytes & 15) == 0 && (((uintptr_t)o) & 15) == 0) {
-            const float4 *o4 = (const float4 *)o;
-            float4 *d4 = (float4 *)s_obs;
-            for (int i = k; i < nbytes / 16; i += blockDim.x) d4[i] = __ldg(o4 + i);
+        constexpr int VW = 16 / (int)sizeof(R);  // elements per 16-byte vector
+        if (nl % VW == 0 && (((uintptr_t)o) & 15) == 0) {
+            for (int i = k; i < 4 * nl / VW; i += blockDim.x) {
+                const int e = i * VW, st = e / nl, j = e - st * nl;
+                if (VW == 4) {
+                    const float4 q = __ldg((const float4 *)o + i);
+                    s_obs[4 * j + st] = R(q.x);
+                    s_obs[4 * (j + 1) + st] = R(q.y);
+                    s_obs[4 * (j + 2) + st] = R(q.z);
+                    s_obs[4 * (j + 3) + st] = R(q.w);
+                } else {
+                    const double2 q = __ldg((const double2 *)o + i);
+                    s_obs[4 * j + st] = R(q.x);
+                    s_obs[4 * (j + 1) + st] = R(q.y);
+                }
+            }
         } else {
-            for (int i = k; i < 4 * nl; i += blockDim.x) s_obs[i] = o[i];
+            for (int i = k; i < 4 * nl; i += blockDim.x) {
+                const int st = i / nl, j = i - st * nl;
+                s_obs[4 * j + st] = o[i];
+            }
         }
         __syncthreads();
         // a2: weights
@@ -314,7 +359,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
             const int elite = block_argmin<R>(s_fit, s_wmin, s_widx);  // a9
             const uint16_t *s_cur = s_genes + cur * npop * ME_NPAR;
             uint16_t *s_nxt = s_genes + (cur ^ 1) * npop * ME_NPAR;
-            breed_one<R>(ga, pid, t, k, npop, s_fit, s_cur, elite, g);  // a10-a12
+            breed_one<R>(ga, pid, t, k, npop, s_fit, s_cur, elite, s_nxt + k * ME_NPAR, g);  // a10-a12
             __syncthreads();  // every tournament has read s_fit
 #pragma unroll
             for (int d = 0; d < ME_NPAR; ++d) {
@@ -372,6 +417,7 @@ __global__ void k_ga_breed(const __grid_constant__ KGa ga, const uint16_t *__res
     double *s_wmin = s_fit + npop;
     int *s_widx = (int *)(s_wmin + 32);
     uint16_t *s_cur = (uint16_t *)(s_widx + 32);
+    uint16_t *s_new = s_cur + npop * ME_NPAR;
     const size_t base = (size_t)prob * npop;
     s_fit[k] = clean_fit(fit[base + k]);
 #pragma unroll
@@ -379,7 +425,8 @@ __global__ void k_ga_breed(const __grid_constant__ KGa ga, const uint16_t *__res
     __syncthreads();
     const int elite = block_argmin<double>(s_fit, s_wmin, s_widx);
     uint16_t g[ME_NPAR];
-    breed_one<double>(ga, ga.pixel_id0 + (uint64_t)prob, gen, k, npop, s_fit, s_cur, elite, g);
+    breed_one<double>(ga, ga.pixel_id0 + (uint64_t)prob, gen, k, npop, s_fit, s_cur, elite,
+                      s_new + k * ME_NPAR, g);
 #pragma unroll
     for (int d = 0; d < ME_NPAR; ++d) child[(base + k) * ME_NPAR + d] = g[d];
     if (k == 0 && elite_out) elite_out[prob] = elite;
@@ -476,7 +523,7 @@ cudaError_t launch_ga_breed(const KGa &ga, const uint16_t *genes, const double *
                             int gen, uint16_t *child, int *elite, cudaStream_t st)
 {
     if (nprob <= 0) return cudaSuccess;
-    const int smem = ga.npop * 8 + 32 * 8 + 32 * 4 + ga.npop * ME_NPAR * 2;
+    const int smem = ga.npop * 8 + 32 * 8 + 32 * 4 + 2 * ga.npop * ME_NPAR * 2;
     k_ga_breed<<<nprob, ga.npop, smem, st>>>(ga, genes, fit, gen, child, elite);
     return cudaGetLastError();
 }

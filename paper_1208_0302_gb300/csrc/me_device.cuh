@@ -36,16 +36,36 @@ struct KProblem {
     double lam[ME_MAX_LAMBDA];  // wavelength grid [A]
 };
 
-// Faddeeva coefficient tables (filled per device at library initialisation).
+// Weideman coefficient tables (filled per device at library initialisation).
 struct FaddeevaTables {
     float w32[17];     // Weideman a_1..a_16 (index n = 1..16), N = 16
     float L32;
-    float cfa32[3];    // continued fraction k = 3: denominator a(u) coefficients (u^0..u^2)
-    float cfb32[2];    // numerator b(u) (u^0..u^1), w = i/sqrt(pi) z b(u) / a(u)
     double w64[37];    // Weideman N = 36
     double L64;
-    double cfa64[6];   // k = 9: a(u) degree 5
-    double cfb64[5];   // b(u) degree 4
+};
+
+// k-th convergent of the Laplace continued fraction of w(z), computed at
+// compile time: t_{k+1} = z, t_m = z - (m/2)/t_m+1, w = (i/sqrt(pi))/t_1.
+// With t_m = A_m/B_m: A_m = z A_{m+1} - (m/2) B_{m+1}, B_m = A_{m+1}.  For odd
+// k, A_1 = a(u) is even and B_1 = z b(u) odd in z (u = z^2), both monic:
+// a has degree (k+1)/2, b degree (k-1)/2; coefficients ascend in u.
+template <int K> struct CfPoly {
+    double a[(K + 1) / 2 + 1];
+    double b[(K - 1) / 2 + 1];
+    constexpr CfPoly() : a(), b()
+    {
+        double A[K + 3] = {}, B[K + 3] = {}, An[K + 3] = {};
+        A[1] = 1.0;  // z
+        B[0] = 1.0;  // 1
+        for (int m = K; m >= 1; --m) {
+            for (int i = 0; i < K + 3; ++i) An[i] = 0.0;
+            for (int i = 0; i + 1 < K + 3; ++i) An[i + 1] += A[i];
+            for (int i = 0; i < K + 3; ++i) An[i] -= 0.5 * m * B[i];
+            for (int i = 0; i < K + 3; ++i) { B[i] = A[i]; A[i] = An[i]; }
+        }
+        for (int i = 0; i <= (K + 1) / 2; ++i) a[i] = A[2 * i];
+        for (int i = 0; i <= (K - 1) / 2; ++i) b[i] = B[2 * i + 1];
+    }
 };
 
 // Each translation unit holds its own copy; genesis::upload_tables() fills all.
@@ -53,15 +73,16 @@ static __constant__ FaddeevaTables c_fad;
 
 template <class R> struct FadCfg;
 template <> struct FadCfg<float> {
-    static constexpr int N = 16;
-    static constexpr int NA = 3, NB = 2;
+    static constexpr int N = 16;        // Weideman terms
+    static constexpr int K = 3;         // continued-fraction depth
     static constexpr float R2 = 36.0f;  // |z|^2 above which the continued fraction is used
 };
 template <> struct FadCfg<double> {
     static constexpr int N = 36;
-    static constexpr int NA = 6, NB = 5;
+    static constexpr int K = 9;
     static constexpr double R2 = 64.0;
 };
+
 
 template <class R> struct C2 { R x, y; };
 
@@ -80,12 +101,6 @@ template <> __device__ __forceinline__ double weid<double>(int n) { return c_fad
 template <class R> __device__ __forceinline__ R weidL();
 template <> __device__ __forceinline__ float weidL<float>() { return c_fad.L32; }
 template <> __device__ __forceinline__ double weidL<double>() { return c_fad.L64; }
-template <class R> __device__ __forceinline__ R cfa(int n);
-template <> __device__ __forceinline__ float cfa<float>(int n) { return c_fad.cfa32[n]; }
-template <> __device__ __forceinline__ double cfa<double>(int n) { return c_fad.cfa64[n]; }
-template <class R> __device__ __forceinline__ R cfb(int n);
-template <> __device__ __forceinline__ float cfb<float>(int n) { return c_fad.cfb32[n]; }
-template <> __device__ __forceinline__ double cfb<double>(int n) { return c_fad.cfb64[n]; }
 
 // w(z) = exp(-z^2) erfc(-i z) for z = x + i y, y >= 0.
 //
@@ -99,67 +114,133 @@ template <> __device__ __forceinline__ double cfb<double>(int n) { return c_fad.
 // written as a ratio of polynomials in u = z^2.  Both branches need one
 // reciprocal.  Absolute error: FP32 ~1e-7 (N = 16, k = 3, R = 6), FP64 ~2e-15
 // (N = 36, k = 9, R = 8).
+// Exterior branch: k-th convergent of the Laplace continued fraction,
+// w = (i/sqrt(pi)) z b(u) / a(u) with u = z^2 and monic a, b.  a2 = y^2.
+template <class R>
+__device__ __forceinline__ C2<R> faddeeva_exterior(R x, R y, R a2)
+{
+    constexpr int NA = (FadCfg<R>::K + 1) / 2, NB = (FadCfg<R>::K - 1) / 2;
+    constexpr CfPoly<FadCfg<R>::K> P{};
+    const R ux = x * x - a2, uy = R(2) * x * y;
+    // monic Horner: start from u + c_{n-1}
+    R ax = ux + R(P.a[NA - 1]), ay = uy;
+#pragma unroll
+    for (int n = NA - 2; n >= 0; --n) {
+        const R tx = ax * ux - ay * uy + R(P.a[n]);
+        ay = ax * uy + ay * ux;
+        ax = tx;
+    }
+    R bx = R(1), by = R(0);
+    if (NB >= 1) {
+        bx = ux + R(P.b[NB - 1]);
+        by = uy;
+    }
+#pragma unroll
+    for (int n = NB - 2; n >= 0; --n) {
+        const R tx = bx * ux - by * uy + R(P.b[n]);
+        by = bx * uy + by * ux;
+        bx = tx;
+    }
+    // num = z b(u); w = (i/sqrt(pi)) num / a(u)
+    const R nx = x * bx - y * by, ny = x * by + y * bx;
+    const R inv = fast_rcp(ax * ax + ay * ay) * R(0.56418958354775628695);  // 1/sqrt(pi)
+    C2<R> w;
+    w.x = (nx * ay - ny * ax) * inv;
+    w.y = (nx * ax + ny * ay) * inv;
+    return w;
+}
+
+// Interior branch: Weideman's rational series.
+template <class R>
+__device__ __forceinline__ C2<R> faddeeva_interior(R x, R y)
+{
+    const R L = weidL<R>();
+    // d = L - i z = (L + y) - i x;  r = 1/d
+    const R dx = L + y, dy = -x;
+    const R inv = fast_rcp(dx * dx + dy * dy);
+    const R rx = dx * inv, ry = -dy * inv;
+    // Z = (L + i z) r = ((L - y) + i x) r
+    const R mx = L - y, my = x;
+    const R Zx = mx * rx - my * ry, Zy = mx * ry + my * rx;
+    R px = weid<R>(FadCfg<R>::N), py = R(0);
+#pragma unroll
+    for (int n = FadCfg<R>::N - 1; n >= 1; --n) {
+        const R tx = px * Zx - py * Zy + weid<R>(n);
+        py = px * Zy + py * Zx;
+        px = tx;
+    }
+    const R r2x = rx * rx - ry * ry, r2y = R(2) * rx * ry;
+    const R s = R(0.56418958354775628695);
+    C2<R> w;
+    w.x = R(2) * (px * r2x - py * r2y) + rx * s;
+    w.y = R(2) * (px * r2y + py * r2x) + ry * s;
+    return w;
+}
+
+// w(z) = exp(-z^2) erfc(-i z) for z = x + i y, y >= 0.
+//
+// Interior |z| <= R: Weideman's (1994) rational series
+//     w(z) = 2 p(Z) / (L - i z)^2 + (1/sqrt(pi)) / (L - i z),
+//     Z = (L + i z) / (L - i z),  p(Z) = sum_{n=1}^{N} a_n Z^{n-1},
+// with a_n the Fourier coefficients of (L^2 + t^2) exp(-t^2) under
+// t = L tan(theta/2) (computed on the host from that integral).
+// Exterior |z| > R: the k-th convergent of the Laplace continued fraction
+//     w(z) = (i/sqrt(pi)) / (z - (1/2)/(z - 1/(z - (3/2)/(z - ...)))),
+// written as a ratio of polynomials in u = z^2.  Both branches need one
+// reciprocal.  Absolute error: FP32 ~1e-7 (N = 16, k = 3, R = 6), FP64 ~2e-15
+// (N = 36, k = 9, R = 8).  r2 = x^2 + y^2 is passed in so that every caller
+// takes the same branch decision.
+template <class R>
+__device__ __forceinline__ C2<R> faddeeva_r2(R x, R y, R a2, R r2)
+{
+    if (r2 > FadCfg<R>::R2) return faddeeva_exterior<R>(x, y, a2);
+    return faddeeva_interior<R>(x, y);
+}
+
 template <class R>
 __device__ __forceinline__ C2<R> faddeeva(R x, R y)
 {
-    const R r2 = x * x + y * y;
-    C2<R> w;
-    if (r2 > FadCfg<R>::R2) {
-        const R ux = x * x - y * y, uy = R(2) * x * y;
-        R ax = cfa<R>(FadCfg<R>::NA - 1), ay = R(0);
-#pragma unroll
-        for (int n = FadCfg<R>::NA - 2; n >= 0; --n) {
-            const R tx = ax * ux - ay * uy + cfa<R>(n);
-            ay = ax * uy + ay * ux;
-            ax = tx;
-        }
-        R bx = cfb<R>(FadCfg<R>::NB - 1), by = R(0);
-#pragma unroll
-        for (int n = FadCfg<R>::NB - 2; n >= 0; --n) {
-            const R tx = bx * ux - by * uy + cfb<R>(n);
-            by = bx * uy + by * ux;
-            bx = tx;
-        }
-        // num = z b(u); w = (i/sqrt(pi)) num / a(u)
-        const R nx = x * bx - y * by, ny = x * by + y * bx;
-        const R inv = fast_rcp(ax * ax + ay * ay);
-        const R qx = (nx * ax + ny * ay) * inv, qy = (ny * ax - nx * ay) * inv;
-        const R s = R(0.56418958354775628695);  // 1/sqrt(pi)
-        w.x = -qy * s;
-        w.y = qx * s;
+    const R a2 = y * y;
+    return faddeeva_r2<R>(x, y, a2, x * x + a2);
+}
+
+// The three Zeeman components of one line at one wavelength: sigma_b at
+// v + v_B, pi at v, sigma_r at v - v_B (each x = doff/D + offset, one FMA).
+// When |v| - |v_B| = m > 0 the smallest |x| is m, so m^2 + a^2 > R^2 puts all
+// three outside |z| = R; they are then evaluated without branches and their
+// continued fractions overlap.  Otherwise each component picks its branch.
+template <class R>
+__device__ __forceinline__ bool triplet_exterior(R v, R vB, R a2)
+{
+    const R m = fabs(v) - fabs(vB);
+    return m > R(0) && m * m + a2 > FadCfg<R>::R2;
+}
+
+template <class R>
+__device__ __forceinline__ void faddeeva_triplet(R xb, R v, R xr, R vB, R a, R a2, C2<R> &wb,
+                                                 C2<R> &wp, C2<R> &wr)
+{
+    if (triplet_exterior<R>(v, vB, a2)) {
+        wb = faddeeva_exterior<R>(xb, a, a2);
+        wp = faddeeva_exterior<R>(v, a, a2);
+        wr = faddeeva_exterior<R>(xr, a, a2);
     } else {
-        const R L = weidL<R>();
-        // d = L - i z = (L + y) - i x;  r = 1/d
-        const R dx = L + y, dy = -x;
-        const R inv = fast_rcp(dx * dx + dy * dy);
-        const R rx = dx * inv, ry = -dy * inv;
-        // Z = (L + i z) r = ((L - y) + i x) r
-        const R mx = L - y, my = x;
-        const R Zx = mx * rx - my * ry, Zy = mx * ry + my * rx;
-        R px = weid<R>(FadCfg<R>::N), py = R(0);
-#pragma unroll
-        for (int n = FadCfg<R>::N - 1; n >= 1; --n) {
-            const R tx = px * Zx - py * Zy + weid<R>(n);
-            py = px * Zy + py * Zx;
-            px = tx;
-        }
-        const R r2x = rx * rx - ry * ry, r2y = R(2) * rx * ry;
-        const R s = R(0.56418958354775628695);
-        w.x = R(2) * (px * r2x - py * r2y) + rx * s;
-        w.y = R(2) * (px * r2y + py * r2x) + ry * s;
+        wb = faddeeva_r2<R>(xb, a, a2, xb * xb + a2);
+        wp = faddeeva_r2<R>(v, a, a2, v * v + a2);
+        wr = faddeeva_r2<R>(xr, a, a2, xr * xr + a2);
     }
-    return w;
 }
 
 // ------------------------------------------------------ per-model geometry
 template <class R> struct Geo {
-    R a;                // damping
+    R a, a2;            // damping, damping^2
     R kIp, kIs;         // eta0 sin^2 t, eta0 (1 + cos^2 t)/2
     R kQ, kU, kV;       // eta0 sin^2 t cos 2chi, eta0 sin^2 t sin 2chi, eta0 cos t
     R S0, muS1;
     R shift[ME_MAX_LINES];  // lambda0 v_LOS / c [A]
     R invD[ME_MAX_LINES];   // 1 / Doppler width [1/A]
     R vB[ME_MAX_LINES];     // Zeeman splitting in Doppler units
+    R cp[ME_MAX_LINES];     // -shift / D: x_pi = doff / D + cp
 };
 
 __device__ __forceinline__ void sincos_deg(float d, float *s, float *c)
@@ -182,6 +263,7 @@ __device__ __forceinline__ Geo<R> make_geo(const KProblem &pb, int nlines, const
     const R eta0 = p[6];
     const R s2 = st * st;
     g.a = p[5];
+    g.a2 = g.a * g.a;
     g.kIp = eta0 * s2;
     g.kIs = eta0 * R(0.5) * (R(1) + ct * ct);
     g.kQ = eta0 * s2 * c2c;
@@ -197,6 +279,7 @@ __device__ __forceinline__ Geo<R> make_geo(const KProblem &pb, int nlines, const
             g.shift[l] = R(ln.lam0_c) * p[3];
             g.invD[l] = R(1) / (p[4] * R(ln.dscale));
             g.vB[l] = R(ln.zfac) * p[0] * g.invD[l];
+            g.cp[l] = -g.shift[l] * g.invD[l];
         }
     }
     return g;
@@ -215,10 +298,11 @@ __device__ __forceinline__ Stokes4<R> me_point(const Geo<R> &g, const R *doff, c
 #pragma unroll
     for (int l = 0; l < (NL > 0 ? NL : ME_MAX_LINES); ++l) {
         if (l < nl) {
-            const R v = (doff[l] - g.shift[l]) * g.invD[l];
-            const C2<R> wb = faddeeva<R>(v + g.vB[l], g.a);
-            const C2<R> wp = faddeeva<R>(v, g.a);
-            const C2<R> wr = faddeeva<R>(v - g.vB[l], g.a);
+            const R v = doff[l] * g.invD[l] + g.cp[l];
+            const R xb = doff[l] * g.invD[l] + (g.cp[l] + g.vB[l]);
+            const R xr = doff[l] * g.invD[l] + (g.cp[l] - g.vB[l]);
+            C2<R> wb, wp, wr;
+            faddeeva_triplet<R>(xb, v, xr, g.vB[l], g.a, g.a2, wb, wp, wr);
             const R q = half_eta[l];
             const R sx = wb.x + wr.x, sy = wb.y + wr.y;
             P += q * wp.x;
@@ -256,11 +340,15 @@ __device__ __forceinline__ unsigned count_interior(const Geo<R> &g, const R *dof
 #pragma unroll
     for (int l = 0; l < (NL > 0 ? NL : ME_MAX_LINES); ++l) {
         if (l < nl) {
-            const R v = (doff[l] - g.shift[l]) * g.invD[l];
-            const R xs[3] = {v + g.vB[l], v, v - g.vB[l]};
-#pragma unroll
-            for (int c3 = 0; c3 < 3; ++c3)
-                c += (xs[c3] * xs[c3] + g.a * g.a > FadCfg<R>::R2) ? 0u : 1u;
+            const R v = doff[l] * g.invD[l] + g.cp[l];
+            const R xb = doff[l] * g.invD[l] + (g.cp[l] + g.vB[l]);
+            const R xr = doff[l] * g.invD[l] + (g.cp[l] - g.vB[l]);
+            const R a2 = g.a2;
+            if (!triplet_exterior<R>(v, g.vB[l], a2)) {
+                c += (xb * xb + a2 > FadCfg<R>::R2) ? 0u : 1u;
+                c += (v * v + a2 > FadCfg<R>::R2) ? 0u : 1u;
+                c += (xr * xr + a2 > FadCfg<R>::R2) ? 0u : 1u;
+            }
         }
     }
     return c;

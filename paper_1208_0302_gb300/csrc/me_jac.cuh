@@ -77,9 +77,10 @@ __device__ __forceinline__ void me_point_jac(const GeoJ<R> &G, const R *doff, co
 #pragma unroll
     for (int l = 0; l < (NL > 0 ? NL : ME_MAX_LINES); ++l) {
         if (l < nl) {
-            const R v = (doff[l] - g.shift[l]) * g.invD[l];
             const R q = half_eta[l];
-            const R xs[3] = {v + g.vB[l], v, v - g.vB[l]};  // blue, pi, red
+            const R xs[3] = {doff[l] * g.invD[l] + (g.cp[l] + g.vB[l]),  // blue
+                             doff[l] * g.invD[l] + g.cp[l],              // pi
+                             doff[l] * g.invD[l] + (g.cp[l] - g.vB[l])}; // red
             C2<R> w[3], wd[3][4];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
