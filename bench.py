@@ -121,11 +121,13 @@ def make_map(api, torch, pb, side, rank, device):
 
 def flop_model(nlines):
     """Algorithmic FP32 flops (FMA = 2, reciprocal = 1) of one synthesis + chi2,
-    counted from the source of faddeeva() and me_point(), per unit: interior
-    (Weideman N = 16) evaluation, exterior (continued fraction) evaluation, and
-    per wavelength point (24 per line for the profile sums, 64 for K and its
-    closed-form inverse, 24 for the Kahan chi2 of four Stokes residuals)."""
-    return {"weideman": 135.0, "cf": 41.0, "point": 24.0 * nlines + 88.0}
+    counted from the source of faddeeva_interior/faddeeva_exterior and
+    me_point, per unit: interior (Weideman N = 16 by real-quadratic synthetic
+    division) evaluation, exterior (3rd continued-fraction convergent)
+    evaluation, and per wavelength point (26 per line for the component
+    arguments and profile sums, 49 for K and its closed-form inverse, 24 for
+    the Kahan chi2 of four residuals).  Branch tests are not counted."""
+    return {"weideman": 94.0, "cf": 32.0, "point": 26.0 * nlines + 73.0}
 
 
 def run_ours(args):

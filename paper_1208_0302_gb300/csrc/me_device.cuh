@@ -102,18 +102,6 @@ template <class R> __device__ __forceinline__ R weidL();
 template <> __device__ __forceinline__ float weidL<float>() { return c_fad.L32; }
 template <> __device__ __forceinline__ double weidL<double>() { return c_fad.L64; }
 
-// w(z) = exp(-z^2) erfc(-i z) for z = x + i y, y >= 0.
-//
-// Interior |z| <= R: Weideman's (1994) rational series
-//     w(z) = 2 p(Z) / (L - i z)^2 + (1/sqrt(pi)) / (L - i z),
-//     Z = (L + i z) / (L - i z),  p(Z) = sum_{n=1}^{N} a_n Z^{n-1},
-// with a_n the Fourier coefficients of (L^2 + t^2) exp(-t^2) under
-// t = L tan(theta/2) (computed on the host from that integral).
-// Exterior |z| > R: the k-th convergent of the Laplace continued fraction
-//     w(z) = (i/sqrt(pi)) / (z - (1/2)/(z - 1/(z - (3/2)/(z - ...)))),
-// written as a ratio of polynomials in u = z^2.  Both branches need one
-// reciprocal.  Absolute error: FP32 ~1e-7 (N = 16, k = 3, R = 6), FP64 ~2e-15
-// (N = 36, k = 9, R = 8).
 // Exterior branch: k-th convergent of the Laplace continued fraction,
 // w = (i/sqrt(pi)) z b(u) / a(u) with u = z^2 and monic a, b.  a2 = y^2.
 template <class R>
@@ -150,10 +138,16 @@ __device__ __forceinline__ C2<R> faddeeva_exterior(R x, R y, R a2)
     return w;
 }
 
-// Interior branch: Weideman's rational series.
+// Interior branch: Weideman's rational series.  The real-coefficient
+// polynomial p(Z) = sum_{n=1}^{N} a_n Z^{n-1} is evaluated at the complex
+// point Z by synthetic division by the real quadratic with roots Z and
+// conj(Z), Z^2 - r Z - s (r = 2 Re Z, s = -|Z|^2): b_{N-1} = a_N,
+// b_{N-2} = a_{N-1} + r b_{N-1}, b_j = a_{j+1} + r b_{j+1} + s b_{j+2}, and
+// p(Z) = b_1 Z + a_1 + s b_2 (two real FMAs per coefficient).
 template <class R>
 __device__ __forceinline__ C2<R> faddeeva_interior(R x, R y)
 {
+    constexpr int N = FadCfg<R>::N;
     const R L = weidL<R>();
     // d = L - i z = (L + y) - i x;  r = 1/d
     const R dx = L + y, dy = -x;
@@ -162,13 +156,16 @@ __device__ __forceinline__ C2<R> faddeeva_interior(R x, R y)
     // Z = (L + i z) r = ((L - y) + i x) r
     const R mx = L - y, my = x;
     const R Zx = mx * rx - my * ry, Zy = mx * ry + my * rx;
-    R px = weid<R>(FadCfg<R>::N), py = R(0);
+    const R r = R(2) * Zx, sq = -(Zx * Zx + Zy * Zy);
+    R b2 = weid<R>(N);
+    R b1 = weid<R>(N - 1) + r * b2;
 #pragma unroll
-    for (int n = FadCfg<R>::N - 1; n >= 1; --n) {
-        const R tx = px * Zx - py * Zy + weid<R>(n);
-        py = px * Zy + py * Zx;
-        px = tx;
+    for (int j = N - 3; j >= 1; --j) {
+        const R b0 = weid<R>(j + 1) + r * b1 + sq * b2;
+        b2 = b1;
+        b1 = b0;
     }
+    const R px = weid<R>(1) + sq * b2 + b1 * Zx, py = b1 * Zy;
     const R r2x = rx * rx - ry * ry, r2y = R(2) * rx * ry;
     const R s = R(0.56418958354775628695);
     C2<R> w;
@@ -236,6 +233,8 @@ template <class R> struct Geo {
     R a, a2;            // damping, damping^2
     R kIp, kIs;         // eta0 sin^2 t, eta0 (1 + cos^2 t)/2
     R kQ, kU, kV;       // eta0 sin^2 t cos 2chi, eta0 sin^2 t sin 2chi, eta0 cos t
+    R kIp2, kV2;        // kIp^2, kV^2
+    R kUV, kQV;         // kU kV, kQ kV
     R S0, muS1;
     R shift[ME_MAX_LINES];  // lambda0 v_LOS / c [A]
     R invD[ME_MAX_LINES];   // 1 / Doppler width [1/A]
@@ -269,6 +268,10 @@ __device__ __forceinline__ Geo<R> make_geo(const KProblem &pb, int nlines, const
     g.kQ = eta0 * s2 * c2c;
     g.kU = eta0 * s2 * s2c;
     g.kV = eta0 * ct;
+    g.kIp2 = g.kIp * g.kIp;
+    g.kV2 = g.kV * g.kV;
+    g.kUV = g.kU * g.kV;
+    g.kQV = g.kQ * g.kV;
     g.S0 = p[7];
     g.muS1 = mu * p[8];
     const int nl = NL > 0 ? NL : nlines;
@@ -313,19 +316,28 @@ __device__ __forceinline__ Stokes4<R> me_point(const Geo<R> &g, const R *doff, c
             Di += q * (wr.y - wb.y);
         }
     }
+    // eta_Q, eta_U share the profile sum T and rho_Q, rho_U share Ti
+    // (eta_Q = kQ T, eta_U = kU T, rho_Q = kQ Ti, rho_U = kU Ti, kQ^2 + kU^2 =
+    // kIp^2), so the closed form of K^-1 e simplifies exactly to
+    //   E2 = eQ^2+eU^2+eV^2 = kIp^2 T^2 + kV^2 Dd^2,  rho2 = kIp^2 Ti^2 + kV^2 Di^2,
+    //   Pi = kIp^2 T Ti + kV^2 Dd Di,  A = eI^2 T + Ti Pi,  C = Dd Ti - T Di,
+    //   Q = -f (kQ A + kU kV eI C),  U = -f (kU A - kQ kV eI C),
+    //   V = -f kV (eI^2 Dd + Di Pi)   (the eI (eU rQ - eQ rU) term vanishes).
     const R eI = R(1) + g.kIp * P + g.kIs * Sg;
-    const R eQ = g.kQ * T, eU = g.kU * T, eV = g.kV * Dd;
-    const R rQ = g.kQ * Ti, rU = g.kU * Ti, rV = g.kV * Di;
+    const R pT = g.kIp2 * T, pTi = g.kIp2 * Ti, vD = g.kV2 * Dd, vDi = g.kV2 * Di;
+    const R E2 = pT * T + vD * Dd;
+    const R rho2 = pTi * Ti + vDi * Di;
+    const R Pi = pT * Ti + vD * Di;
     const R eI2 = eI * eI;
-    const R rho2 = rQ * rQ + rU * rU + rV * rV;
-    const R Pi = eQ * rQ + eU * rU + eV * rV;
-    const R Delta = eI2 * (eI2 - eQ * eQ - eU * eU - eV * eV + rho2) - Pi * Pi;
+    const R Delta = eI2 * (eI2 - E2 + rho2) - Pi * Pi;
     const R f = g.muS1 * fast_rcp(Delta);
+    const R A = eI2 * T + Ti * Pi;
+    const R eIC = eI * (Dd * Ti - T * Di);
     Stokes4<R> s;
     s.I = g.S0 + f * eI * (eI2 + rho2);
-    s.Q = -f * (eI2 * eQ + eI * (eV * rU - eU * rV) + rQ * Pi);
-    s.U = -f * (eI2 * eU + eI * (eQ * rV - eV * rQ) + rU * Pi);
-    s.V = -f * (eI2 * eV + eI * (eU * rQ - eQ * rU) + rV * Pi);
+    s.Q = -f * (g.kQ * A + g.kUV * eIC);
+    s.U = -f * (g.kU * A - g.kQV * eIC);
+    s.V = -f * g.kV * (eI2 * Dd + Di * Pi);
     return s;
 }
 
