@@ -35,6 +35,11 @@ METRIC = "pixels inverted/s at fixed median chi2 vs plain FP64 GA"
 WORKLOAD = "two-line Fe I 6301.5+6302.5 ME inversion, 256x256 px, 128 lambda, npop 128, 200 gen, FP32 GA + 10 L-M"
 NPOP, NGEN, LM_ITERS = 128, 200, 10
 KERNELS_PER_STEP = 4  # GA evolve, FP64 chi2, L-M, FP64 chi2
+# DRAM bytes (read + write) per pixel of one GA launch, from the ncu capture in
+# profiles/k_ga_evolve_two_line_1024px.md (1024-pixel case, scaled per pixel;
+# traffic grows in proportion to pixels).  Set to None when the kernel changes
+# until it is captured again.
+GA_DRAM_BYTES_PER_PIXEL = 2206976 / 1024
 
 
 def parse():
@@ -246,7 +251,8 @@ def run_ours(args):
             "gpu_launches": KERNELS_PER_STEP * args.steps,
             "clocks": clk,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": None if GA_DRAM_BYTES_PER_PIXEL is None else GA_DRAM_BYTES_PER_PIXEL * npix,
                          "kernel": "k_ga_evolve<float,2> (+ FP64 chi2 pass)",
                          "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (derived)",
                          "ga_ms": ga_avg, "flops_per_launch": flops,

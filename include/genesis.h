@@ -216,6 +216,81 @@ int lm_polish(const me_problem *pb, const void *obs, const double *w, const doub
               int npix, const me_bounds *bounds, int iters, double lambda0,
               double *params_inout, double *chi2_out, void *stream);
 
+/* ----------------------------------------------------------------- serving
+ * A continuous-batching request loop for inversions of slit scans and map
+ * tiles of uneven pixel counts (the paper's goal of near real-time pipeline
+ * inversions, Section 6).  serve_submit copies a request and queues it; a
+ * worker thread admits queued requests in arrival order whenever one of
+ * max_inflight slots is free and the request's buffers fit the arena
+ * (admission by memory), then runs the GA (and optional L-M polish) of
+ * ga_invert_batch / lm_polish on a stream of its own, so admitted requests
+ * overlap on the device.  Results are bit-identical to calling
+ * ga_invert_batch + lm_polish on the same request alone.
+ *
+ * The handle owns one device arena and one pinned host arena of arena_bytes
+ * each (the only allocations in this library), plus 2 * max_inflight streams.
+ */
+typedef struct serve_handle serve_handle;
+
+typedef struct serve_config {
+    size_t arena_bytes;       /* device and pinned-host arena size (>= 4096)        */
+    int max_inflight;         /* requests on the device at once, 1..64              */
+    int max_queue;            /* queued requests before serve_submit -> ME_EAGAIN    */
+    int small_pixels;         /* npix <= small_pixels run on high-priority streams   */
+    int fail_next_admissions; /* fault injection: the next N admissions fail with
+                                 ME_ENOMEM (0 in normal use)                         */
+} serve_config;
+
+/* A request.  Host arrays are copied by serve_submit (the caller may reuse
+ * them on return).  obs: [npix][4][n_lambda] of the problem dtype; w: GA
+ * weights [npix][4] (ga.weight_mode == ME_W_USER) or NULL; mu_px: [npix] or
+ * NULL; polish_w: L-M weights [npix][4] or NULL (then w, or inverse-max). */
+typedef struct serve_request {
+    const void *obs;
+    const double *w;
+    const double *mu_px;
+    int npix;
+    uint64_t pixel_id0;
+    ga_config ga;
+    me_bounds bounds;
+    int polish_iters;
+    double lambda0;
+    const double *polish_w;
+} serve_request;
+
+/* Completed request: best [npix][ME_NPAR] and chi2 [npix] are caller-owned
+ * host buffers (either may be NULL); status is the request's own status;
+ * queue_ns = submit -> admission, latency_ns = submit -> results on the host. */
+typedef struct serve_result {
+    double *best;
+    double *chi2;
+    int status;
+    uint64_t queue_ns;
+    uint64_t latency_ns;
+} serve_result;
+
+typedef struct serve_stats_t {
+    int queued;
+    int running;
+    size_t arena_used;
+    size_t arena_bytes;
+} serve_stats_t;
+
+/* Create a serving loop for one problem on the current device.  ME_ENOMEM if
+ * an arena cannot be allocated. */
+int serve_create(const me_problem *pb, const serve_config *cfg, serve_handle **out);
+/* Queue a request; ME_EAGAIN when max_queue requests are waiting, ME_EINVAL
+ * for an invalid request or one larger than the arena.  *ticket identifies it. */
+int serve_submit(serve_handle *h, const serve_request *rq, uint64_t *ticket);
+/* Collect a request: timeout_ms = 0 returns ME_EPENDING at once if it is not
+ * done, > 0 waits up to that long (then ME_ETIMEOUT), < 0 waits until done.
+ * On completion fills *out and forgets the ticket (ME_ENOTFOUND afterwards);
+ * returns the request's status. */
+int serve_poll(serve_handle *h, uint64_t ticket, serve_result *out, int timeout_ms);
+int serve_stats(serve_handle *h, serve_stats_t *out);
+/* Cancel queued requests, wait for running ones, free everything. */
+int serve_destroy(serve_handle *h);
+
 /* ------------------------------------------------ GA operator entry points
  * The operators of ga_invert_batch run alone on caller-given populations, so
  * that they can be checked bit for bit against a reference with injected

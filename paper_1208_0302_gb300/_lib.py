@@ -49,6 +49,27 @@ class GaConfig(C.Structure):
                 ("weight_mode", C.c_int)]
 
 
+class ServeConfig(C.Structure):
+    _fields_ = [("arena_bytes", C.c_size_t), ("max_inflight", C.c_int), ("max_queue", C.c_int),
+                ("small_pixels", C.c_int), ("fail_next_admissions", C.c_int)]
+
+
+class ServeRequest(C.Structure):
+    _fields_ = [("obs", C.c_void_p), ("w", C.c_void_p), ("mu_px", C.c_void_p), ("npix", C.c_int),
+                ("pixel_id0", C.c_uint64), ("ga", GaConfig), ("bounds", MeBounds),
+                ("polish_iters", C.c_int), ("lambda0", C.c_double), ("polish_w", C.c_void_p)]
+
+
+class ServeResult(C.Structure):
+    _fields_ = [("best", C.c_void_p), ("chi2", C.c_void_p), ("status", C.c_int),
+                ("queue_ns", C.c_uint64), ("latency_ns", C.c_uint64)]
+
+
+class ServeStats(C.Structure):
+    _fields_ = [("queued", C.c_int), ("running", C.c_int), ("arena_used", C.c_size_t),
+                ("arena_bytes", C.c_size_t)]
+
+
 class GenesisError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"genesis error {code}: {msg}")
@@ -77,6 +98,11 @@ _SIGNATURES = {
     "ga_breed": ([_VP, _VP, C.c_int, C.c_int, C.c_uint64, C.c_int, C.POINTER(GaConfig), _VP, _VP,
                   _VP], C.c_int),
     "ga_restart": ([_VP, _VP, C.c_int, C.c_int, C.c_uint64, _VP], C.c_int),
+    "serve_create": ([_P, C.POINTER(ServeConfig), C.POINTER(C.c_void_p)], C.c_int),
+    "serve_submit": ([_VP, C.POINTER(ServeRequest), C.POINTER(C.c_uint64)], C.c_int),
+    "serve_poll": ([_VP, C.c_uint64, C.POINTER(ServeResult), C.c_int], C.c_int),
+    "serve_stats": ([_VP, C.POINTER(ServeStats)], C.c_int),
+    "serve_destroy": ([_VP], C.c_int),
     "me_philox": ([_VP, C.c_int, C.c_uint64, _VP, _VP], C.c_int),
     "me_sobol": ([C.c_uint64, C.c_int, C.c_int, _VP, _VP], C.c_int),
 }

@@ -201,6 +201,94 @@ def lm_polish(pb: Problem, obs, params, lo, hi, iters=10, lambda0=1e-3, w=None, 
     return p, chi2
 
 
+# ------------------------------------------------------------------ serving
+
+def _host_f64(a, shape, name):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != shape:
+        raise ValueError(f"{name} must have shape {shape}, got {a.shape}")
+    return a
+
+
+class Server:
+    """Continuous-batching serving loop (serve_create / submit / poll / destroy).
+
+    Requests are host arrays; the library copies them on submit, admits them
+    as in-flight slots and arena memory free up, and runs them concurrently.
+    """
+
+    def __init__(self, pb: Problem, arena_bytes=1 << 30, max_inflight=8, max_queue=4096,
+                 small_pixels=0, fail_next_admissions=0):
+        self.pb = pb
+        cfg = L.ServeConfig(int(arena_bytes), int(max_inflight), int(max_queue), int(small_pixels),
+                            int(fail_next_admissions))
+        h = C.c_void_p()
+        L.check(L.load().serve_create(pb.ref(), C.byref(cfg), C.byref(h)))
+        self._h = h
+        self._npix = {}
+
+    def submit(self, obs, lo, hi, ga: GaSettings, w=None, mu_px=None, pixel_id0=0, polish_iters=0,
+               lambda0=1e-3, polish_w=None):
+        npix = obs.shape[0]
+        dt = np.float32 if self.pb.dtype == F32 else np.float64
+        ob = np.ascontiguousarray(obs, dtype=dt)
+        if ob.shape != (npix, 4, self.pb.n_lambda):
+            raise ValueError("obs must be [npix, 4, n_lambda]")
+        wv = _host_f64(w, (npix, 4), "w")
+        mv = _host_f64(mu_px, (npix,), "mu_px")
+        pw = _host_f64(polish_w, (npix, 4), "polish_w")
+        rq = L.ServeRequest()
+        rq.obs = ob.ctypes.data
+        rq.w = None if wv is None else wv.ctypes.data
+        rq.mu_px = None if mv is None else mv.ctypes.data
+        rq.npix = npix
+        rq.pixel_id0 = int(pixel_id0)
+        rq.ga = ga.to_c(L.ME_W_USER if wv is not None else L.ME_W_INVMAX)
+        rq.bounds = bounds(lo, hi)
+        rq.polish_iters = int(polish_iters)
+        rq.lambda0 = float(lambda0)
+        rq.polish_w = None if pw is None else pw.ctypes.data
+        t = C.c_uint64()
+        L.check(L.load().serve_submit(self._h, C.byref(rq), C.byref(t)))
+        self._npix[t.value] = npix
+        return t.value
+
+    def poll(self, ticket, timeout_ms=-1):
+        """Result dict of a finished request; raises GenesisError with code
+        ME_EPENDING / ME_ETIMEOUT if it is not done, or the request's error."""
+        npix = self._npix.get(ticket, 0)
+        best = np.empty((npix, NPAR))
+        chi2 = np.empty(npix)
+        res = L.ServeResult(best.ctypes.data if npix else None, chi2.ctypes.data if npix else None,
+                            0, 0, 0)
+        rc = L.load().serve_poll(self._h, int(ticket), C.byref(res), int(timeout_ms))
+        if rc in (L.ME_EPENDING, L.ME_ETIMEOUT):
+            L.check(rc)
+        self._npix.pop(ticket, None)
+        L.check(rc)
+        return {"best": best, "chi2": chi2, "status": res.status, "queue_ns": res.queue_ns,
+                "latency_ns": res.latency_ns}
+
+    def stats(self):
+        st = L.ServeStats()
+        L.check(L.load().serve_stats(self._h, C.byref(st)))
+        return {"queued": st.queued, "running": st.running, "arena_used": st.arena_used,
+                "arena_bytes": st.arena_bytes}
+
+    def close(self):
+        if self._h:
+            L.check(L.load().serve_destroy(self._h))
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
 # ---------------------------------------------------------- operator checks
 
 def _u16_to_dev(a, device):

@@ -11,9 +11,9 @@
 
 namespace genesis {
 
-namespace {
-
 thread_local std::string g_last_error;
+
+namespace {
 
 int fail(int code, const std::string &msg)
 {
@@ -103,6 +103,8 @@ HostTables build_tables()
     sobol_directions(t.sobol);
     return t;
 }
+
+}  // namespace
 
 std::mutex g_init_mu;
 bool g_dev_ready[256];
@@ -217,7 +219,9 @@ int make_ga(const ga_config *cfg, const me_bounds *b, uint64_t pid0, KGa &g)
 
 cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
 
-}  // namespace
+int set_error(int code, const std::string &msg) { return fail(code, msg); }
+
+int cuda_error(cudaError_t e, const char *where) { return cuda_fail(e, where); }
 
 const HostTables &host_tables()
 {

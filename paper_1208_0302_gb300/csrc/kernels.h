@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "me_device.cuh"
@@ -65,6 +66,17 @@ cudaError_t launch_chi2_f64(const KProblem &pb, int dtype, const void *obs, cons
 cudaError_t launch_lm(const KProblem &pb, const KLm &lm, int dtype, const void *obs,
                       const double *w, const double *mu_px, int npix, double *params,
                       cudaStream_t st);
+
+// api.cu: argument validation shared by the C entry points and the serving
+// loop.  Each returns ME_OK or an ME_E* code with the thread-local message set.
+extern thread_local std::string g_last_error;
+int set_error(int code, const std::string &msg);
+int cuda_error(cudaError_t e, const char *where);
+int ensure_device();
+int make_problem(const me_problem *pb, KProblem &k);
+int check_bounds(const me_bounds *b);
+int make_ga(const ga_config *cfg, const me_bounds *b, uint64_t pid0, KGa &g);
+cudaStream_t as_stream(void *s);
 
 // Decode of Eq. decode in FP64 without contraction, the same expression the
 // reference evaluation uses: lo + (hi - lo) * (g / 65535).
