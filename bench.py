@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--side", type=int, default=256, help="map side (pixels = side^2)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving sample")
+    ap.add_argument("--serve", action="store_true",
+                    help="run only the serving benchmark (Poisson arrivals at 0.7x and 1.2x capacity)")
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
     return ap.parse_args()
 
 
@@ -263,12 +267,104 @@ def run_ours(args):
         }
         if not args.no_fp64:
             result["fp64_plain_ga"] = fp64_comparator(api, torch, pb64, obs, w, lo, hi, rank)
+        if not args.no_serve:
+            result["serving"] = serving(api, torch, pb32, dev, args.serve_seconds, loads=(0.7,))
         if not args.no_cpu and world == 1:
             result["cpu_baseline"] = cpu_baseline(spec, obs, w, lo, hi)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     return result
+
+
+def _request_obs(api, torch, pb, rq, device):
+    """Observed cube of one request: GPU synthesis of its truth + seeded noise (host float32)."""
+    tp = torch.tensor(rq.truth, device=device)
+    clean = api.me_synth(pb, tp)
+    g = torch.Generator(device=device).manual_seed(rq.seed)
+    noise = torch.randn(clean.shape, generator=g, device=device, dtype=clean.dtype)
+    sig = 1e-3 * (tp[:, 7] + tp[:, 8])
+    obs = clean + sig.to(clean.dtype)[:, None, None] * noise
+    w = (1.0 / sig)[:, None].repeat(1, 4)
+    return obs.cpu().numpy(), w.cpu().numpy()
+
+
+def serving(api, torch, pb, device, seconds, loads=(0.7,), polish=LM_ITERS):
+    """Poisson-arriving requests of 64-4096 pixels with mixed GA budgets
+    (population 64/128, 100/200/300 generations), served by the continuous-
+    batching loop; p50/p99 latency (submit -> results on the host) and pixels/s
+    at each load (a fraction of the capacity measured on a burst)."""
+    import threading
+    pool = gi.draw_requests(600, rate_hz=1.0, seed=4)
+    cache = {}
+
+    def obs_of(i):
+        if i not in cache:
+            cache[i] = _request_obs(api, torch, pb, pool[i], device)
+        return cache[i]
+
+    lo, hi = gi.PRIOR_LO, gi.PRIOR_HI
+
+    def submit(srv, i, pid0):
+        rq = pool[i]
+        o, w = obs_of(i)
+        return srv.submit(o, lo, hi, api.GaSettings(npop=rq.npop, ngen=rq.ngen, seed=rq.seed),
+                          pixel_id0=pid0, polish_iters=polish, polish_w=w)
+
+    out = {"polish_iters": polish}
+    with api.Server(pb, arena_bytes=2 << 30, max_inflight=16, max_queue=100000, small_pixels=256) as srv:
+        # capacity: a burst of 24 requests submitted at once
+        nb = 24
+        for i in range(nb):
+            obs_of(i)
+        t0 = time.perf_counter()
+        ts = [submit(srv, i, i << 20) for i in range(nb)]
+        pix = 0
+        for t, i in zip(ts, range(nb)):
+            srv.poll(t)
+            pix += pool[i].npix
+        dt = time.perf_counter() - t0
+        cap_rps = nb / dt
+        out["capacity"] = {"requests_per_s": cap_rps, "pixels_per_s": pix / dt, "burst_requests": nb}
+        nxt = nb
+        for load in loads:
+            rate = load * cap_rps
+            rng = np.random.default_rng(int(load * 1000))
+            n = max(8, int(rate * seconds))
+            idx = list(range(nxt, min(nxt + n, len(pool))))
+            nxt = idx[-1] + 1 if idx else nxt
+            for i in idx:
+                obs_of(i)
+            gaps = rng.exponential(1.0 / rate, len(idx))
+            tickets, lat, qs = [], [], []
+
+            def poller():
+                k = 0
+                while k < len(idx):
+                    while k >= len(tickets):
+                        time.sleep(0.0005)
+                    r = srv.poll(tickets[k])
+                    lat.append(r["latency_ns"] / 1e6)
+                    qs.append(r["queue_ns"] / 1e6)
+                    k += 1
+
+            th = threading.Thread(target=poller)
+            th.start()
+            t0 = time.perf_counter()
+            at = 0.0
+            for g_, i in zip(gaps, idx):
+                at += g_
+                while time.perf_counter() - t0 < at:
+                    time.sleep(0.0002)
+                tickets.append(submit(srv, i, i << 20))
+            th.join()
+            wall = time.perf_counter() - t0
+            pix = sum(pool[i].npix for i in idx)
+            out[f"load_{load}"] = {"offered_rps": rate, "requests": len(idx), "pixels_per_s": pix / wall,
+                                   "p50_ms": float(np.percentile(lat, 50)),
+                                   "p99_ms": float(np.percentile(lat, 99)),
+                                   "queue_p50_ms": float(np.percentile(qs, 50)), "seconds": wall}
+    return out
 
 
 def fp64_comparator(api, torch, pb64, obs32, w, lo, hi, rank, n=1024):
@@ -343,9 +439,26 @@ def run_reference(args):
             "median_chi2": float(np.median(c2))}
 
 
+def run_serve(args):
+    import torch
+
+    from paper_1208_0302_gb300 import _lib, api
+    torch.cuda.set_device(0)
+    _lib.load()
+    pb = api.Problem.from_spec(gi.two_line_spec(), "f32")
+    res = serving(api, torch, pb, torch.device("cuda", 0), args.serve_seconds, loads=(0.7, 1.2))
+    return {"metric": "serving latency (Poisson arrivals, 64-4096 px requests)", "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "two-line 128-lambda requests, 30% magnetised, npop 64/128, "
+                                   "ngen 100/200/300, FP32 GA + 10 L-M"}, **res}
+
+
 def main():
     args = parse()
-    res = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.serve:
+        res = run_serve(args)
+    else:
+        res = run_reference(args) if args.impl == "reference" else run_ours(args)
     if res is not None:
         print(json.dumps(res))
 
