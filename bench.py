@@ -39,7 +39,7 @@ KERNELS_PER_STEP = 4  # GA evolve, FP64 chi2, L-M, FP64 chi2
 # profiles/k_ga_evolve_two_line_1024px.md (1024-pixel case, scaled per pixel;
 # traffic grows in proportion to pixels).  Set to None when the kernel changes
 # until it is captured again.
-GA_DRAM_BYTES_PER_PIXEL = 2206976 / 1024
+GA_DRAM_BYTES_PER_PIXEL = None  # kernel changed since the last capture
 
 
 def parse():

@@ -8,7 +8,10 @@
 // walks the wavelength grid for its own individual, so every lane of a warp
 // reads the same shared-memory word (broadcast) and the chi2 sum needs no
 // cross-thread reduction.
+#include <type_traits>
+
 #include "kernels.h"
+#include "me_pair.cuh"
 #include "rng_device.cuh"
 
 namespace genesis {
@@ -48,6 +51,20 @@ __device__ __forceinline__ void load4(const double *p, double v[4])
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 
+// Shared-memory layouts.  FP32: wavelength pairs (2p, 2p+1) interleaved for
+// packed FP32x2 use, 8 values per pair: (I, I', Q, Q', U, U', V, V') and
+// (d0, d0', d1, d1', d2, d2', d3, d3') for the per-line offsets; an odd grid
+// repeats its last point as the partner of the last pair.  FP64: rows of 4
+// per wavelength.
+template <class R> __device__ __forceinline__ int obs_idx(int s, int j)
+{
+    return sizeof(R) == 4 ? (j >> 1) * 8 + s * 2 + (j & 1) : j * 4 + s;
+}
+template <class R> __device__ __forceinline__ int padded_lambda(int nl)
+{
+    return sizeof(R) == 4 ? (nl + 1) & ~1 : nl;
+}
+
 template <class R> struct GaDecode;
 template <> struct GaDecode<float> {
     // FP32 GA: p = lo + g (hi - lo) / 65535, scale precomputed on the host
@@ -69,9 +86,9 @@ template <> struct GaDecode<double> {
 // s_obs rows are (I, Q, U, V) of one wavelength; s_doff rows hold
 // lambda_j - lambda0_l for l = 0..3: one vector load each per wavelength.
 template <class R, int NL, bool COUNT>
-__device__ __forceinline__ R fitness(const KProblem &pb, int nlines, int nl, const R *p, R mu,
-                                     const R *s_obs, const R *s_doff, const R *he,
-                                     const R *s_w2, R inv_nu, unsigned long long &ninterior)
+__device__ __forceinline__ R fitness_rows(const KProblem &pb, int nlines, int nl, const R *p, R mu,
+                                          const R *s_obs, const R *s_doff, const R *he,
+                                          const R *s_w2, R inv_nu, unsigned long long &ninterior)
 {
     const Geo<R> geo = make_geo<R, NL>(pb, nlines, p, mu);
     R sI = 0, sQ = 0, sU = 0, sV = 0, cI = 0, cQ = 0, cU = 0, cV = 0;
@@ -87,6 +104,63 @@ __device__ __forceinline__ R fitness(const KProblem &pb, int nlines, int nl, con
         kahan_sq(sV, cV, ob[3] - s.V);
     }
     return (s_w2[0] * sI + s_w2[1] * sQ + s_w2[2] * sU + s_w2[3] * sV) * inv_nu;
+}
+
+__device__ __forceinline__ void kahan_sq2(float2 &s, float2 &c, float2 r)
+{
+    const float2 y = fma2(r, r, neg2(c));
+    const float2 t = add2(s, y);
+    c = sub2(sub2(t, s), y);
+    s = t;
+}
+
+// Eq. chisq for one individual with the FP32 pair path (two wavelengths per
+// step, packed FP32x2 arithmetic).
+template <int NL, bool COUNT>
+__device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, int nl, const float *p,
+                                               float mu, const float *s_obs, const float *s_doff,
+                                               const float *he, const float *s_w2, float inv_nu,
+                                               unsigned long long &ninterior)
+{
+    const Geo<float> geo = make_geo<float, NL>(pb, nlines, p, mu);
+    float2 sI = f2(0.f), sQ = f2(0.f), sU = f2(0.f), sV = f2(0.f);
+    float2 cI = f2(0.f), cQ = f2(0.f), cU = f2(0.f), cV = f2(0.f);
+    const int npair = (nl + 1) >> 1;
+    unsigned cnt = 0;
+    for (int q = 0; q < npair; ++q) {
+        const float4 o0 = *(const float4 *)(s_obs + 8 * q), o1 = *(const float4 *)(s_obs + 8 * q + 4);
+        const float4 d0 = *(const float4 *)(s_doff + 8 * q);
+        float2 doff2[ME_MAX_LINES];
+        doff2[0] = make_float2(d0.x, d0.y);
+        doff2[1] = make_float2(d0.z, d0.w);
+        if (NL == 0 || NL > 2) {
+            const float4 d1 = *(const float4 *)(s_doff + 8 * q + 4);
+            doff2[2] = make_float2(d1.x, d1.y);
+            doff2[3] = make_float2(d1.z, d1.w);
+        }
+        const Stokes4x2 m = me_point_x2<NL, COUNT>(geo, doff2, he, nlines, cnt);
+        float2 rI = sub2(make_float2(o0.x, o0.y), m.I), rQ = sub2(make_float2(o0.z, o0.w), m.Q);
+        float2 rU = sub2(make_float2(o1.x, o1.y), m.U), rV = sub2(make_float2(o1.z, o1.w), m.V);
+        if (2 * q + 1 >= nl) rI.y = rQ.y = rU.y = rV.y = 0.f;  // padded partner
+        kahan_sq2(sI, cI, rI);
+        kahan_sq2(sQ, cQ, rQ);
+        kahan_sq2(sU, cU, rU);
+        kahan_sq2(sV, cV, rV);
+    }
+    if (COUNT) ninterior += cnt;
+    return (s_w2[0] * (sI.x + sI.y) + s_w2[1] * (sQ.x + sQ.y) + s_w2[2] * (sU.x + sU.y) +
+            s_w2[3] * (sV.x + sV.y)) * inv_nu;
+}
+
+template <class R, int NL, bool COUNT>
+__device__ __forceinline__ R fitness(const KProblem &pb, int nlines, int nl, const R *p, R mu,
+                                     const R *s_obs, const R *s_doff, const R *he,
+                                     const R *s_w2, R inv_nu, unsigned long long &ninterior)
+{
+    if constexpr (std::is_same<R, float>::value)
+        return fitness_pairs<NL, COUNT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior);
+    else
+        return fitness_rows<R, NL, COUNT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior);
 }
 
 // argmin over the block's fitness, ties to the lowest index.  Every thread
@@ -203,8 +277,9 @@ __host__ __device__ __forceinline__ GaSmem ga_smem_layout(int nl, int nlines, in
         o += bytes;
         return at;
     };
-    L.obs = take(4 * nl * (int)sizeof(R), 16);
-    L.doff = take(4 * nl * (int)sizeof(R), 16);
+    const int nlp = sizeof(R) == 4 ? (nl + 1) & ~1 : nl;  // padded to whole pairs in FP32
+    L.obs = take(4 * nlp * (int)sizeof(R), 16);
+    L.doff = take(4 * nlp * (int)sizeof(R), 16);
     L.fit = take(npop * (int)sizeof(R), 16);
     L.wmin = take(32 * (int)sizeof(R), 16);
     L.widx = take(32 * 4, 16);
@@ -222,10 +297,11 @@ __device__ __forceinline__ void weights_invmax_w2(const R *s_obs, int nl, R *s_w
     const int lane = threadIdx.x & 31;
     R imax = -R(INFINITY), imin = R(INFINITY), mq = 0, mu = 0, mv = 0;
     for (int j = lane; j < nl; j += 32) {
-        const R I = s_obs[4 * j];
+        const R I = s_obs[obs_idx<R>(0, j)];
         imax = I > imax ? I : imax;
         imin = I < imin ? I : imin;
-        const R aq = fabs(s_obs[4 * j + 1]), au = fabs(s_obs[4 * j + 2]), av = fabs(s_obs[4 * j + 3]);
+        const R aq = fabs(s_obs[obs_idx<R>(1, j)]), au = fabs(s_obs[obs_idx<R>(2, j)]);
+        const R av = fabs(s_obs[obs_idx<R>(3, j)]);
         mq = aq > mq ? aq : mq;
         mu = au > mu ? au : mu;
         mv = av > mv ? av : mv;
@@ -290,15 +366,16 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
     }
     const R inv_nu = R(1) / R(4 * nl - ME_NPAR);
     if (k < 4) s_he[k] = k < nlines ? R(pb.line[k].half_eta) : R(0);
-    for (int i = k; i < 4 * nl; i += blockDim.x) {
+    for (int i = k; i < 4 * padded_lambda<R>(nl); i += blockDim.x) {
         const int j = i >> 2, l = i & 3;
+        const int jj = j < nl ? j : nl - 1;  // a padded partner repeats the last point
         // exact difference in FP64, then rounded
-        s_doff[i] = l < nlines ? R(pb.lam[j] - pb.line[l].lam0) : R(0);
+        s_doff[obs_idx<R>(l, j)] = l < nlines ? R(pb.lam[jj] - pb.line[l].lam0) : R(0);
     }
 
     for (int pix = blockIdx.x; pix < npix; pix += gridDim.x) {
-        // a1: stage the pixel's Stokes profiles, [4][nl] in HBM -> [nl][4] rows in
-        // shared memory (16-byte vector loads when a vector stays in one row)
+        // a1: stage the pixel's Stokes profiles from [4][nl] in HBM into the
+        // shared-memory layout (16-byte vector loads when a vector stays in one row)
         const R *o = obs + (size_t)pix * 4 * nl;
         constexpr int VW = 16 / (int)sizeof(R);  // elements per 16-byte vector
         if (nl % VW == 0 && (((uintptr_t)o) & 15) == 0) {
@@ -306,22 +383,23 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
                 const int e = i * VW, st = e / nl, j = e - st * nl;
                 if (VW == 4) {
                     const float4 q = __ldg((const float4 *)o + i);
-                    s_obs[4 * j + st] = R(q.x);
-                    s_obs[4 * (j + 1) + st] = R(q.y);
-                    s_obs[4 * (j + 2) + st] = R(q.z);
-                    s_obs[4 * (j + 3) + st] = R(q.w);
+                    s_obs[obs_idx<R>(st, j)] = R(q.x);
+                    s_obs[obs_idx<R>(st, j + 1)] = R(q.y);
+                    s_obs[obs_idx<R>(st, j + 2)] = R(q.z);
+                    s_obs[obs_idx<R>(st, j + 3)] = R(q.w);
                 } else {
                     const double2 q = __ldg((const double2 *)o + i);
-                    s_obs[4 * j + st] = R(q.x);
-                    s_obs[4 * (j + 1) + st] = R(q.y);
+                    s_obs[obs_idx<R>(st, j)] = R(q.x);
+                    s_obs[obs_idx<R>(st, j + 1)] = R(q.y);
                 }
             }
         } else {
             for (int i = k; i < 4 * nl; i += blockDim.x) {
                 const int st = i / nl, j = i - st * nl;
-                s_obs[4 * j + st] = o[i];
+                s_obs[obs_idx<R>(st, j)] = o[i];
             }
         }
+        if (padded_lambda<R>(nl) > nl && k < 4) s_obs[obs_idx<R>(k, nl)] = o[k * nl + nl - 1];
         __syncthreads();
         // a2: weights
         if (ga.weight_mode == ME_W_USER) {

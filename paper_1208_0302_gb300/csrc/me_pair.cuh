@@ -1,0 +1,180 @@
+// FP32 synthesis of two wavelength points at once with packed FP32x2 arithmetic
+// (sm_100+ FFMA2/FMUL2/FADD2): the same formulas as me_point<float>, with the
+// .x lane holding wavelength j and the .y lane wavelength j+1.  One packed
+// instruction does the work of two scalar ones, which halves the issue slots
+// of the GA's fitness loop (an issue-bound loop of FP32 arithmetic).
+//
+// Branches are taken per pair: a Zeeman component uses the continued fraction
+// when both points are exterior and Weideman's series otherwise (the series is
+// accurate everywhere, |error| <= 5e-8 for |x| <= 150), so a point's value can
+// depend on its partner's region, always within the FP32 error budget.
+#pragma once
+
+#include "me_device.cuh"
+
+namespace genesis {
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(fast_rcp(a.x), fast_rcp(a.y)); }
+
+// Exterior branch (continued fraction, monic a(u), b(u)) for a pair of real
+// arguments x and a common damping y (a2 = y^2).
+__device__ __forceinline__ void fad_ext2(float2 x, float y, float a2, float2 &wx, float2 &wy)
+{
+    constexpr int K = FadCfg<float>::K;
+    constexpr int NA = (K + 1) / 2, NB = (K - 1) / 2;
+    constexpr CfPoly<K> P{};
+    const float2 ux = fma2(x, x, f2(-a2));
+    const float2 uy = mul2(x, f2(2.0f * y));
+    float2 ax = add2(ux, f2((float)P.a[NA - 1])), ay = uy;
+#pragma unroll
+    for (int n = NA - 2; n >= 0; --n) {
+        const float2 tx = fma2(ax, ux, fma2(neg2(ay), uy, f2((float)P.a[n])));
+        ay = fma2(ax, uy, mul2(ay, ux));
+        ax = tx;
+    }
+    float2 bx = f2(1.0f), by = f2(0.0f);
+    if (NB >= 1) {
+        bx = add2(ux, f2((float)P.b[NB - 1]));
+        by = uy;
+    }
+#pragma unroll
+    for (int n = NB - 2; n >= 0; --n) {
+        const float2 tx = fma2(bx, ux, fma2(neg2(by), uy, f2((float)P.b[n])));
+        by = fma2(bx, uy, mul2(by, ux));
+        bx = tx;
+    }
+    // num = z b(u), z = x + i y;  w = (i/sqrt(pi)) num / a(u)
+    const float2 nx = fma2(x, bx, mul2(f2(-y), by));
+    const float2 ny = fma2(x, by, mul2(f2(y), bx));
+    const float2 inv = mul2(rcp2(fma2(ax, ax, mul2(ay, ay))), f2(0.56418958354775628695f));
+    wx = mul2(fma2(nx, ay, neg2(mul2(ny, ax))), inv);
+    wy = mul2(fma2(nx, ax, mul2(ny, ay)), inv);
+}
+
+// Interior branch (Weideman N = 16, real-quadratic synthetic division) for a
+// pair of real arguments x and common damping y.
+__device__ __forceinline__ void fad_int2(float2 x, float y, float2 &wx, float2 &wy)
+{
+    constexpr int N = FadCfg<float>::N;
+    const float L = c_fad.L32;
+    // 1/(L - i z) = (dx + i x) / (dx^2 + x^2), dx = L + y
+    const float dx = L + y;
+    const float2 inv = rcp2(fma2(x, x, f2(dx * dx)));
+    const float2 rx = mul2(f2(dx), inv), ry = mul2(x, inv);
+    // Z = ((L - y) + i x) (rx + i ry)
+    const float mx = L - y;
+    const float2 Zx = fma2(f2(mx), rx, neg2(mul2(x, ry)));
+    const float2 Zy = fma2(f2(mx), ry, mul2(x, rx));
+    const float2 r = add2(Zx, Zx), sq = neg2(fma2(Zx, Zx, mul2(Zy, Zy)));
+    float2 b2 = c_fad.w32x2[N];
+    float2 b1 = fma2(r, b2, c_fad.w32x2[N - 1]);
+#pragma unroll
+    for (int j = N - 3; j >= 1; --j) {
+        const float2 b0 = fma2(r, b1, fma2(sq, b2, c_fad.w32x2[j + 1]));
+        b2 = b1;
+        b1 = b0;
+    }
+    const float2 px = fma2(sq, b2, fma2(b1, Zx, c_fad.w32x2[1])), py = mul2(b1, Zy);
+    const float2 r2x = fma2(rx, rx, neg2(mul2(ry, ry))), r2y = mul2(add2(rx, rx), ry);
+    const float2 s = f2(0.56418958354775628695f);
+    wx = fma2(f2(2.0f), fma2(px, r2x, neg2(mul2(py, r2y))), mul2(rx, s));
+    wy = fma2(f2(2.0f), fma2(px, r2y, mul2(py, r2x)), mul2(ry, s));
+}
+
+// All three components of a line outside |z| = R at one point (the same test
+// as triplet_exterior<float>).
+__device__ __forceinline__ bool ext3(float v, float vB, float a2)
+{
+    const float m = fabsf(v) - fabsf(vB);
+    return m > 0.0f && m * m + a2 > FadCfg<float>::R2;
+}
+
+__device__ __forceinline__ bool ext1(float x, float a2) { return x * x + a2 > FadCfg<float>::R2; }
+
+// One component for the pair: continued fraction if both exterior.
+__device__ __forceinline__ void fad_pair(float2 x, float y, float a2, float2 &wx, float2 &wy)
+{
+    if (ext1(x.x, a2) && ext1(x.y, a2)) fad_ext2(x, y, a2, wx, wy);
+    else fad_int2(x, y, wx, wy);
+}
+
+// Number of interior (Weideman) evaluations the pair path performs for one
+// line at a pair of points: 0 on the all-exterior fast path, else 2 per
+// component that needs the interior branch at either point.
+__device__ __forceinline__ unsigned count_interior_pair(float2 xb, float2 v, float2 xr, float vB, float a2)
+{
+    if (ext3(v.x, vB, a2) && ext3(v.y, vB, a2)) return 0u;
+    unsigned c = 0;
+    c += (ext1(xb.x, a2) && ext1(xb.y, a2)) ? 0u : 2u;
+    c += (ext1(v.x, a2) && ext1(v.y, a2)) ? 0u : 2u;
+    c += (ext1(xr.x, a2) && ext1(xr.y, a2)) ? 0u : 2u;
+    return c;
+}
+
+struct Stokes4x2 {
+    float2 I, Q, U, V;
+};
+
+// Stokes vectors at two wavelength points.  doff2[l] holds (lambda_j -
+// lambda0_l, lambda_{j+1} - lambda0_l).
+template <int NL, bool COUNT>
+__device__ __forceinline__ Stokes4x2 me_point_x2(const Geo<float> &g, const float2 *doff2,
+                                                 const float *half_eta, int nlines, unsigned &ncount)
+{
+    float2 P = f2(0.f), Sg = f2(0.f), T = f2(0.f), Ti = f2(0.f), Dd = f2(0.f), Di = f2(0.f);
+    const int nl = NL > 0 ? NL : nlines;
+#pragma unroll
+    for (int l = 0; l < (NL > 0 ? NL : ME_MAX_LINES); ++l) {
+        if (l < nl) {
+            const float2 id = f2(g.invD[l]);
+            const float2 v = fma2(doff2[l], id, f2(g.cp[l]));
+            const float2 xb = fma2(doff2[l], id, f2(g.cp[l] + g.vB[l]));
+            const float2 xr = fma2(doff2[l], id, f2(g.cp[l] - g.vB[l]));
+            if (COUNT) ncount += count_interior_pair(xb, v, xr, g.vB[l], g.a2);
+            float2 bx, by, px, py, rx, ry;
+            if (ext3(v.x, g.vB[l], g.a2) && ext3(v.y, g.vB[l], g.a2)) {
+                fad_ext2(xb, g.a, g.a2, bx, by);
+                fad_ext2(v, g.a, g.a2, px, py);
+                fad_ext2(xr, g.a, g.a2, rx, ry);
+            } else {
+                fad_pair(xb, g.a, g.a2, bx, by);
+                fad_pair(v, g.a, g.a2, px, py);
+                fad_pair(xr, g.a, g.a2, rx, ry);
+            }
+            const float2 q = f2(half_eta[l]);
+            const float2 sx = add2(bx, rx), sy = add2(by, ry);
+            P = fma2(q, px, P);
+            Sg = fma2(q, sx, Sg);
+            T = fma2(q, fma2(f2(-0.5f), sx, px), T);
+            Ti = fma2(q, fma2(f2(-0.5f), sy, py), Ti);
+            Dd = fma2(q, sub2(rx, bx), Dd);
+            Di = fma2(q, sub2(ry, by), Di);
+        }
+    }
+    // closed form of K^-1 e (see me_point)
+    const float2 eI = fma2(f2(g.kIs), Sg, fma2(f2(g.kIp), P, f2(1.0f)));
+    const float2 pT = mul2(f2(g.kIp2), T), pTi = mul2(f2(g.kIp2), Ti);
+    const float2 vD = mul2(f2(g.kV2), Dd), vDi = mul2(f2(g.kV2), Di);
+    const float2 E2 = fma2(pT, T, mul2(vD, Dd));
+    const float2 rho2 = fma2(pTi, Ti, mul2(vDi, Di));
+    const float2 Pi = fma2(pT, Ti, mul2(vD, Di));
+    const float2 eI2 = mul2(eI, eI);
+    const float2 Delta = fma2(eI2, add2(sub2(eI2, E2), rho2), neg2(mul2(Pi, Pi)));
+    const float2 f = mul2(f2(g.muS1), rcp2(Delta));
+    const float2 A = fma2(eI2, T, mul2(Ti, Pi));
+    const float2 eIC = mul2(eI, fma2(Dd, Ti, neg2(mul2(T, Di))));
+    Stokes4x2 s;
+    s.I = fma2(mul2(f, eI), add2(eI2, rho2), f2(g.S0));
+    s.Q = mul2(neg2(f), fma2(f2(g.kQ), A, mul2(f2(g.kUV), eIC)));
+    s.U = mul2(neg2(f), fma2(f2(g.kU), A, neg2(mul2(f2(g.kQV), eIC))));
+    s.V = mul2(mul2(neg2(f), f2(g.kV)), fma2(eI2, Dd, mul2(Di, Pi)));
+    return s;
+}
+
+}  // namespace genesis
