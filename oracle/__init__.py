@@ -26,7 +26,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["me.c", "rng.c", "ga.c", "lm.c"]
+_SOURCES = ["me.c", "rng.c", "ga.c", "lm.c", "zeeman.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -55,6 +55,11 @@ class _Problem(C.Structure):
                 ("lambda0", C.c_double * MAX_LINES),
                 ("g", C.c_double * MAX_LINES),
                 ("eta_ratio", C.c_double * MAX_LINES),
+                ("pattern", C.c_int * MAX_LINES),
+                ("j_lower", C.c_int * MAX_LINES),
+                ("j_upper", C.c_int * MAX_LINES),
+                ("g_lower", C.c_double * MAX_LINES),
+                ("g_upper", C.c_double * MAX_LINES),
                 ("lambda_dop", C.c_double),
                 ("n_lambda", C.c_int),
                 ("lam", C.POINTER(C.c_double))]
@@ -93,6 +98,12 @@ def lib():
             L = C.CDLL(_LIB_PATH)
             P = C.POINTER(_Problem)
             L.or_faddeeva_batch.argtypes = [C.c_int, _D, _D, _D, _D]
+            L.or_wigner3j.argtypes = [C.c_int] * 6
+            L.or_wigner3j.restype = C.c_double
+            L.or_zeeman_components.argtypes = [C.c_int, C.c_double, C.c_int, C.c_double,
+                                               np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS"),
+                                               _D, _D]
+            L.or_zeeman_components.restype = C.c_int
             L.or_synth.argtypes = [P, _D, C.c_double, _D]
             L.or_synth_lu.argtypes = [P, _D, C.c_double, _D]
             L.or_synth_batch.argtypes = [P, _D, C.c_int, _DN, C.c_double, _D, C.c_int]
@@ -137,8 +148,11 @@ class Problem:
         self.lam = _f64(lambda_grid)
         s = _Problem()
         s.n_lines = len(lines)
-        for i, (l0, g, r) in enumerate(lines):
-            s.lambda0[i], s.g[i], s.eta_ratio[i] = l0, g, r
+        for i, ln in enumerate(lines):
+            s.lambda0[i], s.g[i], s.eta_ratio[i] = ln[0], ln[1], ln[2]
+            if len(ln) > 3:   # full pattern: (..., j_lower, g_lower, j_upper, g_upper)
+                s.pattern[i] = 1
+                s.j_lower[i], s.g_lower[i], s.j_upper[i], s.g_upper[i] = int(ln[3]), ln[4], int(ln[5]), ln[6]
         s.lambda_dop = float(lambda_dop)
         s.n_lambda = len(self.lam)
         s.lam = self.lam.ctypes.data_as(C.POINTER(C.c_double))
@@ -176,6 +190,22 @@ def faddeeva(x, y):
     im = np.empty_like(x)
     lib().or_faddeeva_batch(len(x), x, y, re, im)
     return (re + 1j * im).reshape(shape)
+
+
+def wigner3j(j1, j2, j3, m1, m2, m3):
+    return lib().or_wigner3j(int(j1), int(j2), int(j3), int(m1), int(m2), int(m3))
+
+
+def zeeman_components(j_lower, g_lower, j_upper, g_upper):
+    """[(shifts, strengths)] for the sigma_b, pi, sigma_r groups (Section 4
+    full Zeeman pattern), shifts in Larmor units toward longer wavelength."""
+    n = np.zeros(3, dtype=np.int32)
+    sh = np.zeros((3, 9))
+    st = np.zeros((3, 9))
+    rc = lib().or_zeeman_components(int(j_lower), float(g_lower), int(j_upper), float(g_upper), n, sh, st)
+    if rc:
+        raise ValueError("invalid transition")
+    return [(sh[g, :n[g]].copy(), st[g, :n[g]].copy()) for g in range(3)]
 
 
 # ----------------------------------------------------------------- synthesis

@@ -108,9 +108,29 @@ static void kmatrix(const or_problem *pb, const double *p, double lam,
         const double v = dl / dD;
         const double vB = OR_ZEEMAN * pb->g[l] * l0 * l0 * B / dD;
         double phb, psb, php, psp, phr, psr;
-        or_faddeeva(v + vB, a, &phb, &psb);
-        or_faddeeva(v, a, &php, &psp);
-        or_faddeeva(v - vB, a, &phr, &psr);
+        if (pb->pattern[l]) {
+            /* full Zeeman pattern: each group is the strength-weighted sum of
+             * its components, centred at v - v_L s with v_L the Larmor
+             * splitting in Doppler units */
+            int n[3];
+            double sh[3][OR_MAX_COMP], st[3][OR_MAX_COMP];
+            or_zeeman_components(pb->j_lower[l], pb->g_lower[l], pb->j_upper[l], pb->g_upper[l],
+                                 n, sh, st);
+            const double vL = OR_ZEEMAN * l0 * l0 * B / dD;
+            double ph[3] = {0, 0, 0}, ps[3] = {0, 0, 0};
+            for (int g = 0; g < 3; ++g)
+                for (int i = 0; i < n[g]; ++i) {
+                    double re, im;
+                    or_faddeeva(v - vL * sh[g][i], a, &re, &im);
+                    ph[g] += st[g][i] * re;
+                    ps[g] += st[g][i] * im;
+                }
+            phb = ph[0]; psb = ps[0]; php = ph[1]; psp = ps[1]; phr = ph[2]; psr = ps[2];
+        } else {
+            or_faddeeva(v + vB, a, &phb, &psb);
+            or_faddeeva(v, a, &php, &psp);
+            or_faddeeva(v - vB, a, &phr, &psr);
+        }
         const double h = 0.5 * eta0 * pb->eta_ratio[l];
         etaI += h * (php * s2 + 0.5 * (phb + phr) * (1.0 + c2));
         etaQ += h * (php - 0.5 * (phb + phr)) * s2 * c2x;

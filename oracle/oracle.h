@@ -35,12 +35,16 @@ extern "C" {
 
 #define OR_MAX_LINES 4
 #define OR_NPAR 9
+#define OR_MAX_COMP 9   /* Zeeman components per group (J <= 4) */
 
 typedef struct {
     int n_lines;
     double lambda0[OR_MAX_LINES];   /* rest wavelength [A] (Table 1) */
     double g[OR_MAX_LINES];         /* effective Lande factor (Table 1) */
     double eta_ratio[OR_MAX_LINES]; /* eta0 of this line / eta0 parameter */
+    int pattern[OR_MAX_LINES];      /* 0: effective triplet with g; 1: full pattern */
+    int j_lower[OR_MAX_LINES], j_upper[OR_MAX_LINES];
+    double g_lower[OR_MAX_LINES], g_upper[OR_MAX_LINES];
     double lambda_dop;              /* [A] wavelength at which param 4 is quoted */
     int n_lambda;
     const double *lambda;           /* [n_lambda] observed wavelengths [A] */
@@ -52,6 +56,15 @@ typedef struct {
     double pmut_lsb, pmut_ratio;    /* per-bit mutation: pmut_lsb * ratio^(15-b) */
     uint64_t seed;
 } or_ga_config;
+
+/* Wigner 3j symbol for integer arguments (Racah's formula). */
+double or_wigner3j(int j1, int j2, int j3, int m1, int m2, int m3);
+/* Zeeman components of lower (J_l, g_l) -> upper (J_u, g_u): per group
+ * (0 = sigma_blue, q = -1; 1 = pi; 2 = sigma_red, q = +1) the number of
+ * components, their shifts in Larmor units (g_l M_l - g_u M_u) and strengths
+ * 3 (J_u J_l 1; M_u -M_l q)^2.  Returns non-zero for an invalid transition. */
+int or_zeeman_components(int j_lower, double g_lower, int j_upper, double g_upper,
+                         int n[3], double shift[3][OR_MAX_COMP], double strength[3][OR_MAX_COMP]);
 
 /* Faddeeva function w(x + i y), y >= 0 (Matta & Reichel 1971 trapezoid). */
 void or_faddeeva(double x, double y, double *re, double *im);
