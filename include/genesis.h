@@ -49,6 +49,7 @@ extern "C" {
 #define ME_NPAR 9
 #define ME_MAX_LINES 4
 #define ME_MAX_LAMBDA 512
+#define ME_MAX_COMP 9 /* Zeeman components per group in a full pattern (J <= 4) */
 #define ME_MIN_POP 32
 #define ME_MAX_POP 1024
 
@@ -59,17 +60,30 @@ extern "C" {
 #define ME_W_USER 1   /* caller-supplied w[npix][4]                     */
 
 /*
- * One spectral line (Table 1), treated as an effective Zeeman triplet
- * (sigma_blue, pi, sigma_red at v + v_B, v, v - v_B, Section 4).
+ * One spectral line (Table 1).
  *   lambda0_A  rest wavelength [A]
- *   g_eff      effective Lande factor; v_B = 4.6686e-13 g lambda0^2 B / dlambda_D
+ *   g_eff      effective Lande factor (pattern == 0): an effective Zeeman
+ *              triplet, sigma_blue, pi, sigma_red at v + v_B, v, v - v_B with
+ *              v_B = 4.6686e-13 g_eff lambda0^2 B / dlambda_D (Section 4)
  *   eta_ratio  eta0 of this line divided by the eta0 parameter (1 for the
  *              reference line); all lines add into one propagation matrix.
+ *   pattern    1: use the line's full Zeeman pattern (Section 4: computed at
+ *              start-up from the transition), built from the lower level
+ *              (j_lower, g_lower) and upper level (j_upper, g_upper) in LS
+ *              coupling: components M_u -> M_l, q = M_l - M_u (-1 sigma_blue,
+ *              0 pi, +1 sigma_red), shift g_l M_l - g_u M_u Larmor units,
+ *              strengths normalised to 1 per group.  |j_lower - j_upper| <= 1,
+ *              integer J <= 4, not both 0.
  */
 typedef struct me_line {
     double lambda0_A;
     double g_eff;
     double eta_ratio;
+    int pattern;
+    int j_lower;
+    int j_upper;
+    double g_lower;
+    double g_upper;
 } me_line;
 
 /*
@@ -123,6 +137,13 @@ typedef struct ga_config {
     uint64_t seed;
     int weight_mode;
 } ga_config;
+
+/* Zeeman components of a line (host only, no GPU): for each group (0 =
+ * sigma_blue, 1 = pi, 2 = sigma_red) the count n[g], the shifts in Larmor
+ * units (toward longer wavelength) and the strengths.  An effective triplet
+ * (pattern == 0) reports one component per group at -g_eff, 0, +g_eff. */
+int me_zeeman_components(const me_line *line, int n[3], double shift[3][ME_MAX_COMP],
+                         double strength[3][ME_MAX_COMP]);
 
 /* Thread-local message describing the last failed call ("" if none). */
 const char *me_last_error(void);
@@ -192,9 +213,9 @@ int ga_invert_batch(const me_problem *pb, const void *obs, const double *w,
 /*
  * ga_count_evaluations - the same GA as ga_invert_batch (float cubes,
  * npop <= 256) run by a separate instantiation that also counts work:
- * counts dev uint64[2] receives (added to its contents) the number of
- * syntheses (fitness evaluations) and of Faddeeva evaluations that took the
- * interior branch; every other Faddeeva evaluation took the exterior branch.
+ * counts dev uint64[3] receives (added to its contents) the number of
+ * syntheses (fitness evaluations), of Faddeeva evaluations that took the
+ * interior branch and of all Faddeeva evaluations.
  * The arithmetic and the result `best` are those of ga_invert_batch; the
  * counts turn into algorithmic flops for roofline reporting.
  */

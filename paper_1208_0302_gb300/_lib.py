@@ -29,8 +29,13 @@ ME_W_INVMAX = 0
 ME_W_USER = 1
 
 
+ME_MAX_COMP = 9
+
+
 class MeLine(C.Structure):
-    _fields_ = [("lambda0_A", C.c_double), ("g_eff", C.c_double), ("eta_ratio", C.c_double)]
+    _fields_ = [("lambda0_A", C.c_double), ("g_eff", C.c_double), ("eta_ratio", C.c_double),
+                ("pattern", C.c_int), ("j_lower", C.c_int), ("j_upper", C.c_int),
+                ("g_lower", C.c_double), ("g_upper", C.c_double)]
 
 
 class MeProblem(C.Structure):
@@ -84,6 +89,7 @@ _P = C.POINTER(MeProblem)
 
 _SIGNATURES = {
     "me_last_error": ([], C.c_char_p),
+    "me_zeeman_components": ([C.POINTER(MeLine), _VP, _VP, _VP], C.c_int),
     "me_version": ([], C.c_int),
     "me_synth": ([_P, _VP, _VP, C.c_int, _VP, _VP], C.c_int),
     "me_synth_jac": ([_P, _VP, _VP, C.c_int, _VP, _VP, _VP], C.c_int),

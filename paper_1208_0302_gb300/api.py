@@ -52,8 +52,13 @@ class Problem:
         self.torch_dtype = torch.float32 if self.dtype == F32 else torch.float64
         s = L.MeProblem()
         s.n_lines = len(self.lines)
-        for i, (l0, g, r) in enumerate(self.lines):
-            s.line[i] = L.MeLine(l0, g, r)
+        for i, ln in enumerate(self.lines):
+            # (lambda0, g_eff, eta_ratio) or, for a full Zeeman pattern,
+            # (lambda0, g_eff, eta_ratio, j_lower, g_lower, j_upper, g_upper)
+            if len(ln) > 3:
+                s.line[i] = L.MeLine(ln[0], ln[1], ln[2], 1, int(ln[3]), int(ln[5]), ln[4], ln[6])
+            else:
+                s.line[i] = L.MeLine(ln[0], ln[1], ln[2], 0, 0, 0, 0.0, 0.0)
         s.n_lambda = len(self.lam)
         s.lambda_A = self.lam.ctypes.data_as(C.POINTER(C.c_double))
         s.lambda_dop_A = self.lambda_dop
@@ -172,7 +177,7 @@ def ga_count_evaluations(pb: Problem, obs, lo, hi, ga: GaSettings, w=None, mu_px
     _need(w, torch.float64, (npix, 4), "w")
     _need(mu_px, torch.float64, (npix,), "mu_px")
     best = torch.empty((npix, NPAR), dtype=torch.float64, device=obs.device)
-    counts = torch.zeros(2, dtype=torch.int64, device=obs.device)
+    counts = torch.zeros(3, dtype=torch.int64, device=obs.device)
     cfg = ga.to_c(L.ME_W_USER if w is not None else L.ME_W_INVMAX)
     b = bounds(lo, hi)
     L.check(L.load().ga_count_evaluations(pb.ref(), _ptr(obs), _ptr(w), _ptr(mu_px), npix,
@@ -180,10 +185,23 @@ def ga_count_evaluations(pb: Problem, obs, lo, hi, ga: GaSettings, w=None, mu_px
                                           _ptr(counts), _stream()))
     c = counts.cpu().numpy()
     syn = int(c[0])
-    points = syn * pb.n_lambda
-    evals = points * 3 * len(pb.lines)
-    return {"syntheses": syn, "points": points, "weideman": int(c[1]), "cf": evals - int(c[1]),
+    points = syn * (pb.n_lambda + (pb.n_lambda & 1))   # padded to wavelength pairs
+    return {"syntheses": syn, "points": points, "weideman": int(c[1]), "cf": int(c[2]) - int(c[1]),
             "best": best}
+
+
+def zeeman_components(line):
+    """The library's Zeeman components of one line tuple (see Problem): list
+    of (shifts, strengths) for sigma_b, pi, sigma_r."""
+    if len(line) > 3:
+        ml = L.MeLine(line[0], line[1], line[2], 1, int(line[3]), int(line[5]), line[4], line[6])
+    else:
+        ml = L.MeLine(line[0], line[1], line[2], 0, 0, 0, 0.0, 0.0)
+    n = np.zeros(3, dtype=np.int32)
+    sh = np.zeros((3, L.ME_MAX_COMP))
+    st = np.zeros((3, L.ME_MAX_COMP))
+    L.check(L.load().me_zeeman_components(C.byref(ml), n.ctypes.data, sh.ctypes.data, st.ctypes.data))
+    return [(sh[g, :n[g]].copy(), st[g, :n[g]].copy()) for g in range(3)]
 
 
 def lm_polish(pb: Problem, obs, params, lo, hi, iters=10, lambda0=1e-3, w=None, mu_px=None):

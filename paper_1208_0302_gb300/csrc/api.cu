@@ -1,6 +1,7 @@
 // C-ABI entry points of libgenesis (see include/genesis.h): argument
 // validation, launch-parameter assembly and per-device table upload.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -129,6 +130,9 @@ int ensure_device()
 }
 
 // ------------------------------------------------------------- validation
+int zeeman_pattern(int jl, double gl, int ju, double gu, int n[3], double sh[3][ME_MAX_COMP],
+                   double st[3][ME_MAX_COMP]);
+
 int make_problem(const me_problem *pb, KProblem &k)
 {
     if (!pb) return fail(ME_EINVAL, "problem is NULL");
@@ -155,6 +159,19 @@ int make_problem(const me_problem *pb, KProblem &k)
         k.line[l].dscale = 1e-3 * ln.lambda0_A / pb->lambda_dop_A;
         k.line[l].zfac = kZeeman * ln.g_eff * ln.lambda0_A * ln.lambda0_A;
         k.line[l].half_eta = 0.5 * ln.eta_ratio;
+        k.line[l].zfacL = kZeeman * ln.lambda0_A * ln.lambda0_A;
+        if (ln.pattern) {
+            int rc = zeeman_pattern(ln.j_lower, ln.g_lower, ln.j_upper, ln.g_upper, k.line[l].ncomp,
+                                    k.line[l].cshift, k.line[l].cstr);
+            if (rc) return rc;
+            for (int g = 0; g < 3; ++g)
+                for (int i = 0; i < k.line[l].ncomp[g]; ++i) {
+                    k.line[l].cshift32[g][i] = (float)k.line[l].cshift[g][i];
+                    k.line[l].cstr32[g][i] = (float)k.line[l].cstr[g][i];
+                }
+        } else if (ln.pattern != 0) {
+            return fail(ME_EINVAL, "pattern must be 0 or 1");
+        }
     }
     for (int j = 0; j < pb->n_lambda; ++j) {
         const double v = pb->lambda_A[j];
@@ -164,6 +181,47 @@ int make_problem(const me_problem *pb, KProblem &k)
             if (v > 2.0 * k.line[l].lam0 || 2.0 * v < k.line[l].lam0)
                 return fail(ME_EINVAL, "wavelength grid more than a factor 2 from a line");
         k.lam[j] = v;
+    }
+    return ME_OK;
+}
+
+// Zeeman components of lower (J_l, g_l) -> upper (J_u, g_u) in LS coupling
+// (Section 4 full pattern), from the closed-form relative line strengths of
+// dipole transitions (Condon & Shortley) for Delta J = 0, +-1, normalised per
+// group q = M_l - M_u (-1 sigma_blue, 0 pi, +1 sigma_red).  Shift of M_u -> M_l
+// in Larmor units toward longer wavelength: g_l M_l - g_u M_u.
+int zeeman_pattern(int jl, double gl, int ju, double gu, int n[3], double sh[3][ME_MAX_COMP],
+                   double st[3][ME_MAX_COMP])
+{
+    if (jl < 0 || ju < 0 || jl > 4 || ju > 4 || std::abs(jl - ju) > 1 || (jl == 0 && ju == 0) ||
+        !std::isfinite(gl) || !std::isfinite(gu))
+        return fail(ME_EINVAL, "invalid Zeeman transition (need |J_l - J_u| <= 1, J <= 4, not 0 -> 0)");
+    const int J = ju;
+    for (int q = -1; q <= 1; ++q) {
+        const int gi = q + 1;
+        n[gi] = 0;
+        double tot = 0.0;
+        for (int mu = -ju; mu <= ju; ++mu) {
+            const int ml = mu + q;
+            if (ml < -jl || ml > jl) continue;
+            double s;
+            if (jl == ju) {  // Delta J = 0
+                s = q == 0 ? double(mu) * mu
+                           : (q < 0 ? double(J + mu) * (J - mu + 1) : double(J - mu) * (J + mu + 1));
+            } else if (ju == jl + 1) {  // J_u = J_l + 1
+                s = q == 0 ? double(J) * J - double(mu) * mu
+                           : (q < 0 ? double(J + mu) * (J + mu - 1) : double(J - mu) * (J - mu - 1));
+            } else {  // J_u = J_l - 1
+                s = q == 0 ? double(J + 1) * (J + 1) - double(mu) * mu
+                           : (q < 0 ? double(J - mu + 1) * (J - mu + 2) : double(J + mu + 1) * (J + mu + 2));
+            }
+            if (s <= 0.0) continue;
+            sh[gi][n[gi]] = gl * ml - gu * mu;
+            st[gi][n[gi]] = s;
+            tot += s;
+            ++n[gi];
+        }
+        for (int i = 0; i < n[gi]; ++i) st[gi][i] /= tot;
     }
     return ME_OK;
 }
@@ -240,7 +298,21 @@ extern "C" {
 
 const char *me_last_error(void) { return g_last_error.c_str(); }
 
-int me_version(void) { return 100; }
+int me_version(void) { return 101; }
+
+int me_zeeman_components(const me_line *line, int n[3], double shift[3][ME_MAX_COMP],
+                         double strength[3][ME_MAX_COMP])
+{
+    if (!line || !n || !shift || !strength) return fail(ME_EINVAL, "NULL argument");
+    if (line->pattern) return zeeman_pattern(line->j_lower, line->g_lower, line->j_upper, line->g_upper,
+                                             n, shift, strength);
+    for (int g = 0; g < 3; ++g) {
+        n[g] = 1;
+        shift[g][0] = (g - 1) * line->g_eff;
+        strength[g][0] = 1.0;
+    }
+    return ME_OK;
+}
 
 int me_synth(const me_problem *pb, const double *params, const double *mu_px, int n, void *stokes,
              void *stream)

@@ -85,7 +85,7 @@ template <> struct GaDecode<double> {
 // Eq. chisq for one individual, FP32 (or FP64) synthesis over the whole grid.
 // s_obs rows are (I, Q, U, V) of one wavelength; s_doff rows hold
 // lambda_j - lambda0_l for l = 0..3: one vector load each per wavelength.
-template <class R, int NL, bool COUNT>
+template <class R, int NL, bool COUNT, bool PAT>
 __device__ __forceinline__ R fitness_rows(const KProblem &pb, int nlines, int nl, const R *p, R mu,
                                           const R *s_obs, const R *s_doff, const R *he,
                                           const R *s_w2, R inv_nu, unsigned long long &ninterior)
@@ -96,8 +96,8 @@ __device__ __forceinline__ R fitness_rows(const KProblem &pb, int nlines, int nl
         R doff[4], ob[4];
         load4(s_doff + 4 * j, doff);
         load4(s_obs + 4 * j, ob);
-        const Stokes4<R> s = me_point<R, NL>(geo, doff, he, nlines);
-        if (COUNT) ninterior += count_interior<R, NL>(geo, doff, nlines);
+        const Stokes4<R> s = me_point<R, NL, PAT>(geo, doff, he, nlines, pb.line);
+        if (COUNT) ninterior += count_interior<R, NL, PAT>(geo, doff, nlines, pb.line);
         kahan_sq(sI, cI, ob[0] - s.I);
         kahan_sq(sQ, cQ, ob[1] - s.Q);
         kahan_sq(sU, cU, ob[2] - s.U);
@@ -116,7 +116,7 @@ __device__ __forceinline__ void kahan_sq2(float2 &s, float2 &c, float2 r)
 
 // Eq. chisq for one individual with the FP32 pair path (two wavelengths per
 // step, packed FP32x2 arithmetic).
-template <int NL, bool COUNT>
+template <int NL, bool COUNT, bool PAT>
 __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, int nl, const float *p,
                                                float mu, const float *s_obs, const float *s_doff,
                                                const float *he, const float *s_w2, float inv_nu,
@@ -138,7 +138,7 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
             doff2[2] = make_float2(d1.x, d1.y);
             doff2[3] = make_float2(d1.z, d1.w);
         }
-        const Stokes4x2 m = me_point_x2<NL, COUNT>(geo, doff2, he, nlines, cnt);
+        const Stokes4x2 m = me_point_x2<NL, COUNT, PAT>(geo, doff2, he, nlines, cnt, pb.line);
         float2 rI = sub2(make_float2(o0.x, o0.y), m.I), rQ = sub2(make_float2(o0.z, o0.w), m.Q);
         float2 rU = sub2(make_float2(o1.x, o1.y), m.U), rV = sub2(make_float2(o1.z, o1.w), m.V);
         if (2 * q + 1 >= nl) rI.y = rQ.y = rU.y = rV.y = 0.f;  // padded partner
@@ -152,15 +152,15 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
             s_w2[3] * (sV.x + sV.y)) * inv_nu;
 }
 
-template <class R, int NL, bool COUNT>
+template <class R, int NL, bool COUNT, bool PAT>
 __device__ __forceinline__ R fitness(const KProblem &pb, int nlines, int nl, const R *p, R mu,
                                      const R *s_obs, const R *s_doff, const R *he,
                                      const R *s_w2, R inv_nu, unsigned long long &ninterior)
 {
     if constexpr (std::is_same<R, float>::value)
-        return fitness_pairs<NL, COUNT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior);
+        return fitness_pairs<NL, COUNT, PAT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior);
     else
-        return fitness_rows<R, NL, COUNT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior);
+        return fitness_rows<R, NL, COUNT, PAT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior);
 }
 
 // argmin over the block's fitness, ties to the lowest index.  Every thread
@@ -334,7 +334,7 @@ __device__ __forceinline__ void weights_invmax_w2(const R *s_obs, int nl, R *s_w
 #define GENESIS_GA_MINB 3
 #endif
 
-template <class R, int NL, int MAXT, bool COUNT>
+template <class R, int NL, int MAXT, bool COUNT, bool PAT>
 __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(R) == 4) ? GENESIS_GA_MINB : 1)
 k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
             const R *__restrict__ obs, const double *__restrict__ w_user,
@@ -428,7 +428,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
         int cur = 0;
 #pragma unroll
         for (int d = 0; d < ME_NPAR; ++d) s_genes[k * ME_NPAR + d] = g[d];
-        s_fit[k] = clean_fit(fitness<R, NL, COUNT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior));
+        s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior));
         if (COUNT) ++nfit;
         uint64_t sobol_next = (uint64_t)npop + 1;
 
@@ -445,7 +445,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
                 p[d] = GaDecode<R>::get(ga, lo32, sc32, d, g[d]);
             }
             cur ^= 1;
-            s_fit[k] = clean_fit(fitness<R, NL, COUNT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior));
+            s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior));
             if (COUNT) ++nfit;
             // a13: worst-half Sobol restart
             if (ga.nsamp > 0 && t % ga.nsamp == 0 && t < ga.ngen) {
@@ -462,7 +462,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
                         p[d] = GaDecode<R>::get(ga, lo32, sc32, d, g[d]);
                     }
                     s_fit[k] = clean_fit(
-                        fitness<R, NL, COUNT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior));
+                        fitness<R, NL, COUNT, PAT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior));
                     if (COUNT) ++nfit;
                 }
                 sobol_next += (uint64_t)(npop / 2);
@@ -479,8 +479,16 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
         __syncthreads();  // shared memory is reused by the next pixel
     }
     if (COUNT) {
+        // evaluations per synthesis: every (padded) wavelength point runs each
+        // line's components
+        unsigned long long per_point = 0;
+        for (int l = 0; l < nlines; ++l) {
+            const int nc = pb.line[l].ncomp[0] + pb.line[l].ncomp[1] + pb.line[l].ncomp[2];
+            per_point += nc ? nc : 3;
+        }
         atomicAdd(counts + 0, nfit);
         atomicAdd(counts + 1, ninterior);
+        atomicAdd(counts + 2, nfit * (unsigned long long)padded_lambda<R>(nl) * per_point);
     }
 }
 
@@ -548,14 +556,14 @@ __global__ void k_sobol(uint64_t first, int n, int ndim, uint32_t *__restrict__ 
     out[i] = sobol_point(first + (uint64_t)pt, d);
 }
 
-template <class R, int NL, int MAXT, bool COUNT = false>
+template <class R, int NL, int MAXT, bool COUNT = false, bool PAT = false>
 cudaError_t launch_evolve_t(const KProblem &pb, const KGa &ga, const void *obs, const double *w,
                             const double *mu_px, int npix, double *best, uint16_t *best_genes,
                             cudaStream_t st, unsigned long long *counts = nullptr)
 {
     const int nlines = NL > 0 ? NL : pb.n_lines;
     const GaSmem L = ga_smem_layout<R>(pb.n_lambda, nlines, ga.npop);
-    auto kern = k_ga_evolve<R, NL, MAXT, COUNT>;
+    auto kern = k_ga_evolve<R, NL, MAXT, COUNT, PAT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     if (e != cudaSuccess) return e;
     kern<<<npix, ga.npop, L.total, st>>>(pb, ga, (const R *)obs, w, mu_px, npix, best, best_genes, counts);
@@ -564,11 +572,24 @@ cudaError_t launch_evolve_t(const KProblem &pb, const KGa &ga, const void *obs, 
 
 }  // namespace
 
+bool has_pattern(const KProblem &pb)
+{
+    for (int l = 0; l < pb.n_lines; ++l)
+        if (pb.line[l].ncomp[0] != 0) return true;
+    return false;
+}
+
 cudaError_t launch_ga_evolve(const KProblem &pb, const KGa &ga, int dtype, const void *obs,
                              const double *w, const double *mu_px, int npix, double *best,
                              uint16_t *best_genes, cudaStream_t st)
 {
     if (npix <= 0) return cudaSuccess;
+    const bool pat = has_pattern(pb);
+    if (dtype == ME_F32 && pat) {
+        if (ga.npop <= 256)
+            return launch_evolve_t<float, 0, 256, false, true>(pb, ga, obs, w, mu_px, npix, best, best_genes, st);
+        return launch_evolve_t<float, 0, 1024, false, true>(pb, ga, obs, w, mu_px, npix, best, best_genes, st);
+    }
     if (dtype == ME_F32) {
         if (ga.npop <= 256) {
             if (pb.n_lines == 1)
@@ -580,8 +601,8 @@ cudaError_t launch_ga_evolve(const KProblem &pb, const KGa &ga, int dtype, const
         return launch_evolve_t<float, 0, 1024>(pb, ga, obs, w, mu_px, npix, best, best_genes, st);
     }
     if (ga.npop <= 256)
-        return launch_evolve_t<double, 0, 256>(pb, ga, obs, w, mu_px, npix, best, best_genes, st);
-    return launch_evolve_t<double, 0, 1024>(pb, ga, obs, w, mu_px, npix, best, best_genes, st);
+        return launch_evolve_t<double, 0, 256, false, true>(pb, ga, obs, w, mu_px, npix, best, best_genes, st);
+    return launch_evolve_t<double, 0, 1024, false, true>(pb, ga, obs, w, mu_px, npix, best, best_genes, st);
 }
 
 cudaError_t launch_ga_count(const KProblem &pb, const KGa &ga, int dtype, const void *obs,
@@ -590,9 +611,11 @@ cudaError_t launch_ga_count(const KProblem &pb, const KGa &ga, int dtype, const 
 {
     if (npix <= 0) return cudaSuccess;
     if (dtype == ME_F32 && ga.npop <= 256) {
+        if (has_pattern(pb))
+            return launch_evolve_t<float, 0, 256, true, true>(pb, ga, obs, w, mu_px, npix, best, nullptr, st, counts);
         if (pb.n_lines == 2)
-            return launch_evolve_t<float, 2, 256, true>(pb, ga, obs, w, mu_px, npix, best, nullptr, st, counts);
-        return launch_evolve_t<float, 0, 256, true>(pb, ga, obs, w, mu_px, npix, best, nullptr, st, counts);
+            return launch_evolve_t<float, 2, 256, true, false>(pb, ga, obs, w, mu_px, npix, best, nullptr, st, counts);
+        return launch_evolve_t<float, 0, 256, true, false>(pb, ga, obs, w, mu_px, npix, best, nullptr, st, counts);
     }
     return cudaErrorNotSupported;
 }

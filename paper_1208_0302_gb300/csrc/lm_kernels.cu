@@ -51,7 +51,7 @@ __device__ double lm_chi2(const KProblem &pb, int nlines, int nl, const double *
         R doff[ME_MAX_LINES];
 #pragma unroll
         for (int l = 0; l < ME_MAX_LINES; ++l) doff[l] = l < nlines ? s_doff[l * nl + j] : R(0);
-        const Stokes4<R> m = me_point<R, NL>(g, doff, he, nlines);
+        const Stokes4<R> m = me_point<R, NL>(g, doff, he, nlines, pb.line);
         kahan_sq(s[0], c[0], R(o[j]) - m.I);
         kahan_sq(s[1], c[1], R(o[nl + j]) - m.Q);
         kahan_sq(s[2], c[2], R(o[2 * nl + j]) - m.U);
@@ -203,7 +203,7 @@ k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const 
                 for (int l = 0; l < ME_MAX_LINES; ++l) doff[l] = l < nlines ? s_doff[l * nl + j] : R(0);
                 Stokes4<R> m;
                 R J[4][ME_NPAR];
-                me_point_jac<R, NL>(G, doff, he, nlines, m, J);
+                me_point_jac<R, NL>(G, doff, he, nlines, pb.line, m, J);
                 const R r[4] = {R(o[j]) - m.I, R(o[nl + j]) - m.Q, R(o[2 * nl + j]) - m.U,
                                 R(o[3 * nl + j]) - m.V};
 #pragma unroll

@@ -22,12 +22,25 @@ struct KLine {
     double lam0;       // rest wavelength [A]
     double lam0_c;     // lambda0 / c [A per km/s]
     double dscale;     // 1e-3 lambda0 / lambda_dop: Doppler width [A] per mA of param 4
-    double zfac;       // 4.6686e-13 g lambda0^2 [A / G]
+    double zfac;       // 4.6686e-13 g_eff lambda0^2 [A / G] (effective triplet)
     double half_eta;   // eta_ratio / 2
+    double zfacL;      // 4.6686e-13 lambda0^2 [A / G]: Larmor displacement per gauss
+    int ncomp[3];      // full Zeeman pattern: components per group (0 = effective triplet)
+    double cshift[3][ME_MAX_COMP];  // component shifts [Larmor units, + = red]
+    double cstr[3][ME_MAX_COMP];    // component strengths (sum 1 per group)
+    float cshift32[3][ME_MAX_COMP];
+    float cstr32[3][ME_MAX_COMP];
 };
 
+template <class R> __device__ __forceinline__ R comp_shift(const KLine &ln, int g, int i);
+template <> __device__ __forceinline__ float comp_shift<float>(const KLine &ln, int g, int i) { return ln.cshift32[g][i]; }
+template <> __device__ __forceinline__ double comp_shift<double>(const KLine &ln, int g, int i) { return ln.cshift[g][i]; }
+template <class R> __device__ __forceinline__ R comp_str(const KLine &ln, int g, int i);
+template <> __device__ __forceinline__ float comp_str<float>(const KLine &ln, int g, int i) { return ln.cstr32[g][i]; }
+template <> __device__ __forceinline__ double comp_str<double>(const KLine &ln, int g, int i) { return ln.cstr[g][i]; }
+
 // Everything a synthesis needs, passed by value in the kernel parameters
-// (about 4.3 KB, within the 32 KB parameter space of sm_70+).
+// (about 6.4 KB, within the 32 KB parameter space of sm_70+).
 struct KProblem {
     int n_lines;
     int n_lambda;
@@ -241,6 +254,7 @@ template <class R> struct Geo {
     R invD[ME_MAX_LINES];   // 1 / Doppler width [1/A]
     R vB[ME_MAX_LINES];     // Zeeman splitting in Doppler units
     R cp[ME_MAX_LINES];     // -shift / D: x_pi = doff / D + cp
+    R vL[ME_MAX_LINES];     // Larmor displacement in Doppler units (full patterns)
 };
 
 __device__ __forceinline__ void sincos_deg(float d, float *s, float *c)
@@ -284,6 +298,7 @@ __device__ __forceinline__ Geo<R> make_geo(const KProblem &pb, int nlines, const
             g.invD[l] = R(1) / (p[4] * R(ln.dscale));
             g.vB[l] = R(ln.zfac) * p[0] * g.invD[l];
             g.cp[l] = -g.shift[l] * g.invD[l];
+            g.vL[l] = R(ln.zfacL) * p[0] * g.invD[l];
         }
     }
     return g;
@@ -291,22 +306,55 @@ __device__ __forceinline__ Geo<R> make_geo(const KProblem &pb, int nlines, const
 
 template <class R> struct Stokes4 { R I, Q, U, V; };
 
+// Group profiles (sigma_b, pi, sigma_r) of a line with a full Zeeman pattern:
+// each is the strength-weighted sum of its components' w(x_i + i a), with
+// x_i = doff / D + cp - v_L s_i.
+template <class R>
+__device__ __forceinline__ void pattern_profiles(const KLine &ln, R dinv, R cp, R vL, R a, R a2,
+                                                 C2<R> &wb, C2<R> &wp, C2<R> &wr)
+{
+    C2<R> out[3];
+#pragma unroll
+    for (int g = 0; g < 3; ++g) {
+        R px = R(0), py = R(0);
+        const int n = ln.ncomp[g];
+        for (int i = 0; i < n; ++i) {
+            const R x = dinv + (cp - vL * comp_shift<R>(ln, g, i));
+            const C2<R> wi = faddeeva_r2<R>(x, a, a2, x * x + a2);
+            const R st = comp_str<R>(ln, g, i);
+            px += st * wi.x;
+            py += st * wi.y;
+        }
+        out[g].x = px;
+        out[g].y = py;
+    }
+    wb = out[0];
+    wp = out[1];
+    wr = out[2];
+}
+
 // Stokes vector at one wavelength.  doff[l] = lambda_j - lambda0_l (exact in
 // FP64, rounded to R), half_eta[l] = eta_ratio_l / 2.
-template <class R, int NL>
+// PAT = false compiles out full-pattern lines (problems with effective
+// triplets only); PAT = true checks each line at run time.
+template <class R, int NL, bool PAT = true>
 __device__ __forceinline__ Stokes4<R> me_point(const Geo<R> &g, const R *doff, const R *half_eta,
-                                               int nlines)
+                                               int nlines, const KLine *lines)
 {
     R P = 0, Sg = 0, T = 0, Dd = 0, Ti = 0, Di = 0;
     const int nl = NL > 0 ? NL : nlines;
 #pragma unroll
     for (int l = 0; l < (NL > 0 ? NL : ME_MAX_LINES); ++l) {
         if (l < nl) {
-            const R v = doff[l] * g.invD[l] + g.cp[l];
-            const R xb = doff[l] * g.invD[l] + (g.cp[l] + g.vB[l]);
-            const R xr = doff[l] * g.invD[l] + (g.cp[l] - g.vB[l]);
             C2<R> wb, wp, wr;
-            faddeeva_triplet<R>(xb, v, xr, g.vB[l], g.a, g.a2, wb, wp, wr);
+            if (!PAT || lines[l].ncomp[0] == 0) {
+                const R v = doff[l] * g.invD[l] + g.cp[l];
+                const R xb = doff[l] * g.invD[l] + (g.cp[l] + g.vB[l]);
+                const R xr = doff[l] * g.invD[l] + (g.cp[l] - g.vB[l]);
+                faddeeva_triplet<R>(xb, v, xr, g.vB[l], g.a, g.a2, wb, wp, wr);
+            } else {
+                pattern_profiles<R>(lines[l], doff[l] * g.invD[l], g.cp[l], g.vL[l], g.a, g.a2, wb, wp, wr);
+            }
             const R q = half_eta[l];
             const R sx = wb.x + wr.x, sy = wb.y + wr.y;
             P += q * wp.x;
@@ -345,14 +393,22 @@ __device__ __forceinline__ Stokes4<R> me_point(const Geo<R> &g, const R *doff, c
 // Number of Faddeeva evaluations at one wavelength that take the interior
 // (Weideman) branch; the same test as faddeeva().  Used only by the counting
 // instantiation of the GA kernel, to turn branch counts into flops.
-template <class R, int NL>
-__device__ __forceinline__ unsigned count_interior(const Geo<R> &g, const R *doff, int nlines)
+template <class R, int NL, bool PAT = true>
+__device__ __forceinline__ unsigned count_interior(const Geo<R> &g, const R *doff, int nlines,
+                                                   const KLine *lines)
 {
     unsigned c = 0;
     const int nl = NL > 0 ? NL : nlines;
 #pragma unroll
     for (int l = 0; l < (NL > 0 ? NL : ME_MAX_LINES); ++l) {
-        if (l < nl) {
+        if (PAT && l < nl && lines[l].ncomp[0] != 0) {
+            const R dinv = doff[l] * g.invD[l];
+            for (int gg = 0; gg < 3; ++gg)
+                for (int i = 0; i < lines[l].ncomp[gg]; ++i) {
+                    const R x = dinv + (g.cp[l] - g.vL[l] * comp_shift<R>(lines[l], gg, i));
+                    c += (x * x + g.a2 > FadCfg<R>::R2) ? 0u : 1u;
+                }
+        } else if (l < nl) {
             const R v = doff[l] * g.invD[l] + g.cp[l];
             const R xb = doff[l] * g.invD[l] + (g.cp[l] + g.vB[l]);
             const R xr = doff[l] * g.invD[l] + (g.cp[l] - g.vB[l]);

@@ -18,6 +18,7 @@ template <class R> struct GeoJ {
     R mu;
     R kv[ME_MAX_LINES];              // d x / d v_LOS = -kv (lambda0 / c / Doppler width)
     R kB[ME_MAX_LINES];              // d v_B / d B
+    R kL[ME_MAX_LINES];              // d v_L / d B (Larmor displacement, full patterns)
 };
 
 template <class R, int NL>
@@ -51,6 +52,7 @@ __device__ __forceinline__ GeoJ<R> make_geoj(const KProblem &pb, int nlines, con
         if (l < nl) {
             G.kv[l] = R(pb.line[l].lam0_c) * G.g.invD[l];
             G.kB[l] = R(pb.line[l].zfac) * G.g.invD[l];
+            G.kL[l] = R(pb.line[l].zfacL) * G.g.invD[l];
         }
     }
     return G;
@@ -65,7 +67,8 @@ template <class R> struct Sums {
 // Stokes vector and J[s][k] = d Stokes_s / d p_k at one wavelength.
 template <class R, int NL>
 __device__ __forceinline__ void me_point_jac(const GeoJ<R> &G, const R *doff, const R *half_eta,
-                                             int nlines, Stokes4<R> &out, R J[4][ME_NPAR])
+                                             int nlines, const KLine *lines, Stokes4<R> &out,
+                                             R J[4][ME_NPAR])
 {
     const Geo<R> &g = G.g;
     Sums<R> S;
@@ -78,23 +81,51 @@ __device__ __forceinline__ void me_point_jac(const GeoJ<R> &G, const R *doff, co
     for (int l = 0; l < (NL > 0 ? NL : ME_MAX_LINES); ++l) {
         if (l < nl) {
             const R q = half_eta[l];
-            const R xs[3] = {doff[l] * g.invD[l] + (g.cp[l] + g.vB[l]),  // blue
-                             doff[l] * g.invD[l] + g.cp[l],              // pi
-                             doff[l] * g.invD[l] + (g.cp[l] - g.vB[l])}; // red
             C2<R> w[3], wd[3][4];
+            const R sv = -G.kv[l];
+            if (lines[l].ncomp[0] == 0) {
+                const R xs[3] = {doff[l] * g.invD[l] + (g.cp[l] + g.vB[l]),  // blue
+                                 doff[l] * g.invD[l] + g.cp[l],              // pi
+                                 doff[l] * g.invD[l] + (g.cp[l] - g.vB[l])}; // red
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                w[c] = faddeeva<R>(xs[c], g.a);
-                // w' = -2 z w + 2i/sqrt(pi)
-                const R dx = R(-2) * (xs[c] * w[c].x - g.a * w[c].y);
-                const R dy = R(-2) * (xs[c] * w[c].y + g.a * w[c].x) + two_isp;
-                const R sB = c == 0 ? G.kB[l] : (c == 2 ? -G.kB[l] : R(0));
-                const R sv = -G.kv[l];
-                const R sD = -xs[c] * G.invDpar;
-                wd[c][0] = {dx * sB, dy * sB};   // d/dB
-                wd[c][1] = {dx * sv, dy * sv};   // d/dv_LOS
-                wd[c][2] = {dx * sD, dy * sD};   // d/dD
-                wd[c][3] = {-dy, dx};            // d/da = i w'
+                for (int c = 0; c < 3; ++c) {
+                    w[c] = faddeeva<R>(xs[c], g.a);
+                    // w' = -2 z w + 2i/sqrt(pi)
+                    const R dx = R(-2) * (xs[c] * w[c].x - g.a * w[c].y);
+                    const R dy = R(-2) * (xs[c] * w[c].y + g.a * w[c].x) + two_isp;
+                    const R sB = c == 0 ? G.kB[l] : (c == 2 ? -G.kB[l] : R(0));
+                    const R sD = -xs[c] * G.invDpar;
+                    wd[c][0] = {dx * sB, dy * sB};   // d/dB
+                    wd[c][1] = {dx * sv, dy * sv};   // d/dv_LOS
+                    wd[c][2] = {dx * sD, dy * sD};   // d/dD
+                    wd[c][3] = {-dy, dx};            // d/da = i w'
+                }
+            } else {
+                // full pattern: strength-weighted sums over each group's
+                // components x_i = doff/D + cp - v_L s_i, dx_i/dB = -s_i k_L
+                const R dinv = doff[l] * g.invD[l];
+                for (int c = 0; c < 3; ++c) {
+                    w[c] = {R(0), R(0)};
+                    for (int d = 0; d < 4; ++d) wd[c][d] = {R(0), R(0)};
+                    for (int i = 0; i < lines[l].ncomp[c]; ++i) {
+                        const R sh = comp_shift<R>(lines[l], c, i), st = comp_str<R>(lines[l], c, i);
+                        const R x = dinv + (g.cp[l] - g.vL[l] * sh);
+                        const C2<R> wi = faddeeva<R>(x, g.a);
+                        const R dx = R(-2) * (x * wi.x - g.a * wi.y);
+                        const R dy = R(-2) * (x * wi.y + g.a * wi.x) + two_isp;
+                        const R sB = -sh * G.kL[l], sD = -x * G.invDpar;
+                        w[c].x += st * wi.x;
+                        w[c].y += st * wi.y;
+                        wd[c][0].x += st * dx * sB;
+                        wd[c][0].y += st * dy * sB;
+                        wd[c][1].x += st * dx * sv;
+                        wd[c][1].y += st * dy * sv;
+                        wd[c][2].x += st * dx * sD;
+                        wd[c][2].y += st * dy * sD;
+                        wd[c][3].x -= st * dy;
+                        wd[c][3].y += st * dx;
+                    }
+                }
             }
             const R sx = w[0].x + w[2].x, sy = w[0].y + w[2].y;
             S.P += q * w[1].x;

@@ -121,17 +121,54 @@ struct Stokes4x2 {
     float2 I, Q, U, V;
 };
 
+// Full Zeeman pattern for a pair of points: each group's strength-weighted sum
+// of components (see pattern_profiles).
+template <bool COUNT>
+__device__ __forceinline__ void pattern_profiles_x2(const KLine &ln, float2 dinv, float cp, float vL,
+                                                    float a, float a2, float2 w[6], unsigned &ncount)
+{
+#pragma unroll
+    for (int g = 0; g < 3; ++g) {
+        float2 px = f2(0.f), py = f2(0.f);
+        const int n = ln.ncomp[g];
+        for (int i = 0; i < n; ++i) {
+            const float2 x = add2(dinv, f2(cp - vL * ln.cshift32[g][i]));
+            if (COUNT) ncount += (ext1(x.x, a2) && ext1(x.y, a2)) ? 0u : 2u;
+            float2 wx, wy;
+            fad_pair(x, a, a2, wx, wy);
+            const float2 st = f2(ln.cstr32[g][i]);
+            px = fma2(st, wx, px);
+            py = fma2(st, wy, py);
+        }
+        w[2 * g] = px;
+        w[2 * g + 1] = py;
+    }
+}
+
 // Stokes vectors at two wavelength points.  doff2[l] holds (lambda_j -
 // lambda0_l, lambda_{j+1} - lambda0_l).
-template <int NL, bool COUNT>
+template <int NL, bool COUNT, bool PAT>
 __device__ __forceinline__ Stokes4x2 me_point_x2(const Geo<float> &g, const float2 *doff2,
-                                                 const float *half_eta, int nlines, unsigned &ncount)
+                                                 const float *half_eta, int nlines, unsigned &ncount,
+                                                 const KLine *lines)
 {
     float2 P = f2(0.f), Sg = f2(0.f), T = f2(0.f), Ti = f2(0.f), Dd = f2(0.f), Di = f2(0.f);
     const int nl = NL > 0 ? NL : nlines;
 #pragma unroll
     for (int l = 0; l < (NL > 0 ? NL : ME_MAX_LINES); ++l) {
-        if (l < nl) {
+        if (PAT && l < nl && lines[l].ncomp[0] != 0) {
+            float2 w[6];
+            pattern_profiles_x2<COUNT>(lines[l], mul2(doff2[l], f2(g.invD[l])), g.cp[l], g.vL[l], g.a, g.a2,
+                                       w, ncount);
+            const float2 q = f2(half_eta[l]);
+            const float2 sx = add2(w[0], w[4]), sy = add2(w[1], w[5]);
+            P = fma2(q, w[2], P);
+            Sg = fma2(q, sx, Sg);
+            T = fma2(q, fma2(f2(-0.5f), sx, w[2]), T);
+            Ti = fma2(q, fma2(f2(-0.5f), sy, w[3]), Ti);
+            Dd = fma2(q, sub2(w[4], w[0]), Dd);
+            Di = fma2(q, sub2(w[5], w[1]), Di);
+        } else if (l < nl) {
             const float2 id = f2(g.invD[l]);
             const float2 v = fma2(doff2[l], id, f2(g.cp[l]));
             const float2 xb = fma2(doff2[l], id, f2(g.cp[l] + g.vB[l]));

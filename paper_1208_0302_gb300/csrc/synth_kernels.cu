@@ -54,7 +54,7 @@ k_synth(const __grid_constant__ KProblem pb, const double *__restrict__ params,
         doff[l] = l < nlines ? s_doff[l * nl + j] : R(0);
         he[l] = s_he[l];
     }
-    const Stokes4<R> s = me_point<R, NL>(g, doff, he, nlines);
+    const Stokes4<R> s = me_point<R, NL>(g, doff, he, nlines, pb.line);
     R *o = stokes + (size_t)m * 4 * nl;
     o[j] = s.I;
     o[nl + j] = s.Q;
@@ -89,7 +89,7 @@ k_jac(const __grid_constant__ KProblem pb, const double *__restrict__ params,
     }
     Stokes4<R> s;
     R J[4][ME_NPAR];
-    me_point_jac<R, NL>(G, doff, he, nlines, s, J);
+    me_point_jac<R, NL>(G, doff, he, nlines, pb.line, s, J);
     if (stokes) {
         R *o = stokes + (size_t)m * 4 * nl;
         o[j] = s.I;
@@ -138,7 +138,7 @@ k_vjp(const __grid_constant__ KProblem pb, const double *__restrict__ params,
         for (int l = 0; l < ME_MAX_LINES; ++l) doff[l] = l < nlines ? s_doff[l * nl + j] : R(0);
         Stokes4<R> s;
         R J[4][ME_NPAR];
-        me_point_jac<R, NL>(G, doff, he, nlines, s, J);
+        me_point_jac<R, NL>(G, doff, he, nlines, pb.line, s, J);
 #pragma unroll
         for (int st = 0; st < 4; ++st) {
             const R gv = g[st * nl + j];
@@ -215,7 +215,7 @@ k_chi2_f64(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
         double doff[ME_MAX_LINES];
 #pragma unroll
         for (int l = 0; l < ME_MAX_LINES; ++l) doff[l] = l < nlines ? pb.lam[j] - pb.line[l].lam0 : 0.0;
-        const Stokes4<double> s = me_point<double, 0>(g, doff, he, nlines);
+        const Stokes4<double> s = me_point<double, 0>(g, doff, he, nlines, pb.line);
         const double r0 = (double)o[j] - s.I, r1 = (double)o[nl + j] - s.Q;
         const double r2 = (double)o[2 * nl + j] - s.U, r3 = (double)o[3 * nl + j] - s.V;
         ss[0] += r0 * r0;
