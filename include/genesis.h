@@ -312,6 +312,18 @@ int serve_stats(serve_handle *h, serve_stats_t *out);
 /* Cancel queued requests, wait for running ones, free everything. */
 int serve_destroy(serve_handle *h);
 
+/*
+ * lm_uncertainty - Section 5 uncertainty estimate at given parameters:
+ * sigma_i^2 = [H^-1]_ii chi2 / M (M = ME_NPAR) with H the Hessian of Eq. chisq
+ * in its Gauss-Newton form H = (2/nu) J^T W^2 J (exact where the residuals
+ * vanish); J analytic in the problem precision, H and its inverse in FP64.
+ *   params  dev double [npix][ME_NPAR] (e.g. the output of lm_polish)
+ *   w       dev double [npix][4] or NULL (inverse-max weights)
+ *   sigma   dev double [npix][ME_NPAR] (output); +infinity where H is singular
+ */
+int lm_uncertainty(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
+                   int npix, const double *params, double *sigma, void *stream);
+
 /* ------------------------------------------------ GA operator entry points
  * The operators of ga_invert_batch run alone on caller-given populations, so
  * that they can be checked bit for bit against a reference with injected

@@ -127,6 +127,7 @@ def lib():
             L.or_lm_polish.argtypes = [P, _D, _DN, _DN, C.c_double, C.c_int, _D, _D,
                                        C.c_int, C.c_double, _D, _D, C.c_int]
             L.or_lm_polish.restype = C.c_int
+            L.or_lm_uncertainty.argtypes = [P, _D, _DN, _DN, C.c_double, C.c_int, _D, _D]
             _lib = L
     return _lib
 
@@ -346,3 +347,15 @@ def lm_polish(pb, obs, params, lo, hi, iters=10, lambda0=1e-3, w=None, mu=1.0,
     if rc != 0:
         raise ValueError("or_lm_polish rejected its arguments")
     return p, c2
+
+
+def lm_uncertainty(pb, obs, params, w=None, mu=1.0, mu_px=None):
+    """Section 5 sigma_i = sqrt([H^-1]_ii chi2 / M), H = (2/nu) J^T W^2 J."""
+    pb = _problem(pb)
+    obs = _f64(obs)
+    npix = obs.shape[0]
+    out = np.empty((npix, NPAR))
+    lib().or_lm_uncertainty(pb.ref(), obs, None if w is None else _f64(w),
+                            None if mu_px is None else _f64(mu_px), float(mu), npix,
+                            _f64(np.reshape(params, (npix, NPAR))), out)
+    return out

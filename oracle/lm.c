@@ -161,6 +161,65 @@ static void lm_pixel(const or_problem *pb, const double *obs, const double *w,
     free(model); free(jac);
 }
 
+/*
+ * Section 5: sigma_i^2 = [H^-1]_ii chi2 / M at p, with H = (2/nu) J^T W^2 J the
+ * Gauss-Newton Hessian of Eq. chisq (J by central differences), inverted by
+ * Gauss-Jordan elimination with partial pivoting; +infinity if singular.
+ */
+static void sigma_pixel(const or_problem *pb, const double *obs, const double *w, double mu,
+                        const double *p, double *sigma)
+{
+    const int nl = pb->n_lambda, ns = 4 * nl, M = OR_NPAR;
+    double *model = (double *)malloc(sizeof(double) * ns);
+    double *jac = (double *)malloc(sizeof(double) * ns * M);
+    or_synth(pb, p, mu, model);
+    const double chi2 = or_chi2(obs, model, w, nl, M);
+    or_jacobian(pb, p, mu, jac);
+    const double nu = (double)(4 * nl - M);
+    double H[OR_NPAR][2 * OR_NPAR];
+    memset(H, 0, sizeof H);
+    for (int i = 0; i < ns; ++i) {
+        const double ws = w[i / nl] * w[i / nl];
+        for (int a = 0; a < M; ++a)
+            for (int b = 0; b < M; ++b)
+                H[a][b] += 2.0 / nu * ws * jac[(size_t)i * M + a] * jac[(size_t)i * M + b];
+    }
+    for (int a = 0; a < M; ++a) H[a][M + a] = 1.0;
+    int ok = 1;
+    for (int c = 0; c < M && ok; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < M; ++r) if (fabs(H[r][c]) > fabs(H[piv][c])) piv = r;
+        if (!(fabs(H[piv][c]) > 0.0)) { ok = 0; break; }
+        if (piv != c)
+            for (int k = 0; k < 2 * M; ++k) { double t = H[c][k]; H[c][k] = H[piv][k]; H[piv][k] = t; }
+        const double d = H[c][c];
+        for (int k = 0; k < 2 * M; ++k) H[c][k] /= d;
+        for (int r = 0; r < M; ++r) {
+            if (r == c) continue;
+            const double f = H[r][c];
+            for (int k = 0; k < 2 * M; ++k) H[r][k] -= f * H[c][k];
+        }
+    }
+    for (int a = 0; a < M; ++a) {
+        const double v = ok ? H[a][M + a] * chi2 / (double)M : INFINITY;
+        sigma[a] = ok && v >= 0.0 ? sqrt(v) : INFINITY;
+    }
+    free(model); free(jac);
+}
+
+void or_lm_uncertainty(const or_problem *pb, const double *obs, const double *w, const double *mu_px,
+                       double mu, int npix, const double *params, double *sigma)
+{
+    const int nl = pb->n_lambda;
+    for (int ip = 0; ip < npix; ++ip) {
+        const double *o = obs + (size_t)ip * 4 * nl;
+        double wv[4];
+        if (w) memcpy(wv, w + (size_t)ip * 4, sizeof wv);
+        else or_weights_invmax(o, nl, wv);
+        sigma_pixel(pb, o, wv, mu_px ? mu_px[ip] : mu, params + (size_t)ip * OR_NPAR, sigma + (size_t)ip * OR_NPAR);
+    }
+}
+
 typedef struct {
     const or_problem *pb;
     const double *obs, *w, *mu_px;

@@ -219,6 +219,19 @@ def lm_polish(pb: Problem, obs, params, lo, hi, iters=10, lambda0=1e-3, w=None, 
     return p, chi2
 
 
+def lm_uncertainty(pb: Problem, obs, params, w=None, mu_px=None):
+    """Section 5 sigma_i = sqrt([H^-1]_ii chi2 / M), H = (2/nu) J^T W^2 J -> [npix, 9]."""
+    npix = obs.shape[0]
+    _need(obs, pb.torch_dtype, (npix, 4, pb.n_lambda), "obs")
+    _need(params, torch.float64, (npix, NPAR), "params")
+    _need(w, torch.float64, (npix, 4), "w")
+    _need(mu_px, torch.float64, (npix,), "mu_px")
+    out = torch.empty((npix, NPAR), dtype=torch.float64, device=obs.device)
+    L.check(L.load().lm_uncertainty(pb.ref(), _ptr(obs), _ptr(w), _ptr(mu_px), npix, _ptr(params),
+                                    _ptr(out), _stream()))
+    return out
+
+
 # ------------------------------------------------------------------ serving
 
 def _host_f64(a, shape, name):

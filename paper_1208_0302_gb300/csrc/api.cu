@@ -456,6 +456,20 @@ int lm_polish(const me_problem *pb, const void *obs, const double *w, const doub
     return ME_OK;
 }
 
+int lm_uncertainty(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
+                   int npix, const double *params, double *sigma, void *stream)
+{
+    KProblem k;
+    int rc = make_problem(pb, k);
+    if (rc) return rc;
+    if (npix < 0) return fail(ME_EINVAL, "npix must be >= 0");
+    if (npix == 0) return ME_OK;
+    if (!obs || !params || !sigma) return fail(ME_EINVAL, "obs, params and sigma must be non-NULL");
+    if ((rc = ensure_device())) return rc;
+    cudaError_t e = launch_lm_sigma(k, pb->dtype, obs, w, mu_px, npix, params, sigma, as_stream(stream));
+    return e == cudaSuccess ? ME_OK : cuda_fail(e, "lm_uncertainty launch");
+}
+
 int ga_breed(const uint16_t *genes, const double *fitness, int nprob, int npop, uint64_t pixel_id0,
              int gen, const ga_config *cfg, uint16_t *child, int *elite, void *stream)
 {

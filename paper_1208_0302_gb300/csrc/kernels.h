@@ -63,6 +63,9 @@ cudaError_t launch_chi2_f64(const KProblem &pb, int dtype, const void *obs, cons
                             cudaStream_t st);
 
 // lm_kernels.cu
+cudaError_t launch_lm_sigma(const KProblem &pb, int dtype, const void *obs, const double *w,
+                            const double *mu_px, int npix, const double *params, double *sigma,
+                            cudaStream_t st);
 cudaError_t launch_lm(const KProblem &pb, const KLm &lm, int dtype, const void *obs,
                       const double *w, const double *mu_px, int npix, double *params,
                       cudaStream_t st);

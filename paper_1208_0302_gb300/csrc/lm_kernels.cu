@@ -109,35 +109,12 @@ struct LmWarpSmem {
     int ok;
 };
 
-template <class R, class RO, int NL>
-__global__ void __launch_bounds__(kLmWarps * 32)
-k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const RO *__restrict__ obs,
-     const double *__restrict__ w_user, const double *__restrict__ mu_px, int npix,
-     double *__restrict__ params)
+// Weights of one pixel into w2 (squared): the caller's, or Section 4.5
+// inverse-max in FP64.  Every lane gets the result.
+template <class RO>
+__device__ void lm_weights(const RO *o, int nl, const double *w_user, int pix, LmWarpSmem &W, double w2[4])
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    LmWarpSmem *s_w = (LmWarpSmem *)smem;
-    R *s_he = (R *)(smem + sizeof(LmWarpSmem) * kLmWarps);
-    R *s_doff = s_he + ME_MAX_LINES;
-    const int nl = pb.n_lambda, nlines = NL > 0 ? NL : pb.n_lines;
-    for (int i = threadIdx.x; i < nlines * nl; i += blockDim.x) {
-        const int l = i / nl, j = i - l * nl;
-        s_doff[i] = R(pb.lam[j] - pb.line[l].lam0);
-    }
-    if (threadIdx.x < ME_MAX_LINES)
-        s_he[threadIdx.x] = threadIdx.x < nlines ? R(pb.line[threadIdx.x].half_eta) : R(0);
-    __syncthreads();
-
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int pix = blockIdx.x * kLmWarps + warp;
-    if (pix >= npix) return;
-    LmWarpSmem &W = s_w[warp];
-    const RO *o = obs + (size_t)pix * 4 * nl;
-    R he[ME_MAX_LINES];
-#pragma unroll
-    for (int l = 0; l < ME_MAX_LINES; ++l) he[l] = s_he[l];
-
-    // weights (Section 4.5 inverse-max in FP64, or the caller's)
+    const int lane = threadIdx.x & 31;
     if (w_user) {
         if (lane < 4) {
             const double w = w_user[(size_t)pix * 4 + lane];
@@ -172,9 +149,94 @@ k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const 
         }
     }
     __syncwarp();
-    double w2[4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) w2[s] = W.w2[s];
+}
+
+// Normal equations at p: W.A = J^T W^2 J (full 9x9) and W.g = J^T W^2 r,
+// per-lane partial sums in R over the lane's wavelengths, warp sums in FP64.
+template <class R, class RO, int NL>
+__device__ void lm_normal(const KProblem &pb, int nlines, int nl, const double *p, double mu,
+                          const RO *o, const R *s_doff, const R *he, const R *w2r, LmWarpSmem &W)
+{
+    const int lane = threadIdx.x & 31;
+    R pr[ME_NPAR];
+#pragma unroll
+    for (int d = 0; d < ME_NPAR; ++d) pr[d] = R(p[d]);
+    const GeoJ<R> G = make_geoj<R, NL>(pb, nlines, pr, R(mu));
+    R Aacc[kNT], gacc[ME_NPAR];
+#pragma unroll
+    for (int a = 0; a < kNT; ++a) Aacc[a] = R(0);
+#pragma unroll
+    for (int a = 0; a < ME_NPAR; ++a) gacc[a] = R(0);
+    for (int j = lane; j < nl; j += 32) {
+        R doff[ME_MAX_LINES];
+#pragma unroll
+        for (int l = 0; l < ME_MAX_LINES; ++l) doff[l] = l < nlines ? s_doff[l * nl + j] : R(0);
+        Stokes4<R> m;
+        R J[4][ME_NPAR];
+        me_point_jac<R, NL>(G, doff, he, nlines, pb.line, m, J);
+        const R r[4] = {R(o[j]) - m.I, R(o[nl + j]) - m.Q, R(o[2 * nl + j]) - m.U,
+                        R(o[3 * nl + j]) - m.V};
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            int t = 0;
+#pragma unroll
+            for (int a = 0; a < ME_NPAR; ++a) {
+                const R wa = w2r[s] * J[s][a];
+                gacc[a] += wa * r[s];
+#pragma unroll
+                for (int b = 0; b <= a; ++b) Aacc[t++] += wa * J[s][b];
+            }
+        }
+    }
+    int t = 0;
+#pragma unroll
+    for (int a = 0; a < ME_NPAR; ++a) {
+        const double gv = warp_sum((double)gacc[a]);
+        if (lane == 0) W.g[a] = gv;
+#pragma unroll
+        for (int b = 0; b <= a; ++b) {
+            const double v = warp_sum((double)Aacc[t++]);
+            if (lane == 0) {
+                W.A[a * ME_NPAR + b] = v;
+                W.A[b * ME_NPAR + a] = v;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+template <class R, class RO, int NL>
+__global__ void __launch_bounds__(kLmWarps * 32)
+k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const RO *__restrict__ obs,
+     const double *__restrict__ w_user, const double *__restrict__ mu_px, int npix,
+     double *__restrict__ params)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    LmWarpSmem *s_w = (LmWarpSmem *)smem;
+    R *s_he = (R *)(smem + sizeof(LmWarpSmem) * kLmWarps);
+    R *s_doff = s_he + ME_MAX_LINES;
+    const int nl = pb.n_lambda, nlines = NL > 0 ? NL : pb.n_lines;
+    for (int i = threadIdx.x; i < nlines * nl; i += blockDim.x) {
+        const int l = i / nl, j = i - l * nl;
+        s_doff[i] = R(pb.lam[j] - pb.line[l].lam0);
+    }
+    if (threadIdx.x < ME_MAX_LINES)
+        s_he[threadIdx.x] = threadIdx.x < nlines ? R(pb.line[threadIdx.x].half_eta) : R(0);
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int pix = blockIdx.x * kLmWarps + warp;
+    if (pix >= npix) return;
+    LmWarpSmem &W = s_w[warp];
+    const RO *o = obs + (size_t)pix * 4 * nl;
+    R he[ME_MAX_LINES];
+#pragma unroll
+    for (int l = 0; l < ME_MAX_LINES; ++l) he[l] = s_he[l];
+
+    double w2[4];
+    lm_weights(o, nl, w_user, pix, W, w2);
     R w2r[4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) w2r[s] = R(w2[s]);
@@ -188,49 +250,8 @@ k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const 
     bool need = true;
     for (int it = 0; it < lm.iters; ++it) {
         if (need) {
-            R pr[ME_NPAR];
-#pragma unroll
-            for (int d = 0; d < ME_NPAR; ++d) pr[d] = R(p[d]);
-            const GeoJ<R> G = make_geoj<R, NL>(pb, nlines, pr, R(mu));
-            R Aacc[kNT], gacc[ME_NPAR];
-#pragma unroll
-            for (int a = 0; a < kNT; ++a) Aacc[a] = R(0);
-#pragma unroll
-            for (int a = 0; a < ME_NPAR; ++a) gacc[a] = R(0);
-            for (int j = lane; j < nl; j += 32) {
-                R doff[ME_MAX_LINES];
-#pragma unroll
-                for (int l = 0; l < ME_MAX_LINES; ++l) doff[l] = l < nlines ? s_doff[l * nl + j] : R(0);
-                Stokes4<R> m;
-                R J[4][ME_NPAR];
-                me_point_jac<R, NL>(G, doff, he, nlines, pb.line, m, J);
-                const R r[4] = {R(o[j]) - m.I, R(o[nl + j]) - m.Q, R(o[2 * nl + j]) - m.U,
-                                R(o[3 * nl + j]) - m.V};
-#pragma unroll
-                for (int s = 0; s < 4; ++s) {
-                    int t = 0;
-#pragma unroll
-                    for (int a = 0; a < ME_NPAR; ++a) {
-                        const R wa = w2r[s] * J[s][a];
-                        gacc[a] += wa * r[s];
-#pragma unroll
-                        for (int b = 0; b <= a; ++b) Aacc[t++] += wa * J[s][b];
-                    }
-                }
-            }
-            int t = 0;
-#pragma unroll
-            for (int a = 0; a < ME_NPAR; ++a) {
-                const double gv = warp_sum((double)gacc[a]);
-                if (lane == 0) W.g[a] = gv;
-#pragma unroll
-                for (int b = 0; b <= a; ++b) {
-                    const double v = warp_sum((double)Aacc[t++]);
-                    if (lane == 0) { W.A[a * ME_NPAR + b] = v; W.A[b * ME_NPAR + a] = v; }
-                }
-            }
+            lm_normal<R, RO, NL>(pb, nlines, nl, p, mu, o, s_doff, he, w2r, W);
             need = false;
-            __syncwarp();
         }
         if (lane == 0) {
             bool ok = false;
@@ -275,6 +296,99 @@ k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const 
     }
 }
 
+// Section 5 uncertainty estimate at given parameters: sigma_i^2 =
+// [H^-1]_ii chi2 / M with H the Gauss-Newton Hessian of Eq. chisq,
+// H = (2/nu) J^T W^2 J.  Warp per pixel; J in the problem precision, sums in
+// FP64, Cholesky inverse diagonal in FP64 (lane 0).  A parameter without
+// influence (singular H) gets +infinity.
+template <class R, class RO, int NL>
+__global__ void __launch_bounds__(kLmWarps * 32)
+k_lm_sigma(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
+           const double *__restrict__ w_user, const double *__restrict__ mu_px, int npix,
+           const double *__restrict__ params, double *__restrict__ sigma)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    LmWarpSmem *s_w = (LmWarpSmem *)smem;
+    R *s_he = (R *)(smem + sizeof(LmWarpSmem) * kLmWarps);
+    R *s_doff = s_he + ME_MAX_LINES;
+    const int nl = pb.n_lambda, nlines = NL > 0 ? NL : pb.n_lines;
+    for (int i = threadIdx.x; i < nlines * nl; i += blockDim.x) {
+        const int l = i / nl, j = i - l * nl;
+        s_doff[i] = R(pb.lam[j] - pb.line[l].lam0);
+    }
+    if (threadIdx.x < ME_MAX_LINES)
+        s_he[threadIdx.x] = threadIdx.x < nlines ? R(pb.line[threadIdx.x].half_eta) : R(0);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int pix = blockIdx.x * kLmWarps + warp;
+    if (pix >= npix) return;
+    LmWarpSmem &W = s_w[warp];
+    const RO *o = obs + (size_t)pix * 4 * nl;
+    R he[ME_MAX_LINES];
+#pragma unroll
+    for (int l = 0; l < ME_MAX_LINES; ++l) he[l] = s_he[l];
+    double w2[4];
+    lm_weights(o, nl, w_user, pix, W, w2);
+    R w2r[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) w2r[s] = R(w2[s]);
+    const double mu = mu_px ? mu_px[pix] : pb.mu;
+    double p[ME_NPAR];
+#pragma unroll
+    for (int d = 0; d < ME_NPAR; ++d) p[d] = params[(size_t)pix * ME_NPAR + d];
+    const double chi2 = lm_chi2<R, RO, NL>(pb, nlines, nl, p, mu, o, s_doff, he, w2);
+    lm_normal<R, RO, NL>(pb, nlines, nl, p, mu, o, s_doff, he, w2r, W);
+    if (lane == 0) {
+        const double nu = (double)(4 * nl - ME_NPAR);
+        // H = (2/nu) A;  [H^-1]_ii = (nu/2) [A^-1]_ii
+        double *N = W.N;
+        for (int a = 0; a < ME_NPAR * ME_NPAR; ++a) N[a] = W.A[a];
+        bool ok = true;
+        for (int j = 0; j < ME_NPAR && ok; ++j) {
+            double d = N[j * ME_NPAR + j];
+            for (int k = 0; k < j; ++k) d -= N[j * ME_NPAR + k] * N[j * ME_NPAR + k];
+            if (!(d > 0.0)) { ok = false; break; }
+            const double ljj = sqrt(d);
+            N[j * ME_NPAR + j] = ljj;
+            for (int i = j + 1; i < ME_NPAR; ++i) {
+                double t = N[i * ME_NPAR + j];
+                for (int k = 0; k < j; ++k) t -= N[i * ME_NPAR + k] * N[j * ME_NPAR + k];
+                N[i * ME_NPAR + j] = t / ljj;
+            }
+        }
+        for (int i = 0; i < ME_NPAR; ++i) {
+            double v = INFINITY;
+            if (ok) {
+                // [A^-1]_ii = || L^-1 e_i ||^2 (forward substitution of e_i)
+                double y[ME_NPAR];
+                double acc = 0.0;
+                for (int r = 0; r < ME_NPAR; ++r) {
+                    double t = (r == i) ? 1.0 : 0.0;
+                    for (int k = 0; k < r; ++k) t -= N[r * ME_NPAR + k] * y[k];
+                    y[r] = t / N[r * ME_NPAR + r];
+                    acc += y[r] * y[r];
+                }
+                v = sqrt(0.5 * nu * acc * chi2 / (double)ME_NPAR);
+            }
+            sigma[(size_t)pix * ME_NPAR + i] = v;
+        }
+    }
+}
+
+template <class R, class RO, int NL>
+cudaError_t sigma_t(const KProblem &pb, const void *obs, const double *w, const double *mu_px, int npix,
+                    const double *params, double *sigma, cudaStream_t st)
+{
+    const int nlines = NL > 0 ? NL : pb.n_lines;
+    const size_t smem = sizeof(LmWarpSmem) * kLmWarps + sizeof(R) * (ME_MAX_LINES + (size_t)nlines * pb.n_lambda);
+    auto kern = k_lm_sigma<R, RO, NL>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(npix + kLmWarps - 1) / kLmWarps, kLmWarps * 32, smem, st>>>(pb, (const RO *)obs, w, mu_px, npix,
+                                                                       params, sigma);
+    return cudaGetLastError();
+}
+
 template <class R, class RO, int NL>
 cudaError_t lm_t(const KProblem &pb, const KLm &lm, const void *obs, const double *w,
                  const double *mu_px, int npix, double *params, cudaStream_t st)
@@ -290,6 +404,19 @@ cudaError_t lm_t(const KProblem &pb, const KLm &lm, const void *obs, const doubl
 }
 
 }  // namespace
+
+cudaError_t launch_lm_sigma(const KProblem &pb, int dtype, const void *obs, const double *w,
+                            const double *mu_px, int npix, const double *params, double *sigma,
+                            cudaStream_t st)
+{
+    if (npix <= 0) return cudaSuccess;
+    if (dtype == ME_F32) {
+        if (pb.n_lines == 1) return sigma_t<float, float, 1>(pb, obs, w, mu_px, npix, params, sigma, st);
+        if (pb.n_lines == 2) return sigma_t<float, float, 2>(pb, obs, w, mu_px, npix, params, sigma, st);
+        return sigma_t<float, float, 0>(pb, obs, w, mu_px, npix, params, sigma, st);
+    }
+    return sigma_t<double, double, 0>(pb, obs, w, mu_px, npix, params, sigma, st);
+}
 
 cudaError_t launch_lm(const KProblem &pb, const KLm &lm, int dtype, const void *obs,
                       const double *w, const double *mu_px, int npix, double *params,

@@ -73,3 +73,33 @@ def test_lm_never_increases_chi2(orc):
         p, c2 = orc.lm_polish(spec, obs, start, gi.PRIOR_LO, gi.PRIOR_HI, iters=iters)
         assert np.all(c2 <= c0 * (1 + 1e-15))
         assert np.all(p >= gi.PRIOR_LO) and np.all(p <= gi.PRIOR_HI)
+
+
+def test_uncertainty_matches_finite_difference_hessian(orc):
+    """Section 5: sigma_i^2 = [H^-1]_ii chi2 / M.  The oracle forms H = (2/nu)
+    J^T W^2 J; at a least-squares optimum with small residuals this equals the
+    Hessian of chi2 itself, recomputed here by central second differences."""
+    spec = gi.two_line_spec(n_lambda=64)
+    truth = np.array([[1200.0, 55.0, 35.0, 0.5, 30.0, 0.2, 7.0, 0.35, 0.65]])
+    clean = orc.synth(spec, truth)
+    obs = clean + 1e-4 * 1.0 * gi.draw_noise(1, 64, seed=50)
+    w = np.full((1, 4), 1e4)
+    p, c2 = orc.lm_polish(spec, obs, truth, gi.PRIOR_LO, gi.PRIOR_HI, iters=40, w=w)
+    sig = orc.lm_uncertainty(spec, obs, p, w=w)[0]
+
+    def chi2(q):
+        return orc.chi2(obs[0], orc.synth(spec, q)[0], w[0])
+
+    x = p[0]
+    h = 2e-4 * np.maximum(np.abs(x), [100.0, 1.0, 1.0, 0.1, 1.0, 0.01, 0.1, 0.01, 0.01])
+    H = np.empty((9, 9))
+    for a in range(9):
+        for b in range(9):
+            def f(sa, sb):
+                q = x.copy()
+                q[a] += sa * h[a]
+                q[b] += sb * h[b]
+                return chi2(q)
+            H[a, b] = (f(1, 1) - f(1, -1) - f(-1, 1) + f(-1, -1)) / (4 * h[a] * h[b])
+    sig_fd = np.sqrt(np.diag(np.linalg.inv(H)) * c2[0] / 9)
+    assert np.max(np.abs(sig / sig_fd - 1)) < 2e-2, (sig, sig_fd)
