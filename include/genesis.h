@@ -324,6 +324,21 @@ int serve_destroy(serve_handle *h);
 int lm_uncertainty(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
                    int npix, const double *params, double *sigma, void *stream);
 
+/*
+ * me_line_centre - Section 4.1 line-centre estimate by centre of symmetry:
+ * S_i = sum_{j=1..W} |I(lambda_{i+j}) - I(lambda_{i-j})|, lambda_sym = the
+ * lambda_i minimising S over candidates i in [i_lo, i_hi] intersected with
+ * [W, n_lambda-1-W] (ties: lowest index), refined by the vertex of the
+ * parabola through (lambda, S) at i-1, i, i+1 when both are candidates.  All
+ * in FP64.
+ *   obs        dev [npix][4][n_lambda] of pb->dtype (the Stokes I rows are used)
+ *   half_width W >= 1 grid points
+ *   lambda_c   dev double [npix] (output; NaN if no candidate)
+ *   index      dev int [npix] (output, argmin index or -1; may be NULL)
+ */
+int me_line_centre(const me_problem *pb, const void *obs, int npix, int half_width, int i_lo,
+                   int i_hi, double *lambda_c, int *index, void *stream);
+
 /* ------------------------------------------------ GA operator entry points
  * The operators of ga_invert_batch run alone on caller-given populations, so
  * that they can be checked bit for bit against a reference with injected

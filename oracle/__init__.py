@@ -127,6 +127,8 @@ def lib():
             L.or_lm_polish.argtypes = [P, _D, _DN, _DN, C.c_double, C.c_int, _D, _D,
                                        C.c_int, C.c_double, _D, _D, C.c_int]
             L.or_lm_polish.restype = C.c_int
+            L.or_line_centre.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, C.c_int, C.c_int, C.c_int,
+                                         _D, _I32]
             L.or_lm_uncertainty.argtypes = [P, _D, _DN, _DN, C.c_double, C.c_int, _D, _D]
             _lib = L
     return _lib
@@ -359,3 +361,15 @@ def lm_uncertainty(pb, obs, params, w=None, mu=1.0, mu_px=None):
                             None if mu_px is None else _f64(mu_px), float(mu), npix,
                             _f64(np.reshape(params, (npix, NPAR))), out)
     return out
+
+
+def line_centre(obs, lambda_grid, half_width, i_lo=0, i_hi=1 << 30):
+    """Section 4.1 centre-of-symmetry line centre of each pixel's Stokes I
+    (obs [npix, 4, n_lambda]) -> (lambda_c [npix], index [npix])."""
+    obs = _f64(obs)
+    npix, _, nl = obs.shape
+    lc = np.empty(npix)
+    idx = np.empty(npix, dtype=np.int32)
+    lib().or_line_centre(obs, npix, 4 * nl, nl, _f64(lambda_grid), int(half_width), int(i_lo),
+                         int(i_hi), lc, idx)
+    return lc, idx

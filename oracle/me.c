@@ -268,3 +268,47 @@ void or_faddeeva_batch(int n, const double *x, const double *y, double *re, doub
 {
     for (int i = 0; i < n; ++i) or_faddeeva(x[i], y[i], re + i, im + i);
 }
+
+/*
+ * Section 4.1: line centre by centre of symmetry.  For candidate index i,
+ * S_i = sum_{j=1..W} |I(lambda_{i+j}) - I(lambda_{i-j})| (W = half_width, in
+ * grid points); lambda_sym = argmin_i S_i over i in [i_lo, i_hi] restricted to
+ * [W, N-1-W] (ties: lowest index), refined by the vertex of the parabola
+ * through (lambda, S) at i-1, i, i+1 when both neighbours are candidates.
+ * I rows are read with the given stride (4 n_lambda for a Stokes cube).
+ */
+static double sym_S(const double *row, int i, int W)
+{
+    double s = 0.0;
+    for (int j = 1; j <= W; ++j) s += fabs(row[i + j] - row[i - j]);
+    return s;
+}
+
+void or_line_centre(const double *rows, int npix, int stride, int nl, const double *lam, int half_width,
+                    int i_lo, int i_hi, double *lam_c, int *idx)
+{
+    const int W = half_width;
+    const int lo = i_lo > W ? i_lo : W;
+    const int hi = i_hi < nl - 1 - W ? i_hi : nl - 1 - W;
+    for (int ip = 0; ip < npix; ++ip) {
+        const double *row = rows + (size_t)ip * stride;
+        double best = INFINITY;
+        int bi = -1;
+        for (int i = lo; i <= hi; ++i) {
+            const double s = sym_S(row, i, W);
+            if (s < best) { best = s; bi = i; }
+        }
+        idx[ip] = bi;
+        if (bi < 0) { lam_c[ip] = NAN; continue; }
+        double xc = lam[bi];
+        if (bi - 1 >= lo && bi + 1 <= hi) {
+            const double x0 = lam[bi - 1], x1 = lam[bi], x2 = lam[bi + 1];
+            const double y0 = sym_S(row, bi - 1, W), y1 = best, y2 = sym_S(row, bi + 1, W);
+            const double d0 = x1 - x0, d2 = x1 - x2, e0 = y1 - y0, e2 = y1 - y2;
+            const double num = d0 * d0 * e2 - d2 * d2 * e0;
+            const double den = d0 * e2 - d2 * e0;
+            if (den != 0.0) xc = x1 - 0.5 * num / den;
+        }
+        lam_c[ip] = xc;
+    }
+}

@@ -131,6 +131,10 @@ int or_lm_polish(const or_problem *pb, const double *obs, const double *w,
                  const double *hi, int iters, double lambda0,
                  double *params_inout, double *chi2_out, int nthreads);
 
+/* Section 4.1 line centre by centre of symmetry (see me.c). */
+void or_line_centre(const double *rows, int npix, int stride, int nl, const double *lam, int half_width,
+                    int i_lo, int i_hi, double *lam_c, int *idx);
+
 /* Section 5 uncertainties sigma [npix][OR_NPAR] at params. */
 void or_lm_uncertainty(const or_problem *pb, const double *obs, const double *w, const double *mu_px,
                        double mu, int npix, const double *params, double *sigma);

@@ -102,6 +102,7 @@ _SIGNATURES = {
     "lm_polish": ([_P, _VP, _VP, _VP, C.c_int, C.POINTER(MeBounds), C.c_int, C.c_double, _VP,
                    _VP, _VP], C.c_int),
     "lm_uncertainty": ([_P, _VP, _VP, _VP, C.c_int, _VP, _VP, _VP], C.c_int),
+    "me_line_centre": ([_P, _VP, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP], C.c_int),
     "ga_breed": ([_VP, _VP, C.c_int, C.c_int, C.c_uint64, C.c_int, C.POINTER(GaConfig), _VP, _VP,
                   _VP], C.c_int),
     "ga_restart": ([_VP, _VP, C.c_int, C.c_int, C.c_uint64, _VP], C.c_int),

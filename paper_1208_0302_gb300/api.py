@@ -232,6 +232,17 @@ def lm_uncertainty(pb: Problem, obs, params, w=None, mu_px=None):
     return out
 
 
+def line_centre(pb: Problem, obs, half_width, i_lo=0, i_hi=1 << 30):
+    """Section 4.1 centre-of-symmetry line centre -> (lambda_c [npix] f64, index [npix] i32)."""
+    npix = obs.shape[0]
+    _need(obs, pb.torch_dtype, (npix, 4, pb.n_lambda), "obs")
+    lc = torch.empty(npix, dtype=torch.float64, device=obs.device)
+    idx = torch.empty(npix, dtype=torch.int32, device=obs.device)
+    L.check(L.load().me_line_centre(pb.ref(), _ptr(obs), npix, int(half_width), int(i_lo), int(i_hi),
+                                    _ptr(lc), _ptr(idx), _stream()))
+    return lc, idx
+
+
 # ------------------------------------------------------------------ serving
 
 def _host_f64(a, shape, name):

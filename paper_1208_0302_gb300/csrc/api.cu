@@ -1,5 +1,6 @@
 // C-ABI entry points of libgenesis (see include/genesis.h): argument
 // validation, launch-parameter assembly and per-device table upload.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -468,6 +469,22 @@ int lm_uncertainty(const me_problem *pb, const void *obs, const double *w, const
     if ((rc = ensure_device())) return rc;
     cudaError_t e = launch_lm_sigma(k, pb->dtype, obs, w, mu_px, npix, params, sigma, as_stream(stream));
     return e == cudaSuccess ? ME_OK : cuda_fail(e, "lm_uncertainty launch");
+}
+
+int me_line_centre(const me_problem *pb, const void *obs, int npix, int half_width, int i_lo,
+                   int i_hi, double *lambda_c, int *index, void *stream)
+{
+    KProblem k;
+    int rc = make_problem(pb, k);
+    if (rc) return rc;
+    if (npix < 0 || half_width < 1) return fail(ME_EINVAL, "need npix >= 0 and half_width >= 1");
+    if (npix == 0) return ME_OK;
+    if (!obs || !lambda_c) return fail(ME_EINVAL, "obs and lambda_c must be non-NULL");
+    const int lo = std::max(i_lo, half_width), hi = std::min(i_hi, pb->n_lambda - 1 - half_width);
+    if ((rc = ensure_device())) return rc;
+    cudaError_t e = launch_line_centre(k, pb->dtype, obs, npix, half_width, lo, hi, lambda_c, index,
+                                       as_stream(stream));
+    return e == cudaSuccess ? ME_OK : cuda_fail(e, "me_line_centre launch");
 }
 
 int ga_breed(const uint16_t *genes, const double *fitness, int nprob, int npop, uint64_t pixel_id0,

@@ -62,6 +62,9 @@ cudaError_t launch_chi2_f64(const KProblem &pb, int dtype, const void *obs, cons
                             const double *mu_px, int npix, const double *params, double *chi2,
                             cudaStream_t st);
 
+cudaError_t launch_line_centre(const KProblem &pb, int dtype, const void *obs, int npix, int W, int lo,
+                               int hi, double *lam_c, int *idx, cudaStream_t st);
+
 // lm_kernels.cu
 cudaError_t launch_lm_sigma(const KProblem &pb, int dtype, const void *obs, const double *w,
                             const double *mu_px, int npix, const double *params, double *sigma,

@@ -242,6 +242,57 @@ k_chi2_f64(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
     }
 }
 
+// Section 4.1 centre of symmetry, one warp per pixel: lanes scan candidates,
+// each sums |I(i+j) - I(i-j)| in FP64 in increasing j; warp argmin (ties to
+// the lowest index); lane 0 refines with the three-point parabola vertex,
+// written without contraction.
+template <class RO>
+__global__ void __launch_bounds__(kSynthBlock)
+k_line_centre(const __grid_constant__ KProblem pb, const RO *__restrict__ obs, int npix, int W, int lo,
+              int hi, double *__restrict__ lam_c, int *__restrict__ idx)
+{
+    const int lane = threadIdx.x & 31;
+    const int pix = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (pix >= npix) return;
+    const int nl = pb.n_lambda;
+    const RO *I = obs + (size_t)pix * 4 * nl;
+    auto S = [&](int i) {
+        double s = 0.0;
+        for (int j = 1; j <= W; ++j) s = __dadd_rn(s, fabs(__dsub_rn((double)I[i + j], (double)I[i - j])));
+        return s;
+    };
+    double best = INFINITY;
+    int bi = 0x7fffffff;
+    for (int i = lo + lane; i <= hi; i += 32) {
+        const double s = S(i);
+        if (s < best || (s == best && i < bi)) { best = s; bi = i; }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double os = __shfl_xor_sync(0xffffffffu, best, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (os < best || (os == best && oi < bi)) { best = os; bi = oi; }
+    }
+    if (lane != 0) return;
+    if (bi == 0x7fffffff) {
+        lam_c[pix] = NAN;
+        if (idx) idx[pix] = -1;
+        return;
+    }
+    double xc = pb.lam[bi];
+    if (bi - 1 >= lo && bi + 1 <= hi) {
+        const double x0 = pb.lam[bi - 1], x1 = pb.lam[bi], x2 = pb.lam[bi + 1];
+        const double y0 = S(bi - 1), y1 = best, y2 = S(bi + 1);
+        const double d0 = __dsub_rn(x1, x0), d2 = __dsub_rn(x1, x2);
+        const double e0 = __dsub_rn(y1, y0), e2 = __dsub_rn(y1, y2);
+        const double num = __dsub_rn(__dmul_rn(__dmul_rn(d0, d0), e2), __dmul_rn(__dmul_rn(d2, d2), e0));
+        const double den = __dsub_rn(__dmul_rn(d0, e2), __dmul_rn(d2, e0));
+        if (den != 0.0) xc = __dsub_rn(x1, __dmul_rn(0.5, __ddiv_rn(num, den)));
+    }
+    lam_c[pix] = xc;
+    if (idx) idx[pix] = bi;
+}
+
 template <class R> size_t offsets_smem(const KProblem &pb)
 {
     return sizeof(R) * (ME_MAX_LINES + (size_t)pb.n_lines * pb.n_lambda);
@@ -314,6 +365,20 @@ cudaError_t launch_vjp(const KProblem &pb, int dtype, const double *params, cons
         return vjp_t<float, 0>(pb, params, mu_px, n, gs, gp, st);
     }
     return vjp_t<double, 0>(pb, params, mu_px, n, gs, gp, st);
+}
+
+cudaError_t launch_line_centre(const KProblem &pb, int dtype, const void *obs, int npix, int W, int lo,
+                               int hi, double *lam_c, int *idx, cudaStream_t st)
+{
+    if (npix <= 0) return cudaSuccess;
+    const int per = kSynthBlock / 32;
+    if (dtype == ME_F32)
+        k_line_centre<float><<<(npix + per - 1) / per, kSynthBlock, 0, st>>>(pb, (const float *)obs, npix, W, lo,
+                                                                            hi, lam_c, idx);
+    else
+        k_line_centre<double><<<(npix + per - 1) / per, kSynthBlock, 0, st>>>(pb, (const double *)obs, npix, W,
+                                                                             lo, hi, lam_c, idx);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_chi2_f64(const KProblem &pb, int dtype, const void *obs, const double *w,

@@ -1,0 +1,51 @@
+"""Pins of the oracle's Section 4.1 centre-of-symmetry line centre."""
+import numpy as np
+
+import genesis_inputs as gi
+
+
+def _cube(I):
+    obs = np.zeros((I.shape[0], 4, I.shape[1]))
+    obs[:, 0] = I
+    return obs
+
+
+def test_symmetric_line_on_grid_point_is_exact(orc):
+    lam = np.linspace(6302.0, 6303.0, 101)
+    c = lam[57]
+    I = 1 - 0.5 * np.exp(-((lam - c) / 0.08) ** 2)
+    lc, idx = orc.line_centre(_cube(I[None]), lam, half_width=12)
+    assert idx[0] == 57 and lc[0] == c
+
+
+def test_subgrid_centres_of_gaussians(orc):
+    lam = np.linspace(6302.0, 6303.0, 101)
+    d = lam[1] - lam[0]
+    for frac in np.linspace(-0.45, 0.45, 10):
+        c = lam[50] + frac * d
+        I = 1 - 0.6 * np.exp(-((lam - c) / 0.07) ** 2)
+        # candidates bracket the core (far from the line the flat continuum is
+        # trivially symmetric, so the search window must hold the core)
+        lc, idx = orc.line_centre(_cube(I[None]), lam, half_width=10, i_lo=45, i_hi=55)
+        assert abs(idx[0] - 50) <= 1
+        assert abs(lc[0] - c) < 0.1 * d, (frac, (lc[0] - c) / d)   # S is V-shaped: <= 0.09 step bias
+
+
+def test_recovers_doppler_shift_of_field_free_me_line(orc):
+    l0 = gi.FE6302[0]
+    lam = np.linspace(l0 - 0.5, l0 + 0.5, 81)
+    spec = gi.ProblemSpec(lines=[(l0, 2.5, 1.0)], lambda_grid=lam)
+    P = gi.draw_params_uniform(20, seed=90)
+    P[:, 0] = 0.0
+    obs = orc.synth(spec, P)
+    # +-3 km/s is +-5 grid points around lambda0 (index 40)
+    lc, idx = orc.line_centre(obs, lam, half_width=8, i_lo=34, i_hi=46)
+    expect = l0 * (1 + P[:, 3] / 299792.458)
+    d = lam[1] - lam[0]
+    assert np.max(np.abs(lc - expect)) < 0.1 * d
+
+
+def test_no_candidate(orc):
+    lam = np.linspace(6302.0, 6303.0, 11)
+    lc, idx = orc.line_centre(_cube(np.ones((1, 11))), lam, half_width=6)
+    assert idx[0] == -1 and np.isnan(lc[0])
