@@ -88,6 +88,7 @@ def _optional(arr_type):
 
 _DN = _optional(_D)
 _U16N = _optional(_U16)
+_I32N = _optional(_I32)
 
 
 def lib():
@@ -120,8 +121,12 @@ def lib():
             L.or_ga_breed.restype = C.c_int
             L.or_ga_restart.argtypes = [_U16, _D, C.c_int, C.c_int, C.c_uint64, _I32]
             L.or_ga_invert.argtypes = [P, _D, _DN, _DN, C.c_double, C.c_int, C.c_uint64,
-                                       _D, _D, C.POINTER(_GaConfig), _D, _D, _U16N, _DN,
-                                       C.c_int]
+                                       _D, _D, C.POINTER(_GaConfig), _DN, C.c_int, _I32N,
+                                       _D, _D, _U16N, _DN, C.c_int]
+            L.or_ga_encode.argtypes = [C.c_double, C.c_double, C.c_double]
+            L.or_ga_encode.restype = C.c_uint16
+            L.or_polarity_bounds.argtypes = [C.c_int, C.c_double, C.c_double, C.POINTER(C.c_double),
+                                             C.POINTER(C.c_double)]
             L.or_ga_invert.restype = C.c_int
             L.or_jacobian.argtypes = [P, _D, C.c_double, _D]
             L.or_lm_polish.argtypes = [P, _D, _DN, _DN, C.c_double, C.c_int, _D, _D,
@@ -129,6 +134,8 @@ def lib():
             L.or_lm_polish.restype = C.c_int
             L.or_line_centre.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, C.c_int, C.c_int, C.c_int,
                                          _D, _I32]
+            L.or_classify.argtypes = [P, _D, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int,
+                                      C.c_int, _I32, _I32, _D, _D, _D]
             L.or_lm_uncertainty.argtypes = [P, _D, _DN, _DN, C.c_double, C.c_int, _D, _D]
             _lib = L
     return _lib
@@ -303,19 +310,26 @@ def ga_restart(genes, f, sobol_next):
 
 
 def ga_invert(pb, obs, lo, hi, cfg, w=None, mu=1.0, mu_px=None, pixel_id0=0,
-              nthreads=None, want_margin=False):
-    """Algorithm 1 per pixel; returns dict(best, chi2, genes[, margin])."""
+              nthreads=None, want_margin=False, seeds=None, polarity=None):
+    """Algorithm 1 per pixel; returns dict(best, chi2, genes[, margin]).
+    seeds [npix][nseed][3] (B, psi, chi) and polarity [npix] of Section 4.5."""
     pb = _problem(pb)
     obs = _f64(obs)
     npix = obs.shape[0]
+    nseed = 0
+    if seeds is not None:
+        seeds = _f64(np.asarray(seeds, dtype=np.float64).reshape(npix, -1, 3))
+        nseed = seeds.shape[1]
+    if polarity is not None:
+        polarity = np.ascontiguousarray(polarity, dtype=np.int32).reshape(npix)
     best = np.empty((npix, NPAR))
     c2 = np.empty(npix)
     genes = np.empty((npix, NPAR), dtype=np.uint16)
     margin = np.empty(npix) if want_margin else None
     rc = lib().or_ga_invert(pb.ref(), obs, None if w is None else _f64(w),
                             None if mu_px is None else _f64(mu_px), float(mu), npix,
-                            int(pixel_id0), _f64(lo), _f64(hi), C.byref(cfg), best, c2,
-                            genes, margin, nthreads or nthreads_default())
+                            int(pixel_id0), _f64(lo), _f64(hi), C.byref(cfg), seeds, nseed,
+                            polarity, best, c2, genes, margin, nthreads or nthreads_default())
     if rc != 0:
         raise ValueError("or_ga_invert rejected its arguments")
     out = {"best": best, "chi2": c2, "genes": genes}
@@ -373,3 +387,35 @@ def line_centre(obs, lambda_grid, half_width, i_lo=0, i_hi=1 << 30):
     lib().or_line_centre(obs, npix, 4 * nl, nl, _f64(lambda_grid), int(half_width), int(i_lo),
                          int(i_hi), lc, idx)
     return lc, idx
+
+
+def classify(pb, obs, p_thresh, quiet, line, core):
+    """Section 2 selection, weak-field fallback and Section 4.5 seeds.
+    quiet = (lo, hi) half-open quiet window, core = (lo, hi) inclusive line
+    window.  Returns dict(flag, polarity, p, sigma_p, B, theta, chi, B_par,
+    B_perp, seeds [npix][4][3] = (B, psi, chi) of the weak-field, integral,
+    centre-of-gravity and non-magnetic seeds)."""
+    pb = _problem(pb)
+    obs = _f64(obs)
+    npix = obs.shape[0]
+    flag = np.empty(npix, dtype=np.int32)
+    pol = np.empty(npix, dtype=np.int32)
+    pp = np.empty((npix, 2))
+    weak = np.empty((npix, 5))
+    seeds = np.empty((npix, 4, 3))
+    lib().or_classify(pb.ref(), obs, npix, float(p_thresh), int(quiet[0]), int(quiet[1]), int(line),
+                      int(core[0]), int(core[1]), flag, pol, pp, weak, seeds)
+    return {"flag": flag, "polarity": pol, "p": pp[:, 0], "sigma_p": pp[:, 1], "B": weak[:, 0],
+            "theta": weak[:, 1], "chi": weak[:, 2], "B_par": weak[:, 3], "B_perp": weak[:, 4], "seeds": seeds}
+
+
+def ga_encode(x, lo, hi):
+    """Nearest gene of a seed value (the inverse of the decode)."""
+    return int(lib().or_ga_encode(float(x), float(lo), float(hi)))
+
+
+def polarity_bounds(pol, lo, hi):
+    """Inclination domain of Section 4.5's polarity restriction."""
+    a, b = C.c_double(), C.c_double()
+    lib().or_polarity_bounds(int(pol), float(lo), float(hi), C.byref(a), C.byref(b))
+    return a.value, b.value

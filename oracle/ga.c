@@ -157,6 +157,28 @@ void or_ga_decode(const uint16_t *g, const double *lo, const double *hi, int m, 
     decode(g, lo, hi, m, p);
 }
 
+/* The inverse of the decode for a seed value, rounded to the nearest gene:
+ * t = (x - u) / (v - u) clamped to [0, 1], g = floor(t (2^N - 1) + 1/2). */
+uint16_t or_ga_encode(double x, double lo, double hi)
+{
+    double t = (x - lo) / (hi - lo);
+    if (!(t > 0.0)) t = 0.0;
+    if (t > 1.0) t = 1.0;
+    return (uint16_t)floor(t * 65535.0 + 0.5);
+}
+
+/* Section 4.5 polarity restriction of the inclination domain: +1 keeps
+ * [u, min(v, 90)], -1 keeps [max(u, 90), v], 0 (or an empty half) keeps [u, v]. */
+void or_polarity_bounds(int pol, double lo, double hi, double *plo, double *phi)
+{
+    double a = lo, b = hi;
+    if (pol > 0 && hi > 90.0) b = 90.0;
+    if (pol < 0 && lo < 90.0) a = 90.0;
+    if (!(a < b)) { a = lo; b = hi; }
+    *plo = a;
+    *phi = b;
+}
+
 /* ---------------------------------------------------------------- margins */
 
 static inline double rel_gap(double a, double b)
@@ -211,8 +233,11 @@ typedef struct {
     double mu;
     int npix;
     uint64_t pid0;
-    const double *lo, *hi;
+    const double *glo, *ghi;
     const or_ga_config *cfg;
+    const double *seeds;
+    int nseed;
+    const int *polarity;
     double *best, *chi2, *margin;
     uint16_t *best_genes;
     int t0, t1;
@@ -235,6 +260,10 @@ static void ga_pixel(const ga_job *J, int ip)
     const double *obs = J->obs + (size_t)ip * 4 * nl;
     const double mu = J->mu_px ? J->mu_px[ip] : J->mu;
     const uint64_t pid = J->pid0 + (uint64_t)ip;
+    double lo[OR_NPAR], hi[OR_NPAR];
+    memcpy(lo, J->glo, sizeof lo);
+    memcpy(hi, J->ghi, sizeof hi);
+    if (J->polarity) or_polarity_bounds(J->polarity[ip], J->glo[1], J->ghi[1], &lo[1], &hi[1]);
     double w[4];
     if (J->w) memcpy(w, J->w + (size_t)ip * 4, sizeof w);
     else or_weights_invmax(obs, nl, w);
@@ -246,11 +275,18 @@ static void ga_pixel(const ga_job *J, int ip)
     int *replaced = (int *)malloc(sizeof(int) * npop);
     double margin = INFINITY;
 
-    /* create P0 from Sobol points 1..npop and evaluate F0 */
+    /* create P0 from Sobol points 1..npop, the last nseed individuals taking
+     * the seeds' (B, psi, chi) genes (Section 4.5), and evaluate F0 */
     for (int k = 0; k < npop; ++k) {
         for (int d = 0; d < m; ++d)
             genes[(size_t)k * m + d] = (uint16_t)(or_sobol_u32((uint64_t)(k + 1), d) >> 16);
-        f[k] = fitness(pb, obs, w, mu, genes + (size_t)k * m, J->lo, J->hi, model);
+        const int si = k - (npop - J->nseed);
+        if (si >= 0) {
+            const double *sd = J->seeds + ((size_t)ip * J->nseed + si) * 3;
+            for (int d = 0; d < 3; ++d)
+                if (sd[d] == sd[d]) genes[(size_t)k * m + d] = or_ga_encode(sd[d], lo[d], hi[d]);
+        }
+        f[k] = fitness(pb, obs, w, mu, genes + (size_t)k * m, lo, hi, model);
     }
     uint64_t sobol_next = (uint64_t)npop + 1;
     const int ngen = J->cfg->ngen, nsamp = J->cfg->nsamp;
@@ -261,13 +297,13 @@ static void ga_pixel(const ga_job *J, int ip)
         uint16_t *tmp = genes; genes = child; child = tmp;
         f[0] = fe;
         for (int k = 1; k < npop; ++k)
-            f[k] = fitness(pb, obs, w, mu, genes + (size_t)k * m, J->lo, J->hi, model);
+            f[k] = fitness(pb, obs, w, mu, genes + (size_t)k * m, lo, hi, model);
         if (nsamp > 0 && t % nsamp == 0 && t < ngen) {
             if (J->margin) restart_margin(&margin, genes, f, npop, m);
             or_ga_restart(genes, f, npop, m, sobol_next, replaced);
             for (int r = 0; r < npop / 2; ++r) {
                 const int k = replaced[r];
-                f[k] = fitness(pb, obs, w, mu, genes + (size_t)k * m, J->lo, J->hi, model);
+                f[k] = fitness(pb, obs, w, mu, genes + (size_t)k * m, lo, hi, model);
             }
             sobol_next += (uint64_t)(npop / 2);
         }
@@ -281,7 +317,7 @@ static void ga_pixel(const ga_job *J, int ip)
     }
     const int b = argmin_f(f, npop);
     double *best = J->best + (size_t)ip * m;
-    decode(genes + (size_t)b * m, J->lo, J->hi, m, best);
+    decode(genes + (size_t)b * m, lo, hi, m, best);
     or_synth(pb, best, mu, model);
     J->chi2[ip] = or_chi2(obs, model, w, nl, m);
     if (J->best_genes) memcpy(J->best_genes + (size_t)ip * m, genes + (size_t)b * m, sizeof(uint16_t) * m);
@@ -298,17 +334,19 @@ static void *ga_worker(void *arg)
 int or_ga_invert(const or_problem *pb, const double *obs, const double *w,
                  const double *mu_px, double mu, int npix, uint64_t pid0,
                  const double *lo, const double *hi, const or_ga_config *cfg,
+                 const double *seeds, int nseed, const int *polarity,
                  double *best, double *chi2, uint16_t *best_genes,
                  double *margin, int nthreads)
 {
     if (cfg->npop < 2 || (cfg->npop & 1) || cfg->ngen < 0 || npix < 0) return 1;
+    if (nseed < 0 || nseed > cfg->npop / 2 || (nseed > 0 && !seeds)) return 1;
     if (nthreads < 1) nthreads = 1;
     if (nthreads > npix) nthreads = npix > 0 ? npix : 1;
     pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * nthreads);
     ga_job *jobs = (ga_job *)malloc(sizeof(ga_job) * nthreads);
     for (int t = 0; t < nthreads; ++t) {
-        ga_job J = {pb, obs, w, mu_px, mu, npix, pid0, lo, hi, cfg, best, chi2, margin,
-                    best_genes, (int)((long)npix * t / nthreads),
+        ga_job J = {pb, obs, w, mu_px, mu, npix, pid0, lo, hi, cfg, seeds, nseed, polarity,
+                    best, chi2, margin, best_genes, (int)((long)npix * t / nthreads),
                     (int)((long)npix * (t + 1) / nthreads)};
         jobs[t] = J;
         pthread_create(&th[t], NULL, ga_worker, &jobs[t]);

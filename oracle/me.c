@@ -312,3 +312,171 @@ void or_line_centre(const double *rows, int npix, int stride, int nl, const doub
         lam_c[ip] = xc;
     }
 }
+
+/*
+ * Section 2 pixel selection, the weak-field fallback and the Section 4.5
+ * seeds.  Window sums run in index order; extrema take the lowest index on ties.
+ *   Threshold: I_c = mean of I over the quiet window [q_lo, q_hi); sigma_s^2
+ *   the (1/n) variance of s = Q, U, V there; p = sqrt(Qmax^2 + Umax^2 +
+ *   Vmax^2) / I_c with X_max = max |X| over the whole grid; sigma_P = P_thresh
+ *   sqrt(sigma_Q^2 + sigma_U^2 + sigma_V^2) / I_c; flag = p > sigma_P.
+ *   Line window [c_lo, c_hi] (inclusive) of line `line` (g, lambda0),
+ *   kz = 4.6686e-13 g lambda0^2 (Angstrom per gauss).
+ *   Weak field (Auer et al. 1977): the I+V and I-V cores are argmins refined
+ *   by the parabola vertex through i-1, i, i+1; B_par = (lambda(I+V) -
+ *   lambda(I-V)) / (2 kz).  m = argmax of Q^2 + U^2; chi = atan2(-s U_m,
+ *   -s Q_m)/2 in [0, 180) with s = -1 where I''_m < 0 (a sigma lobe: the linear
+ *   polarization there has the sign opposite to the line core's), else +1; B_perp = sqrt(4 L_m / D2) / kz with L_m = sqrt(Q_m^2 + U_m^2)
+ *   and D2 = max |I''| (three-point second differences); theta = atan2(B_perp,
+ *   B_par) in degrees, B = sqrt(B_par^2 + B_perp^2).
+ *   Polarity: +1 when the positive V lobe lies blueward of the negative one
+ *   (argmax V < argmin V), -1 when redward, 0 when they coincide.
+ *   Seeds (B, psi, chi) rows: 0 weak field; 1 integral form of the same
+ *   relations, B_par = s int|V| / (kz TV(I)), B_perp = sqrt(4 int L / TV(I')) / kz
+ *   (TV = total variation over the window, trapezoid integrals, s the polarity,
+ *   +1 when 0); 2 centre of gravity of I_c - (I +- V) (Rees & Semel 1979) for
+ *   B_par with the weak-field B_perp; 3 the non-magnetic solution B = 0 with
+ *   the weak-field angles.  A seed whose psi lies in the other polarity's half
+ *   is reflected, psi -> 180 - psi.
+ * out_pol [npix][2] = (p, sigma_P); out_weak [npix][5] = (B, theta, chi,
+ * B_par, B_perp); seeds [npix][4][3].
+ */
+static double vertex3(double x0, double x1, double x2, double y0, double y1, double y2)
+{
+    const double d0 = x1 - x0, d2 = x1 - x2, e0 = y1 - y0, e2 = y1 - y2;
+    const double num = d0 * d0 * e2 - d2 * d2 * e0;
+    const double den = d0 * e2 - d2 * e0;
+    return den != 0.0 ? x1 - 0.5 * num / den : x1;
+}
+
+static double core_of(const double *row, const double *lam, int nl, int lo, int hi)
+{
+    int bi = lo;
+    for (int i = lo + 1; i <= hi; ++i)
+        if (row[i] < row[bi]) bi = i;
+    if (bi - 1 >= 0 && bi + 1 < nl)
+        return vertex3(lam[bi - 1], lam[bi], lam[bi + 1], row[bi - 1], row[bi], row[bi + 1]);
+    return lam[bi];
+}
+
+static double second_diff(const double *lam, const double *y, int c)
+{
+    const double h1 = lam[c] - lam[c - 1], h2 = lam[c + 1] - lam[c];
+    return 2.0 * (h1 * (y[c + 1] - y[c]) - h2 * (y[c] - y[c - 1])) / (h1 * h2 * (h1 + h2));
+}
+
+static double trap_w(const double *lam, int lo, int hi, int j)
+{
+    if (lo == hi) return 0.0;
+    const double a = j > lo ? lam[j] - lam[j - 1] : 0.0;
+    const double b = j < hi ? lam[j + 1] - lam[j] : 0.0;
+    return 0.5 * (a + b);
+}
+
+static void put_seed(double *sd, double bpar, double bperp, double chi, int pol)
+{
+    double psi = atan2(bperp, bpar) * 180.0 / M_PI;
+    if ((pol > 0 && psi > 90.0) || (pol < 0 && psi < 90.0)) psi = 180.0 - psi;
+    sd[0] = sqrt(bpar * bpar + bperp * bperp);
+    sd[1] = psi;
+    sd[2] = chi;
+}
+
+void or_classify(const or_problem *pb, const double *obs, int npix, double p_thresh, int q_lo, int q_hi,
+                 int line, int c_lo, int c_hi, int *flag, int *polarity, double *out_pol, double *out_weak,
+                 double *seeds)
+{
+    const int nl = pb->n_lambda;
+    const double *lam = pb->lambda;
+    const double l0 = pb->lambda0[line], g = pb->g[line];
+    const double kz = OR_ZEEMAN * g * l0 * l0;
+    double *ipv = (double *)malloc(sizeof(double) * nl);
+    double *imv = (double *)malloc(sizeof(double) * nl);
+    for (int ip = 0; ip < npix; ++ip) {
+        const double *sI = obs + (size_t)ip * 4 * nl, *sQ = sI + nl, *sU = sI + 2 * nl, *sV = sI + 3 * nl;
+        /* threshold */
+        const int nq = q_hi - q_lo;
+        double ic = 0.0, mq = 0.0, mu = 0.0, mv = 0.0;
+        for (int j = q_lo; j < q_hi; ++j) { ic += sI[j]; mq += sQ[j]; mu += sU[j]; mv += sV[j]; }
+        ic /= nq; mq /= nq; mu /= nq; mv /= nq;
+        double vq = 0.0, vu = 0.0, vv = 0.0;
+        for (int j = q_lo; j < q_hi; ++j) {
+            vq += (sQ[j] - mq) * (sQ[j] - mq);
+            vu += (sU[j] - mu) * (sU[j] - mu);
+            vv += (sV[j] - mv) * (sV[j] - mv);
+        }
+        vq /= nq; vu /= nq; vv /= nq;
+        double qx = 0.0, ux = 0.0, vx = 0.0;
+        for (int j = 0; j < nl; ++j) {
+            if (fabs(sQ[j]) > qx) qx = fabs(sQ[j]);
+            if (fabs(sU[j]) > ux) ux = fabs(sU[j]);
+            if (fabs(sV[j]) > vx) vx = fabs(sV[j]);
+        }
+        const double p = sqrt(qx * qx + ux * ux + vx * vx) / ic;
+        const double sp = p_thresh * sqrt(vq + vu + vv) / ic;
+        flag[ip] = p > sp ? 1 : 0;
+        out_pol[(size_t)ip * 2] = p;
+        out_pol[(size_t)ip * 2 + 1] = sp;
+
+        /* polarity from the order of the V lobes */
+        int jmax = c_lo, jmin = c_lo;
+        for (int j = c_lo + 1; j <= c_hi; ++j) {
+            if (sV[j] > sV[jmax]) jmax = j;
+            if (sV[j] < sV[jmin]) jmin = j;
+        }
+        const int pol = jmax < jmin ? 1 : (jmax > jmin ? -1 : 0);
+        polarity[ip] = pol;
+
+        /* weak field */
+        for (int j = 0; j < nl; ++j) { ipv[j] = sI[j] + sV[j]; imv[j] = sI[j] - sV[j]; }
+        const double bpar = (core_of(ipv, lam, nl, c_lo, c_hi) - core_of(imv, lam, nl, c_lo, c_hi)) / (2.0 * kz);
+        double qa = 0.0, ub = 0.0, dd = 0.0;
+        for (int j = c_lo > 1 ? c_lo : 1; j <= c_hi && j + 1 < nl; ++j) {
+            const double d2 = second_diff(lam, sI, j);
+            qa += sQ[j] * d2;
+            ub += sU[j] * d2;
+            dd += d2 * d2;
+        }
+        double chi = 0.5 * atan2(-ub, -qa) * 180.0 / M_PI;
+        if (chi < 0.0) chi += 180.0;
+        const double amp = sqrt(qa * qa + ub * ub);
+        const double bperp = dd > 0.0 ? sqrt(4.0 * amp / dd) / kz : 0.0;
+        double *wo = out_weak + (size_t)ip * 5;
+        wo[0] = sqrt(bpar * bpar + bperp * bperp);
+        wo[1] = atan2(bperp, bpar) * 180.0 / M_PI;
+        wo[2] = chi;
+        wo[3] = bpar;
+        wo[4] = bperp;
+
+        /* seeds */
+        double *sd = seeds + (size_t)ip * 12;
+        put_seed(sd, bpar, bperp, chi, pol);
+        double av = 0.0, al = 0.0, tvi = 0.0, tvd = 0.0;
+        for (int j = c_lo; j <= c_hi; ++j) {
+            const double wj = trap_w(lam, c_lo, c_hi, j);
+            av += wj * fabs(sV[j]);
+            al += wj * sqrt(sQ[j] * sQ[j] + sU[j] * sU[j]);
+        }
+        for (int j = c_lo; j < c_hi; ++j) tvi += fabs(sI[j + 1] - sI[j]);
+        for (int j = c_lo + 1; j < c_hi; ++j) {
+            const double sl = (sI[j + 1] - sI[j]) / (lam[j + 1] - lam[j]);
+            const double sr = (sI[j] - sI[j - 1]) / (lam[j] - lam[j - 1]);
+            tvd += fabs(sl - sr);
+        }
+        const double bpi = tvi > 0.0 ? (pol < 0 ? -1.0 : 1.0) * av / (kz * tvi) : 0.0;
+        const double bti = tvd > 0.0 ? sqrt(4.0 * al / tvd) / kz : 0.0;
+        put_seed(sd + 3, bpi, bti, chi, pol);
+        double np = 0.0, dp = 0.0, nm = 0.0, dm = 0.0;
+        for (int j = c_lo; j <= c_hi; ++j) {
+            const double wj = trap_w(lam, c_lo, c_hi, j);
+            const double ap = wj * (ic - ipv[j]), am = wj * (ic - imv[j]);
+            np += ap * lam[j]; dp += ap;
+            nm += am * lam[j]; dm += am;
+        }
+        const double bcog = (dp != 0.0 && dm != 0.0) ? (np / dp - nm / dm) / (2.0 * kz) : 0.0;
+        put_seed(sd + 6, bcog, bperp, chi, pol);
+        put_seed(sd + 9, bpar, bperp, chi, pol);
+        sd[9] = 0.0;
+    }
+    free(ipv); free(imv);
+}

@@ -113,10 +113,16 @@ void or_ga_restart(uint16_t *genes, const double *f, int npop, int m,
  * re-evaluation with the fitness weights), best_genes [npix][m] (may be NULL)
  * and margin [npix] (may be NULL): the smallest relative gap between two
  * unequal fitness values whose order decided a selection, elitism or restart
- * step. */
+ * step.  Section 4.5: seeds [npix][nseed][3] (B, psi, chi; NaN keeps the
+ * Sobol gene) replace those genes of the last nseed <= npop/2 individuals of
+ * P0; polarity [npix] (may be NULL) restricts the inclination domain per
+ * pixel (or_polarity_bounds). */
+uint16_t or_ga_encode(double x, double lo, double hi);
+void or_polarity_bounds(int pol, double lo, double hi, double *plo, double *phi);
 int or_ga_invert(const or_problem *pb, const double *obs, const double *w,
                  const double *mu_px, double mu, int npix, uint64_t pixel_id0,
                  const double *lo, const double *hi, const or_ga_config *cfg,
+                 const double *seeds, int nseed, const int *polarity,
                  double *best, double *chi2, uint16_t *best_genes,
                  double *margin, int nthreads);
 
@@ -134,6 +140,11 @@ int or_lm_polish(const or_problem *pb, const double *obs, const double *w,
 /* Section 4.1 line centre by centre of symmetry (see me.c). */
 void or_line_centre(const double *rows, int npix, int stride, int nl, const double *lam, int half_width,
                     int i_lo, int i_hi, double *lam_c, int *idx);
+
+/* Section 2 pixel selection and weak-field fallback (see me.c). */
+void or_classify(const or_problem *pb, const double *obs, int npix, double p_thresh, int q_lo, int q_hi,
+                 int line, int c_lo, int c_hi, int *flag, int *polarity, double *out_pol, double *out_weak,
+                 double *seeds);
 
 /* Section 5 uncertainties sigma [npix][OR_NPAR] at params. */
 void or_lm_uncertainty(const or_problem *pb, const double *obs, const double *w, const double *mu_px,
