@@ -339,6 +339,80 @@ int lm_uncertainty(const me_problem *pb, const void *obs, const double *w, const
 int me_line_centre(const me_problem *pb, const void *obs, int npix, int half_width, int i_lo,
                    int i_hi, double *lambda_c, int *index, void *stream);
 
+/* ------------------------------------------ pixel selection and seeding
+ * me_classify - Section 2 pixel selection with the weak-field fallback, and
+ * the Section 4.5 seeds and polarity, one pixel per warp in FP64.
+ *   Threshold: I_c = mean of I over the quiet window [q_lo, q_hi); sigma_s^2
+ *   the variance (1/n) of s = Q, U, V there; p = sqrt(Qmax^2 + Umax^2 +
+ *   Vmax^2) / I_c with X_max = max |X| over the grid; sigma_P = p_thresh
+ *   sqrt(sigma_Q^2 + sigma_U^2 + sigma_V^2) / I_c; flag = (p > sigma_P).
+ *   Weak field for line `line` in the window [c_lo, c_hi] (inclusive), kz =
+ *   4.6686e-13 g lambda0^2: B_par = (lambda(I+V core) - lambda(I-V core)) /
+ *   (2 kz), each core the argmin refined by the three-point parabola vertex;
+ *   chi = atan2(-sum U I'', -sum Q I'') / 2 in [0, 180) and B_perp =
+ *   sqrt(4 sqrt((sum Q I'')^2 + (sum U I'')^2) / sum I''^2) / kz, the least-
+ *   squares fit of (Q, U) = -(kz^2 B_perp^2 / 4)(cos 2chi, sin 2chi) I'' with
+ *   I'' the three-point second difference; theta = atan2(B_perp, B_par).
+ *   Polarity: +1 when the positive V lobe lies blueward of the negative one,
+ *   -1 when redward, 0 when they coincide.
+ *   Seeds (B, psi, chi) rows: weak field; integral (B_par = s int|V| /
+ *   (kz TV(I)), B_perp = sqrt(4 int L / TV(I')) / kz); centre of gravity of
+ *   I_c - (I +- V) for B_par (Rees & Semel 1979); non-magnetic (B = 0).
+ *   psi is reflected (180 - psi) into the polarity's half.
+ * Sums run in increasing index, so all outputs but the angles are
+ * bit-identical to a plain sequential FP64 evaluation.  obs must be finite.
+ *   obs       dev [npix][4][n_lambda] of pb->dtype
+ *   flag      dev int [npix] (output; may be NULL)
+ *   polarity  dev int [npix] (output; may be NULL)
+ *   pol       dev double [npix][2] = (p, sigma_P) (output; may be NULL)
+ *   weak      dev double [npix][5] = (B, theta, chi, B_par, B_perp) (may be NULL)
+ *   seeds     dev double [npix][4][3] (output; may be NULL)
+ *   best      dev double [npix][ME_NPAR] or NULL: rows of pixels below the
+ *             threshold receive (B, theta, chi, NaN x 6); others are untouched
+ * Errors: ME_EINVAL for windows outside the grid or line out of range.
+ */
+int me_classify(const me_problem *pb, const void *obs, int npix, double p_thresh, int q_lo,
+                int q_hi, int line, int c_lo, int c_hi, int *flag, int *polarity, double *pol,
+                double *weak, double *seeds, double *best, void *stream);
+
+/*
+ * me_select - the pixels i (increasing) with flag[i] == want: index dev int
+ * [npix] receives them and count dev int [1] their number, both written on
+ * the stream (no host synchronisation).  scratch is caller-owned device
+ * memory of at least me_select_scratch_bytes(npix) bytes, 4-byte aligned, not
+ * shared with a concurrent call.  Selection precedes Algorithm 1 in Section 2:
+ * only the pixels above the polarization threshold are inverted.
+ */
+size_t me_select_scratch_bytes(int npix);
+int me_select(const int *flag, int npix, int want, int *index, int *count, void *scratch,
+              size_t scratch_bytes, void *stream);
+
+/*
+ * ga_invert_subset - ga_invert_batch on a subset of a map, with the Section
+ * 4.5 seeds and polarity restriction.  Block b inverts pixel index[b] for
+ * b < *count (index and count on the device, e.g. from me_select; index NULL
+ * = identity, count NULL = npix); every per-pixel array (obs, w, mu_px,
+ * seeds, polarity, best, chi2, best_genes) is indexed by that pixel number,
+ * and the random streams by pixel_id0 + pixel number, so a pixel's result is
+ * the one a whole-map run gives it.  Out-of-range indices are skipped.
+ *   seeds     dev double [npix][nseed][3] of (B, psi, chi); NaN keeps the Sobol
+ *             gene.  They replace those genes of the last nseed <= npop/2
+ *             individuals of P0, encoded to the nearest gene.
+ *   polarity  dev int [npix] or NULL: +1 restricts the inclination domain to
+ *             [lo, min(hi, 90)], -1 to [max(lo, 90), hi] (0, or an empty half:
+ *             unrestricted); the decode of that gene uses it throughout.
+ */
+int ga_invert_subset(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
+                     int npix, uint64_t pixel_id0, const me_bounds *bounds, const ga_config *cfg,
+                     const double *seeds, int nseed, const int *polarity, const int *index,
+                     const int *count, double *best, double *chi2, uint16_t *best_genes,
+                     void *stream);
+
+/* lm_polish on the subset index[0 .. *count) of a map (as ga_invert_subset). */
+int lm_polish_subset(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
+                     int npix, const me_bounds *bounds, int iters, double lambda0, const int *index,
+                     const int *count, double *params_inout, double *chi2_out, void *stream);
+
 /* ------------------------------------------------ GA operator entry points
  * The operators of ga_invert_batch run alone on caller-given populations, so
  * that they can be checked bit for bit against a reference with injected

@@ -103,6 +103,14 @@ _SIGNATURES = {
                    _VP, _VP], C.c_int),
     "lm_uncertainty": ([_P, _VP, _VP, _VP, C.c_int, _VP, _VP, _VP], C.c_int),
     "me_line_centre": ([_P, _VP, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP], C.c_int),
+    "me_classify": ([_P, _VP, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP,
+                     _VP, _VP, _VP, _VP, _VP], C.c_int),
+    "me_select_scratch_bytes": ([C.c_int], C.c_size_t),
+    "me_select": ([_VP, C.c_int, C.c_int, _VP, _VP, _VP, C.c_size_t, _VP], C.c_int),
+    "ga_invert_subset": ([_P, _VP, _VP, _VP, C.c_int, C.c_uint64, C.POINTER(MeBounds), C.POINTER(GaConfig),
+                          _VP, C.c_int, _VP, _VP, _VP, _VP, _VP, _VP, _VP], C.c_int),
+    "lm_polish_subset": ([_P, _VP, _VP, _VP, C.c_int, C.POINTER(MeBounds), C.c_int, C.c_double, _VP, _VP,
+                          _VP, _VP, _VP], C.c_int),
     "ga_breed": ([_VP, _VP, C.c_int, C.c_int, C.c_uint64, C.c_int, C.POINTER(GaConfig), _VP, _VP,
                   _VP], C.c_int),
     "ga_restart": ([_VP, _VP, C.c_int, C.c_int, C.c_uint64, _VP], C.c_int),

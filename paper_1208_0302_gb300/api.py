@@ -243,6 +243,132 @@ def line_centre(pb: Problem, obs, half_width, i_lo=0, i_hi=1 << 30):
     return lc, idx
 
 
+# ------------------------------------------------- selection and seeding
+
+def classify(pb: Problem, obs, p_thresh, quiet, line, core, best=None):
+    """Section 2 selection, weak-field fallback and Section 4.5 seeds.
+    quiet = (lo, hi) half-open quiet window, core = (lo, hi) inclusive line
+    window (grid indices).  Returns dict of device tensors: flag, polarity
+    (int32 [npix]), p, sigma_p (f64 [npix]), weak (f64 [npix, 5] = B, theta,
+    chi, B_par, B_perp) and seeds (f64 [npix, 4, 3]).  If best (f64 [npix, 9])
+    is given, the rows of pixels below the threshold receive the weak-field
+    answer (B, theta, chi, NaN...)."""
+    npix = obs.shape[0]
+    _need(obs, pb.torch_dtype, (npix, 4, pb.n_lambda), "obs")
+    _need(best, torch.float64, (npix, NPAR), "best")
+    dev = obs.device
+    flag = torch.empty(npix, dtype=torch.int32, device=dev)
+    polarity = torch.empty(npix, dtype=torch.int32, device=dev)
+    pol = torch.empty((npix, 2), dtype=torch.float64, device=dev)
+    weak = torch.empty((npix, 5), dtype=torch.float64, device=dev)
+    seeds = torch.empty((npix, 4, 3), dtype=torch.float64, device=dev)
+    L.check(L.load().me_classify(pb.ref(), _ptr(obs), npix, float(p_thresh), int(quiet[0]), int(quiet[1]),
+                                 int(line), int(core[0]), int(core[1]), _ptr(flag), _ptr(polarity), _ptr(pol),
+                                 _ptr(weak), _ptr(seeds), _ptr(best), _stream()))
+    return {"flag": flag, "polarity": polarity, "p": pol[:, 0], "sigma_p": pol[:, 1], "weak": weak,
+            "seeds": seeds}
+
+
+def select(flag, want=1):
+    """Pixels with flag == want, in increasing order -> (index int32 [npix],
+    count int32 [1]); both stay on the device."""
+    npix = flag.shape[0]
+    _need(flag, torch.int32, (npix,), "flag")
+    lib = L.load()
+    index = torch.empty(max(npix, 1), dtype=torch.int32, device=flag.device)
+    count = torch.empty(1, dtype=torch.int32, device=flag.device)
+    nbytes = int(lib.me_select_scratch_bytes(npix))
+    scratch = torch.empty(max(nbytes, 4), dtype=torch.uint8, device=flag.device)
+    L.check(lib.me_select(_ptr(flag), npix, int(want), _ptr(index), _ptr(count), _ptr(scratch), nbytes,
+                          _stream()))
+    return index[:npix], count
+
+
+def ga_invert_subset(pb: Problem, obs, lo, hi, ga: GaSettings, index=None, count=None, seeds=None,
+                     polarity=None, w=None, mu_px=None, pixel_id0=0, best=None, chi2=None, want_genes=False):
+    """ga_invert_batch on the pixels index[:count] of a map, seeded and
+    polarity-restricted (Section 4.5).  best/chi2 (map-sized) are written in
+    place for those pixels and returned."""
+    npix = obs.shape[0]
+    _need(obs, pb.torch_dtype, (npix, 4, pb.n_lambda), "obs")
+    _need(w, torch.float64, (npix, 4), "w")
+    _need(mu_px, torch.float64, (npix,), "mu_px")
+    _need(index, torch.int32, None, "index")
+    _need(count, torch.int32, (1,), "count")
+    _need(polarity, torch.int32, (npix,), "polarity")
+    nseed = 0
+    if seeds is not None:
+        _need(seeds, torch.float64, None, "seeds")
+        if seeds.dim() != 3 or seeds.shape[0] != npix or seeds.shape[2] != 3:
+            raise ValueError("seeds must have shape (npix, nseed, 3)")
+        nseed = seeds.shape[1]
+    if index is not None and count is None and index.shape[0] != npix:
+        raise ValueError("an index without count must hold npix entries")
+    if index is not None and index.shape[0] < npix and count is not None:
+        raise ValueError("index must hold npix entries")
+    dev = obs.device
+    if best is None:
+        best = torch.full((npix, NPAR), float("nan"), dtype=torch.float64, device=dev)
+    if chi2 is None:
+        chi2 = torch.full((npix,), float("nan"), dtype=torch.float64, device=dev)
+    _need(best, torch.float64, (npix, NPAR), "best")
+    _need(chi2, torch.float64, (npix,), "chi2")
+    genes = torch.zeros((npix, NPAR), dtype=torch.int16, device=dev) if want_genes else None
+    cfg = ga.to_c(L.ME_W_USER if w is not None else L.ME_W_INVMAX)
+    b = bounds(lo, hi)
+    L.check(L.load().ga_invert_subset(pb.ref(), _ptr(obs), _ptr(w), _ptr(mu_px), npix, int(pixel_id0),
+                                      C.byref(b), C.byref(cfg), _ptr(seeds), nseed, _ptr(polarity),
+                                      _ptr(index), _ptr(count), _ptr(best), _ptr(chi2), _ptr(genes),
+                                      _stream()))
+    if want_genes:
+        return best, chi2, genes
+    return best, chi2
+
+
+def lm_polish_subset(pb: Problem, obs, params, lo, hi, index=None, count=None, iters=10, lambda0=1e-3,
+                     w=None, mu_px=None, chi2=None):
+    """lm_polish on the pixels index[:count] of a map; params (map-sized) and
+    chi2 are updated in place for those pixels and returned."""
+    npix = obs.shape[0]
+    _need(obs, pb.torch_dtype, (npix, 4, pb.n_lambda), "obs")
+    _need(params, torch.float64, (npix, NPAR), "params")
+    _need(w, torch.float64, (npix, 4), "w")
+    _need(mu_px, torch.float64, (npix,), "mu_px")
+    _need(index, torch.int32, None, "index")
+    _need(count, torch.int32, (1,), "count")
+    if index is not None and index.shape[0] < npix:
+        raise ValueError("index must hold npix entries")
+    _need(chi2, torch.float64, (npix,), "chi2")
+    b = bounds(lo, hi)
+    L.check(L.load().lm_polish_subset(pb.ref(), _ptr(obs), _ptr(w), _ptr(mu_px), npix, C.byref(b), int(iters),
+                                      float(lambda0), _ptr(index), _ptr(count), _ptr(params), _ptr(chi2),
+                                      _stream()))
+    return params, chi2
+
+
+def invert_map(pb: Problem, obs, lo, hi, ga: GaSettings, p_thresh, quiet, line, core, nseed=4,
+               polarity=True, polish_iters=10, lambda0=1e-3, w=None, polish_w=None, mu_px=None, pixel_id0=0):
+    """The Section 2 pipeline on a map, asynchronous on the current stream:
+    classification (weak-field answer below the threshold), selection of the
+    pixels above it, the seeded, polarity-restricted GA and the L-M polish
+    on those.  Returns dict(best [npix, 9], chi2 [npix] (NaN for weak-field
+    pixels), flag, polarity, index, count, weak, seeds)."""
+    npix = obs.shape[0]
+    dev = obs.device
+    best = torch.full((npix, NPAR), float("nan"), dtype=torch.float64, device=dev)
+    chi2 = torch.full((npix,), float("nan"), dtype=torch.float64, device=dev)
+    cls = classify(pb, obs, p_thresh, quiet, line, core, best=best)
+    index, count = select(cls["flag"], 1)
+    sd = cls["seeds"][:, :nseed].contiguous() if nseed > 0 else None
+    pol = cls["polarity"] if polarity else None
+    ga_invert_subset(pb, obs, lo, hi, ga, index=index, count=count, seeds=sd, polarity=pol, w=w, mu_px=mu_px,
+                     pixel_id0=pixel_id0, best=best, chi2=chi2)
+    if polish_iters > 0:
+        lm_polish_subset(pb, obs, best, lo, hi, index=index, count=count, iters=polish_iters, lambda0=lambda0,
+                         w=polish_w if polish_w is not None else w, mu_px=mu_px, chi2=chi2)
+    return dict(cls, best=best, chi2=chi2, index=index, count=count)
+
+
 # ------------------------------------------------------------------ serving
 
 def _host_f64(a, shape, name):

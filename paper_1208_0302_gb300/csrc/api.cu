@@ -299,7 +299,7 @@ extern "C" {
 
 const char *me_last_error(void) { return g_last_error.c_str(); }
 
-int me_version(void) { return 101; }
+int me_version(void) { return 102; }
 
 int me_zeeman_components(const me_line *line, int n[3], double shift[3][ME_MAX_COMP],
                          double strength[3][ME_MAX_COMP])
@@ -374,9 +374,10 @@ int me_chi2(const me_problem *pb, const void *obs, const double *w, const double
     return e == cudaSuccess ? ME_OK : cuda_fail(e, "me_chi2 launch");
 }
 
-int ga_invert_batch(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
-                    int npix, uint64_t pixel_id0, const me_bounds *bounds, const ga_config *cfg,
-                    double *best, double *chi2, uint16_t *best_genes, void *stream)
+static int ga_invert_impl(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
+                          int npix, uint64_t pixel_id0, const me_bounds *bounds, const ga_config *cfg,
+                          KSeed sd, KSub sub, double *best, double *chi2, uint16_t *best_genes,
+                          void *stream, const char *who)
 {
     KProblem k;
     int rc = make_problem(pb, k);
@@ -389,6 +390,8 @@ int ga_invert_batch(const me_problem *pb, const void *obs, const double *w, cons
     if (!obs || !best || !chi2) return fail(ME_EINVAL, "obs, best and chi2 must be non-NULL");
     if (cfg->weight_mode == ME_W_USER && !w) return fail(ME_EINVAL, "ME_W_USER needs w");
     if (pixel_id0 + (uint64_t)npix < pixel_id0) return fail(ME_EINVAL, "pixel id range overflows");
+    if (sd.nseed < 0 || sd.nseed > cfg->npop / 2) return fail(ME_EINVAL, "nseed must be in [0, npop / 2]");
+    if (sd.nseed > 0 && !sd.seeds) return fail(ME_EINVAL, "nseed > 0 needs seeds");
     // shared memory: obs + offsets + fitness + genes must fit one block
     const size_t rs = pb->dtype == ME_F32 ? 4 : 8;
     const size_t need = rs * (4 + pb->n_lines) * pb->n_lambda + rs * (cfg->npop + 72) + 128 +
@@ -396,12 +399,29 @@ int ga_invert_batch(const me_problem *pb, const void *obs, const double *w, cons
     if (need > 220 * 1024) return fail(ME_EINVAL, "population and grid exceed shared memory");
     if ((rc = ensure_device())) return rc;
     const KGa &gc = g;
-    cudaError_t e = launch_ga_evolve(k, gc, pb->dtype, obs, cfg->weight_mode == ME_W_USER ? w : nullptr,
-                                     mu_px, npix, best, best_genes, as_stream(stream));
-    if (e != cudaSuccess) return cuda_fail(e, "ga_invert_batch launch");
-    e = launch_chi2_f64(k, pb->dtype, obs, cfg->weight_mode == ME_W_USER ? w : nullptr, mu_px, npix,
-                        best, chi2, as_stream(stream));
-    return e == cudaSuccess ? ME_OK : cuda_fail(e, "ga_invert_batch chi2 launch");
+    const double *wu = cfg->weight_mode == ME_W_USER ? w : nullptr;
+    cudaError_t e = launch_ga_evolve(k, gc, pb->dtype, obs, wu, mu_px, npix, best, best_genes,
+                                     as_stream(stream), sd, sub);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    e = launch_chi2_f64(k, pb->dtype, obs, wu, mu_px, npix, best, chi2, as_stream(stream), sub);
+    return e == cudaSuccess ? ME_OK : cuda_fail(e, who);
+}
+
+int ga_invert_batch(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
+                    int npix, uint64_t pixel_id0, const me_bounds *bounds, const ga_config *cfg,
+                    double *best, double *chi2, uint16_t *best_genes, void *stream)
+{
+    return ga_invert_impl(pb, obs, w, mu_px, npix, pixel_id0, bounds, cfg, KSeed{}, KSub{}, best, chi2,
+                          best_genes, stream, "ga_invert_batch launch");
+}
+
+int ga_invert_subset(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
+                     int npix, uint64_t pixel_id0, const me_bounds *bounds, const ga_config *cfg,
+                     const double *seeds, int nseed, const int *polarity, const int *index,
+                     const int *count, double *best, double *chi2, uint16_t *best_genes, void *stream)
+{
+    return ga_invert_impl(pb, obs, w, mu_px, npix, pixel_id0, bounds, cfg, KSeed{seeds, nseed, polarity},
+                          KSub{index, count}, best, chi2, best_genes, stream, "ga_invert_subset launch");
 }
 
 int ga_count_evaluations(const me_problem *pb, const void *obs, const double *w,
@@ -427,9 +447,9 @@ int ga_count_evaluations(const me_problem *pb, const void *obs, const double *w,
     return e == cudaSuccess ? ME_OK : cuda_fail(e, "ga_count_evaluations launch");
 }
 
-int lm_polish(const me_problem *pb, const void *obs, const double *w, const double *mu_px, int npix,
-              const me_bounds *bounds, int iters, double lambda0, double *params_inout,
-              double *chi2_out, void *stream)
+static int lm_polish_impl(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
+                          int npix, const me_bounds *bounds, int iters, double lambda0, KSub sub,
+                          double *params_inout, double *chi2_out, void *stream)
 {
     KProblem k;
     int rc = make_problem(pb, k);
@@ -448,13 +468,77 @@ int lm_polish(const me_problem *pb, const void *obs, const double *w, const doub
         lm.lo[d] = bounds->lo[d];
         lm.hi[d] = bounds->hi[d];
     }
-    cudaError_t e = launch_lm(k, lm, pb->dtype, obs, w, mu_px, npix, params_inout, as_stream(stream));
+    cudaError_t e = launch_lm(k, lm, pb->dtype, obs, w, mu_px, npix, params_inout, as_stream(stream), sub);
     if (e != cudaSuccess) return cuda_fail(e, "lm_polish launch");
     if (chi2_out) {
-        e = launch_chi2_f64(k, pb->dtype, obs, w, mu_px, npix, params_inout, chi2_out, as_stream(stream));
+        e = launch_chi2_f64(k, pb->dtype, obs, w, mu_px, npix, params_inout, chi2_out, as_stream(stream), sub);
         if (e != cudaSuccess) return cuda_fail(e, "lm_polish chi2 launch");
     }
     return ME_OK;
+}
+
+int lm_polish(const me_problem *pb, const void *obs, const double *w, const double *mu_px, int npix,
+              const me_bounds *bounds, int iters, double lambda0, double *params_inout,
+              double *chi2_out, void *stream)
+{
+    return lm_polish_impl(pb, obs, w, mu_px, npix, bounds, iters, lambda0, KSub{}, params_inout, chi2_out,
+                          stream);
+}
+
+int lm_polish_subset(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
+                     int npix, const me_bounds *bounds, int iters, double lambda0, const int *index,
+                     const int *count, double *params_inout, double *chi2_out, void *stream)
+{
+    return lm_polish_impl(pb, obs, w, mu_px, npix, bounds, iters, lambda0, KSub{index, count}, params_inout,
+                          chi2_out, stream);
+}
+
+int me_classify(const me_problem *pb, const void *obs, int npix, double p_thresh, int q_lo, int q_hi,
+                int line, int c_lo, int c_hi, int *flag, int *polarity, double *pol, double *weak,
+                double *seeds, double *best, void *stream)
+{
+    KProblem k;
+    int rc = make_problem(pb, k);
+    if (rc) return rc;
+    if (npix < 0) return fail(ME_EINVAL, "npix must be >= 0");
+    if (!(p_thresh >= 0.0) || !std::isfinite(p_thresh)) return fail(ME_EINVAL, "p_thresh must be finite, >= 0");
+    if (q_lo < 0 || q_hi > pb->n_lambda || q_lo >= q_hi) return fail(ME_EINVAL, "quiet window out of range");
+    if (c_lo < 0 || c_hi >= pb->n_lambda || c_lo > c_hi) return fail(ME_EINVAL, "line window out of range");
+    if (line < 0 || line >= pb->n_lines) return fail(ME_EINVAL, "line out of range");
+    if (npix == 0) return ME_OK;
+    if (!obs) return fail(ME_EINVAL, "obs must be non-NULL");
+    if ((rc = ensure_device())) return rc;
+    KClassify c;
+    c.p_thresh = p_thresh;
+    c.kz = k.line[line].zfac;
+    c.q_lo = q_lo;
+    c.q_hi = q_hi;
+    c.c_lo = c_lo;
+    c.c_hi = c_hi;
+    c.flag = flag;
+    c.polarity = polarity;
+    c.pol = pol;
+    c.weak = weak;
+    c.seeds = seeds;
+    c.best = best;
+    cudaError_t e = launch_classify(k, pb->dtype, obs, npix, c, as_stream(stream));
+    return e == cudaSuccess ? ME_OK : cuda_fail(e, "me_classify launch");
+}
+
+size_t me_select_scratch_bytes(int npix) { return select_scratch_bytes(npix); }
+
+int me_select(const int *flag, int npix, int want, int *index, int *count, void *scratch,
+              size_t scratch_bytes, void *stream)
+{
+    if (npix < 0) return fail(ME_EINVAL, "npix must be >= 0");
+    if (!count) return fail(ME_EINVAL, "count must be non-NULL");
+    if (npix > 0 && (!flag || !index || !scratch)) return fail(ME_EINVAL, "flag, index and scratch must be non-NULL");
+    if (scratch_bytes < select_scratch_bytes(npix)) return fail(ME_EINVAL, "scratch smaller than me_select_scratch_bytes");
+    if (((uintptr_t)scratch & 3) != 0) return fail(ME_EINVAL, "scratch must be 4-byte aligned");
+    int rc = ensure_device();
+    if (rc) return rc;
+    cudaError_t e = launch_select(flag, npix, want, index, count, scratch, as_stream(stream));
+    return e == cudaSuccess ? ME_OK : cuda_fail(e, "me_select launch");
 }
 
 int lm_uncertainty(const me_problem *pb, const void *obs, const double *w, const double *mu_px,

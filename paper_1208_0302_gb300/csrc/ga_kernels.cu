@@ -66,19 +66,22 @@ template <class R> __device__ __forceinline__ int padded_lambda(int nl)
 }
 
 template <class R> struct GaDecode;
+// The inclination (d = 1) decodes in the pixel's polarity-restricted domain,
+// held in shared memory (s_psi: double lo, hi; then float lo, scale).
 template <> struct GaDecode<float> {
-    // FP32 GA: p = lo + g (hi - lo) / 65535, scale precomputed on the host
+    // FP32 GA: p = lo + g (hi - lo) / 65535, scale precomputed
     static __device__ __forceinline__ float get(const KGa &ga, const float *lo32,
-                                                const float *sc32, int d, uint16_t g)
+                                                const float *sc32, const double *s_psi, int d, uint16_t g)
     {
-        return fmaf((float)g, sc32[d], lo32[d]);
+        const float *p32 = (const float *)(s_psi + 2);
+        return d == 1 ? fmaf((float)g, p32[1], p32[0]) : fmaf((float)g, sc32[d], lo32[d]);
     }
 };
 template <> struct GaDecode<double> {
     static __device__ __forceinline__ double get(const KGa &ga, const float *, const float *,
-                                                 int d, uint16_t g)
+                                                 const double *s_psi, int d, uint16_t g)
     {
-        return decode64(g, ga.lo[d], ga.hi[d]);
+        return d == 1 ? decode64(g, s_psi[0], s_psi[1]) : decode64(g, ga.lo[d], ga.hi[d]);
     }
 };
 
@@ -263,7 +266,7 @@ __device__ __forceinline__ void breed_one(const KGa &ga, uint64_t pid, int t, in
 
 struct GaSmem {
     // byte offsets into dynamic shared memory
-    int obs, doff, fit, wmin, widx, w2, he, genes, total;
+    int obs, doff, fit, wmin, widx, w2, he, psi, genes, total;
 };
 
 template <class R>
@@ -285,6 +288,7 @@ __host__ __device__ __forceinline__ GaSmem ga_smem_layout(int nl, int nlines, in
     L.widx = take(32 * 4, 16);
     L.w2 = take(4 * (int)sizeof(R), 16);
     L.he = take(4 * (int)sizeof(R), 16);
+    L.psi = take(32, 16);  // the pixel's inclination domain: double lo, hi; float lo, scale
     L.genes = take(2 * npop * ME_NPAR * 2, 16);
     L.total = (o + 15) / 16 * 16;
     return L;
@@ -339,7 +343,8 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(R) == 4) ? GENESI
 k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
             const R *__restrict__ obs, const double *__restrict__ w_user,
             const double *__restrict__ mu_px, int npix, double *__restrict__ best,
-            uint16_t *__restrict__ best_genes, unsigned long long *__restrict__ counts)
+            uint16_t *__restrict__ best_genes, unsigned long long *__restrict__ counts,
+            const KSeed sd, const KSub sub)
 {
     unsigned long long nfit = 0, ninterior = 0;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -355,6 +360,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
     int *s_widx = (int *)(smem + L.widx);
     R *s_w2 = (R *)(smem + L.w2);
     R *s_he = (R *)(smem + L.he);
+    double *s_psi = (double *)(smem + L.psi);
     uint16_t *s_genes = (uint16_t *)(smem + L.genes);
 
     // per-launch constants
@@ -373,7 +379,19 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
         s_doff[obs_idx<R>(l, j)] = l < nlines ? R(pb.lam[jj] - pb.line[l].lam0) : R(0);
     }
 
-    for (int pix = blockIdx.x; pix < npix; pix += gridDim.x) {
+    const int nrun = sub.count ? min(*sub.count, npix) : npix;
+    for (int blk = blockIdx.x; blk < nrun; blk += gridDim.x) {
+        const int pix = sub.index ? sub.index[blk] : blk;
+        if (pix < 0 || pix >= npix) continue;  // a bad index skips the block, uniformly
+        if (k == 0) {  // the pixel's inclination domain (Section 4.5 polarity restriction)
+            double a = ga.lo[1], b = ga.hi[1];
+            if (sd.polarity) polarity_bounds(sd.polarity[pix], ga.lo[1], ga.hi[1], a, b);
+            s_psi[0] = a;
+            s_psi[1] = b;
+            float *p32 = (float *)(s_psi + 2);
+            p32[0] = (float)a;
+            p32[1] = (float)((b - a) / 65535.0);
+        }
         // a1: stage the pixel's Stokes profiles from [4][nl] in HBM into the
         // shared-memory layout (16-byte vector loads when a vector stays in one row)
         const R *o = obs + (size_t)pix * 4 * nl;
@@ -417,14 +435,21 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
         const R mu = mu_px ? R(mu_px[pix]) : R(pb.mu);
         const uint64_t pid = ga.pixel_id0 + (uint64_t)pix;
 
-        // a3 + a4: Sobol points 1..npop, decode, evaluate
+        // a3 + a4: Sobol points 1..npop, the last nseed taking the seeds'
+        // (B, psi, chi) genes, decode, evaluate
         uint16_t g[ME_NPAR];
         R p[ME_NPAR];
 #pragma unroll
-        for (int d = 0; d < ME_NPAR; ++d) {
-            g[d] = (uint16_t)(sobol_point((uint64_t)(k + 1), d) >> 16);
-            p[d] = GaDecode<R>::get(ga, lo32, sc32, d, g[d]);
+        for (int d = 0; d < ME_NPAR; ++d) g[d] = (uint16_t)(sobol_point((uint64_t)(k + 1), d) >> 16);
+        if (k >= npop - sd.nseed) {
+            const double *sv = sd.seeds + ((size_t)pix * sd.nseed + (k - (npop - sd.nseed))) * 3;
+            const double x0 = sv[0], x1 = sv[1], x2 = sv[2];
+            if (x0 == x0) g[0] = encode64(x0, ga.lo[0], ga.hi[0]);
+            if (x1 == x1) g[1] = encode64(x1, s_psi[0], s_psi[1]);
+            if (x2 == x2) g[2] = encode64(x2, ga.lo[2], ga.hi[2]);
         }
+#pragma unroll
+        for (int d = 0; d < ME_NPAR; ++d) p[d] = GaDecode<R>::get(ga, lo32, sc32, s_psi, d, g[d]);
         int cur = 0;
 #pragma unroll
         for (int d = 0; d < ME_NPAR; ++d) s_genes[k * ME_NPAR + d] = g[d];
@@ -442,7 +467,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
 #pragma unroll
             for (int d = 0; d < ME_NPAR; ++d) {
                 s_nxt[k * ME_NPAR + d] = g[d];
-                p[d] = GaDecode<R>::get(ga, lo32, sc32, d, g[d]);
+                p[d] = GaDecode<R>::get(ga, lo32, sc32, s_psi, d, g[d]);
             }
             cur ^= 1;
             s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior));
@@ -459,7 +484,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
                     for (int d = 0; d < ME_NPAR; ++d) {
                         g[d] = (uint16_t)(sobol_point(n, d) >> 16);
                         s_c[k * ME_NPAR + d] = g[d];
-                        p[d] = GaDecode<R>::get(ga, lo32, sc32, d, g[d]);
+                        p[d] = GaDecode<R>::get(ga, lo32, sc32, s_psi, d, g[d]);
                     }
                     s_fit[k] = clean_fit(
                         fitness<R, NL, COUNT, PAT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior));
@@ -473,7 +498,8 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
         // a14: decoded best individual (its FP64 chi2 is a separate pass)
         if (k < ME_NPAR) {
             const uint16_t gb = s_genes[cur * npop * ME_NPAR + b * ME_NPAR + k];
-            best[(size_t)pix * ME_NPAR + k] = decode64(gb, ga.lo[k], ga.hi[k]);
+            best[(size_t)pix * ME_NPAR + k] =
+                k == 1 ? decode64(gb, s_psi[0], s_psi[1]) : decode64(gb, ga.lo[k], ga.hi[k]);
             if (best_genes) best_genes[(size_t)pix * ME_NPAR + k] = gb;
         }
         __syncthreads();  // shared memory is reused by the next pixel
@@ -559,14 +585,16 @@ __global__ void k_sobol(uint64_t first, int n, int ndim, uint32_t *__restrict__ 
 template <class R, int NL, int MAXT, bool COUNT = false, bool PAT = false>
 cudaError_t launch_evolve_t(const KProblem &pb, const KGa &ga, const void *obs, const double *w,
                             const double *mu_px, int npix, double *best, uint16_t *best_genes,
-                            cudaStream_t st, unsigned long long *counts = nullptr)
+                            cudaStream_t st, unsigned long long *counts = nullptr, KSeed sd = {},
+                            KSub sub = {})
 {
     const int nlines = NL > 0 ? NL : pb.n_lines;
     const GaSmem L = ga_smem_layout<R>(pb.n_lambda, nlines, ga.npop);
     auto kern = k_ga_evolve<R, NL, MAXT, COUNT, PAT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     if (e != cudaSuccess) return e;
-    kern<<<npix, ga.npop, L.total, st>>>(pb, ga, (const R *)obs, w, mu_px, npix, best, best_genes, counts);
+    kern<<<npix, ga.npop, L.total, st>>>(pb, ga, (const R *)obs, w, mu_px, npix, best, best_genes, counts,
+                                          sd, sub);
     return cudaGetLastError();
 }
 
@@ -581,28 +609,27 @@ bool has_pattern(const KProblem &pb)
 
 cudaError_t launch_ga_evolve(const KProblem &pb, const KGa &ga, int dtype, const void *obs,
                              const double *w, const double *mu_px, int npix, double *best,
-                             uint16_t *best_genes, cudaStream_t st)
+                             uint16_t *best_genes, cudaStream_t st, KSeed sd, KSub sub)
 {
     if (npix <= 0) return cudaSuccess;
     const bool pat = has_pattern(pb);
+#define GENESIS_EVOLVE(R, NL, MAXT, PAT) \
+    launch_evolve_t<R, NL, MAXT, false, PAT>(pb, ga, obs, w, mu_px, npix, best, best_genes, st, nullptr, sd, sub)
     if (dtype == ME_F32 && pat) {
-        if (ga.npop <= 256)
-            return launch_evolve_t<float, 0, 256, false, true>(pb, ga, obs, w, mu_px, npix, best, best_genes, st);
-        return launch_evolve_t<float, 0, 1024, false, true>(pb, ga, obs, w, mu_px, npix, best, best_genes, st);
+        if (ga.npop <= 256) return GENESIS_EVOLVE(float, 0, 256, true);
+        return GENESIS_EVOLVE(float, 0, 1024, true);
     }
     if (dtype == ME_F32) {
         if (ga.npop <= 256) {
-            if (pb.n_lines == 1)
-                return launch_evolve_t<float, 1, 256>(pb, ga, obs, w, mu_px, npix, best, best_genes, st);
-            if (pb.n_lines == 2)
-                return launch_evolve_t<float, 2, 256>(pb, ga, obs, w, mu_px, npix, best, best_genes, st);
-            return launch_evolve_t<float, 0, 256>(pb, ga, obs, w, mu_px, npix, best, best_genes, st);
+            if (pb.n_lines == 1) return GENESIS_EVOLVE(float, 1, 256, false);
+            if (pb.n_lines == 2) return GENESIS_EVOLVE(float, 2, 256, false);
+            return GENESIS_EVOLVE(float, 0, 256, false);
         }
-        return launch_evolve_t<float, 0, 1024>(pb, ga, obs, w, mu_px, npix, best, best_genes, st);
+        return GENESIS_EVOLVE(float, 0, 1024, false);
     }
-    if (ga.npop <= 256)
-        return launch_evolve_t<double, 0, 256, false, true>(pb, ga, obs, w, mu_px, npix, best, best_genes, st);
-    return launch_evolve_t<double, 0, 1024, false, true>(pb, ga, obs, w, mu_px, npix, best, best_genes, st);
+    if (ga.npop <= 256) return GENESIS_EVOLVE(double, 0, 256, true);
+    return GENESIS_EVOLVE(double, 0, 1024, true);
+#undef GENESIS_EVOLVE
 }
 
 cudaError_t launch_ga_count(const KProblem &pb, const KGa &ga, int dtype, const void *obs,

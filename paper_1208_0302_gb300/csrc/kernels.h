@@ -18,6 +18,21 @@ struct KGa {
     double lo[ME_NPAR], hi[ME_NPAR];
 };
 
+// Section 4.5 seeds and polarity restriction: seeds [npix][nseed][3] of
+// (B, psi, chi), NaN = keep the Sobol gene; polarity [npix] of -1, 0, +1.
+struct KSeed {
+    const double *seeds;
+    int nseed;
+    const int *polarity;
+};
+
+// A subset of a map: block b processes pixel index[b] for b < *count (both
+// on the device; NULL index = identity, NULL count = all npix).
+struct KSub {
+    const int *index;
+    const int *count;
+};
+
 struct KLm {
     int iters;
     double lambda0;
@@ -40,7 +55,7 @@ cudaError_t upload_tables_lm(const HostTables &t);
 // ga_kernels.cu
 cudaError_t launch_ga_evolve(const KProblem &pb, const KGa &ga, int dtype, const void *obs,
                              const double *w, const double *mu_px, int npix, double *best,
-                             uint16_t *best_genes, cudaStream_t st);
+                             uint16_t *best_genes, cudaStream_t st, KSeed sd = {}, KSub sub = {});
 cudaError_t launch_ga_count(const KProblem &pb, const KGa &ga, int dtype, const void *obs,
                             const double *w, const double *mu_px, int npix, double *best,
                             unsigned long long *counts, cudaStream_t st);
@@ -60,7 +75,21 @@ cudaError_t launch_vjp(const KProblem &pb, int dtype, const double *params, cons
                        int n, const void *grad_stokes, double *grad_params, cudaStream_t st);
 cudaError_t launch_chi2_f64(const KProblem &pb, int dtype, const void *obs, const double *w,
                             const double *mu_px, int npix, const double *params, double *chi2,
+                            cudaStream_t st, KSub sub = {});
+
+// Section 2 selection, weak-field estimate and Section 4.5 seeds.
+struct KClassify {
+    double p_thresh, kz;  // kz = 4.6686e-13 g lambda0^2 of the chosen line
+    int q_lo, q_hi, c_lo, c_hi;
+    int *flag, *polarity;
+    double *pol, *weak, *seeds, *best;
+};
+cudaError_t launch_classify(const KProblem &pb, int dtype, const void *obs, int npix, const KClassify &c,
                             cudaStream_t st);
+// Order-preserving selection of the pixels whose flag equals want.
+size_t select_scratch_bytes(int npix);
+cudaError_t launch_select(const int *flag, int npix, int want, int *index, int *count, void *scratch,
+                          cudaStream_t st);
 
 cudaError_t launch_line_centre(const KProblem &pb, int dtype, const void *obs, int npix, int W, int lo,
                                int hi, double *lam_c, int *idx, cudaStream_t st);
@@ -71,7 +100,7 @@ cudaError_t launch_lm_sigma(const KProblem &pb, int dtype, const void *obs, cons
                             cudaStream_t st);
 cudaError_t launch_lm(const KProblem &pb, const KLm &lm, int dtype, const void *obs,
                       const double *w, const double *mu_px, int npix, double *params,
-                      cudaStream_t st);
+                      cudaStream_t st, KSub sub = {});
 
 // api.cu: argument validation shared by the C entry points and the serving
 // loop.  Each returns ME_OK or an ME_E* code with the thread-local message set.
@@ -89,6 +118,32 @@ cudaStream_t as_stream(void *s);
 __device__ __forceinline__ double decode64(uint16_t g, double lo, double hi)
 {
     return __dadd_rn(lo, __dmul_rn(__dsub_rn(hi, lo), __ddiv_rn((double)g, 65535.0)));
+}
+
+// Nearest gene of a seed value (Section 4.5), the inverse of the decode:
+// t = (x - lo) / (hi - lo) clamped to [0, 1], g = floor(65535 t + 1/2).
+__device__ __forceinline__ uint16_t encode64(double x, double lo, double hi)
+{
+    double t = __ddiv_rn(__dsub_rn(x, lo), __dsub_rn(hi, lo));
+    if (!(t > 0.0)) t = 0.0;
+    if (t > 1.0) t = 1.0;
+    return (uint16_t)floor(__dadd_rn(__dmul_rn(t, 65535.0), 0.5));
+}
+
+// Section 4.5 polarity restriction of the inclination domain [lo, hi]:
+// +1 keeps [lo, min(hi, 90)], -1 keeps [max(lo, 90), hi]; 0, or a half
+// that would be empty, keeps [lo, hi].
+__host__ __device__ __forceinline__ void polarity_bounds(int pol, double lo, double hi, double &a,
+                                                         double &b)
+{
+    a = lo;
+    b = hi;
+    if (pol > 0 && hi > 90.0) b = 90.0;
+    if (pol < 0 && lo < 90.0) a = 90.0;
+    if (!(a < b)) {
+        a = lo;
+        b = hi;
+    }
 }
 
 }  // namespace genesis

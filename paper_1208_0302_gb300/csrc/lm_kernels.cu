@@ -211,7 +211,7 @@ template <class R, class RO, int NL>
 __global__ void __launch_bounds__(kLmWarps * 32)
 k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const RO *__restrict__ obs,
      const double *__restrict__ w_user, const double *__restrict__ mu_px, int npix,
-     double *__restrict__ params)
+     double *__restrict__ params, const KSub sub)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     LmWarpSmem *s_w = (LmWarpSmem *)smem;
@@ -227,8 +227,10 @@ k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const 
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int pix = blockIdx.x * kLmWarps + warp;
-    if (pix >= npix) return;
+    const int b = blockIdx.x * kLmWarps + warp;
+    if (b >= (sub.count ? min(*sub.count, npix) : npix)) return;
+    const int pix = sub.index ? sub.index[b] : b;
+    if (pix < 0 || pix >= npix) return;  // a bad index skips the warp, uniformly
     LmWarpSmem &W = s_w[warp];
     const RO *o = obs + (size_t)pix * 4 * nl;
     R he[ME_MAX_LINES];
@@ -391,7 +393,7 @@ cudaError_t sigma_t(const KProblem &pb, const void *obs, const double *w, const 
 
 template <class R, class RO, int NL>
 cudaError_t lm_t(const KProblem &pb, const KLm &lm, const void *obs, const double *w,
-                 const double *mu_px, int npix, double *params, cudaStream_t st)
+                 const double *mu_px, int npix, double *params, cudaStream_t st, KSub sub)
 {
     const int nlines = NL > 0 ? NL : pb.n_lines;
     const size_t smem = sizeof(LmWarpSmem) * kLmWarps + sizeof(R) * (ME_MAX_LINES + (size_t)nlines * pb.n_lambda);
@@ -399,7 +401,7 @@ cudaError_t lm_t(const KProblem &pb, const KLm &lm, const void *obs, const doubl
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<(npix + kLmWarps - 1) / kLmWarps, kLmWarps * 32, smem, st>>>(pb, lm, (const RO *)obs, w, mu_px,
-                                                                      npix, params);
+                                                                      npix, params, sub);
     return cudaGetLastError();
 }
 
@@ -420,15 +422,15 @@ cudaError_t launch_lm_sigma(const KProblem &pb, int dtype, const void *obs, cons
 
 cudaError_t launch_lm(const KProblem &pb, const KLm &lm, int dtype, const void *obs,
                       const double *w, const double *mu_px, int npix, double *params,
-                      cudaStream_t st)
+                      cudaStream_t st, KSub sub)
 {
     if (npix <= 0 || lm.iters <= 0) return cudaSuccess;
     if (dtype == ME_F32) {
-        if (pb.n_lines == 1) return lm_t<float, float, 1>(pb, lm, obs, w, mu_px, npix, params, st);
-        if (pb.n_lines == 2) return lm_t<float, float, 2>(pb, lm, obs, w, mu_px, npix, params, st);
-        return lm_t<float, float, 0>(pb, lm, obs, w, mu_px, npix, params, st);
+        if (pb.n_lines == 1) return lm_t<float, float, 1>(pb, lm, obs, w, mu_px, npix, params, st, sub);
+        if (pb.n_lines == 2) return lm_t<float, float, 2>(pb, lm, obs, w, mu_px, npix, params, st, sub);
+        return lm_t<float, float, 0>(pb, lm, obs, w, mu_px, npix, params, st, sub);
     }
-    return lm_t<double, double, 0>(pb, lm, obs, w, mu_px, npix, params, st);
+    return lm_t<double, double, 0>(pb, lm, obs, w, mu_px, npix, params, st, sub);
 }
 
 }  // namespace genesis

@@ -162,12 +162,15 @@ template <class RO>
 __global__ void __launch_bounds__(kSynthBlock)
 k_chi2_f64(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
            const double *__restrict__ w_user, const double *__restrict__ mu_px, int npix,
-           const double *__restrict__ params, double *__restrict__ chi2)
+           const double *__restrict__ params, double *__restrict__ chi2, const KSub sub)
 {
     __shared__ double s_red[kSynthBlock / 32][4];
     __shared__ double s_w2[4];
     const int nl = pb.n_lambda, nlines = pb.n_lines;
-    const int pix = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (sub.count && b >= *sub.count) return;
+    const int pix = sub.index ? sub.index[b] : b;
+    if (pix < 0 || pix >= npix) return;
     const RO *o = obs + (size_t)pix * 4 * nl;
     if (w_user) {
         if (threadIdx.x < 4) {
@@ -383,13 +386,15 @@ cudaError_t launch_line_centre(const KProblem &pb, int dtype, const void *obs, i
 
 cudaError_t launch_chi2_f64(const KProblem &pb, int dtype, const void *obs, const double *w,
                             const double *mu_px, int npix, const double *params, double *chi2,
-                            cudaStream_t st)
+                            cudaStream_t st, KSub sub)
 {
     if (npix <= 0) return cudaSuccess;
     if (dtype == ME_F32)
-        k_chi2_f64<float><<<npix, kSynthBlock, 0, st>>>(pb, (const float *)obs, w, mu_px, npix, params, chi2);
+        k_chi2_f64<float><<<npix, kSynthBlock, 0, st>>>(pb, (const float *)obs, w, mu_px, npix, params, chi2,
+                                                        sub);
     else
-        k_chi2_f64<double><<<npix, kSynthBlock, 0, st>>>(pb, (const double *)obs, w, mu_px, npix, params, chi2);
+        k_chi2_f64<double><<<npix, kSynthBlock, 0, st>>>(pb, (const double *)obs, w, mu_px, npix, params,
+                                                         chi2, sub);
     return cudaGetLastError();
 }
 
