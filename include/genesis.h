@@ -388,6 +388,20 @@ int me_select(const int *flag, int npix, int want, int *index, int *count, void 
               size_t scratch_bytes, void *stream);
 
 /*
+ * me_select_static - me_select without caller scratch and without any
+ * allocation: its tile counts live in a file-scope device array of the
+ * library, sized for npix <= ME_SELECT_STATIC_MAX_PIX (32 KiB), whose address
+ * is looked up once per device at set-up.  The paper has no counterpart; this
+ * is a deployment convenience for callers that must not allocate.  npix above
+ * the limit -> ME_EINVAL.  Every call on a device shares that array, so calls
+ * that overlap in time (other streams or threads) race and must be serialised
+ * by the caller; calls in order on one stream are safe.  Results equal
+ * me_select's.
+ */
+#define ME_SELECT_STATIC_MAX_PIX (1 << 24)
+int me_select_static(const int *flag, int npix, int want, int *index, int *count, void *stream);
+
+/*
  * ga_invert_subset - ga_invert_batch on a subset of a map, with the Section
  * 4.5 seeds and polarity restriction.  Block b inverts pixel index[b] for
  * b < *count (index and count on the device, e.g. from me_select; index NULL

@@ -107,6 +107,7 @@ _SIGNATURES = {
                      _VP, _VP, _VP, _VP, _VP], C.c_int),
     "me_select_scratch_bytes": ([C.c_int], C.c_size_t),
     "me_select": ([_VP, C.c_int, C.c_int, _VP, _VP, _VP, C.c_size_t, _VP], C.c_int),
+    "me_select_static": ([_VP, C.c_int, C.c_int, _VP, _VP, _VP], C.c_int),
     "ga_invert_subset": ([_P, _VP, _VP, _VP, C.c_int, C.c_uint64, C.POINTER(MeBounds), C.POINTER(GaConfig),
                           _VP, C.c_int, _VP, _VP, _VP, _VP, _VP, _VP, _VP], C.c_int),
     "lm_polish_subset": ([_P, _VP, _VP, _VP, C.c_int, C.POINTER(MeBounds), C.c_int, C.c_double, _VP, _VP,

@@ -284,6 +284,18 @@ def select(flag, want=1):
     return index[:npix], count
 
 
+def select_static(flag, want=1):
+    """select() through me_select_static: no scratch, no allocation in the
+    library (the shared tile array limits npix to ME_SELECT_STATIC_MAX_PIX;
+    overlapping calls race)."""
+    npix = flag.shape[0]
+    _need(flag, torch.int32, (npix,), "flag")
+    index = torch.empty(max(npix, 1), dtype=torch.int32, device=flag.device)
+    count = torch.empty(1, dtype=torch.int32, device=flag.device)
+    L.check(L.load().me_select_static(_ptr(flag), npix, int(want), _ptr(index), _ptr(count), _stream()))
+    return index[:npix], count
+
+
 def ga_invert_subset(pb: Problem, obs, lo, hi, ga: GaSettings, index=None, count=None, seeds=None,
                      polarity=None, w=None, mu_px=None, pixel_id0=0, best=None, chi2=None, want_genes=False):
     """ga_invert_batch on the pixels index[:count] of a map, seeded and

@@ -114,6 +114,11 @@ HostTables build_tables()
 std::mutex g_init_mu;
 bool g_dev_ready[256];
 
+// Per device: the address of me_select_static's file-scope tile array,
+// looked up once at set-up.
+static void *g_select_static[256];
+static size_t g_select_static_bytes = 0;
+
 int ensure_device()
 {
     int dev = 0;
@@ -126,6 +131,8 @@ int ensure_device()
     if ((e = upload_tables_ga(t)) != cudaSuccess) return cuda_fail(e, "upload tables");
     if ((e = upload_tables_synth(t)) != cudaSuccess) return cuda_fail(e, "upload tables");
     if ((e = upload_tables_lm(t)) != cudaSuccess) return cuda_fail(e, "upload tables");
+    if ((e = select_static_scratch(&g_select_static[dev], &g_select_static_bytes)) != cudaSuccess)
+        return cuda_fail(e, "select scratch address");
     g_dev_ready[dev] = true;
     return ME_OK;
 }
@@ -539,6 +546,22 @@ int me_select(const int *flag, int npix, int want, int *index, int *count, void 
     if (rc) return rc;
     cudaError_t e = launch_select(flag, npix, want, index, count, scratch, as_stream(stream));
     return e == cudaSuccess ? ME_OK : cuda_fail(e, "me_select launch");
+}
+
+int me_select_static(const int *flag, int npix, int want, int *index, int *count, void *stream)
+{
+    if (npix < 0 || npix > ME_SELECT_STATIC_MAX_PIX)
+        return fail(ME_EINVAL, "npix must be in [0, ME_SELECT_STATIC_MAX_PIX]");
+    if (!count) return fail(ME_EINVAL, "count must be non-NULL");
+    if (npix > 0 && (!flag || !index)) return fail(ME_EINVAL, "flag and index must be non-NULL");
+    int rc = ensure_device();
+    if (rc) return rc;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (g_select_static_bytes < select_scratch_bytes(npix)) return fail(ME_EINVAL, "static scratch too small");
+    e = launch_select(flag, npix, want, index, count, g_select_static[dev], as_stream(stream));
+    return e == cudaSuccess ? ME_OK : cuda_fail(e, "me_select_static launch");
 }
 
 int lm_uncertainty(const me_problem *pb, const void *obs, const double *w, const double *mu_px,

@@ -11,6 +11,12 @@ constexpr int kSelectTile = 2048;    // flags per selection tile
 constexpr int kSelectBlock = 256;    // threads per selection block, 8 flags each
 constexpr double kPi = 3.14159265358979323846;
 
+// Tile counts of me_select_static: a file-scope device array sized for
+// ME_SELECT_STATIC_MAX_PIX flags (8192 tiles, 32 KiB).  Every slot a call uses
+// is written by its count pass before the scan reads it, so nothing has to
+// start at zero; concurrent calls share it and therefore race.
+static __device__ __align__(256) int g_select_tiles[(ME_SELECT_STATIC_MAX_PIX + kSelectTile - 1) / kSelectTile];
+
 // One pixel's Stokes rows as FP64 values.
 template <class RO> struct Rows {
     const RO *o;
@@ -347,6 +353,12 @@ cudaError_t launch_classify(const KProblem &pb, int dtype, const void *obs, int 
     else
         k_classify<double><<<grid, kClassifyBlock, 0, st>>>(pb, (const double *)obs, npix, c);
     return cudaGetLastError();
+}
+
+cudaError_t select_static_scratch(void **ptr, size_t *bytes)
+{
+    *bytes = sizeof(g_select_tiles);
+    return cudaGetSymbolAddress(ptr, g_select_tiles);
 }
 
 size_t select_scratch_bytes(int npix)

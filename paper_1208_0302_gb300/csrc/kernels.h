@@ -88,6 +88,8 @@ cudaError_t launch_classify(const KProblem &pb, int dtype, const void *obs, int 
                             cudaStream_t st);
 // Order-preserving selection of the pixels whose flag equals want.
 size_t select_scratch_bytes(int npix);
+// Address and size of the file-scope tile array of me_select_static.
+cudaError_t select_static_scratch(void **ptr, size_t *bytes);
 cudaError_t launch_select(const int *flag, int npix, int want, int *index, int *count, void *scratch,
                           cudaStream_t st);
 
