@@ -122,7 +122,7 @@ def lib():
             L.or_ga_restart.argtypes = [_U16, _D, C.c_int, C.c_int, C.c_uint64, _I32]
             L.or_ga_invert.argtypes = [P, _D, _DN, _DN, C.c_double, C.c_int, C.c_uint64,
                                        _D, _D, C.POINTER(_GaConfig), _DN, C.c_int, _I32N,
-                                       _D, _D, _U16N, _DN, C.c_int]
+                                       _DN, _D, _D, _U16N, _DN, C.c_int]
             L.or_ga_encode.argtypes = [C.c_double, C.c_double, C.c_double]
             L.or_ga_encode.restype = C.c_uint16
             L.or_polarity_bounds.argtypes = [C.c_int, C.c_double, C.c_double, C.POINTER(C.c_double),
@@ -130,7 +130,8 @@ def lib():
             L.or_ga_invert.restype = C.c_int
             L.or_jacobian.argtypes = [P, _D, C.c_double, _D]
             L.or_lm_polish.argtypes = [P, _D, _DN, _DN, C.c_double, C.c_int, _D, _D,
-                                       C.c_int, C.c_double, _D, _D, C.c_int]
+                                       C.c_int, C.c_double, C.c_uint, _D, _D, C.c_int]
+            L.or_prefit_bounds.argtypes = [_D, C.c_int, _D, _D, _D, _D, _D]
             L.or_lm_polish.restype = C.c_int
             L.or_line_centre.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, C.c_int, C.c_int, C.c_int,
                                          _D, _I32]
@@ -310,9 +311,10 @@ def ga_restart(genes, f, sobol_next):
 
 
 def ga_invert(pb, obs, lo, hi, cfg, w=None, mu=1.0, mu_px=None, pixel_id0=0,
-              nthreads=None, want_margin=False, seeds=None, polarity=None):
+              nthreads=None, want_margin=False, seeds=None, polarity=None, bounds_px=None):
     """Algorithm 1 per pixel; returns dict(best, chi2, genes[, margin]).
-    seeds [npix][nseed][3] (B, psi, chi) and polarity [npix] of Section 4.5."""
+    seeds [npix][nseed][3] (B, psi, chi) and polarity [npix] of Section 4.5;
+    bounds_px [npix][2][9] per-pixel bounds (Section 4.3)."""
     pb = _problem(pb)
     obs = _f64(obs)
     npix = obs.shape[0]
@@ -329,7 +331,8 @@ def ga_invert(pb, obs, lo, hi, cfg, w=None, mu=1.0, mu_px=None, pixel_id0=0,
     rc = lib().or_ga_invert(pb.ref(), obs, None if w is None else _f64(w),
                             None if mu_px is None else _f64(mu_px), float(mu), npix,
                             int(pixel_id0), _f64(lo), _f64(hi), C.byref(cfg), seeds, nseed,
-                            polarity, best, c2, genes, margin, nthreads or nthreads_default())
+                            polarity, None if bounds_px is None else _f64(bounds_px), best, c2, genes,
+                            margin, nthreads or nthreads_default())
     if rc != 0:
         raise ValueError("or_ga_invert rejected its arguments")
     out = {"best": best, "chi2": c2, "genes": genes}
@@ -349,8 +352,9 @@ def jacobian(pb, params, mu=1.0):
 
 
 def lm_polish(pb, obs, params, lo, hi, iters=10, lambda0=1e-3, w=None, mu=1.0,
-              mu_px=None, nthreads=None):
-    """Levenberg-Marquardt polish; returns (params [npix,9], chi2 [npix])."""
+              mu_px=None, nthreads=None, free_mask=0x1FF):
+    """Levenberg-Marquardt polish; returns (params [npix,9], chi2 [npix]).
+    Parameters outside free_mask (bit k = parameter k) are held."""
     pb = _problem(pb)
     obs = _f64(obs)
     npix = obs.shape[0]
@@ -358,7 +362,7 @@ def lm_polish(pb, obs, params, lo, hi, iters=10, lambda0=1e-3, w=None, mu=1.0,
     c2 = np.empty(npix)
     rc = lib().or_lm_polish(pb.ref(), obs, None if w is None else _f64(w),
                             None if mu_px is None else _f64(mu_px), float(mu), npix,
-                            _f64(lo), _f64(hi), int(iters), float(lambda0), p, c2,
+                            _f64(lo), _f64(hi), int(iters), float(lambda0), int(free_mask), p, c2,
                             nthreads or nthreads_default())
     if rc != 0:
         raise ValueError("or_lm_polish rejected its arguments")
@@ -419,3 +423,11 @@ def polarity_bounds(pol, lo, hi):
     a, b = C.c_double(), C.c_double()
     lib().or_polarity_bounds(int(pol), float(lo), float(hi), C.byref(a), C.byref(b))
     return a.value, b.value
+
+
+def prefit_bounds(p_hat, lo, hi, lower, upper):
+    """Per-pixel bounds [npix][2][9] around a thermodynamic prefit (Section 4.3)."""
+    p = _f64(np.asarray(p_hat, dtype=np.float64).reshape(-1, NPAR))
+    out = np.empty((p.shape[0], 2, NPAR))
+    lib().or_prefit_bounds(p, p.shape[0], _f64(lo), _f64(hi), _f64(lower), _f64(upper), out)
+    return out

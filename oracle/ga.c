@@ -238,6 +238,7 @@ typedef struct {
     const double *seeds;
     int nseed;
     const int *polarity;
+    const double *bounds_px;
     double *best, *chi2, *margin;
     uint16_t *best_genes;
     int t0, t1;
@@ -261,9 +262,14 @@ static void ga_pixel(const ga_job *J, int ip)
     const double mu = J->mu_px ? J->mu_px[ip] : J->mu;
     const uint64_t pid = J->pid0 + (uint64_t)ip;
     double lo[OR_NPAR], hi[OR_NPAR];
-    memcpy(lo, J->glo, sizeof lo);
-    memcpy(hi, J->ghi, sizeof hi);
-    if (J->polarity) or_polarity_bounds(J->polarity[ip], J->glo[1], J->ghi[1], &lo[1], &hi[1]);
+    if (J->bounds_px) {
+        memcpy(lo, J->bounds_px + (size_t)ip * 2 * OR_NPAR, sizeof lo);
+        memcpy(hi, J->bounds_px + (size_t)ip * 2 * OR_NPAR + OR_NPAR, sizeof hi);
+    } else {
+        memcpy(lo, J->glo, sizeof lo);
+        memcpy(hi, J->ghi, sizeof hi);
+    }
+    if (J->polarity) or_polarity_bounds(J->polarity[ip], lo[1], hi[1], &lo[1], &hi[1]);
     double w[4];
     if (J->w) memcpy(w, J->w + (size_t)ip * 4, sizeof w);
     else or_weights_invmax(obs, nl, w);
@@ -335,7 +341,7 @@ int or_ga_invert(const or_problem *pb, const double *obs, const double *w,
                  const double *mu_px, double mu, int npix, uint64_t pid0,
                  const double *lo, const double *hi, const or_ga_config *cfg,
                  const double *seeds, int nseed, const int *polarity,
-                 double *best, double *chi2, uint16_t *best_genes,
+                 const double *bounds_px, double *best, double *chi2, uint16_t *best_genes,
                  double *margin, int nthreads)
 {
     if (cfg->npop < 2 || (cfg->npop & 1) || cfg->ngen < 0 || npix < 0) return 1;
@@ -346,7 +352,7 @@ int or_ga_invert(const or_problem *pb, const double *obs, const double *w,
     ga_job *jobs = (ga_job *)malloc(sizeof(ga_job) * nthreads);
     for (int t = 0; t < nthreads; ++t) {
         ga_job J = {pb, obs, w, mu_px, mu, npix, pid0, lo, hi, cfg, seeds, nseed, polarity,
-                    best, chi2, margin, best_genes, (int)((long)npix * t / nthreads),
+                    bounds_px, best, chi2, margin, best_genes, (int)((long)npix * t / nthreads),
                     (int)((long)npix * (t + 1) / nthreads)};
         jobs[t] = J;
         pthread_create(&th[t], NULL, ga_worker, &jobs[t]);
@@ -354,4 +360,21 @@ int or_ga_invert(const or_problem *pb, const double *obs, const double *w,
     for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
     free(th); free(jobs);
     return 0;
+}
+
+void or_prefit_bounds(const double *p_hat, int npix, const double *lo, const double *hi,
+                      const double *lower, const double *upper, double *out)
+{
+    for (int ip = 0; ip < npix; ++ip) {
+        const double *p = p_hat + (size_t)ip * OR_NPAR;
+        double *ol = out + (size_t)ip * 2 * OR_NPAR, *oh = ol + OR_NPAR;
+        for (int k = 0; k < OR_NPAR; ++k) {
+            double a = p[k] - lower[k], b = p[k] + upper[k];
+            if (!(a > lo[k])) a = lo[k];
+            if (!(b < hi[k])) b = hi[k];
+            if (!(a < b)) { a = lo[k]; b = hi[k]; }
+            ol[k] = a;
+            oh[k] = b;
+        }
+    }
 }

@@ -11,7 +11,10 @@
  * and retries.  The trial vector p + delta has its azimuth wrapped into
  * [0, 180) and is then clamped to the bounds; it is accepted if its chi2 is
  * lower (lambda /= 10), otherwise rejected (lambda *= 10).  A fixed number of
- * trial steps is taken.
+ * trial steps is taken.  Parameters outside free_mask (bit k = parameter k)
+ * are held: their Jacobian columns are zero, so A and g have zero rows and
+ * columns there and delta_k = 0 (Section 4.3's prefit fits Stokes I with the
+ * field held at B = 0).
  */
 #include <math.h>
 #include <pthread.h>
@@ -93,7 +96,7 @@ static double wrap_azimuth(double chi)
 
 static void lm_pixel(const or_problem *pb, const double *obs, const double *w,
                      double mu, const double *lo, const double *hi, int iters,
-                     double lambda0, double *p, double *chi2_out)
+                     double lambda0, unsigned free_mask, double *p, double *chi2_out)
 {
     const int nl = pb->n_lambda, ns = 4 * nl, M = OR_NPAR;
     double *model = (double *)malloc(sizeof(double) * ns);
@@ -106,6 +109,9 @@ static void lm_pixel(const or_problem *pb, const double *obs, const double *w,
     for (int it = 0; it < iters; ++it) {
         if (need_jac) {
             or_jacobian(pb, p, mu, jac);
+            for (int i = 0; i < ns; ++i)
+                for (int a = 0; a < M; ++a)
+                    if (!((free_mask >> a) & 1u)) jac[(size_t)i * M + a] = 0.0;
             memset(A, 0, sizeof A);
             memset(g, 0, sizeof g);
             for (int i = 0; i < ns; ++i) {
@@ -227,6 +233,7 @@ typedef struct {
     const double *lo, *hi;
     int iters;
     double lambda0;
+    unsigned free_mask;
     double *params, *chi2;
     const double *sparams;
     double *stokes;
@@ -243,7 +250,7 @@ static void *lm_worker(void *arg)
         if (J->w) memcpy(w, J->w + (size_t)ip * 4, sizeof w);
         else or_weights_invmax(obs, nl, w);
         const double mu = J->mu_px ? J->mu_px[ip] : J->mu;
-        lm_pixel(J->pb, obs, w, mu, J->lo, J->hi, J->iters, J->lambda0,
+        lm_pixel(J->pb, obs, w, mu, J->lo, J->hi, J->iters, J->lambda0, J->free_mask,
                  J->params + (size_t)ip * OR_NPAR, J->chi2 + ip);
     }
     return NULL;
@@ -278,7 +285,7 @@ static void run_threads(lm_job *base, int n, int nthreads, void *(*fn)(void *))
 
 int or_lm_polish(const or_problem *pb, const double *obs, const double *w,
                  const double *mu_px, double mu, int npix, const double *lo,
-                 const double *hi, int iters, double lambda0,
+                 const double *hi, int iters, double lambda0, unsigned free_mask,
                  double *params_inout, double *chi2_out, int nthreads)
 {
     if (npix < 0 || iters < 0) return 1;
@@ -286,6 +293,7 @@ int or_lm_polish(const or_problem *pb, const double *obs, const double *w,
     memset(&base, 0, sizeof base);
     base.pb = pb; base.obs = obs; base.w = w; base.mu_px = mu_px; base.mu = mu;
     base.lo = lo; base.hi = hi; base.iters = iters; base.lambda0 = lambda0;
+    base.free_mask = free_mask;
     base.params = params_inout; base.chi2 = chi2_out;
     run_threads(&base, npix, nthreads, lm_worker);
     return 0;

@@ -116,14 +116,15 @@ void or_ga_restart(uint16_t *genes, const double *f, int npop, int m,
  * step.  Section 4.5: seeds [npix][nseed][3] (B, psi, chi; NaN keeps the
  * Sobol gene) replace those genes of the last nseed <= npop/2 individuals of
  * P0; polarity [npix] (may be NULL) restricts the inclination domain per
- * pixel (or_polarity_bounds). */
+ * pixel (or_polarity_bounds).  bounds_px [npix][2][m] (may be NULL) replaces
+ * lo/hi per pixel (Section 4.3), the polarity applying on top. */
 uint16_t or_ga_encode(double x, double lo, double hi);
 void or_polarity_bounds(int pol, double lo, double hi, double *plo, double *phi);
 int or_ga_invert(const or_problem *pb, const double *obs, const double *w,
                  const double *mu_px, double mu, int npix, uint64_t pixel_id0,
                  const double *lo, const double *hi, const or_ga_config *cfg,
                  const double *seeds, int nseed, const int *polarity,
-                 double *best, double *chi2, uint16_t *best_genes,
+                 const double *bounds_px, double *best, double *chi2, uint16_t *best_genes,
                  double *margin, int nthreads);
 
 /* Jacobian d stokes / d p, [4*n_lambda][OR_NPAR], by central differences
@@ -131,11 +132,18 @@ int or_ga_invert(const or_problem *pb, const double *obs, const double *w,
 void or_jacobian(const or_problem *pb, const double *p, double mu, double *jac);
 
 /* Levenberg-Marquardt polish of npix pixels (Marquardt damping). params_inout
- * [npix][OR_NPAR]; chi2_out [npix]. */
+ * [npix][OR_NPAR]; chi2_out [npix]; parameters outside free_mask are held. */
 int or_lm_polish(const or_problem *pb, const double *obs, const double *w,
                  const double *mu_px, double mu, int npix, const double *lo,
-                 const double *hi, int iters, double lambda0,
+                 const double *hi, int iters, double lambda0, unsigned free_mask,
                  double *params_inout, double *chi2_out, int nthreads);
+
+/* Section 4.3 bounds from a thermodynamic prefit p_hat [npix][OR_NPAR]:
+ * lo'_k = max(lo_k, p_hat_k - lower_k), hi'_k = min(hi_k, p_hat_k + upper_k)
+ * (an infinite margin keeps the global bound); where that leaves no interval
+ * (or p_hat_k is NaN) the global bounds stay.  out [npix][2][OR_NPAR]. */
+void or_prefit_bounds(const double *p_hat, int npix, const double *lo, const double *hi,
+                      const double *lower, const double *upper, double *out);
 
 /* Section 4.1 line centre by centre of symmetry (see me.c). */
 void or_line_centre(const double *rows, int npix, int stride, int nl, const double *lam, int half_width,
