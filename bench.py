@@ -35,11 +35,12 @@ METRIC = "pixels inverted/s at fixed median chi2 vs plain FP64 GA"
 WORKLOAD = "two-line Fe I 6301.5+6302.5 ME inversion, 256x256 px, 128 lambda, npop 128, 200 gen, FP32 GA + 10 L-M"
 NPOP, NGEN, LM_ITERS = 128, 200, 10
 KERNELS_PER_STEP = 4  # GA evolve, FP64 chi2, L-M, FP64 chi2
-# DRAM bytes (read + write) per pixel of one GA launch, from the ncu capture in
-# profiles/k_ga_evolve_two_line_1024px.md (1024-pixel case, scaled per pixel;
-# traffic grows in proportion to pixels).  Set to None when the kernel changes
-# until it is captured again.
-GA_DRAM_BYTES_PER_PIXEL = None  # kernel changed since the last capture
+# DRAM bytes (read + write) per pixel of one GA launch, from an ncu capture of
+# k_ga_evolve on the 1024-pixel two-line case (dram__bytes_read.sum 2213888 +
+# dram__bytes_write.sum 1536, divided by 1024; traffic grows in proportion to
+# pixels: each block reads its pixel's cube row once).  Set to None whenever
+# the kernel changes, until it is captured again.
+GA_DRAM_BYTES_PER_PIXEL = (2213888 + 1536) / 1024
 
 
 def parse():

@@ -415,17 +415,42 @@ int me_select_static(const int *flag, int npix, int want, int *index, int *count
  *   polarity  dev int [npix] or NULL: +1 restricts the inclination domain to
  *             [lo, min(hi, 90)], -1 to [max(lo, 90), hi] (0, or an empty half:
  *             unrestricted); the decode of that gene uses it throughout.
+ *   bounds_px dev double [npix][2][ME_NPAR] or NULL: per-pixel search domain
+ *             (lo row, hi row; Section 4.3, e.g. from me_prefit_bounds) in
+ *             place of *bounds for the decode and the seed encoding; the
+ *             polarity restriction applies on top of it.
  */
 int ga_invert_subset(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
                      int npix, uint64_t pixel_id0, const me_bounds *bounds, const ga_config *cfg,
-                     const double *seeds, int nseed, const int *polarity, const int *index,
-                     const int *count, double *best, double *chi2, uint16_t *best_genes,
-                     void *stream);
+                     const double *seeds, int nseed, const int *polarity, const double *bounds_px,
+                     const int *index, const int *count, double *best, double *chi2,
+                     uint16_t *best_genes, void *stream);
 
-/* lm_polish on the subset index[0 .. *count) of a map (as ga_invert_subset). */
-int lm_polish_subset(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
-                     int npix, const me_bounds *bounds, int iters, double lambda0, const int *index,
-                     const int *count, double *params_inout, double *chi2_out, void *stream);
+/*
+ * lm_fit - lm_polish with a parameter mask, on the subset index[0 .. *count)
+ * of a map (as ga_invert_subset; NULL index and count = all npix pixels).
+ * Parameters whose bit in free_mask is clear are held: their rows and
+ * columns of the normal equations are zeroed, so their step is exactly 0.
+ * With B, theta, chi held at B = 0 and weights (w_I, 0, 0, 0) this is the
+ * Section 4.3 thermodynamic prefit: a non-magnetic fit of Stokes I.
+ */
+int lm_fit(const me_problem *pb, const void *obs, const double *w, const double *mu_px, int npix,
+           const me_bounds *bounds, int iters, double lambda0, unsigned free_mask, const int *index,
+           const int *count, double *params_inout, double *chi2_out, void *stream);
+
+/*
+ * me_prefit_bounds - Section 4.3: the prefit's values constrain the GA's
+ * search to ranges around them.  For pixel i and parameter k:
+ *   lo'_ik = max(lo_k, p_hat_ik - lower[k]), hi'_ik = min(hi_k, p_hat_ik + upper[k]),
+ * an infinite margin keeping the global bound; where that leaves no interval
+ * (or p_hat_ik is NaN) the global [lo_k, hi_k] stays.
+ *   p_hat      dev double [npix][ME_NPAR] (e.g. lm_fit's prefit)
+ *   lower, upper  host double [ME_NPAR] margins (not NaN)
+ *   bounds_px  dev double [npix][2][ME_NPAR] (output: lo' row, then hi' row),
+ *              the input of ga_invert_subset
+ */
+int me_prefit_bounds(const double *p_hat, int npix, const me_bounds *bounds, const double *lower,
+                     const double *upper, double *bounds_px, void *stream);
 
 /* ------------------------------------------------ GA operator entry points
  * The operators of ga_invert_batch run alone on caller-given populations, so

@@ -109,9 +109,10 @@ _SIGNATURES = {
     "me_select": ([_VP, C.c_int, C.c_int, _VP, _VP, _VP, C.c_size_t, _VP], C.c_int),
     "me_select_static": ([_VP, C.c_int, C.c_int, _VP, _VP, _VP], C.c_int),
     "ga_invert_subset": ([_P, _VP, _VP, _VP, C.c_int, C.c_uint64, C.POINTER(MeBounds), C.POINTER(GaConfig),
-                          _VP, C.c_int, _VP, _VP, _VP, _VP, _VP, _VP, _VP], C.c_int),
-    "lm_polish_subset": ([_P, _VP, _VP, _VP, C.c_int, C.POINTER(MeBounds), C.c_int, C.c_double, _VP, _VP,
-                          _VP, _VP, _VP], C.c_int),
+                          _VP, C.c_int, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], C.c_int),
+    "lm_fit": ([_P, _VP, _VP, _VP, C.c_int, C.POINTER(MeBounds), C.c_int, C.c_double, C.c_uint, _VP, _VP,
+                _VP, _VP, _VP], C.c_int),
+    "me_prefit_bounds": ([_VP, C.c_int, C.POINTER(MeBounds), _VP, _VP, _VP, _VP], C.c_int),
     "ga_breed": ([_VP, _VP, C.c_int, C.c_int, C.c_uint64, C.c_int, C.POINTER(GaConfig), _VP, _VP,
                   _VP], C.c_int),
     "ga_restart": ([_VP, _VP, C.c_int, C.c_int, C.c_uint64, _VP], C.c_int),

@@ -16,6 +16,7 @@ from . import _lib as L
 
 NPAR = L.ME_NPAR
 F32, F64 = L.ME_F32, L.ME_F64
+ALL_FREE = (1 << NPAR) - 1
 
 
 def _stream():
@@ -297,10 +298,12 @@ def select_static(flag, want=1):
 
 
 def ga_invert_subset(pb: Problem, obs, lo, hi, ga: GaSettings, index=None, count=None, seeds=None,
-                     polarity=None, w=None, mu_px=None, pixel_id0=0, best=None, chi2=None, want_genes=False):
+                     polarity=None, bounds_px=None, w=None, mu_px=None, pixel_id0=0, best=None, chi2=None,
+                     want_genes=False):
     """ga_invert_batch on the pixels index[:count] of a map, seeded and
-    polarity-restricted (Section 4.5).  best/chi2 (map-sized) are written in
-    place for those pixels and returned."""
+    polarity-restricted (Section 4.5), optionally in per-pixel bounds
+    (Section 4.3).  best/chi2 (map-sized) are written in place for those
+    pixels and returned."""
     npix = obs.shape[0]
     _need(obs, pb.torch_dtype, (npix, 4, pb.n_lambda), "obs")
     _need(w, torch.float64, (npix, 4), "w")
@@ -308,6 +311,7 @@ def ga_invert_subset(pb: Problem, obs, lo, hi, ga: GaSettings, index=None, count
     _need(index, torch.int32, None, "index")
     _need(count, torch.int32, (1,), "count")
     _need(polarity, torch.int32, (npix,), "polarity")
+    _need(bounds_px, torch.float64, (npix, 2, NPAR), "bounds_px")
     nseed = 0
     if seeds is not None:
         _need(seeds, torch.float64, None, "seeds")
@@ -330,17 +334,18 @@ def ga_invert_subset(pb: Problem, obs, lo, hi, ga: GaSettings, index=None, count
     b = bounds(lo, hi)
     L.check(L.load().ga_invert_subset(pb.ref(), _ptr(obs), _ptr(w), _ptr(mu_px), npix, int(pixel_id0),
                                       C.byref(b), C.byref(cfg), _ptr(seeds), nseed, _ptr(polarity),
-                                      _ptr(index), _ptr(count), _ptr(best), _ptr(chi2), _ptr(genes),
-                                      _stream()))
+                                      _ptr(bounds_px), _ptr(index), _ptr(count), _ptr(best), _ptr(chi2),
+                                      _ptr(genes), _stream()))
     if want_genes:
         return best, chi2, genes
     return best, chi2
 
 
-def lm_polish_subset(pb: Problem, obs, params, lo, hi, index=None, count=None, iters=10, lambda0=1e-3,
-                     w=None, mu_px=None, chi2=None):
-    """lm_polish on the pixels index[:count] of a map; params (map-sized) and
-    chi2 are updated in place for those pixels and returned."""
+def lm_fit(pb: Problem, obs, params, lo, hi, index=None, count=None, iters=10, lambda0=1e-3, w=None,
+           mu_px=None, chi2=None, free_mask=ALL_FREE):
+    """L-M on the pixels index[:count] of a map with the parameters outside
+    free_mask held; params (map-sized) and chi2 are updated in place for
+    those pixels and returned."""
     npix = obs.shape[0]
     _need(obs, pb.torch_dtype, (npix, 4, pb.n_lambda), "obs")
     _need(params, torch.float64, (npix, NPAR), "params")
@@ -352,19 +357,67 @@ def lm_polish_subset(pb: Problem, obs, params, lo, hi, index=None, count=None, i
         raise ValueError("index must hold npix entries")
     _need(chi2, torch.float64, (npix,), "chi2")
     b = bounds(lo, hi)
-    L.check(L.load().lm_polish_subset(pb.ref(), _ptr(obs), _ptr(w), _ptr(mu_px), npix, C.byref(b), int(iters),
-                                      float(lambda0), _ptr(index), _ptr(count), _ptr(params), _ptr(chi2),
-                                      _stream()))
+    L.check(L.load().lm_fit(pb.ref(), _ptr(obs), _ptr(w), _ptr(mu_px), npix, C.byref(b), int(iters),
+                            float(lambda0), int(free_mask), _ptr(index), _ptr(count), _ptr(params), _ptr(chi2),
+                            _stream()))
     return params, chi2
 
 
+def lm_polish_subset(pb: Problem, obs, params, lo, hi, index=None, count=None, iters=10, lambda0=1e-3,
+                     w=None, mu_px=None, chi2=None):
+    """lm_fit with every parameter free."""
+    return lm_fit(pb, obs, params, lo, hi, index=index, count=count, iters=iters, lambda0=lambda0, w=w,
+                  mu_px=mu_px, chi2=chi2)
+
+
+# Section 4.3 prefit: Stokes I, non-magnetic (B, theta, chi held at 0, 90, 0)
+PREFIT_MASK = 0x1F8
+PREFIT_START = (0.0, 90.0, 0.0, 0.0, 35.0, 0.2, 5.0, 0.3, 0.7)
+# margins of the bound rule (B theta chi v dlD a eta0 S0 S1): Zeeman broadening
+# only widens the profile, so the non-magnetic fit bounds the Doppler width
+# and damping from above and the line strength from below
+PREFIT_LOWER = (float("inf"),) * 3 + (1.0, float("inf"), float("inf"), 3.0, 0.15, 0.15)
+PREFIT_UPPER = (float("inf"),) * 3 + (1.0, 3.0, 0.15, float("inf"), 0.15, 0.15)
+
+
+def thermo_prefit(pb: Problem, obs, lo, hi, index=None, count=None, iters=40, lambda0=1e-3, mu_px=None,
+                  start=PREFIT_START):
+    """Section 4.3 thermodynamic prefit: L-M fit of Stokes I alone with the
+    field held at zero, from a generic start -> (params [npix, 9], chi2)."""
+    npix = obs.shape[0]
+    dev = obs.device
+    params = torch.tensor(start, dtype=torch.float64, device=dev).repeat(npix, 1).contiguous()
+    w = torch.zeros((npix, 4), dtype=torch.float64, device=dev)
+    w[:, 0] = 1.0
+    chi2 = torch.full((npix,), float("nan"), dtype=torch.float64, device=dev)
+    return lm_fit(pb, obs, params, lo, hi, index=index, count=count, iters=iters, lambda0=lambda0, w=w,
+                  mu_px=mu_px, chi2=chi2, free_mask=PREFIT_MASK)
+
+
+def prefit_bounds(p_hat, lo, hi, lower=PREFIT_LOWER, upper=PREFIT_UPPER):
+    """Per-pixel search bounds [npix, 2, 9] around a prefit (me_prefit_bounds)."""
+    npix = p_hat.shape[0]
+    _need(p_hat, torch.float64, (npix, NPAR), "p_hat")
+    out = torch.empty((npix, 2, NPAR), dtype=torch.float64, device=p_hat.device)
+    lw = np.ascontiguousarray(lower, dtype=np.float64)
+    up = np.ascontiguousarray(upper, dtype=np.float64)
+    if lw.shape != (NPAR,) or up.shape != (NPAR,):
+        raise ValueError("lower and upper must hold 9 margins")
+    b = bounds(lo, hi)
+    L.check(L.load().me_prefit_bounds(_ptr(p_hat), npix, C.byref(b), C.c_void_p(lw.ctypes.data),
+                                      C.c_void_p(up.ctypes.data), _ptr(out), _stream()))
+    return out
+
+
 def invert_map(pb: Problem, obs, lo, hi, ga: GaSettings, p_thresh, quiet, line, core, nseed=4,
-               polarity=True, polish_iters=10, lambda0=1e-3, w=None, polish_w=None, mu_px=None, pixel_id0=0):
+               polarity=True, prefit=False, prefit_iters=40, polish_iters=10, lambda0=1e-3, w=None,
+               polish_w=None, mu_px=None, pixel_id0=0):
     """The Section 2 pipeline on a map, asynchronous on the current stream:
     classification (weak-field answer below the threshold), selection of the
-    pixels above it, the seeded, polarity-restricted GA and the L-M polish
-    on those.  Returns dict(best [npix, 9], chi2 [npix] (NaN for weak-field
-    pixels), flag, polarity, index, count, weak, seeds)."""
+    pixels above it, optionally the Section 4.3 prefit and its per-pixel
+    bounds, the seeded, polarity-restricted GA and the L-M polish on those.
+    Returns dict(best [npix, 9], chi2 [npix] (NaN for weak-field pixels),
+    flag, polarity, index, count, weak, seeds[, prefit, bounds_px])."""
     npix = obs.shape[0]
     dev = obs.device
     best = torch.full((npix, NPAR), float("nan"), dtype=torch.float64, device=dev)
@@ -373,12 +426,18 @@ def invert_map(pb: Problem, obs, lo, hi, ga: GaSettings, p_thresh, quiet, line, 
     index, count = select(cls["flag"], 1)
     sd = cls["seeds"][:, :nseed].contiguous() if nseed > 0 else None
     pol = cls["polarity"] if polarity else None
-    ga_invert_subset(pb, obs, lo, hi, ga, index=index, count=count, seeds=sd, polarity=pol, w=w, mu_px=mu_px,
-                     pixel_id0=pixel_id0, best=best, chi2=chi2)
+    extra = {}
+    bpx = None
+    if prefit:
+        p_hat, _ = thermo_prefit(pb, obs, lo, hi, index=index, count=count, iters=prefit_iters, mu_px=mu_px)
+        bpx = prefit_bounds(p_hat, lo, hi)
+        extra = {"prefit": p_hat, "bounds_px": bpx}
+    ga_invert_subset(pb, obs, lo, hi, ga, index=index, count=count, seeds=sd, polarity=pol, bounds_px=bpx, w=w,
+                     mu_px=mu_px, pixel_id0=pixel_id0, best=best, chi2=chi2)
     if polish_iters > 0:
         lm_polish_subset(pb, obs, best, lo, hi, index=index, count=count, iters=polish_iters, lambda0=lambda0,
                          w=polish_w if polish_w is not None else w, mu_px=mu_px, chi2=chi2)
-    return dict(cls, best=best, chi2=chi2, index=index, count=count)
+    return dict(cls, best=best, chi2=chi2, index=index, count=count, **extra)
 
 
 # ------------------------------------------------------------------ serving

@@ -424,10 +424,12 @@ int ga_invert_batch(const me_problem *pb, const void *obs, const double *w, cons
 
 int ga_invert_subset(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
                      int npix, uint64_t pixel_id0, const me_bounds *bounds, const ga_config *cfg,
-                     const double *seeds, int nseed, const int *polarity, const int *index,
-                     const int *count, double *best, double *chi2, uint16_t *best_genes, void *stream)
+                     const double *seeds, int nseed, const int *polarity, const double *bounds_px,
+                     const int *index, const int *count, double *best, double *chi2, uint16_t *best_genes,
+                     void *stream)
 {
-    return ga_invert_impl(pb, obs, w, mu_px, npix, pixel_id0, bounds, cfg, KSeed{seeds, nseed, polarity},
+    return ga_invert_impl(pb, obs, w, mu_px, npix, pixel_id0, bounds, cfg,
+                          KSeed{seeds, nseed, polarity, bounds_px},
                           KSub{index, count}, best, chi2, best_genes, stream, "ga_invert_subset launch");
 }
 
@@ -455,8 +457,8 @@ int ga_count_evaluations(const me_problem *pb, const void *obs, const double *w,
 }
 
 static int lm_polish_impl(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
-                          int npix, const me_bounds *bounds, int iters, double lambda0, KSub sub,
-                          double *params_inout, double *chi2_out, void *stream)
+                          int npix, const me_bounds *bounds, int iters, double lambda0, unsigned free_mask,
+                          KSub sub, double *params_inout, double *chi2_out, void *stream)
 {
     KProblem k;
     int rc = make_problem(pb, k);
@@ -471,6 +473,7 @@ static int lm_polish_impl(const me_problem *pb, const void *obs, const double *w
     std::memset(&lm, 0, sizeof lm);
     lm.iters = iters;
     lm.lambda0 = lambda0;
+    lm.free_mask = free_mask & ((1u << ME_NPAR) - 1u);
     for (int d = 0; d < ME_NPAR; ++d) {
         lm.lo[d] = bounds->lo[d];
         lm.hi[d] = bounds->hi[d];
@@ -488,16 +491,39 @@ int lm_polish(const me_problem *pb, const void *obs, const double *w, const doub
               const me_bounds *bounds, int iters, double lambda0, double *params_inout,
               double *chi2_out, void *stream)
 {
-    return lm_polish_impl(pb, obs, w, mu_px, npix, bounds, iters, lambda0, KSub{}, params_inout, chi2_out,
-                          stream);
+    return lm_polish_impl(pb, obs, w, mu_px, npix, bounds, iters, lambda0, (1u << ME_NPAR) - 1u, KSub{},
+                          params_inout, chi2_out, stream);
 }
 
-int lm_polish_subset(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
-                     int npix, const me_bounds *bounds, int iters, double lambda0, const int *index,
-                     const int *count, double *params_inout, double *chi2_out, void *stream)
+int lm_fit(const me_problem *pb, const void *obs, const double *w, const double *mu_px, int npix,
+           const me_bounds *bounds, int iters, double lambda0, unsigned free_mask, const int *index,
+           const int *count, double *params_inout, double *chi2_out, void *stream)
 {
-    return lm_polish_impl(pb, obs, w, mu_px, npix, bounds, iters, lambda0, KSub{index, count}, params_inout,
-                          chi2_out, stream);
+    return lm_polish_impl(pb, obs, w, mu_px, npix, bounds, iters, lambda0, free_mask, KSub{index, count},
+                          params_inout, chi2_out, stream);
+}
+
+int me_prefit_bounds(const double *p_hat, int npix, const me_bounds *bounds, const double *lower,
+                     const double *upper, double *bounds_px, void *stream)
+{
+    int rc = check_bounds(bounds);
+    if (rc) return rc;
+    if (npix < 0) return fail(ME_EINVAL, "npix must be >= 0");
+    if (!lower || !upper) return fail(ME_EINVAL, "lower and upper margins must be non-NULL");
+    if (npix == 0) return ME_OK;
+    if (!p_hat || !bounds_px) return fail(ME_EINVAL, "p_hat and bounds_px must be non-NULL");
+    if ((size_t)npix * ME_NPAR > (size_t)INT32_MAX) return fail(ME_EINVAL, "npix too large");
+    KPrefitBounds r;
+    for (int k = 0; k < ME_NPAR; ++k) {
+        if (std::isnan(lower[k]) || std::isnan(upper[k])) return fail(ME_EINVAL, "margins must not be NaN");
+        r.lo[k] = bounds->lo[k];
+        r.hi[k] = bounds->hi[k];
+        r.lower[k] = lower[k];
+        r.upper[k] = upper[k];
+    }
+    if ((rc = ensure_device())) return rc;
+    cudaError_t e = launch_prefit_bounds(p_hat, npix, r, bounds_px, as_stream(stream));
+    return e == cudaSuccess ? ME_OK : cuda_fail(e, "me_prefit_bounds launch");
 }
 
 int me_classify(const me_problem *pb, const void *obs, int npix, double p_thresh, int q_lo, int q_hi,

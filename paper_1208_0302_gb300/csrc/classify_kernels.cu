@@ -340,7 +340,37 @@ k_select_scatter(const int *__restrict__ flag, int npix, int want, const int *__
         if (bits & (1u << e)) index[pos++] = first + e;
 }
 
+// Section 4.3 bound rule, one thread per (pixel, parameter): [max(lo,
+// p - lower), min(hi, p + upper)], the global interval where that is empty
+// or the prefit is NaN.
+__global__ void k_prefit_bounds(const double *__restrict__ p_hat, int npix, const KPrefitBounds r,
+                                double *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npix * ME_NPAR) return;
+    const int pix = i / ME_NPAR, k = i - pix * ME_NPAR;
+    const double p = p_hat[i];
+    double a = __dsub_rn(p, r.lower[k]), b = __dadd_rn(p, r.upper[k]);
+    if (!(a > r.lo[k])) a = r.lo[k];
+    if (!(b < r.hi[k])) b = r.hi[k];
+    if (!(a < b)) {
+        a = r.lo[k];
+        b = r.hi[k];
+    }
+    out[(size_t)pix * 2 * ME_NPAR + k] = a;
+    out[(size_t)pix * 2 * ME_NPAR + ME_NPAR + k] = b;
+}
+
 }  // namespace
+
+cudaError_t launch_prefit_bounds(const double *p_hat, int npix, const KPrefitBounds &r, double *out,
+                                 cudaStream_t st)
+{
+    if (npix <= 0) return cudaSuccess;
+    const int n = npix * ME_NPAR;
+    k_prefit_bounds<<<(n + 255) / 256, 256, 0, st>>>(p_hat, npix, r, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_classify(const KProblem &pb, int dtype, const void *obs, int npix, const KClassify &c,
                             cudaStream_t st)

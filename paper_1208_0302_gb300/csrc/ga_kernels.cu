@@ -66,22 +66,23 @@ template <class R> __device__ __forceinline__ int padded_lambda(int nl)
 }
 
 template <class R> struct GaDecode;
-// The inclination (d = 1) decodes in the pixel's polarity-restricted domain,
-// held in shared memory (s_psi: double lo, hi; then float lo, scale).
+// The pixel's decode domain in shared memory (per-pixel bounds of Section
+// 4.3 and the polarity restriction of Section 4.5 already applied):
+// double lo[M], hi[M], then float lo[M], scale[M] = (hi - lo) / 65535.
+struct DecodeDomain {
+    double lo[ME_NPAR], hi[ME_NPAR];
+    float lo32[ME_NPAR], sc32[ME_NPAR];
+};
 template <> struct GaDecode<float> {
-    // FP32 GA: p = lo + g (hi - lo) / 65535, scale precomputed
-    static __device__ __forceinline__ float get(const KGa &ga, const float *lo32,
-                                                const float *sc32, const double *s_psi, int d, uint16_t g)
+    static __device__ __forceinline__ float get(const DecodeDomain &D, int d, uint16_t g)
     {
-        const float *p32 = (const float *)(s_psi + 2);
-        return d == 1 ? fmaf((float)g, p32[1], p32[0]) : fmaf((float)g, sc32[d], lo32[d]);
+        return fmaf((float)g, D.sc32[d], D.lo32[d]);
     }
 };
 template <> struct GaDecode<double> {
-    static __device__ __forceinline__ double get(const KGa &ga, const float *, const float *,
-                                                 const double *s_psi, int d, uint16_t g)
+    static __device__ __forceinline__ double get(const DecodeDomain &D, int d, uint16_t g)
     {
-        return d == 1 ? decode64(g, s_psi[0], s_psi[1]) : decode64(g, ga.lo[d], ga.hi[d]);
+        return decode64(g, D.lo[d], D.hi[d]);
     }
 };
 
@@ -266,7 +267,7 @@ __device__ __forceinline__ void breed_one(const KGa &ga, uint64_t pid, int t, in
 
 struct GaSmem {
     // byte offsets into dynamic shared memory
-    int obs, doff, fit, wmin, widx, w2, he, psi, genes, total;
+    int obs, doff, fit, wmin, widx, w2, he, dom, genes, total;
 };
 
 template <class R>
@@ -288,7 +289,7 @@ __host__ __device__ __forceinline__ GaSmem ga_smem_layout(int nl, int nlines, in
     L.widx = take(32 * 4, 16);
     L.w2 = take(4 * (int)sizeof(R), 16);
     L.he = take(4 * (int)sizeof(R), 16);
-    L.psi = take(32, 16);  // the pixel's inclination domain: double lo, hi; float lo, scale
+    L.dom = take((int)sizeof(DecodeDomain), 16);  // the pixel's decode domain
     L.genes = take(2 * npop * ME_NPAR * 2, 16);
     L.total = (o + 15) / 16 * 16;
     return L;
@@ -360,16 +361,10 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
     int *s_widx = (int *)(smem + L.widx);
     R *s_w2 = (R *)(smem + L.w2);
     R *s_he = (R *)(smem + L.he);
-    double *s_psi = (double *)(smem + L.psi);
+    DecodeDomain &D = *(DecodeDomain *)(smem + L.dom);
     uint16_t *s_genes = (uint16_t *)(smem + L.genes);
 
     // per-launch constants
-    float lo32[ME_NPAR], sc32[ME_NPAR];
-#pragma unroll
-    for (int d = 0; d < ME_NPAR; ++d) {
-        lo32[d] = (float)ga.lo[d];
-        sc32[d] = (float)((ga.hi[d] - ga.lo[d]) / 65535.0);
-    }
     const R inv_nu = R(1) / R(4 * nl - ME_NPAR);
     if (k < 4) s_he[k] = k < nlines ? R(pb.line[k].half_eta) : R(0);
     for (int i = k; i < 4 * padded_lambda<R>(nl); i += blockDim.x) {
@@ -383,14 +378,14 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
     for (int blk = blockIdx.x; blk < nrun; blk += gridDim.x) {
         const int pix = sub.index ? sub.index[blk] : blk;
         if (pix < 0 || pix >= npix) continue;  // a bad index skips the block, uniformly
-        if (k == 0) {  // the pixel's inclination domain (Section 4.5 polarity restriction)
-            double a = ga.lo[1], b = ga.hi[1];
-            if (sd.polarity) polarity_bounds(sd.polarity[pix], ga.lo[1], ga.hi[1], a, b);
-            s_psi[0] = a;
-            s_psi[1] = b;
-            float *p32 = (float *)(s_psi + 2);
-            p32[0] = (float)a;
-            p32[1] = (float)((b - a) / 65535.0);
+        if (k < ME_NPAR) {  // the pixel's decode domain of parameter k
+            double a = sd.bounds_px ? sd.bounds_px[(size_t)pix * 2 * ME_NPAR + k] : ga.lo[k];
+            double b = sd.bounds_px ? sd.bounds_px[(size_t)pix * 2 * ME_NPAR + ME_NPAR + k] : ga.hi[k];
+            if (k == 1 && sd.polarity) polarity_bounds(sd.polarity[pix], a, b, a, b);
+            D.lo[k] = a;
+            D.hi[k] = b;
+            D.lo32[k] = (float)a;
+            D.sc32[k] = (float)((b - a) / 65535.0);
         }
         // a1: stage the pixel's Stokes profiles from [4][nl] in HBM into the
         // shared-memory layout (16-byte vector loads when a vector stays in one row)
@@ -444,12 +439,12 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
         if (k >= npop - sd.nseed) {
             const double *sv = sd.seeds + ((size_t)pix * sd.nseed + (k - (npop - sd.nseed))) * 3;
             const double x0 = sv[0], x1 = sv[1], x2 = sv[2];
-            if (x0 == x0) g[0] = encode64(x0, ga.lo[0], ga.hi[0]);
-            if (x1 == x1) g[1] = encode64(x1, s_psi[0], s_psi[1]);
-            if (x2 == x2) g[2] = encode64(x2, ga.lo[2], ga.hi[2]);
+            if (x0 == x0) g[0] = encode64(x0, D.lo[0], D.hi[0]);
+            if (x1 == x1) g[1] = encode64(x1, D.lo[1], D.hi[1]);
+            if (x2 == x2) g[2] = encode64(x2, D.lo[2], D.hi[2]);
         }
 #pragma unroll
-        for (int d = 0; d < ME_NPAR; ++d) p[d] = GaDecode<R>::get(ga, lo32, sc32, s_psi, d, g[d]);
+        for (int d = 0; d < ME_NPAR; ++d) p[d] = GaDecode<R>::get(D, d, g[d]);
         int cur = 0;
 #pragma unroll
         for (int d = 0; d < ME_NPAR; ++d) s_genes[k * ME_NPAR + d] = g[d];
@@ -467,7 +462,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
 #pragma unroll
             for (int d = 0; d < ME_NPAR; ++d) {
                 s_nxt[k * ME_NPAR + d] = g[d];
-                p[d] = GaDecode<R>::get(ga, lo32, sc32, s_psi, d, g[d]);
+                p[d] = GaDecode<R>::get(D, d, g[d]);
             }
             cur ^= 1;
             s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior));
@@ -484,7 +479,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
                     for (int d = 0; d < ME_NPAR; ++d) {
                         g[d] = (uint16_t)(sobol_point(n, d) >> 16);
                         s_c[k * ME_NPAR + d] = g[d];
-                        p[d] = GaDecode<R>::get(ga, lo32, sc32, s_psi, d, g[d]);
+                        p[d] = GaDecode<R>::get(D, d, g[d]);
                     }
                     s_fit[k] = clean_fit(
                         fitness<R, NL, COUNT, PAT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior));
@@ -499,7 +494,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
         if (k < ME_NPAR) {
             const uint16_t gb = s_genes[cur * npop * ME_NPAR + b * ME_NPAR + k];
             best[(size_t)pix * ME_NPAR + k] =
-                k == 1 ? decode64(gb, s_psi[0], s_psi[1]) : decode64(gb, ga.lo[k], ga.hi[k]);
+                decode64(gb, D.lo[k], D.hi[k]);
             if (best_genes) best_genes[(size_t)pix * ME_NPAR + k] = gb;
         }
         __syncthreads();  // shared memory is reused by the next pixel

@@ -19,11 +19,13 @@ struct KGa {
 };
 
 // Section 4.5 seeds and polarity restriction: seeds [npix][nseed][3] of
-// (B, psi, chi), NaN = keep the Sobol gene; polarity [npix] of -1, 0, +1.
+// (B, psi, chi), NaN = keep the Sobol gene; polarity [npix] of -1, 0, +1;
+// per-pixel bounds [npix][2][M] of Section 4.3 (NULL = the launch's).
 struct KSeed {
     const double *seeds;
     int nseed;
     const int *polarity;
+    const double *bounds_px;
 };
 
 // A subset of a map: block b processes pixel index[b] for b < *count (both
@@ -36,7 +38,13 @@ struct KSub {
 struct KLm {
     int iters;
     double lambda0;
+    unsigned free_mask;  // bit k set: parameter k is fitted, else held
     double lo[ME_NPAR], hi[ME_NPAR];
+};
+
+// Section 4.3 bound rule around a prefit (margins per parameter).
+struct KPrefitBounds {
+    double lo[ME_NPAR], hi[ME_NPAR], lower[ME_NPAR], upper[ME_NPAR];
 };
 
 // Coefficient tables, computed once on the host.
@@ -86,6 +94,8 @@ struct KClassify {
 };
 cudaError_t launch_classify(const KProblem &pb, int dtype, const void *obs, int npix, const KClassify &c,
                             cudaStream_t st);
+cudaError_t launch_prefit_bounds(const double *p_hat, int npix, const KPrefitBounds &r, double *out,
+                                 cudaStream_t st);
 // Order-preserving selection of the pixels whose flag equals want.
 size_t select_scratch_bytes(int npix);
 // Address and size of the file-scope tile array of me_select_static.

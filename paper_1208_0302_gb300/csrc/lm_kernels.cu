@@ -256,6 +256,15 @@ k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const 
             need = false;
         }
         if (lane == 0) {
+            // held parameters: zero rows and columns, so their step is 0
+            for (int a = 0; a < ME_NPAR; ++a) {
+                if ((lm.free_mask >> a) & 1u) continue;
+                W.g[a] = 0.0;
+                for (int b = 0; b < ME_NPAR; ++b) {
+                    W.A[a * ME_NPAR + b] = 0.0;
+                    W.A[b * ME_NPAR + a] = 0.0;
+                }
+            }
             bool ok = false;
             for (int tries = 0; tries < 30 && !ok; ++tries) {
                 ok = damped_cholesky(W.A, W.g, lam, W.N, W.x);

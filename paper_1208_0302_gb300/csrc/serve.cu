@@ -139,6 +139,7 @@ int launch_request(serve_handle *h, Request *r)
         std::memset(&lm, 0, sizeof lm);
         lm.iters = q.polish_iters;
         lm.lambda0 = q.lambda0;
+        lm.free_mask = (1u << ME_NPAR) - 1u;
         for (int d = 0; d < ME_NPAR; ++d) {
             lm.lo[d] = q.bounds.lo[d];
             lm.hi[d] = q.bounds.hi[d];
