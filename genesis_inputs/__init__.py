@@ -48,15 +48,20 @@ def eta_ratio_6301(temperature_k: float = 5000.0) -> float:
 # prior ranges (uniform per pixel) = GA bounds
 PRIOR_LO = np.array([0.0, 0.0, 0.0, -3.0, 20.0, 0.0, 1.0, 0.1, 0.1])
 PRIOR_HI = np.array([3000.0, 180.0, 180.0, 3.0, 50.0, 0.5, 20.0, 1.0, 1.0])
+# with the fill fraction alpha in [0, 1] as a 10th parameter
+PRIOR_LO_FILL = np.append(PRIOR_LO, 0.0)
+PRIOR_HI_FILL = np.append(PRIOR_HI, 1.0)
 
 
 @dataclass
 class ProblemSpec:
-    """Line list + wavelength grid; lines are (lambda0 [A], g_eff, eta_ratio)."""
+    """Line list + wavelength grid; lines are (lambda0 [A], g_eff, eta_ratio).
+    fill: the magnetic fill fraction alpha is a 10th parameter."""
     lines: list
     lambda_grid: np.ndarray
     lambda_dop: float = FE6302[0]   # Doppler-width parameter quoted at 6302.5 A
     mu: float = 1.0
+    fill: bool = False
 
     @property
     def n_lambda(self) -> int:
@@ -114,9 +119,9 @@ def _rng(seed: int, stream: int) -> np.random.Generator:
 
 
 def draw_truth(npix: int, seed: int = 0, lo=PRIOR_LO, hi=PRIOR_HI) -> np.ndarray:
-    """Truth parameters [npix, 9], uniform per pixel within [lo, hi]."""
+    """Truth parameters [npix, len(lo)], uniform per pixel within [lo, hi]."""
     r = _rng(seed, 1)
-    u = r.random((npix, NPAR))
+    u = r.random((npix, len(lo)))
     return lo + (hi - lo) * u
 
 
@@ -129,7 +134,7 @@ def draw_noise(npix: int, n_lambda: int, seed: int = 0) -> np.ndarray:
 def draw_params_uniform(n: int, seed: int, lo=PRIOR_LO, hi=PRIOR_HI) -> np.ndarray:
     """Random parameter vectors for parity / finite-difference checks."""
     r = _rng(seed, 3)
-    return lo + (hi - lo) * r.random((n, NPAR))
+    return lo + (hi - lo) * r.random((n, len(lo)))
 
 
 # ------------------------------------------------------------------ c4

@@ -62,7 +62,8 @@ class _Problem(C.Structure):
                 ("g_upper", C.c_double * MAX_LINES),
                 ("lambda_dop", C.c_double),
                 ("n_lambda", C.c_int),
-                ("lam", C.POINTER(C.c_double))]
+                ("lam", C.POINTER(C.c_double)),
+                ("fill", C.c_int)]
 
 
 class _GaConfig(C.Structure):
@@ -131,7 +132,7 @@ def lib():
             L.or_jacobian.argtypes = [P, _D, C.c_double, _D]
             L.or_lm_polish.argtypes = [P, _D, _DN, _DN, C.c_double, C.c_int, _D, _D,
                                        C.c_int, C.c_double, C.c_uint, _D, _D, C.c_int]
-            L.or_prefit_bounds.argtypes = [_D, C.c_int, _D, _D, _D, _D, _D]
+            L.or_prefit_bounds.argtypes = [_D, C.c_int, C.c_int, _D, _D, _D, _D, _D]
             L.or_lm_polish.restype = C.c_int
             L.or_line_centre.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, C.c_int, C.c_int, C.c_int,
                                          _D, _I32]
@@ -153,7 +154,7 @@ def nthreads_default() -> int:
 class Problem:
     """ctypes view of a line list + wavelength grid (keeps the grid alive)."""
 
-    def __init__(self, lines, lambda_grid, lambda_dop):
+    def __init__(self, lines, lambda_grid, lambda_dop, fill=False):
         if not 1 <= len(lines) <= MAX_LINES:
             raise ValueError("1..4 lines")
         self.lam = _f64(lambda_grid)
@@ -167,13 +168,16 @@ class Problem:
         s.lambda_dop = float(lambda_dop)
         s.n_lambda = len(self.lam)
         s.lam = self.lam.ctypes.data_as(C.POINTER(C.c_double))
+        s.fill = 1 if fill else 0
         self.s = s
         self.n_lambda = len(self.lam)
+        self.npar = NPAR + (1 if fill else 0)
 
     @classmethod
     def from_spec(cls, spec):
-        """From any object with .lines [(lambda0, g, eta_ratio)], .lambda_grid, .lambda_dop."""
-        return cls(spec.lines, spec.lambda_grid, spec.lambda_dop)
+        """From any object with .lines [(lambda0, g, eta_ratio)], .lambda_grid,
+        .lambda_dop (and optionally .fill: the fill fraction is parameter 9)."""
+        return cls(spec.lines, spec.lambda_grid, spec.lambda_dop, getattr(spec, "fill", False))
 
     def ref(self):
         return C.byref(self.s)
@@ -222,9 +226,11 @@ def zeeman_components(j_lower, g_lower, j_upper, g_upper):
 # ----------------------------------------------------------------- synthesis
 
 def synth(pb, params, mu=1.0, mu_px=None, nthreads=None):
-    """Stokes [n,4,n_lambda] of params [n,9] (Section 4 ME solution)."""
+    """Stokes [n,4,n_lambda] of params [n,M] (Section 4 ME solution)."""
     pb = _problem(pb)
     p = _f64(np.atleast_2d(params))
+    if p.shape[1] != pb.npar:
+        raise ValueError(f"params must have {pb.npar} columns")
     n = p.shape[0]
     out = np.empty((n, 4, pb.n_lambda))
     mp = None if mu_px is None else _f64(mu_px)
@@ -324,9 +330,10 @@ def ga_invert(pb, obs, lo, hi, cfg, w=None, mu=1.0, mu_px=None, pixel_id0=0,
         nseed = seeds.shape[1]
     if polarity is not None:
         polarity = np.ascontiguousarray(polarity, dtype=np.int32).reshape(npix)
-    best = np.empty((npix, NPAR))
+    m = pb.npar
+    best = np.empty((npix, m))
     c2 = np.empty(npix)
-    genes = np.empty((npix, NPAR), dtype=np.uint16)
+    genes = np.empty((npix, m), dtype=np.uint16)
     margin = np.empty(npix) if want_margin else None
     rc = lib().or_ga_invert(pb.ref(), obs, None if w is None else _f64(w),
                             None if mu_px is None else _f64(mu_px), float(mu), npix,
@@ -344,21 +351,21 @@ def ga_invert(pb, obs, lo, hi, cfg, w=None, mu=1.0, mu_px=None, pixel_id0=0,
 # ------------------------------------------------------------------- L-M
 
 def jacobian(pb, params, mu=1.0):
-    """d stokes / d p as [4, n_lambda, 9] (central differences + Richardson)."""
+    """d stokes / d p as [4, n_lambda, M] (central differences + Richardson)."""
     pb = _problem(pb)
-    jac = np.empty((4 * pb.n_lambda, NPAR))
+    jac = np.empty((4 * pb.n_lambda, pb.npar))
     lib().or_jacobian(pb.ref(), _f64(params), float(mu), jac)
-    return jac.reshape(4, pb.n_lambda, NPAR)
+    return jac.reshape(4, pb.n_lambda, pb.npar)
 
 
 def lm_polish(pb, obs, params, lo, hi, iters=10, lambda0=1e-3, w=None, mu=1.0,
-              mu_px=None, nthreads=None, free_mask=0x1FF):
-    """Levenberg-Marquardt polish; returns (params [npix,9], chi2 [npix]).
+              mu_px=None, nthreads=None, free_mask=0x3FF):
+    """Levenberg-Marquardt polish; returns (params [npix,M], chi2 [npix]).
     Parameters outside free_mask (bit k = parameter k) are held."""
     pb = _problem(pb)
     obs = _f64(obs)
     npix = obs.shape[0]
-    p = np.array(params, dtype=np.float64, order="C").reshape(npix, NPAR)
+    p = np.array(params, dtype=np.float64, order="C").reshape(npix, pb.npar)
     c2 = np.empty(npix)
     rc = lib().or_lm_polish(pb.ref(), obs, None if w is None else _f64(w),
                             None if mu_px is None else _f64(mu_px), float(mu), npix,
@@ -374,10 +381,10 @@ def lm_uncertainty(pb, obs, params, w=None, mu=1.0, mu_px=None):
     pb = _problem(pb)
     obs = _f64(obs)
     npix = obs.shape[0]
-    out = np.empty((npix, NPAR))
+    out = np.empty((npix, pb.npar))
     lib().or_lm_uncertainty(pb.ref(), obs, None if w is None else _f64(w),
                             None if mu_px is None else _f64(mu_px), float(mu), npix,
-                            _f64(np.reshape(params, (npix, NPAR))), out)
+                            _f64(np.reshape(params, (npix, pb.npar))), out)
     return out
 
 
@@ -426,8 +433,11 @@ def polarity_bounds(pol, lo, hi):
 
 
 def prefit_bounds(p_hat, lo, hi, lower, upper):
-    """Per-pixel bounds [npix][2][9] around a thermodynamic prefit (Section 4.3)."""
-    p = _f64(np.asarray(p_hat, dtype=np.float64).reshape(-1, NPAR))
-    out = np.empty((p.shape[0], 2, NPAR))
-    lib().or_prefit_bounds(p, p.shape[0], _f64(lo), _f64(hi), _f64(lower), _f64(upper), out)
+    """Per-pixel bounds [npix][2][M] around a thermodynamic prefit (Section 4.3);
+    M = the number of columns of p_hat."""
+    p_hat = np.asarray(p_hat, dtype=np.float64)
+    m = p_hat.shape[-1]
+    p = _f64(p_hat.reshape(-1, m))
+    out = np.empty((p.shape[0], 2, m))
+    lib().or_prefit_bounds(p, p.shape[0], m, _f64(lo), _f64(hi), _f64(lower), _f64(upper), out)
     return out

@@ -248,26 +248,26 @@ static double fitness(const or_problem *pb, const double *obs, const double *w,
                       double mu, const uint16_t *g, const double *lo,
                       const double *hi, double *model)
 {
-    double p[OR_NPAR];
-    decode(g, lo, hi, OR_NPAR, p);
+    double p[OR_MAXPAR];
+    decode(g, lo, hi, or_npar(pb), p);
     or_synth(pb, p, mu, model);
-    return clean(or_chi2(obs, model, w, pb->n_lambda, OR_NPAR));
+    return clean(or_chi2(obs, model, w, pb->n_lambda, or_npar(pb)));
 }
 
 static void ga_pixel(const ga_job *J, int ip)
 {
     const or_problem *pb = J->pb;
-    const int nl = pb->n_lambda, npop = J->cfg->npop, m = OR_NPAR;
+    const int nl = pb->n_lambda, npop = J->cfg->npop, m = or_npar(pb);
     const double *obs = J->obs + (size_t)ip * 4 * nl;
     const double mu = J->mu_px ? J->mu_px[ip] : J->mu;
     const uint64_t pid = J->pid0 + (uint64_t)ip;
-    double lo[OR_NPAR], hi[OR_NPAR];
+    double lo[OR_MAXPAR], hi[OR_MAXPAR];
     if (J->bounds_px) {
-        memcpy(lo, J->bounds_px + (size_t)ip * 2 * OR_NPAR, sizeof lo);
-        memcpy(hi, J->bounds_px + (size_t)ip * 2 * OR_NPAR + OR_NPAR, sizeof hi);
+        memcpy(lo, J->bounds_px + (size_t)ip * 2 * m, sizeof(double) * m);
+        memcpy(hi, J->bounds_px + (size_t)ip * 2 * m + m, sizeof(double) * m);
     } else {
-        memcpy(lo, J->glo, sizeof lo);
-        memcpy(hi, J->ghi, sizeof hi);
+        memcpy(lo, J->glo, sizeof(double) * m);
+        memcpy(hi, J->ghi, sizeof(double) * m);
     }
     if (J->polarity) or_polarity_bounds(J->polarity[ip], lo[1], hi[1], &lo[1], &hi[1]);
     double w[4];
@@ -362,13 +362,13 @@ int or_ga_invert(const or_problem *pb, const double *obs, const double *w,
     return 0;
 }
 
-void or_prefit_bounds(const double *p_hat, int npix, const double *lo, const double *hi,
+void or_prefit_bounds(const double *p_hat, int npix, int m, const double *lo, const double *hi,
                       const double *lower, const double *upper, double *out)
 {
     for (int ip = 0; ip < npix; ++ip) {
-        const double *p = p_hat + (size_t)ip * OR_NPAR;
-        double *ol = out + (size_t)ip * 2 * OR_NPAR, *oh = ol + OR_NPAR;
-        for (int k = 0; k < OR_NPAR; ++k) {
+        const double *p = p_hat + (size_t)ip * m;
+        double *ol = out + (size_t)ip * 2 * m, *oh = ol + m;
+        for (int k = 0; k < m; ++k) {
             double a = p[k] - lower[k], b = p[k] + upper[k];
             if (!(a > lo[k])) a = lo[k];
             if (!(b < hi[k])) b = hi[k];

@@ -24,7 +24,7 @@
 #include "oracle.h"
 
 /* typical magnitude of each parameter, used to size finite-difference steps */
-static const double fd_scale[OR_NPAR] = {100.0, 1.0, 1.0, 0.1, 1.0, 0.01, 0.1, 0.01, 0.01};
+static const double fd_scale[OR_MAXPAR] = {100.0, 1.0, 1.0, 0.1, 1.0, 0.01, 0.1, 0.01, 0.01, 0.01};
 
 /*
  * d stokes / d p_k by central differences D(h) = (f(p + h) - f(p - h)) / 2h,
@@ -33,16 +33,16 @@ static const double fd_scale[OR_NPAR] = {100.0, 1.0, 1.0, 0.1, 1.0, 0.01, 0.1, 0
  */
 void or_jacobian(const or_problem *pb, const double *p, double mu, double *jac)
 {
-    const int nl = pb->n_lambda, ns = 4 * nl;
+    const int nl = pb->n_lambda, ns = 4 * nl, M = or_npar(pb);
     double *fp = (double *)malloc(sizeof(double) * ns);
     double *fm = (double *)malloc(sizeof(double) * ns);
     double *d1 = (double *)malloc(sizeof(double) * ns);
-    for (int k = 0; k < OR_NPAR; ++k) {
+    for (int k = 0; k < M; ++k) {
         const double h = 1e-3 * (fabs(p[k]) > fd_scale[k] ? fabs(p[k]) : fd_scale[k]);
-        double q[OR_NPAR];
+        double q[OR_MAXPAR];
         for (int pass = 0; pass < 2; ++pass) {
             const double hh = pass == 0 ? h : 0.5 * h;
-            memcpy(q, p, sizeof q);
+            memcpy(q, p, sizeof(double) * M);
             q[k] = p[k] + hh;
             or_synth(pb, q, mu, fp);
             q[k] = p[k] - hh;
@@ -50,7 +50,7 @@ void or_jacobian(const or_problem *pb, const double *p, double mu, double *jac)
             for (int i = 0; i < ns; ++i) {
                 const double d = (fp[i] - fm[i]) / (2.0 * hh);
                 if (pass == 0) d1[i] = d;
-                else jac[(size_t)i * OR_NPAR + k] = (4.0 * d - d1[i]) / 3.0;
+                else jac[(size_t)i * M + k] = (4.0 * d - d1[i]) / 3.0;
             }
         }
     }
@@ -98,10 +98,10 @@ static void lm_pixel(const or_problem *pb, const double *obs, const double *w,
                      double mu, const double *lo, const double *hi, int iters,
                      double lambda0, unsigned free_mask, double *p, double *chi2_out)
 {
-    const int nl = pb->n_lambda, ns = 4 * nl, M = OR_NPAR;
+    const int nl = pb->n_lambda, ns = 4 * nl, M = or_npar(pb);
     double *model = (double *)malloc(sizeof(double) * ns);
     double *jac = (double *)malloc(sizeof(double) * ns * M);
-    double A[OR_NPAR * OR_NPAR], g[OR_NPAR];
+    double A[OR_MAXPAR * OR_MAXPAR], g[OR_MAXPAR];
     or_synth(pb, p, mu, model);
     double chi2 = or_chi2(obs, model, w, nl, M);
     double lam = lambda0;
@@ -128,21 +128,21 @@ static void lm_pixel(const or_problem *pb, const double *obs, const double *w,
         double dmax = 0.0;
         for (int a = 0; a < M; ++a) if (A[a * M + a] > dmax) dmax = A[a * M + a];
         if (!(dmax > 0.0)) break;
-        double delta[OR_NPAR];
+        double delta[OR_MAXPAR];
         int ok = 0;
         for (int tries = 0; tries < 30 && !ok; ++tries) {
-            double N[OR_NPAR * OR_NPAR];
-            memcpy(N, A, sizeof N);
+            double N[OR_MAXPAR * OR_MAXPAR];
+            memcpy(N, A, sizeof(double) * M * M);
             for (int a = 0; a < M; ++a) {
                 const double d = A[a * M + a] > 1e-12 * dmax ? A[a * M + a] : 1e-12 * dmax;
                 N[a * M + a] += lam * d;
             }
-            memcpy(delta, g, sizeof delta);
+            memcpy(delta, g, sizeof(double) * M);
             ok = cholesky_solve(M, N, delta);
             if (!ok) lam *= 10.0;
         }
         if (!ok) break;
-        double q[OR_NPAR];
+        double q[OR_MAXPAR];
         for (int a = 0; a < M; ++a) q[a] = p[a] + delta[a];
         q[2] = wrap_azimuth(q[2]);
         for (int a = 0; a < M; ++a) {
@@ -153,7 +153,7 @@ static void lm_pixel(const or_problem *pb, const double *obs, const double *w,
         or_synth(pb, q, mu, mtrial);
         const double c2 = or_chi2(obs, mtrial, w, nl, M);
         if (c2 < chi2) {
-            memcpy(p, q, sizeof q);
+            memcpy(p, q, sizeof(double) * M);
             memcpy(model, mtrial, sizeof(double) * ns);
             chi2 = c2;
             lam /= 10.0;
@@ -175,14 +175,14 @@ static void lm_pixel(const or_problem *pb, const double *obs, const double *w,
 static void sigma_pixel(const or_problem *pb, const double *obs, const double *w, double mu,
                         const double *p, double *sigma)
 {
-    const int nl = pb->n_lambda, ns = 4 * nl, M = OR_NPAR;
+    const int nl = pb->n_lambda, ns = 4 * nl, M = or_npar(pb);
     double *model = (double *)malloc(sizeof(double) * ns);
     double *jac = (double *)malloc(sizeof(double) * ns * M);
     or_synth(pb, p, mu, model);
     const double chi2 = or_chi2(obs, model, w, nl, M);
     or_jacobian(pb, p, mu, jac);
     const double nu = (double)(4 * nl - M);
-    double H[OR_NPAR][2 * OR_NPAR];
+    double H[OR_MAXPAR][2 * OR_MAXPAR];
     memset(H, 0, sizeof H);
     for (int i = 0; i < ns; ++i) {
         const double ws = w[i / nl] * w[i / nl];
@@ -222,7 +222,8 @@ void or_lm_uncertainty(const or_problem *pb, const double *obs, const double *w,
         double wv[4];
         if (w) memcpy(wv, w + (size_t)ip * 4, sizeof wv);
         else or_weights_invmax(o, nl, wv);
-        sigma_pixel(pb, o, wv, mu_px ? mu_px[ip] : mu, params + (size_t)ip * OR_NPAR, sigma + (size_t)ip * OR_NPAR);
+        const int M = or_npar(pb);
+        sigma_pixel(pb, o, wv, mu_px ? mu_px[ip] : mu, params + (size_t)ip * M, sigma + (size_t)ip * M);
     }
 }
 
@@ -251,7 +252,7 @@ static void *lm_worker(void *arg)
         else or_weights_invmax(obs, nl, w);
         const double mu = J->mu_px ? J->mu_px[ip] : J->mu;
         lm_pixel(J->pb, obs, w, mu, J->lo, J->hi, J->iters, J->lambda0, J->free_mask,
-                 J->params + (size_t)ip * OR_NPAR, J->chi2 + ip);
+                 J->params + (size_t)ip * or_npar(J->pb), J->chi2 + ip);
     }
     return NULL;
 }
@@ -262,7 +263,7 @@ static void *synth_worker(void *arg)
     const int nl = J->pb->n_lambda;
     for (int ip = J->t0; ip < J->t1; ++ip) {
         const double mu = J->mu_px ? J->mu_px[ip] : J->mu;
-        or_synth(J->pb, J->sparams + (size_t)ip * OR_NPAR, mu, J->stokes + (size_t)ip * 4 * nl);
+        or_synth(J->pb, J->sparams + (size_t)ip * or_npar(J->pb), mu, J->stokes + (size_t)ip * 4 * nl);
     }
     return NULL;
 }

@@ -153,6 +153,41 @@ static void kmatrix(const or_problem *pb, const double *p, double lam,
  *   I = eI (eI^2 + rQ^2 + rU^2 + rV^2) / Delta,
  *   Q = -[eI^2 eQ + eI (eV rU - eU rV) + rQ Pi] / Delta, U, V cyclic.
  */
+/*
+ * Section 4.2 fill fraction: I <- alpha I_mag + (1 - alpha) I_nm e.  The
+ * field-free part is read as the same Milne-Eddington atmosphere without a
+ * field (the paper's quiet-sun CLV profile is not printed):
+ *   I_nm = S0 + mu S1 / (1 + sum_l eta0_l Re w(v_l, a)),
+ * v_l the unshifted profile argument of line l.
+ */
+static double nonmagnetic_I(const or_problem *pb, const double *p, double mu, double lam)
+{
+    const double vlos = p[3], dld_mA = p[4], a = p[5], eta0 = p[6];
+    double eta = 1.0;
+    for (int l = 0; l < pb->n_lines; ++l) {
+        const double l0 = pb->lambda0[l];
+        const double dl = (lam - l0) - l0 * vlos / OR_C_KMS;
+        const double dD = dld_mA * 1e-3 * l0 / pb->lambda_dop;
+        double re, im;
+        or_faddeeva(dl / dD, a, &re, &im);
+        eta += eta0 * pb->eta_ratio[l] * re;
+    }
+    return p[7] + mu * p[8] / eta;
+}
+
+static void apply_fill(const or_problem *pb, const double *p, double mu, double *stokes)
+{
+    if (!pb->fill) return;
+    const int nl = pb->n_lambda;
+    const double alpha = p[9];
+    for (int j = 0; j < nl; ++j) {
+        stokes[0 * nl + j] = alpha * stokes[0 * nl + j] + (1.0 - alpha) * nonmagnetic_I(pb, p, mu, pb->lambda[j]);
+        stokes[1 * nl + j] = alpha * stokes[1 * nl + j];
+        stokes[2 * nl + j] = alpha * stokes[2 * nl + j];
+        stokes[3 * nl + j] = alpha * stokes[3 * nl + j];
+    }
+}
+
 void or_synth(const or_problem *pb, const double *p, double mu, double *stokes)
 {
     const int nl = pb->n_lambda;
@@ -173,6 +208,7 @@ void or_synth(const or_problem *pb, const double *p, double mu, double *stokes)
         stokes[2 * nl + j] = -f * (eI2 * eU + eI * (eQ * rV - eV * rQ) + rU * Pi);
         stokes[3 * nl + j] = -f * (eI2 * eV + eI * (eU * rQ - eQ * rU) + rV * Pi);
     }
+    apply_fill(pb, p, mu, stokes);
 }
 
 /* Same Stokes vector, solving K x = e directly (Gaussian elimination with
@@ -214,6 +250,7 @@ void or_synth_lu(const or_problem *pb, const double *p, double mu, double *stoke
         stokes[0 * nl + j] = S0 + mu * S1 * x[0];
         for (int s = 1; s < 4; ++s) stokes[s * nl + j] = mu * S1 * x[s];
     }
+    apply_fill(pb, p, mu, stokes);
 }
 
 /*

@@ -12,9 +12,10 @@
  * Built with -O2 -ffp-contract=off: every a*b+c is rounded twice, so the
  * results are the same on x86-64 and aarch64 hosts.
  *
- * Parameter vector (M = 9), fixed order:
+ * Parameter vector (M = 9, or 10 with the fill fraction), fixed order:
  *   0 B [G], 1 theta [deg], 2 chi [deg], 3 v_LOS [km/s], 4 Doppler width
- *   [mA] (quoted at lambda_dop), 5 damping a, 6 eta0, 7 S0, 8 S1.
+ *   [mA] (quoted at lambda_dop), 5 damping a, 6 eta0, 7 S0, 8 S1, and with
+ *   fill != 0: 9 alpha, the magnetic fill fraction of Section 4.2.
  *
  * Pins (tests/test_oracle_*.py): the Faddeeva routine against brute-force
  * quadrature, the a->0 closed forms and scipy.special.wofz; the closed-form ME
@@ -35,6 +36,7 @@ extern "C" {
 
 #define OR_MAX_LINES 4
 #define OR_NPAR 9
+#define OR_MAXPAR 10   /* with the fill fraction alpha */
 #define OR_MAX_COMP 9   /* Zeeman components per group (J <= 4) */
 
 typedef struct {
@@ -48,7 +50,11 @@ typedef struct {
     double lambda_dop;              /* [A] wavelength at which param 4 is quoted */
     int n_lambda;
     const double *lambda;           /* [n_lambda] observed wavelengths [A] */
+    int fill;                       /* 1: the fill fraction alpha is parameter 9 */
 } or_problem;
+
+/* Number of model parameters M of a problem: 9, or 10 with alpha. */
+static inline int or_npar(const or_problem *pb) { return OR_NPAR + (pb->fill ? 1 : 0); }
 
 typedef struct {
     int npop, ngen, nsamp;          /* nsamp <= 0: no restarts */
@@ -127,22 +133,22 @@ int or_ga_invert(const or_problem *pb, const double *obs, const double *w,
                  const double *bounds_px, double *best, double *chi2, uint16_t *best_genes,
                  double *margin, int nthreads);
 
-/* Jacobian d stokes / d p, [4*n_lambda][OR_NPAR], by central differences
+/* Jacobian d stokes / d p, [4*n_lambda][M], by central differences
  * with Richardson extrapolation. */
 void or_jacobian(const or_problem *pb, const double *p, double mu, double *jac);
 
 /* Levenberg-Marquardt polish of npix pixels (Marquardt damping). params_inout
- * [npix][OR_NPAR]; chi2_out [npix]; parameters outside free_mask are held. */
+ * [npix][M]; chi2_out [npix]; parameters outside free_mask are held. */
 int or_lm_polish(const or_problem *pb, const double *obs, const double *w,
                  const double *mu_px, double mu, int npix, const double *lo,
                  const double *hi, int iters, double lambda0, unsigned free_mask,
                  double *params_inout, double *chi2_out, int nthreads);
 
-/* Section 4.3 bounds from a thermodynamic prefit p_hat [npix][OR_NPAR]:
+/* Section 4.3 bounds from a thermodynamic prefit p_hat [npix][m]:
  * lo'_k = max(lo_k, p_hat_k - lower_k), hi'_k = min(hi_k, p_hat_k + upper_k)
  * (an infinite margin keeps the global bound); where that leaves no interval
- * (or p_hat_k is NaN) the global bounds stay.  out [npix][2][OR_NPAR]. */
-void or_prefit_bounds(const double *p_hat, int npix, const double *lo, const double *hi,
+ * (or p_hat_k is NaN) the global bounds stay.  out [npix][2][m]. */
+void or_prefit_bounds(const double *p_hat, int npix, int m, const double *lo, const double *hi,
                       const double *lower, const double *upper, double *out);
 
 /* Section 4.1 line centre by centre of symmetry (see me.c). */
@@ -154,7 +160,7 @@ void or_classify(const or_problem *pb, const double *obs, int npix, double p_thr
                  int line, int c_lo, int c_hi, int *flag, int *polarity, double *out_pol, double *out_weak,
                  double *seeds);
 
-/* Section 5 uncertainties sigma [npix][OR_NPAR] at params. */
+/* Section 5 uncertainties sigma [npix][M] at params. */
 void or_lm_uncertainty(const or_problem *pb, const double *obs, const double *w, const double *mu_px,
                        double mu, int npix, const double *params, double *sigma);
 
