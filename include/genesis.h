@@ -15,13 +15,14 @@
  *    synchronising; results are valid once the stream reaches that point.
  *  - Invalid arguments are rejected on the host (ME_EINVAL) before anything
  *    is launched; a failed launch returns ME_ECUDA.
- *  - Parameter vectors have ME_NPAR = 9 entries in this fixed order
+ *  - Parameter vectors have M = ME_NPAR = 9 entries in this fixed order
  *    (Section 4, model vector p; v_LOS replaces lambda0 and S0, S1 replace
- *    S0, beta0 with beta0 = S1/S0):
+ *    S0, beta0 with beta0 = S1/S0), or M = 10 with the fill fraction:
  *       0 B [G]          1 theta inclination [deg]   2 chi azimuth [deg]
  *       3 v_LOS [km/s]   4 Doppler width [mA] at lambda_dop_A
  *       5 damping a      6 eta0 (line/continuum opacity ratio)
  *       7 S0             8 S1 (source function S0 + S1 tau)
+ *       9 alpha (me_problem.fill_fraction = 1; Section 4.2)
  *  - Stokes arrays are [n][4][n_lambda] (I, Q, U, V), pixel-major, of the
  *    problem's dtype (float for ME_F32, double for ME_F64).
  */
@@ -46,7 +47,8 @@ extern "C" {
 #define ME_ENOTFOUND (-7) /* unknown serve ticket                          */
 
 /* ------------------------------------------------------------ limits/enums */
-#define ME_NPAR 9
+#define ME_NPAR 9      /* model parameters without the fill fraction          */
+#define ME_NPAR_MAX 10 /* with it: parameter 9 is alpha (Section 4.2)         */
 #define ME_MAX_LINES 4
 #define ME_MAX_LAMBDA 512
 #define ME_MAX_COMP 9 /* Zeeman components per group in a full pattern (J <= 4) */
@@ -97,6 +99,14 @@ typedef struct me_line {
  *   mu            cosine of the heliocentric angle used when mu_px is NULL
  *   dtype         ME_F32 or ME_F64: element type of obs/stokes arrays and the
  *                 arithmetic of synthesis and chi2
+ *   fill_fraction 1: the magnetic fill fraction alpha of Section 4.2 is a 10th
+ *                 parameter, Stokes = alpha S_mag + (1 - alpha) I_nm (1,0,0,0)
+ *                 with I_nm = S0 + mu S1 / (1 + sum_l eta0_l Re w(v_l, a)), the
+ *                 same atmosphere without a field; 0: 9 parameters.
+ *
+ * Every parameter array of the interface is [n][M] with M = ME_NPAR +
+ * fill_fraction, in the order B [G], theta [deg], chi [deg], v_LOS [km/s],
+ * Doppler width [mA], damping a, eta0, S0, S1 (, alpha).
  */
 typedef struct me_problem {
     int n_lines;
@@ -106,13 +116,15 @@ typedef struct me_problem {
     double lambda_dop_A;
     double mu;
     int dtype;
+    int fill_fraction;
 } me_problem;
 
-/* Parameter bounds u_j <= p_j <= v_j (Section 3, Eq. decode).  lo[5] (damping)
- * must be >= 0 and lo[4] (Doppler width) > 0. */
+/* Parameter bounds u_j <= p_j <= v_j (Section 3, Eq. decode) for j < M; the
+ * entries beyond M are ignored.  lo[5] (damping) must be >= 0, lo[4] (Doppler
+ * width) > 0 and, with the fill fraction, 0 <= lo[9] < hi[9] <= 1. */
 typedef struct me_bounds {
-    double lo[ME_NPAR];
-    double hi[ME_NPAR];
+    double lo[ME_NPAR_MAX];
+    double hi[ME_NPAR_MAX];
 } me_bounds;
 
 /*
@@ -154,7 +166,7 @@ int me_version(void);
 /*
  * me_synth - Unno-Rachkovsky Stokes vectors of n parameter vectors
  * (Section 4: K = 1 + eta0 Phi, Stokes = S0 e + mu S1 K^-1 e, I_c = S0 + mu S1).
- *   params  dev double [n][ME_NPAR]
+ *   params  dev double [n][M]
  *   mu_px   dev double [n] or NULL (then pb->mu)
  *   stokes  dev [n][4][n_lambda] of pb->dtype (output)
  * n = 0 is a no-op.
@@ -166,7 +178,7 @@ int me_synth(const me_problem *pb, const double *params, const double *mu_px, in
  * me_synth_jac - analytic Jacobian d stokes / d p of the same synthesis
  * (the derivative of Section 4's closed form, with w'(z) = -2 z w + 2i/sqrt(pi)).
  *   stokes  dev [n][4][n_lambda] of pb->dtype, or NULL
- *   jac     dev [n][4][n_lambda][ME_NPAR] of pb->dtype (output)
+ *   jac     dev [n][4][n_lambda][M] of pb->dtype (output)
  */
 int me_synth_jac(const me_problem *pb, const double *params, const double *mu_px, int n,
                  void *stokes, void *jac, void *stream);
@@ -175,14 +187,14 @@ int me_synth_jac(const me_problem *pb, const double *params, const double *mu_px
  * me_synth_vjp - vector-Jacobian product grad_params = J^T grad_stokes, the
  * adjoint used by the torch.autograd.Function wrapper.
  *   grad_stokes  dev [n][4][n_lambda] of pb->dtype
- *   grad_params  dev double [n][ME_NPAR] (output)
+ *   grad_params  dev double [n][M] (output)
  */
 int me_synth_vjp(const me_problem *pb, const double *params, const double *mu_px, int n,
                  const void *grad_stokes, double *grad_params, void *stream);
 
 /*
  * me_chi2 - Eq. chisq, chi2 = (1/nu) sum_s w_s^2 sum_j (O - M)^2 with
- * nu = 4 n_lambda - ME_NPAR, evaluated in FP64 for each pixel's parameters.
+ * nu = 4 n_lambda - M, evaluated in FP64 for each pixel's parameters.
  *   obs   dev [npix][4][n_lambda] of pb->dtype
  *   w     dev double [npix][4] (ME_W_USER) or NULL (inverse-max, Section 4.5)
  *   chi2  dev double [npix] (output)
@@ -201,9 +213,9 @@ int me_chi2(const me_problem *pb, const void *obs, const double *w, const double
  *   obs         dev [npix][4][n_lambda] of pb->dtype
  *   w           dev double [npix][4] if cfg->weight_mode == ME_W_USER, else NULL
  *   mu_px       dev double [npix] or NULL
- *   best        dev double [npix][ME_NPAR]: decoded best individual (output)
+ *   best        dev double [npix][M]: decoded best individual (output)
  *   chi2        dev double [npix]: FP64 re-evaluation of best (output)
- *   best_genes  dev uint16 [npix][ME_NPAR] or NULL (output)
+ *   best_genes  dev uint16 [npix][M] or NULL (output)
  */
 int ga_invert_batch(const me_problem *pb, const void *obs, const double *w,
                     const double *mu_px, int npix, uint64_t pixel_id0,
@@ -230,7 +242,7 @@ int ga_count_evaluations(const me_problem *pb, const void *obs, const double *w,
  * (J^T W^2 J + lambda D) delta = J^T W^2 r reduced and solved by Cholesky in
  * FP64, trial step with the azimuth wrapped into [0, 180) and clamped to the
  * bounds, accepted when chi2 decreases.  iters trial steps are taken.
- *   params_inout  dev double [npix][ME_NPAR]
+ *   params_inout  dev double [npix][M]
  *   chi2_out      dev double [npix]: FP64 chi2 of the final parameters
  */
 int lm_polish(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
@@ -279,7 +291,7 @@ typedef struct serve_request {
     const double *polish_w;
 } serve_request;
 
-/* Completed request: best [npix][ME_NPAR] and chi2 [npix] are caller-owned
+/* Completed request: best [npix][M] and chi2 [npix] are caller-owned
  * host buffers (either may be NULL); status is the request's own status;
  * queue_ns = submit -> admission, latency_ns = submit -> results on the host. */
 typedef struct serve_result {
@@ -314,12 +326,12 @@ int serve_destroy(serve_handle *h);
 
 /*
  * lm_uncertainty - Section 5 uncertainty estimate at given parameters:
- * sigma_i^2 = [H^-1]_ii chi2 / M (M = ME_NPAR) with H the Hessian of Eq. chisq
+ * sigma_i^2 = [H^-1]_ii chi2 / M (M parameters) with H the Hessian of Eq. chisq
  * in its Gauss-Newton form H = (2/nu) J^T W^2 J (exact where the residuals
  * vanish); J analytic in the problem precision, H and its inverse in FP64.
- *   params  dev double [npix][ME_NPAR] (e.g. the output of lm_polish)
+ *   params  dev double [npix][M] (e.g. the output of lm_polish)
  *   w       dev double [npix][4] or NULL (inverse-max weights)
- *   sigma   dev double [npix][ME_NPAR] (output); +infinity where H is singular
+ *   sigma   dev double [npix][M] (output); +infinity where H is singular
  */
 int lm_uncertainty(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
                    int npix, const double *params, double *sigma, void *stream);
@@ -367,8 +379,8 @@ int me_line_centre(const me_problem *pb, const void *obs, int npix, int half_wid
  *   pol       dev double [npix][2] = (p, sigma_P) (output; may be NULL)
  *   weak      dev double [npix][5] = (B, theta, chi, B_par, B_perp) (may be NULL)
  *   seeds     dev double [npix][4][3] (output; may be NULL)
- *   best      dev double [npix][ME_NPAR] or NULL: rows of pixels below the
- *             threshold receive (B, theta, chi, NaN x 6); others are untouched
+ *   best      dev double [npix][M] or NULL: rows of pixels below the
+ *             threshold receive (B, theta, chi, NaN ...); others are untouched
  * Errors: ME_EINVAL for windows outside the grid or line out of range.
  */
 int me_classify(const me_problem *pb, const void *obs, int npix, double p_thresh, int q_lo,
@@ -415,7 +427,7 @@ int me_select_static(const int *flag, int npix, int want, int *index, int *count
  *   polarity  dev int [npix] or NULL: +1 restricts the inclination domain to
  *             [lo, min(hi, 90)], -1 to [max(lo, 90), hi] (0, or an empty half:
  *             unrestricted); the decode of that gene uses it throughout.
- *   bounds_px dev double [npix][2][ME_NPAR] or NULL: per-pixel search domain
+ *   bounds_px dev double [npix][2][M] or NULL: per-pixel search domain
  *             (lo row, hi row; Section 4.3, e.g. from me_prefit_bounds) in
  *             place of *bounds for the decode and the seed encoding; the
  *             polarity restriction applies on top of it.
@@ -444,44 +456,46 @@ int lm_fit(const me_problem *pb, const void *obs, const double *w, const double 
  *   lo'_ik = max(lo_k, p_hat_ik - lower[k]), hi'_ik = min(hi_k, p_hat_ik + upper[k]),
  * an infinite margin keeping the global bound; where that leaves no interval
  * (or p_hat_ik is NaN) the global [lo_k, hi_k] stays.
- *   p_hat      dev double [npix][ME_NPAR] (e.g. lm_fit's prefit)
- *   lower, upper  host double [ME_NPAR] margins (not NaN)
- *   bounds_px  dev double [npix][2][ME_NPAR] (output: lo' row, then hi' row),
+ *   p_hat      dev double [npix][M] (e.g. lm_fit's prefit), M = npar (ME_NPAR or
+ *              ME_NPAR_MAX)
+ *   lower, upper  host double [M] margins (not NaN)
+ *   bounds_px  dev double [npix][2][M] (output: lo' row, then hi' row),
  *              the input of ga_invert_subset
  */
-int me_prefit_bounds(const double *p_hat, int npix, const me_bounds *bounds, const double *lower,
+int me_prefit_bounds(const double *p_hat, int npix, int npar, const me_bounds *bounds, const double *lower,
                      const double *upper, double *bounds_px, void *stream);
 
 /* ------------------------------------------------ GA operator entry points
  * The operators of ga_invert_batch run alone on caller-given populations, so
  * that they can be checked bit for bit against a reference with injected
- * fitness values.  nprob independent populations of npop individuals.
+ * fitness values.  nprob independent populations of npop individuals of
+ * npar (ME_NPAR or ME_NPAR_MAX) genes; the crossover string has 16 npar bits.
  *
  * ga_breed - one generation of selection, crossover, mutation and elitism
  * (Algorithm 1 Select/Recombine/Mutate) at generation `gen` for pixel ids
  * pixel_id0 + p.
- *   genes    dev uint16 [nprob][npop][ME_NPAR]
+ *   genes    dev uint16 [nprob][npop][npar]
  *   fitness  dev double [nprob][npop] (NaN counts as +infinity)
- *   child    dev uint16 [nprob][npop][ME_NPAR] (output)
+ *   child    dev uint16 [nprob][npop][npar] (output)
  *   elite    dev int [nprob] (output, may be NULL)
  */
-int ga_breed(const uint16_t *genes, const double *fitness, int nprob, int npop,
+int ga_breed(const uint16_t *genes, const double *fitness, int nprob, int npop, int npar,
              uint64_t pixel_id0, int gen, const ga_config *cfg, uint16_t *child,
              int *elite, void *stream);
 
 /*
  * ga_restart - Section 4.6 restart: the worst npop/2 individuals (stable rank by
  * fitness, then index) take Sobol points sobol_next + r in rank order r.
- *   genes  dev uint16 [nprob][npop][ME_NPAR], modified in place
+ *   genes  dev uint16 [nprob][npop][npar], modified in place
  */
-int ga_restart(uint16_t *genes, const double *fitness, int nprob, int npop,
+int ga_restart(uint16_t *genes, const double *fitness, int nprob, int npop, int npar,
                uint64_t sobol_next, void *stream);
 
 /* Philox4x32-10 of n counters: ctr dev uint32 [n][4], key {lo, hi}, out dev
  * uint32 [n][4]. */
 int me_philox(const uint32_t *ctr, int n, uint64_t key, uint32_t *out, void *stream);
 
-/* Sobol points first..first+n-1 of dimensions 0..ndim-1 (ndim <= ME_NPAR + 1)
+/* Sobol points first..first+n-1 of dimensions 0..ndim-1 (ndim <= ME_NPAR_MAX)
  * as 32-bit integers: out dev uint32 [n][ndim]. */
 int me_sobol(uint64_t first, int n, int ndim, uint32_t *out, void *stream);
 

@@ -21,6 +21,7 @@ ME_ETIMEOUT = -6
 ME_ENOTFOUND = -7
 
 ME_NPAR = 9
+ME_NPAR_MAX = 10
 ME_MAX_LINES = 4
 ME_MAX_LAMBDA = 512
 ME_F32 = 0
@@ -41,11 +42,11 @@ class MeLine(C.Structure):
 class MeProblem(C.Structure):
     _fields_ = [("n_lines", C.c_int), ("line", MeLine * ME_MAX_LINES), ("n_lambda", C.c_int),
                 ("lambda_A", C.POINTER(C.c_double)), ("lambda_dop_A", C.c_double),
-                ("mu", C.c_double), ("dtype", C.c_int)]
+                ("mu", C.c_double), ("dtype", C.c_int), ("fill_fraction", C.c_int)]
 
 
 class MeBounds(C.Structure):
-    _fields_ = [("lo", C.c_double * ME_NPAR), ("hi", C.c_double * ME_NPAR)]
+    _fields_ = [("lo", C.c_double * ME_NPAR_MAX), ("hi", C.c_double * ME_NPAR_MAX)]
 
 
 class GaConfig(C.Structure):
@@ -112,10 +113,10 @@ _SIGNATURES = {
                           _VP, C.c_int, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], C.c_int),
     "lm_fit": ([_P, _VP, _VP, _VP, C.c_int, C.POINTER(MeBounds), C.c_int, C.c_double, C.c_uint, _VP, _VP,
                 _VP, _VP, _VP], C.c_int),
-    "me_prefit_bounds": ([_VP, C.c_int, C.POINTER(MeBounds), _VP, _VP, _VP, _VP], C.c_int),
-    "ga_breed": ([_VP, _VP, C.c_int, C.c_int, C.c_uint64, C.c_int, C.POINTER(GaConfig), _VP, _VP,
-                  _VP], C.c_int),
-    "ga_restart": ([_VP, _VP, C.c_int, C.c_int, C.c_uint64, _VP], C.c_int),
+    "me_prefit_bounds": ([_VP, C.c_int, C.c_int, C.POINTER(MeBounds), _VP, _VP, _VP, _VP], C.c_int),
+    "ga_breed": ([_VP, _VP, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int, C.POINTER(GaConfig), _VP,
+                  _VP, _VP], C.c_int),
+    "ga_restart": ([_VP, _VP, C.c_int, C.c_int, C.c_int, C.c_uint64, _VP], C.c_int),
     "serve_create": ([_P, C.POINTER(ServeConfig), C.POINTER(C.c_void_p)], C.c_int),
     "serve_submit": ([_VP, C.POINTER(ServeRequest), C.POINTER(C.c_uint64)], C.c_int),
     "serve_poll": ([_VP, C.c_uint64, C.POINTER(ServeResult), C.c_int], C.c_int),

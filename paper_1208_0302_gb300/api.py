@@ -14,9 +14,10 @@ import torch
 
 from . import _lib as L
 
-NPAR = L.ME_NPAR
+NPAR = L.ME_NPAR          # parameters without the fill fraction
+NPAR_MAX = L.ME_NPAR_MAX  # with it (Section 4.2): Problem(fill=True)
 F32, F64 = L.ME_F32, L.ME_F64
-ALL_FREE = (1 << NPAR) - 1
+ALL_FREE = (1 << NPAR_MAX) - 1
 
 
 def _stream():
@@ -44,8 +45,10 @@ def _need(t, dtype, shape=None, name="tensor"):
 class Problem:
     """Line list, wavelength grid and precision (me_problem)."""
 
-    def __init__(self, lines, lambda_grid, lambda_dop, mu=1.0, dtype="f32"):
+    def __init__(self, lines, lambda_grid, lambda_dop, mu=1.0, dtype="f32", fill=False):
         self.lines = [tuple(map(float, ln)) for ln in lines]
+        self.fill = bool(fill)
+        self.npar = NPAR + (1 if self.fill else 0)
         self.lam = np.ascontiguousarray(lambda_grid, dtype=np.float64)
         self.lambda_dop = float(lambda_dop)
         self.mu = float(mu)
@@ -65,11 +68,12 @@ class Problem:
         s.lambda_dop_A = self.lambda_dop
         s.mu = self.mu
         s.dtype = self.dtype
+        s.fill_fraction = 1 if self.fill else 0
         self._s = s
 
     @classmethod
     def from_spec(cls, spec, dtype="f32"):
-        return cls(spec.lines, spec.lambda_grid, spec.lambda_dop, spec.mu, dtype)
+        return cls(spec.lines, spec.lambda_grid, spec.lambda_dop, spec.mu, dtype, getattr(spec, "fill", False))
 
     @property
     def n_lambda(self):
@@ -80,10 +84,13 @@ class Problem:
 
 
 def bounds(lo, hi) -> L.MeBounds:
+    """me_bounds from 9 or 10 lower/upper values (a missing alpha row is [0, 1])."""
+    if len(lo) not in (NPAR, NPAR_MAX) or len(hi) != len(lo):
+        raise ValueError("bounds need 9 or 10 entries")
     b = L.MeBounds()
-    for d in range(NPAR):
-        b.lo[d] = float(lo[d])
-        b.hi[d] = float(hi[d])
+    for d in range(NPAR_MAX):
+        b.lo[d] = float(lo[d]) if d < len(lo) else 0.0
+        b.hi[d] = float(hi[d]) if d < len(hi) else 1.0
     return b
 
 
@@ -107,7 +114,7 @@ class GaSettings:
 def me_synth(pb: Problem, params, mu_px=None):
     """Stokes [n, 4, n_lambda] of params [n, 9] (float64 CUDA)."""
     n = params.shape[0]
-    _need(params, torch.float64, (n, NPAR), "params")
+    _need(params, torch.float64, (n, pb.npar), "params")
     _need(mu_px, torch.float64, (n,), "mu_px")
     out = torch.empty((n, 4, pb.n_lambda), dtype=pb.torch_dtype, device=params.device)
     L.check(L.load().me_synth(pb.ref(), _ptr(params), _ptr(mu_px), n, _ptr(out), _stream()))
@@ -117,9 +124,9 @@ def me_synth(pb: Problem, params, mu_px=None):
 def me_synth_jac(pb: Problem, params, mu_px=None, want_stokes=False):
     """Jacobian [n, 4, n_lambda, 9] (and Stokes if asked)."""
     n = params.shape[0]
-    _need(params, torch.float64, (n, NPAR), "params")
+    _need(params, torch.float64, (n, pb.npar), "params")
     _need(mu_px, torch.float64, (n,), "mu_px")
-    jac = torch.empty((n, 4, pb.n_lambda, NPAR), dtype=pb.torch_dtype, device=params.device)
+    jac = torch.empty((n, 4, pb.n_lambda, pb.npar), dtype=pb.torch_dtype, device=params.device)
     st = torch.empty((n, 4, pb.n_lambda), dtype=pb.torch_dtype, device=params.device) if want_stokes else None
     L.check(L.load().me_synth_jac(pb.ref(), _ptr(params), _ptr(mu_px), n, _ptr(st), _ptr(jac), _stream()))
     return (jac, st) if want_stokes else jac
@@ -128,10 +135,10 @@ def me_synth_jac(pb: Problem, params, mu_px=None, want_stokes=False):
 def me_synth_vjp(pb: Problem, params, grad_stokes, mu_px=None):
     """J^T grad_stokes -> [n, 9] float64."""
     n = params.shape[0]
-    _need(params, torch.float64, (n, NPAR), "params")
+    _need(params, torch.float64, (n, pb.npar), "params")
     _need(grad_stokes, pb.torch_dtype, (n, 4, pb.n_lambda), "grad_stokes")
     _need(mu_px, torch.float64, (n,), "mu_px")
-    out = torch.empty((n, NPAR), dtype=torch.float64, device=params.device)
+    out = torch.empty((n, pb.npar), dtype=torch.float64, device=params.device)
     L.check(L.load().me_synth_vjp(pb.ref(), _ptr(params), _ptr(mu_px), n, _ptr(grad_stokes),
                                   _ptr(out), _stream()))
     return out
@@ -141,7 +148,7 @@ def me_chi2(pb: Problem, obs, params, w=None, mu_px=None):
     """FP64 chi2 [npix] of params against obs (Eq. chisq)."""
     npix = obs.shape[0]
     _need(obs, pb.torch_dtype, (npix, 4, pb.n_lambda), "obs")
-    _need(params, torch.float64, (npix, NPAR), "params")
+    _need(params, torch.float64, (npix, pb.npar), "params")
     _need(w, torch.float64, (npix, 4), "w")
     _need(mu_px, torch.float64, (npix,), "mu_px")
     out = torch.empty(npix, dtype=torch.float64, device=obs.device)
@@ -158,9 +165,9 @@ def ga_invert_batch(pb: Problem, obs, lo, hi, ga: GaSettings, w=None, mu_px=None
     _need(w, torch.float64, (npix, 4), "w")
     _need(mu_px, torch.float64, (npix,), "mu_px")
     dev = obs.device
-    best = torch.empty((npix, NPAR), dtype=torch.float64, device=dev)
+    best = torch.empty((npix, pb.npar), dtype=torch.float64, device=dev)
     chi2 = torch.empty(npix, dtype=torch.float64, device=dev)
-    genes = torch.empty((npix, NPAR), dtype=torch.int16, device=dev) if want_genes else None
+    genes = torch.empty((npix, pb.npar), dtype=torch.int16, device=dev) if want_genes else None
     cfg = ga.to_c(L.ME_W_USER if w is not None else L.ME_W_INVMAX)
     b = bounds(lo, hi)
     L.check(L.load().ga_invert_batch(pb.ref(), _ptr(obs), _ptr(w), _ptr(mu_px), npix,
@@ -177,7 +184,7 @@ def ga_count_evaluations(pb: Problem, obs, lo, hi, ga: GaSettings, w=None, mu_px
     _need(obs, pb.torch_dtype, (npix, 4, pb.n_lambda), "obs")
     _need(w, torch.float64, (npix, 4), "w")
     _need(mu_px, torch.float64, (npix,), "mu_px")
-    best = torch.empty((npix, NPAR), dtype=torch.float64, device=obs.device)
+    best = torch.empty((npix, pb.npar), dtype=torch.float64, device=obs.device)
     counts = torch.zeros(3, dtype=torch.int64, device=obs.device)
     cfg = ga.to_c(L.ME_W_USER if w is not None else L.ME_W_INVMAX)
     b = bounds(lo, hi)
@@ -209,7 +216,7 @@ def lm_polish(pb: Problem, obs, params, lo, hi, iters=10, lambda0=1e-3, w=None, 
     """L-M refinement; returns (params [npix, 9], chi2 [npix]) (params updated in a copy)."""
     npix = obs.shape[0]
     _need(obs, pb.torch_dtype, (npix, 4, pb.n_lambda), "obs")
-    _need(params, torch.float64, (npix, NPAR), "params")
+    _need(params, torch.float64, (npix, pb.npar), "params")
     _need(w, torch.float64, (npix, 4), "w")
     _need(mu_px, torch.float64, (npix,), "mu_px")
     p = params.clone()
@@ -224,10 +231,10 @@ def lm_uncertainty(pb: Problem, obs, params, w=None, mu_px=None):
     """Section 5 sigma_i = sqrt([H^-1]_ii chi2 / M), H = (2/nu) J^T W^2 J -> [npix, 9]."""
     npix = obs.shape[0]
     _need(obs, pb.torch_dtype, (npix, 4, pb.n_lambda), "obs")
-    _need(params, torch.float64, (npix, NPAR), "params")
+    _need(params, torch.float64, (npix, pb.npar), "params")
     _need(w, torch.float64, (npix, 4), "w")
     _need(mu_px, torch.float64, (npix,), "mu_px")
-    out = torch.empty((npix, NPAR), dtype=torch.float64, device=obs.device)
+    out = torch.empty((npix, pb.npar), dtype=torch.float64, device=obs.device)
     L.check(L.load().lm_uncertainty(pb.ref(), _ptr(obs), _ptr(w), _ptr(mu_px), npix, _ptr(params),
                                     _ptr(out), _stream()))
     return out
@@ -256,7 +263,7 @@ def classify(pb: Problem, obs, p_thresh, quiet, line, core, best=None):
     answer (B, theta, chi, NaN...)."""
     npix = obs.shape[0]
     _need(obs, pb.torch_dtype, (npix, 4, pb.n_lambda), "obs")
-    _need(best, torch.float64, (npix, NPAR), "best")
+    _need(best, torch.float64, (npix, pb.npar), "best")
     dev = obs.device
     flag = torch.empty(npix, dtype=torch.int32, device=dev)
     polarity = torch.empty(npix, dtype=torch.int32, device=dev)
@@ -311,7 +318,7 @@ def ga_invert_subset(pb: Problem, obs, lo, hi, ga: GaSettings, index=None, count
     _need(index, torch.int32, None, "index")
     _need(count, torch.int32, (1,), "count")
     _need(polarity, torch.int32, (npix,), "polarity")
-    _need(bounds_px, torch.float64, (npix, 2, NPAR), "bounds_px")
+    _need(bounds_px, torch.float64, (npix, 2, pb.npar), "bounds_px")
     nseed = 0
     if seeds is not None:
         _need(seeds, torch.float64, None, "seeds")
@@ -324,12 +331,12 @@ def ga_invert_subset(pb: Problem, obs, lo, hi, ga: GaSettings, index=None, count
         raise ValueError("index must hold npix entries")
     dev = obs.device
     if best is None:
-        best = torch.full((npix, NPAR), float("nan"), dtype=torch.float64, device=dev)
+        best = torch.full((npix, pb.npar), float("nan"), dtype=torch.float64, device=dev)
     if chi2 is None:
         chi2 = torch.full((npix,), float("nan"), dtype=torch.float64, device=dev)
-    _need(best, torch.float64, (npix, NPAR), "best")
+    _need(best, torch.float64, (npix, pb.npar), "best")
     _need(chi2, torch.float64, (npix,), "chi2")
-    genes = torch.zeros((npix, NPAR), dtype=torch.int16, device=dev) if want_genes else None
+    genes = torch.zeros((npix, pb.npar), dtype=torch.int16, device=dev) if want_genes else None
     cfg = ga.to_c(L.ME_W_USER if w is not None else L.ME_W_INVMAX)
     b = bounds(lo, hi)
     L.check(L.load().ga_invert_subset(pb.ref(), _ptr(obs), _ptr(w), _ptr(mu_px), npix, int(pixel_id0),
@@ -348,7 +355,7 @@ def lm_fit(pb: Problem, obs, params, lo, hi, index=None, count=None, iters=10, l
     those pixels and returned."""
     npix = obs.shape[0]
     _need(obs, pb.torch_dtype, (npix, 4, pb.n_lambda), "obs")
-    _need(params, torch.float64, (npix, NPAR), "params")
+    _need(params, torch.float64, (npix, pb.npar), "params")
     _need(w, torch.float64, (npix, 4), "w")
     _need(mu_px, torch.float64, (npix,), "mu_px")
     _need(index, torch.int32, None, "index")
@@ -383,9 +390,11 @@ PREFIT_UPPER = (float("inf"),) * 3 + (1.0, 3.0, 0.15, float("inf"), 0.15, 0.15)
 def thermo_prefit(pb: Problem, obs, lo, hi, index=None, count=None, iters=40, lambda0=1e-3, mu_px=None,
                   start=PREFIT_START):
     """Section 4.3 thermodynamic prefit: L-M fit of Stokes I alone with the
-    field held at zero, from a generic start -> (params [npix, 9], chi2)."""
+    field held at zero, from a generic start -> (params [npix, M], chi2).
+    With the fill fraction, alpha is held at 1 (at B = 0 it has no effect)."""
     npix = obs.shape[0]
     dev = obs.device
+    start = tuple(start) + ((1.0,) if pb.fill and len(start) == NPAR else ())
     params = torch.tensor(start, dtype=torch.float64, device=dev).repeat(npix, 1).contiguous()
     w = torch.zeros((npix, 4), dtype=torch.float64, device=dev)
     w[:, 0] = 1.0
@@ -395,16 +404,20 @@ def thermo_prefit(pb: Problem, obs, lo, hi, index=None, count=None, iters=40, la
 
 
 def prefit_bounds(p_hat, lo, hi, lower=PREFIT_LOWER, upper=PREFIT_UPPER):
-    """Per-pixel search bounds [npix, 2, 9] around a prefit (me_prefit_bounds)."""
-    npix = p_hat.shape[0]
-    _need(p_hat, torch.float64, (npix, NPAR), "p_hat")
-    out = torch.empty((npix, 2, NPAR), dtype=torch.float64, device=p_hat.device)
-    lw = np.ascontiguousarray(lower, dtype=np.float64)
-    up = np.ascontiguousarray(upper, dtype=np.float64)
-    if lw.shape != (NPAR,) or up.shape != (NPAR,):
-        raise ValueError("lower and upper must hold 9 margins")
+    """Per-pixel search bounds [npix, 2, M] around a prefit (me_prefit_bounds);
+    M = p_hat's columns (a 10th margin defaults to infinite: alpha unbounded)."""
+    npix, m = p_hat.shape
+    if m not in (NPAR, NPAR_MAX):
+        raise ValueError("p_hat must have 9 or 10 columns")
+    _need(p_hat, torch.float64, (npix, m), "p_hat")
+    out = torch.empty((npix, 2, m), dtype=torch.float64, device=p_hat.device)
+    pad = (float("inf"),) * (m - len(lower))
+    lw = np.ascontiguousarray(tuple(lower) + pad, dtype=np.float64)
+    up = np.ascontiguousarray(tuple(upper) + pad, dtype=np.float64)
+    if lw.shape != (m,) or up.shape != (m,):
+        raise ValueError("lower and upper must hold one margin per parameter")
     b = bounds(lo, hi)
-    L.check(L.load().me_prefit_bounds(_ptr(p_hat), npix, C.byref(b), C.c_void_p(lw.ctypes.data),
+    L.check(L.load().me_prefit_bounds(_ptr(p_hat), npix, m, C.byref(b), C.c_void_p(lw.ctypes.data),
                                       C.c_void_p(up.ctypes.data), _ptr(out), _stream()))
     return out
 
@@ -420,7 +433,7 @@ def invert_map(pb: Problem, obs, lo, hi, ga: GaSettings, p_thresh, quiet, line, 
     flag, polarity, index, count, weak, seeds[, prefit, bounds_px])."""
     npix = obs.shape[0]
     dev = obs.device
-    best = torch.full((npix, NPAR), float("nan"), dtype=torch.float64, device=dev)
+    best = torch.full((npix, pb.npar), float("nan"), dtype=torch.float64, device=dev)
     chi2 = torch.full((npix,), float("nan"), dtype=torch.float64, device=dev)
     cls = classify(pb, obs, p_thresh, quiet, line, core, best=best)
     index, count = select(cls["flag"], 1)
@@ -461,6 +474,7 @@ class Server:
     def __init__(self, pb: Problem, arena_bytes=1 << 30, max_inflight=8, max_queue=4096,
                  small_pixels=0, fail_next_admissions=0):
         self.pb = pb
+        self._npar = pb.npar
         cfg = L.ServeConfig(int(arena_bytes), int(max_inflight), int(max_queue), int(small_pixels),
                             int(fail_next_admissions))
         h = C.c_void_p()
@@ -498,7 +512,7 @@ class Server:
         """Result dict of a finished request; raises GenesisError with code
         ME_EPENDING / ME_ETIMEOUT if it is not done, or the request's error."""
         npix = self._npix.get(ticket, 0)
-        best = np.empty((npix, NPAR))
+        best = np.empty((npix, self._npar))
         chi2 = np.empty(npix)
         res = L.ServeResult(best.ctypes.data if npix else None, chi2.ctypes.data if npix else None,
                             0, 0, 0)
@@ -539,8 +553,8 @@ def _dev_to_u16(t):
 
 
 def ga_breed(genes_u16, fitness, pixel_id0, gen, ga: GaSettings, device="cuda"):
-    """One breeding step of nprob populations (numpy uint16 [nprob, npop, 9],
-    float64 [nprob, npop]) -> (child uint16, elite int)."""
+    """One breeding step of nprob populations (numpy uint16 [nprob, npop, M],
+    M = 9 or 10; float64 [nprob, npop]) -> (child uint16, elite int)."""
     g = np.ascontiguousarray(genes_u16, dtype=np.uint16)
     nprob, npop, _ = g.shape
     gd = _u16_to_dev(g, device)
@@ -548,7 +562,7 @@ def ga_breed(genes_u16, fitness, pixel_id0, gen, ga: GaSettings, device="cuda"):
     child = torch.empty_like(gd)
     elite = torch.empty(nprob, dtype=torch.int32, device=device)
     cfg = ga.to_c(L.ME_W_INVMAX)
-    L.check(L.load().ga_breed(_ptr(gd), _ptr(fd), nprob, npop, int(pixel_id0), int(gen),
+    L.check(L.load().ga_breed(_ptr(gd), _ptr(fd), nprob, npop, g.shape[2], int(pixel_id0), int(gen),
                               C.byref(cfg), _ptr(child), _ptr(elite), _stream()))
     return _dev_to_u16(child), elite.cpu().numpy()
 
@@ -558,7 +572,7 @@ def ga_restart(genes_u16, fitness, sobol_next, device="cuda"):
     nprob, npop, _ = g.shape
     gd = _u16_to_dev(g, device)
     fd = torch.as_tensor(np.ascontiguousarray(fitness, dtype=np.float64)).to(device)
-    L.check(L.load().ga_restart(_ptr(gd), _ptr(fd), nprob, npop, int(sobol_next), _stream()))
+    L.check(L.load().ga_restart(_ptr(gd), _ptr(fd), nprob, npop, g.shape[2], int(sobol_next), _stream()))
     return _dev_to_u16(gd)
 
 

@@ -131,6 +131,7 @@ int ensure_device()
     if ((e = upload_tables_ga(t)) != cudaSuccess) return cuda_fail(e, "upload tables");
     if ((e = upload_tables_synth(t)) != cudaSuccess) return cuda_fail(e, "upload tables");
     if ((e = upload_tables_lm(t)) != cudaSuccess) return cuda_fail(e, "upload tables");
+    if ((e = upload_tables_ga_fill(t)) != cudaSuccess) return cuda_fail(e, "upload tables");
     if ((e = select_static_scratch(&g_select_static[dev], &g_select_static_bytes)) != cudaSuccess)
         return cuda_fail(e, "select scratch address");
     g_dev_ready[dev] = true;
@@ -147,7 +148,9 @@ int make_problem(const me_problem *pb, KProblem &k)
     if (pb->n_lines < 1 || pb->n_lines > ME_MAX_LINES) return fail(ME_EINVAL, "n_lines must be 1..4");
     if (pb->n_lambda < 1 || pb->n_lambda > ME_MAX_LAMBDA)
         return fail(ME_EINVAL, "n_lambda must be 1..ME_MAX_LAMBDA");
-    if (4 * pb->n_lambda <= ME_NPAR) return fail(ME_EINVAL, "n_lambda too small: 4 n_lambda must exceed 9");
+    if (pb->fill_fraction != 0 && pb->fill_fraction != 1) return fail(ME_EINVAL, "fill_fraction must be 0 or 1");
+    if (4 * pb->n_lambda <= npar_of(pb))
+        return fail(ME_EINVAL, "n_lambda too small: 4 n_lambda must exceed the parameter count");
     if (!pb->lambda_A) return fail(ME_EINVAL, "lambda_A is NULL");
     if (pb->dtype != ME_F32 && pb->dtype != ME_F64) return fail(ME_EINVAL, "dtype must be ME_F32 or ME_F64");
     if (!(pb->lambda_dop_A > 0.0) || !std::isfinite(pb->lambda_dop_A))
@@ -156,6 +159,7 @@ int make_problem(const me_problem *pb, KProblem &k)
     std::memset(&k, 0, sizeof k);
     k.n_lines = pb->n_lines;
     k.n_lambda = pb->n_lambda;
+    k.fill = pb->fill_fraction;
     k.mu = pb->mu;
     for (int l = 0; l < pb->n_lines; ++l) {
         const me_line &ln = pb->line[l];
@@ -234,14 +238,18 @@ int zeeman_pattern(int jl, double gl, int ju, double gu, int n[3], double sh[3][
     return ME_OK;
 }
 
-int check_bounds(const me_bounds *b)
+int npar_of(const me_problem *pb) { return ME_NPAR + (pb && pb->fill_fraction ? 1 : 0); }
+
+int check_bounds(const me_bounds *b, int npar)
 {
     if (!b) return fail(ME_EINVAL, "bounds is NULL");
-    for (int d = 0; d < ME_NPAR; ++d)
+    for (int d = 0; d < npar; ++d)
         if (!std::isfinite(b->lo[d]) || !std::isfinite(b->hi[d]) || b->lo[d] > b->hi[d])
             return fail(ME_EINVAL, "bounds must be finite with lo <= hi");
     if (b->lo[5] < 0.0) return fail(ME_EINVAL, "damping lower bound must be >= 0");
     if (!(b->lo[4] > 0.0)) return fail(ME_EINVAL, "Doppler-width lower bound must be > 0");
+    if (npar > ME_NPAR && (b->lo[ME_NPAR] < 0.0 || b->hi[ME_NPAR] > 1.0))
+        return fail(ME_EINVAL, "fill-fraction bounds must lie in [0, 1]");
     return ME_OK;
 }
 
@@ -253,7 +261,7 @@ uint64_t prob_threshold(double p)
     return (uint64_t)std::floor(p * 4294967296.0);
 }
 
-int make_ga(const ga_config *cfg, const me_bounds *b, uint64_t pid0, KGa &g)
+int make_ga(const ga_config *cfg, const me_bounds *b, uint64_t pid0, KGa &g, int npar)
 {
     if (!cfg) return fail(ME_EINVAL, "ga_config is NULL");
     if (cfg->npop < ME_MIN_POP || cfg->npop > ME_MAX_POP || cfg->npop % 32)
@@ -278,7 +286,7 @@ int make_ga(const ga_config *cfg, const me_bounds *b, uint64_t pid0, KGa &g)
         g.t_mut[bit] = prob_threshold(cfg->pmut_lsb * r);
     }
     if (b) {
-        for (int d = 0; d < ME_NPAR; ++d) {
+        for (int d = 0; d < npar; ++d) {
             g.lo[d] = b->lo[d];
             g.hi[d] = b->hi[d];
         }
@@ -306,7 +314,7 @@ extern "C" {
 
 const char *me_last_error(void) { return g_last_error.c_str(); }
 
-int me_version(void) { return 102; }
+int me_version(void) { return 103; }
 
 int me_zeeman_components(const me_line *line, int n[3], double shift[3][ME_MAX_COMP],
                          double strength[3][ME_MAX_COMP])
@@ -389,9 +397,10 @@ static int ga_invert_impl(const me_problem *pb, const void *obs, const double *w
     KProblem k;
     int rc = make_problem(pb, k);
     if (rc) return rc;
-    if ((rc = check_bounds(bounds))) return rc;
+    const int npar = npar_of(pb);
+    if ((rc = check_bounds(bounds, npar))) return rc;
     KGa g;
-    if ((rc = make_ga(cfg, bounds, pixel_id0, g))) return rc;
+    if ((rc = make_ga(cfg, bounds, pixel_id0, g, npar))) return rc;
     if (npix < 0) return fail(ME_EINVAL, "npix must be >= 0");
     if (npix == 0) return ME_OK;
     if (!obs || !best || !chi2) return fail(ME_EINVAL, "obs, best and chi2 must be non-NULL");
@@ -402,7 +411,7 @@ static int ga_invert_impl(const me_problem *pb, const void *obs, const double *w
     // shared memory: obs + offsets + fitness + genes must fit one block
     const size_t rs = pb->dtype == ME_F32 ? 4 : 8;
     const size_t need = rs * (4 + pb->n_lines) * pb->n_lambda + rs * (cfg->npop + 72) + 128 +
-                        (size_t)4 * cfg->npop * ME_NPAR + 256;
+                        (size_t)4 * cfg->npop * npar + 256;
     if (need > 220 * 1024) return fail(ME_EINVAL, "population and grid exceed shared memory");
     if ((rc = ensure_device())) return rc;
     const KGa &gc = g;
@@ -441,9 +450,10 @@ int ga_count_evaluations(const me_problem *pb, const void *obs, const double *w,
     KProblem k;
     int rc = make_problem(pb, k);
     if (rc) return rc;
-    if ((rc = check_bounds(bounds))) return rc;
+    const int npar = npar_of(pb);
+    if ((rc = check_bounds(bounds, npar))) return rc;
     KGa g;
-    if ((rc = make_ga(cfg, bounds, pixel_id0, g))) return rc;
+    if ((rc = make_ga(cfg, bounds, pixel_id0, g, npar))) return rc;
     if (pb->dtype != ME_F32 || cfg->npop > 256)
         return fail(ME_EINVAL, "counting runs support float cubes with npop <= 256");
     if (npix < 0) return fail(ME_EINVAL, "npix must be >= 0");
@@ -463,7 +473,8 @@ static int lm_polish_impl(const me_problem *pb, const void *obs, const double *w
     KProblem k;
     int rc = make_problem(pb, k);
     if (rc) return rc;
-    if ((rc = check_bounds(bounds))) return rc;
+    const int npar = npar_of(pb);
+    if ((rc = check_bounds(bounds, npar))) return rc;
     if (npix < 0 || iters < 0) return fail(ME_EINVAL, "npix and iters must be >= 0");
     if (!(lambda0 > 0.0) || !std::isfinite(lambda0)) return fail(ME_EINVAL, "lambda0 must be positive");
     if (npix == 0) return ME_OK;
@@ -473,8 +484,8 @@ static int lm_polish_impl(const me_problem *pb, const void *obs, const double *w
     std::memset(&lm, 0, sizeof lm);
     lm.iters = iters;
     lm.lambda0 = lambda0;
-    lm.free_mask = free_mask & ((1u << ME_NPAR) - 1u);
-    for (int d = 0; d < ME_NPAR; ++d) {
+    lm.free_mask = free_mask & ((1u << npar) - 1u);
+    for (int d = 0; d < npar; ++d) {
         lm.lo[d] = bounds->lo[d];
         lm.hi[d] = bounds->hi[d];
     }
@@ -491,7 +502,7 @@ int lm_polish(const me_problem *pb, const void *obs, const double *w, const doub
               const me_bounds *bounds, int iters, double lambda0, double *params_inout,
               double *chi2_out, void *stream)
 {
-    return lm_polish_impl(pb, obs, w, mu_px, npix, bounds, iters, lambda0, (1u << ME_NPAR) - 1u, KSub{},
+    return lm_polish_impl(pb, obs, w, mu_px, npix, bounds, iters, lambda0, ~0u, KSub{},
                           params_inout, chi2_out, stream);
 }
 
@@ -503,18 +514,21 @@ int lm_fit(const me_problem *pb, const void *obs, const double *w, const double 
                           params_inout, chi2_out, stream);
 }
 
-int me_prefit_bounds(const double *p_hat, int npix, const me_bounds *bounds, const double *lower,
+int me_prefit_bounds(const double *p_hat, int npix, int npar, const me_bounds *bounds, const double *lower,
                      const double *upper, double *bounds_px, void *stream)
 {
-    int rc = check_bounds(bounds);
+    if (npar != ME_NPAR && npar != ME_NPAR_MAX) return fail(ME_EINVAL, "npar must be ME_NPAR or ME_NPAR_MAX");
+    int rc = check_bounds(bounds, npar);
     if (rc) return rc;
     if (npix < 0) return fail(ME_EINVAL, "npix must be >= 0");
     if (!lower || !upper) return fail(ME_EINVAL, "lower and upper margins must be non-NULL");
     if (npix == 0) return ME_OK;
     if (!p_hat || !bounds_px) return fail(ME_EINVAL, "p_hat and bounds_px must be non-NULL");
-    if ((size_t)npix * ME_NPAR > (size_t)INT32_MAX) return fail(ME_EINVAL, "npix too large");
+    if ((size_t)npix * npar > (size_t)INT32_MAX) return fail(ME_EINVAL, "npix too large");
     KPrefitBounds r;
-    for (int k = 0; k < ME_NPAR; ++k) {
+    std::memset(&r, 0, sizeof r);
+    r.npar = npar;
+    for (int k = 0; k < npar; ++k) {
         if (std::isnan(lower[k]) || std::isnan(upper[k])) return fail(ME_EINVAL, "margins must not be NaN");
         r.lo[k] = bounds->lo[k];
         r.hi[k] = bounds->hi[k];
@@ -554,6 +568,7 @@ int me_classify(const me_problem *pb, const void *obs, int npix, double p_thresh
     c.weak = weak;
     c.seeds = seeds;
     c.best = best;
+    c.npar = npar_of(pb);
     cudaError_t e = launch_classify(k, pb->dtype, obs, npix, c, as_stream(stream));
     return e == cudaSuccess ? ME_OK : cuda_fail(e, "me_classify launch");
 }
@@ -620,35 +635,37 @@ int me_line_centre(const me_problem *pb, const void *obs, int npix, int half_wid
     return e == cudaSuccess ? ME_OK : cuda_fail(e, "me_line_centre launch");
 }
 
-int ga_breed(const uint16_t *genes, const double *fitness, int nprob, int npop, uint64_t pixel_id0,
+int ga_breed(const uint16_t *genes, const double *fitness, int nprob, int npop, int npar, uint64_t pixel_id0,
              int gen, const ga_config *cfg, uint16_t *child, int *elite, void *stream)
 {
     KGa g;
     ga_config c = cfg ? *cfg : ga_config{};
     if (!cfg) return fail(ME_EINVAL, "ga_config is NULL");
+    if (npar != ME_NPAR && npar != ME_NPAR_MAX) return fail(ME_EINVAL, "npar must be ME_NPAR or ME_NPAR_MAX");
     c.npop = npop;
-    int rc = make_ga(&c, nullptr, pixel_id0, g);
+    int rc = make_ga(&c, nullptr, pixel_id0, g, npar);
     if (rc) return rc;
     if (nprob < 0) return fail(ME_EINVAL, "nprob must be >= 0");
     if (nprob == 0) return ME_OK;
     if (!genes || !fitness || !child) return fail(ME_EINVAL, "genes, fitness and child must be non-NULL");
     if ((rc = ensure_device())) return rc;
-    cudaError_t e = launch_ga_breed(g, genes, fitness, nprob, gen, child, elite, as_stream(stream));
+    cudaError_t e = launch_ga_breed(g, npar, genes, fitness, nprob, gen, child, elite, as_stream(stream));
     return e == cudaSuccess ? ME_OK : cuda_fail(e, "ga_breed launch");
 }
 
-int ga_restart(uint16_t *genes, const double *fitness, int nprob, int npop, uint64_t sobol_next,
+int ga_restart(uint16_t *genes, const double *fitness, int nprob, int npop, int npar, uint64_t sobol_next,
                void *stream)
 {
     if (npop < ME_MIN_POP || npop > ME_MAX_POP || npop % 32)
         return fail(ME_EINVAL, "npop must be a multiple of 32 in [32, 1024]");
+    if (npar != ME_NPAR && npar != ME_NPAR_MAX) return fail(ME_EINVAL, "npar must be ME_NPAR or ME_NPAR_MAX");
     if (nprob < 0) return fail(ME_EINVAL, "nprob must be >= 0");
     if (nprob == 0) return ME_OK;
     if (!genes || !fitness) return fail(ME_EINVAL, "genes and fitness must be non-NULL");
     if (sobol_next + (uint64_t)npop > (1ull << 32)) return fail(ME_EINVAL, "Sobol index beyond 2^32");
     int rc = ensure_device();
     if (rc) return rc;
-    cudaError_t e = launch_ga_restart(npop, genes, fitness, nprob, sobol_next, as_stream(stream));
+    cudaError_t e = launch_ga_restart(npop, npar, genes, fitness, nprob, sobol_next, as_stream(stream));
     return e == cudaSuccess ? ME_OK : cuda_fail(e, "ga_restart launch");
 }
 

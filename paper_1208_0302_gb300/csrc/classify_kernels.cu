@@ -242,11 +242,11 @@ k_classify(const __grid_constant__ KProblem pb, const RO *__restrict__ obs, int 
         sd[9] = 0.0;
     }
     if (c.best && !flag) {  // weak-field answer for the pixels below the threshold
-        double *bo = c.best + (size_t)pix * ME_NPAR;
+        double *bo = c.best + (size_t)pix * c.npar;
         bo[0] = bmag;
         bo[1] = theta;
         bo[2] = chi;
-        for (int d = 3; d < ME_NPAR; ++d) bo[d] = __longlong_as_double(0x7ff8000000000000ll);
+        for (int d = 3; d < c.npar; ++d) bo[d] = __longlong_as_double(0x7ff8000000000000ll);
     }
 }
 
@@ -347,8 +347,9 @@ __global__ void k_prefit_bounds(const double *__restrict__ p_hat, int npix, cons
                                 double *__restrict__ out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= npix * ME_NPAR) return;
-    const int pix = i / ME_NPAR, k = i - pix * ME_NPAR;
+    const int M = r.npar;
+    if (i >= npix * M) return;
+    const int pix = i / M, k = i - pix * M;
     const double p = p_hat[i];
     double a = __dsub_rn(p, r.lower[k]), b = __dadd_rn(p, r.upper[k]);
     if (!(a > r.lo[k])) a = r.lo[k];
@@ -357,8 +358,8 @@ __global__ void k_prefit_bounds(const double *__restrict__ p_hat, int npix, cons
         a = r.lo[k];
         b = r.hi[k];
     }
-    out[(size_t)pix * 2 * ME_NPAR + k] = a;
-    out[(size_t)pix * 2 * ME_NPAR + ME_NPAR + k] = b;
+    out[(size_t)pix * 2 * M + k] = a;
+    out[(size_t)pix * 2 * M + M + k] = b;
 }
 
 }  // namespace
@@ -367,7 +368,7 @@ cudaError_t launch_prefit_bounds(const double *p_hat, int npix, const KPrefitBou
                                  cudaStream_t st)
 {
     if (npix <= 0) return cudaSuccess;
-    const int n = npix * ME_NPAR;
+    const int n = npix * r.npar;
     k_prefit_bounds<<<(n + 255) / 256, 256, 0, st>>>(p_hat, npix, r, out);
     return cudaGetLastError();
 }

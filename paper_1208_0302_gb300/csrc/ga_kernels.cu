@@ -8,11 +8,7 @@
 // walks the wavelength grid for its own individual, so every lane of a warp
 // reads the same shared-memory word (broadcast) and the chi2 sum needs no
 // cross-thread reduction.
-#include <type_traits>
-
-#include "kernels.h"
-#include "me_pair.cuh"
-#include "rng_device.cuh"
+#include "ga_evolve.cuh"
 
 namespace genesis {
 
@@ -25,495 +21,8 @@ cudaError_t upload_tables_ga(const HostTables &t)
 
 namespace {
 
-template <class R> __device__ __forceinline__ R clean_fit(R f)
-{
-    return f == f ? f : R(INFINITY);  // NaN ranks as +infinity
-}
-
-// Kahan-compensated accumulation of r^2.
-template <class R> __device__ __forceinline__ void kahan_sq(R &s, R &c, R r)
-{
-    const R y = r * r - c;
-    const R t = s + y;
-    c = (t - s) - y;
-    s = t;
-}
-
-// Four consecutive R values of a 16-byte aligned shared-memory row.
-__device__ __forceinline__ void load4(const float *p, float v[4])
-{
-    const float4 q = *(const float4 *)p;
-    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-}
-__device__ __forceinline__ void load4(const double *p, double v[4])
-{
-    const double2 a = *(const double2 *)p, b = *(const double2 *)(p + 2);
-    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-}
-
-// Shared-memory layouts.  FP32: wavelength pairs (2p, 2p+1) interleaved for
-// packed FP32x2 use, 8 values per pair: (I, I', Q, Q', U, U', V, V') and
-// (d0, d0', d1, d1', d2, d2', d3, d3') for the per-line offsets; an odd grid
-// repeats its last point as the partner of the last pair.  FP64: rows of 4
-// per wavelength.
-template <class R> __device__ __forceinline__ int obs_idx(int s, int j)
-{
-    return sizeof(R) == 4 ? (j >> 1) * 8 + s * 2 + (j & 1) : j * 4 + s;
-}
-template <class R> __device__ __forceinline__ int padded_lambda(int nl)
-{
-    return sizeof(R) == 4 ? (nl + 1) & ~1 : nl;
-}
-
-template <class R> struct GaDecode;
-// The pixel's decode domain in shared memory (per-pixel bounds of Section
-// 4.3 and the polarity restriction of Section 4.5 already applied):
-// double lo[M], hi[M], then float lo[M], scale[M] = (hi - lo) / 65535.
-struct DecodeDomain {
-    double lo[ME_NPAR], hi[ME_NPAR];
-    float lo32[ME_NPAR], sc32[ME_NPAR];
-};
-template <> struct GaDecode<float> {
-    static __device__ __forceinline__ float get(const DecodeDomain &D, int d, uint16_t g)
-    {
-        return fmaf((float)g, D.sc32[d], D.lo32[d]);
-    }
-};
-template <> struct GaDecode<double> {
-    static __device__ __forceinline__ double get(const DecodeDomain &D, int d, uint16_t g)
-    {
-        return decode64(g, D.lo[d], D.hi[d]);
-    }
-};
-
-// Eq. chisq for one individual, FP32 (or FP64) synthesis over the whole grid.
-// s_obs rows are (I, Q, U, V) of one wavelength; s_doff rows hold
-// lambda_j - lambda0_l for l = 0..3: one vector load each per wavelength.
-template <class R, int NL, bool COUNT, bool PAT>
-__device__ __forceinline__ R fitness_rows(const KProblem &pb, int nlines, int nl, const R *p, R mu,
-                                          const R *s_obs, const R *s_doff, const R *he,
-                                          const R *s_w2, R inv_nu, unsigned long long &ninterior)
-{
-    const Geo<R> geo = make_geo<R, NL>(pb, nlines, p, mu);
-    R sI = 0, sQ = 0, sU = 0, sV = 0, cI = 0, cQ = 0, cU = 0, cV = 0;
-    for (int j = 0; j < nl; ++j) {
-        R doff[4], ob[4];
-        load4(s_doff + 4 * j, doff);
-        load4(s_obs + 4 * j, ob);
-        const Stokes4<R> s = me_point<R, NL, PAT>(geo, doff, he, nlines, pb.line);
-        if (COUNT) ninterior += count_interior<R, NL, PAT>(geo, doff, nlines, pb.line);
-        kahan_sq(sI, cI, ob[0] - s.I);
-        kahan_sq(sQ, cQ, ob[1] - s.Q);
-        kahan_sq(sU, cU, ob[2] - s.U);
-        kahan_sq(sV, cV, ob[3] - s.V);
-    }
-    return (s_w2[0] * sI + s_w2[1] * sQ + s_w2[2] * sU + s_w2[3] * sV) * inv_nu;
-}
-
-__device__ __forceinline__ void kahan_sq2(float2 &s, float2 &c, float2 r)
-{
-    const float2 y = fma2(r, r, neg2(c));
-    const float2 t = add2(s, y);
-    c = sub2(sub2(t, s), y);
-    s = t;
-}
-
-// Eq. chisq for one individual with the FP32 pair path (two wavelengths per
-// step, packed FP32x2 arithmetic).
-template <int NL, bool COUNT, bool PAT>
-__device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, int nl, const float *p,
-                                               float mu, const float *s_obs, const float *s_doff,
-                                               const float *he, const float *s_w2, float inv_nu,
-                                               unsigned long long &ninterior)
-{
-    const Geo<float> geo = make_geo<float, NL>(pb, nlines, p, mu);
-    float2 sI = f2(0.f), sQ = f2(0.f), sU = f2(0.f), sV = f2(0.f);
-    float2 cI = f2(0.f), cQ = f2(0.f), cU = f2(0.f), cV = f2(0.f);
-    const int npair = (nl + 1) >> 1;
-    unsigned cnt = 0;
-    for (int q = 0; q < npair; ++q) {
-        const float4 o0 = *(const float4 *)(s_obs + 8 * q), o1 = *(const float4 *)(s_obs + 8 * q + 4);
-        const float4 d0 = *(const float4 *)(s_doff + 8 * q);
-        float2 doff2[ME_MAX_LINES];
-        doff2[0] = make_float2(d0.x, d0.y);
-        doff2[1] = make_float2(d0.z, d0.w);
-        if (NL == 0 || NL > 2) {
-            const float4 d1 = *(const float4 *)(s_doff + 8 * q + 4);
-            doff2[2] = make_float2(d1.x, d1.y);
-            doff2[3] = make_float2(d1.z, d1.w);
-        }
-        const Stokes4x2 m = me_point_x2<NL, COUNT, PAT>(geo, doff2, he, nlines, cnt, pb.line);
-        float2 rI = sub2(make_float2(o0.x, o0.y), m.I), rQ = sub2(make_float2(o0.z, o0.w), m.Q);
-        float2 rU = sub2(make_float2(o1.x, o1.y), m.U), rV = sub2(make_float2(o1.z, o1.w), m.V);
-        if (2 * q + 1 >= nl) rI.y = rQ.y = rU.y = rV.y = 0.f;  // padded partner
-        kahan_sq2(sI, cI, rI);
-        kahan_sq2(sQ, cQ, rQ);
-        kahan_sq2(sU, cU, rU);
-        kahan_sq2(sV, cV, rV);
-    }
-    if (COUNT) ninterior += cnt;
-    return (s_w2[0] * (sI.x + sI.y) + s_w2[1] * (sQ.x + sQ.y) + s_w2[2] * (sU.x + sU.y) +
-            s_w2[3] * (sV.x + sV.y)) * inv_nu;
-}
-
-template <class R, int NL, bool COUNT, bool PAT>
-__device__ __forceinline__ R fitness(const KProblem &pb, int nlines, int nl, const R *p, R mu,
-                                     const R *s_obs, const R *s_doff, const R *he,
-                                     const R *s_w2, R inv_nu, unsigned long long &ninterior)
-{
-    if constexpr (std::is_same<R, float>::value)
-        return fitness_pairs<NL, COUNT, PAT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior);
-    else
-        return fitness_rows<R, NL, COUNT, PAT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior);
-}
-
-// argmin over the block's fitness, ties to the lowest index.  Every thread
-// gets the result.  Uses one __syncthreads().
-template <class R>
-__device__ __forceinline__ int block_argmin(const R *s_fit, R *s_wmin, int *s_widx)
-{
-    const int k = threadIdx.x, lane = k & 31, warp = k >> 5, nw = blockDim.x >> 5;
-    R v = s_fit[k];
-    int idx = k;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const R ov = __shfl_down_sync(0xffffffffu, v, off);
-        const int oi = __shfl_down_sync(0xffffffffu, idx, off);
-        if (ov < v || (ov == v && oi < idx)) { v = ov; idx = oi; }
-    }
-    if (lane == 0) { s_wmin[warp] = v; s_widx[warp] = idx; }
-    __syncthreads();
-    R bv = s_wmin[0];
-    int bi = s_widx[0];
-    for (int w = 1; w < nw; ++w) {
-        const R ov = s_wmin[w];
-        const int oi = s_widx[w];
-        if (ov < bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-    }
-    return bi;
-}
-
-// Stable rank of individual k in (fitness, index) order.
-template <class R> __device__ __forceinline__ int stable_rank(const R *s_fit, int npop, int k)
-{
-    const R fk = s_fit[k];
-    int r = 0;
-    for (int j = 0; j < npop; ++j) {
-        const R fj = s_fit[j];
-        r += (fj < fk || (fj == fk && j < k)) ? 1 : 0;
-    }
-    return r;
-}
-
-// Select (binary tournament), recombine (one-point crossover with lane k^1),
-// mutate (per-bit, LSB-biased) and elitism for child slot k.  Must be called
-// by all lanes of full warps (npop is a multiple of 32).
-template <class R>
-__device__ __forceinline__ void breed_one(const KGa &ga, uint64_t pid, int t, int k, int npop,
-                                          const R *s_fit, const uint16_t *s_cur, int elite,
-                                          uint16_t *s_row, uint16_t g[ME_NPAR])
-{
-    const U4 u = ga_random(ga.seed, pid, t, (uint32_t)k, kPurposeSelect);
-    const int i = (int)(((uint64_t)u.x * (uint64_t)npop) >> 32);
-    const int j = (i + 1 + (int)(((uint64_t)u.y * (uint64_t)(npop - 1)) >> 32)) % npop;
-    const R fi = s_fit[i], fj = s_fit[j];
-    const int win = (fj < fi || (fj == fi && j < i)) ? j : i;
-#pragma unroll
-    for (int d = 0; d < ME_NPAR; ++d) g[d] = s_cur[win * ME_NPAR + d];
-
-    const U4 uc = ga_random(ga.seed, pid, t, (uint32_t)(k >> 1), kPurposeCross);
-    const bool cross = (uint64_t)uc.x < ga.t_cross;
-    const int c = 1 + (int)(((uint64_t)uc.y * (uint64_t)(16 * ME_NPAR - 1)) >> 32);
-#pragma unroll
-    for (int d = 0; d < ME_NPAR; ++d) {
-        const uint32_t pg = __shfl_xor_sync(0xffffffffu, (uint32_t)g[d], 1);
-        if (cross) {
-            const int b0 = 16 * d;  // MSB-first string bits [b0, b0 + 16)
-            if (b0 >= c) {
-                g[d] = (uint16_t)pg;
-            } else if (b0 + 16 > c) {
-                const uint32_t mask = (1u << (16 - (c - b0))) - 1u;  // bits at or after the cut
-                g[d] = (uint16_t)(((uint32_t)g[d] & ~mask) | (pg & mask));
-            }
-        }
-    }
-
-    // Mutation word by word through this slot's shared-memory row (a rolled
-    // loop keeps the code small): bits 16d..16d+15 use Philox calls 4d..4d+3.
-#pragma unroll
-    for (int d = 0; d < ME_NPAR; ++d) s_row[d] = g[d];
-#pragma unroll 1
-    for (int d = 0; d < ME_NPAR; ++d) {
-        uint32_t word = s_row[d];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const U4 um = ga_random(ga.seed, pid, t, (uint32_t)k, kPurposeMutate + (uint32_t)(4 * d + q));
-            const uint32_t uu[4] = {um.x, um.y, um.z, um.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int b = 4 * q + e;  // bit within the word, 0 = MSB
-                if ((uint64_t)uu[e] < ga.t_mut[b]) word ^= 1u << (15 - b);
-            }
-        }
-        s_row[d] = (uint16_t)word;
-    }
-#pragma unroll
-    for (int d = 0; d < ME_NPAR; ++d) g[d] = s_row[d];
-    if (k == 0) {
-#pragma unroll
-        for (int d = 0; d < ME_NPAR; ++d) g[d] = s_cur[elite * ME_NPAR + d];
-    }
-}
-
-struct GaSmem {
-    // byte offsets into dynamic shared memory
-    int obs, doff, fit, wmin, widx, w2, he, dom, genes, total;
-};
-
-template <class R>
-__host__ __device__ __forceinline__ GaSmem ga_smem_layout(int nl, int nlines, int npop)
-{
-    GaSmem L;
-    int o = 0;
-    auto take = [&](int bytes, int align) {
-        o = (o + align - 1) / align * align;
-        const int at = o;
-        o += bytes;
-        return at;
-    };
-    const int nlp = sizeof(R) == 4 ? (nl + 1) & ~1 : nl;  // padded to whole pairs in FP32
-    L.obs = take(4 * nlp * (int)sizeof(R), 16);
-    L.doff = take(4 * nlp * (int)sizeof(R), 16);
-    L.fit = take(npop * (int)sizeof(R), 16);
-    L.wmin = take(32 * (int)sizeof(R), 16);
-    L.widx = take(32 * 4, 16);
-    L.w2 = take(4 * (int)sizeof(R), 16);
-    L.he = take(4 * (int)sizeof(R), 16);
-    L.dom = take((int)sizeof(DecodeDomain), 16);  // the pixel's decode domain
-    L.genes = take(2 * npop * ME_NPAR * 2, 16);
-    L.total = (o + 15) / 16 * 16;
-    return L;
-}
-
-// Section 4.5 inverse-max weights of the staged pixel (warp 0), written as w^2.
-template <class R>
-__device__ __forceinline__ void weights_invmax_w2(const R *s_obs, int nl, R *s_w2)
-{
-    const int lane = threadIdx.x & 31;
-    R imax = -R(INFINITY), imin = R(INFINITY), mq = 0, mu = 0, mv = 0;
-    for (int j = lane; j < nl; j += 32) {
-        const R I = s_obs[obs_idx<R>(0, j)];
-        imax = I > imax ? I : imax;
-        imin = I < imin ? I : imin;
-        const R aq = fabs(s_obs[obs_idx<R>(1, j)]), au = fabs(s_obs[obs_idx<R>(2, j)]);
-        const R av = fabs(s_obs[obs_idx<R>(3, j)]);
-        mq = aq > mq ? aq : mq;
-        mu = au > mu ? au : mu;
-        mv = av > mv ? av : mv;
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        R o = __shfl_xor_sync(0xffffffffu, imax, off); imax = o > imax ? o : imax;
-        o = __shfl_xor_sync(0xffffffffu, imin, off); imin = o < imin ? o : imin;
-        o = __shfl_xor_sync(0xffffffffu, mq, off); mq = o > mq ? o : mq;
-        o = __shfl_xor_sync(0xffffffffu, mu, off); mu = o > mu ? o : mu;
-        o = __shfl_xor_sync(0xffffffffu, mv, off); mv = o > mv ? o : mv;
-    }
-    if (lane == 0) {
-        const R d[4] = {imax - imin, mq, mu, mv};
-        const R fl = R(1e-6) * fabs(imax);
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            const R dd = d[s] > fl ? d[s] : fl;
-            const R w = dd > R(0) ? R(1) / dd : R(0);
-            s_w2[s] = w * w;
-        }
-    }
-}
-
-// Register budget of the FP32 npop <= 256 instantiations: MAXT * GENESIS_GA_MINB
-// threads must fit an SM's 64K registers, which caps registers per thread
-// (more resident warps hide the FP32 pipe latency).  FP64 instantiations are
-// bound by the FP64 units and keep the compiler's register choice.
-#ifndef GENESIS_GA_MINB
-#define GENESIS_GA_MINB 3
-#endif
-
-template <class R, int NL, int MAXT, bool COUNT, bool PAT>
-__global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(R) == 4) ? GENESIS_GA_MINB : 1)
-k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
-            const R *__restrict__ obs, const double *__restrict__ w_user,
-            const double *__restrict__ mu_px, int npix, double *__restrict__ best,
-            uint16_t *__restrict__ best_genes, unsigned long long *__restrict__ counts,
-            const KSeed sd, const KSub sub)
-{
-    unsigned long long nfit = 0, ninterior = 0;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int nl = pb.n_lambda;
-    const int nlines = NL > 0 ? NL : pb.n_lines;
-    const int npop = ga.npop;
-    const int k = threadIdx.x;
-    const GaSmem L = ga_smem_layout<R>(nl, nlines, npop);
-    R *s_obs = (R *)(smem + L.obs);
-    R *s_doff = (R *)(smem + L.doff);
-    R *s_fit = (R *)(smem + L.fit);
-    R *s_wmin = (R *)(smem + L.wmin);
-    int *s_widx = (int *)(smem + L.widx);
-    R *s_w2 = (R *)(smem + L.w2);
-    R *s_he = (R *)(smem + L.he);
-    DecodeDomain &D = *(DecodeDomain *)(smem + L.dom);
-    uint16_t *s_genes = (uint16_t *)(smem + L.genes);
-
-    // per-launch constants
-    const R inv_nu = R(1) / R(4 * nl - ME_NPAR);
-    if (k < 4) s_he[k] = k < nlines ? R(pb.line[k].half_eta) : R(0);
-    for (int i = k; i < 4 * padded_lambda<R>(nl); i += blockDim.x) {
-        const int j = i >> 2, l = i & 3;
-        const int jj = j < nl ? j : nl - 1;  // a padded partner repeats the last point
-        // exact difference in FP64, then rounded
-        s_doff[obs_idx<R>(l, j)] = l < nlines ? R(pb.lam[jj] - pb.line[l].lam0) : R(0);
-    }
-
-    const int nrun = sub.count ? min(*sub.count, npix) : npix;
-    for (int blk = blockIdx.x; blk < nrun; blk += gridDim.x) {
-        const int pix = sub.index ? sub.index[blk] : blk;
-        if (pix < 0 || pix >= npix) continue;  // a bad index skips the block, uniformly
-        if (k < ME_NPAR) {  // the pixel's decode domain of parameter k
-            double a = sd.bounds_px ? sd.bounds_px[(size_t)pix * 2 * ME_NPAR + k] : ga.lo[k];
-            double b = sd.bounds_px ? sd.bounds_px[(size_t)pix * 2 * ME_NPAR + ME_NPAR + k] : ga.hi[k];
-            if (k == 1 && sd.polarity) polarity_bounds(sd.polarity[pix], a, b, a, b);
-            D.lo[k] = a;
-            D.hi[k] = b;
-            D.lo32[k] = (float)a;
-            D.sc32[k] = (float)((b - a) / 65535.0);
-        }
-        // a1: stage the pixel's Stokes profiles from [4][nl] in HBM into the
-        // shared-memory layout (16-byte vector loads when a vector stays in one row)
-        const R *o = obs + (size_t)pix * 4 * nl;
-        constexpr int VW = 16 / (int)sizeof(R);  // elements per 16-byte vector
-        if (nl % VW == 0 && (((uintptr_t)o) & 15) == 0) {
-            for (int i = k; i < 4 * nl / VW; i += blockDim.x) {
-                const int e = i * VW, st = e / nl, j = e - st * nl;
-                if (VW == 4) {
-                    const float4 q = __ldg((const float4 *)o + i);
-                    s_obs[obs_idx<R>(st, j)] = R(q.x);
-                    s_obs[obs_idx<R>(st, j + 1)] = R(q.y);
-                    s_obs[obs_idx<R>(st, j + 2)] = R(q.z);
-                    s_obs[obs_idx<R>(st, j + 3)] = R(q.w);
-                } else {
-                    const double2 q = __ldg((const double2 *)o + i);
-                    s_obs[obs_idx<R>(st, j)] = R(q.x);
-                    s_obs[obs_idx<R>(st, j + 1)] = R(q.y);
-                }
-            }
-        } else {
-            for (int i = k; i < 4 * nl; i += blockDim.x) {
-                const int st = i / nl, j = i - st * nl;
-                s_obs[obs_idx<R>(st, j)] = o[i];
-            }
-        }
-        if (padded_lambda<R>(nl) > nl && k < 4) s_obs[obs_idx<R>(k, nl)] = o[k * nl + nl - 1];
-        __syncthreads();
-        // a2: weights
-        if (ga.weight_mode == ME_W_USER) {
-            if (k < 4) {
-                const double wv = w_user[(size_t)pix * 4 + k];
-                s_w2[k] = R(wv * wv);
-            }
-        } else if (k < 32) {
-            weights_invmax_w2<R>(s_obs, nl, s_w2);
-        }
-        __syncthreads();
-        R he[ME_MAX_LINES];
-#pragma unroll
-        for (int l = 0; l < ME_MAX_LINES; ++l) he[l] = s_he[l];
-        const R mu = mu_px ? R(mu_px[pix]) : R(pb.mu);
-        const uint64_t pid = ga.pixel_id0 + (uint64_t)pix;
-
-        // a3 + a4: Sobol points 1..npop, the last nseed taking the seeds'
-        // (B, psi, chi) genes, decode, evaluate
-        uint16_t g[ME_NPAR];
-        R p[ME_NPAR];
-#pragma unroll
-        for (int d = 0; d < ME_NPAR; ++d) g[d] = (uint16_t)(sobol_point((uint64_t)(k + 1), d) >> 16);
-        if (k >= npop - sd.nseed) {
-            const double *sv = sd.seeds + ((size_t)pix * sd.nseed + (k - (npop - sd.nseed))) * 3;
-            const double x0 = sv[0], x1 = sv[1], x2 = sv[2];
-            if (x0 == x0) g[0] = encode64(x0, D.lo[0], D.hi[0]);
-            if (x1 == x1) g[1] = encode64(x1, D.lo[1], D.hi[1]);
-            if (x2 == x2) g[2] = encode64(x2, D.lo[2], D.hi[2]);
-        }
-#pragma unroll
-        for (int d = 0; d < ME_NPAR; ++d) p[d] = GaDecode<R>::get(D, d, g[d]);
-        int cur = 0;
-#pragma unroll
-        for (int d = 0; d < ME_NPAR; ++d) s_genes[k * ME_NPAR + d] = g[d];
-        s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior));
-        if (COUNT) ++nfit;
-        uint64_t sobol_next = (uint64_t)npop + 1;
-
-        for (int t = 1; t <= ga.ngen; ++t) {
-            __syncthreads();  // fitness and genes of generation t-1 complete
-            const int elite = block_argmin<R>(s_fit, s_wmin, s_widx);  // a9
-            const uint16_t *s_cur = s_genes + cur * npop * ME_NPAR;
-            uint16_t *s_nxt = s_genes + (cur ^ 1) * npop * ME_NPAR;
-            breed_one<R>(ga, pid, t, k, npop, s_fit, s_cur, elite, s_nxt + k * ME_NPAR, g);  // a10-a12
-            __syncthreads();  // every tournament has read s_fit
-#pragma unroll
-            for (int d = 0; d < ME_NPAR; ++d) {
-                s_nxt[k * ME_NPAR + d] = g[d];
-                p[d] = GaDecode<R>::get(D, d, g[d]);
-            }
-            cur ^= 1;
-            s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior));
-            if (COUNT) ++nfit;
-            // a13: worst-half Sobol restart
-            if (ga.nsamp > 0 && t % ga.nsamp == 0 && t < ga.ngen) {
-                __syncthreads();
-                const int rank = stable_rank<R>(s_fit, npop, k);
-                __syncthreads();
-                if (rank >= npop / 2) {
-                    const uint64_t n = sobol_next + (uint64_t)(rank - npop / 2);
-                    uint16_t *s_c = s_genes + cur * npop * ME_NPAR;
-#pragma unroll
-                    for (int d = 0; d < ME_NPAR; ++d) {
-                        g[d] = (uint16_t)(sobol_point(n, d) >> 16);
-                        s_c[k * ME_NPAR + d] = g[d];
-                        p[d] = GaDecode<R>::get(D, d, g[d]);
-                    }
-                    s_fit[k] = clean_fit(
-                        fitness<R, NL, COUNT, PAT>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior));
-                    if (COUNT) ++nfit;
-                }
-                sobol_next += (uint64_t)(npop / 2);
-            }
-        }
-        __syncthreads();
-        const int b = block_argmin<R>(s_fit, s_wmin, s_widx);
-        // a14: decoded best individual (its FP64 chi2 is a separate pass)
-        if (k < ME_NPAR) {
-            const uint16_t gb = s_genes[cur * npop * ME_NPAR + b * ME_NPAR + k];
-            best[(size_t)pix * ME_NPAR + k] =
-                decode64(gb, D.lo[k], D.hi[k]);
-            if (best_genes) best_genes[(size_t)pix * ME_NPAR + k] = gb;
-        }
-        __syncthreads();  // shared memory is reused by the next pixel
-    }
-    if (COUNT) {
-        // evaluations per synthesis: every (padded) wavelength point runs each
-        // line's components
-        unsigned long long per_point = 0;
-        for (int l = 0; l < nlines; ++l) {
-            const int nc = pb.line[l].ncomp[0] + pb.line[l].ncomp[1] + pb.line[l].ncomp[2];
-            per_point += nc ? nc : 3;
-        }
-        atomicAdd(counts + 0, nfit);
-        atomicAdd(counts + 1, ninterior);
-        atomicAdd(counts + 2, nfit * (unsigned long long)padded_lambda<R>(nl) * per_point);
-    }
-}
-
 // ------------------------------------------------- operator-only kernels
+template <int M>
 __global__ void k_ga_breed(const __grid_constant__ KGa ga, const uint16_t *__restrict__ genes,
                            const double *__restrict__ fit, int gen, uint16_t *__restrict__ child,
                            int *__restrict__ elite_out)
@@ -524,21 +33,22 @@ __global__ void k_ga_breed(const __grid_constant__ KGa ga, const uint16_t *__res
     double *s_wmin = s_fit + npop;
     int *s_widx = (int *)(s_wmin + 32);
     uint16_t *s_cur = (uint16_t *)(s_widx + 32);
-    uint16_t *s_new = s_cur + npop * ME_NPAR;
+    uint16_t *s_new = s_cur + npop * M;
     const size_t base = (size_t)prob * npop;
     s_fit[k] = clean_fit(fit[base + k]);
 #pragma unroll
-    for (int d = 0; d < ME_NPAR; ++d) s_cur[k * ME_NPAR + d] = genes[(base + k) * ME_NPAR + d];
+    for (int d = 0; d < M; ++d) s_cur[k * M + d] = genes[(base + k) * M + d];
     __syncthreads();
     const int elite = block_argmin<double>(s_fit, s_wmin, s_widx);
-    uint16_t g[ME_NPAR];
-    breed_one<double>(ga, ga.pixel_id0 + (uint64_t)prob, gen, k, npop, s_fit, s_cur, elite,
-                      s_new + k * ME_NPAR, g);
+    uint16_t g[M];
+    breed_one<double, M>(ga, ga.pixel_id0 + (uint64_t)prob, gen, k, npop, s_fit, s_cur, elite,
+                      s_new + k * M, g);
 #pragma unroll
-    for (int d = 0; d < ME_NPAR; ++d) child[(base + k) * ME_NPAR + d] = g[d];
+    for (int d = 0; d < M; ++d) child[(base + k) * M + d] = g[d];
     if (k == 0 && elite_out) elite_out[prob] = elite;
 }
 
+template <int M>
 __global__ void k_ga_restart(int npop, uint16_t *__restrict__ genes, const double *__restrict__ fit,
                              uint64_t sobol_next)
 {
@@ -552,8 +62,8 @@ __global__ void k_ga_restart(int npop, uint16_t *__restrict__ genes, const doubl
     if (rank >= npop / 2) {
         const uint64_t n = sobol_next + (uint64_t)(rank - npop / 2);
 #pragma unroll
-        for (int d = 0; d < ME_NPAR; ++d)
-            genes[(base + k) * ME_NPAR + d] = (uint16_t)(sobol_point(n, d) >> 16);
+        for (int d = 0; d < M; ++d)
+            genes[(base + k) * M + d] = (uint16_t)(sobol_point(n, d) >> 16);
     }
 }
 
@@ -577,22 +87,6 @@ __global__ void k_sobol(uint64_t first, int n, int ndim, uint32_t *__restrict__ 
     out[i] = sobol_point(first + (uint64_t)pt, d);
 }
 
-template <class R, int NL, int MAXT, bool COUNT = false, bool PAT = false>
-cudaError_t launch_evolve_t(const KProblem &pb, const KGa &ga, const void *obs, const double *w,
-                            const double *mu_px, int npix, double *best, uint16_t *best_genes,
-                            cudaStream_t st, unsigned long long *counts = nullptr, KSeed sd = {},
-                            KSub sub = {})
-{
-    const int nlines = NL > 0 ? NL : pb.n_lines;
-    const GaSmem L = ga_smem_layout<R>(pb.n_lambda, nlines, ga.npop);
-    auto kern = k_ga_evolve<R, NL, MAXT, COUNT, PAT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
-    if (e != cudaSuccess) return e;
-    kern<<<npix, ga.npop, L.total, st>>>(pb, ga, (const R *)obs, w, mu_px, npix, best, best_genes, counts,
-                                          sd, sub);
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 bool has_pattern(const KProblem &pb)
@@ -607,6 +101,7 @@ cudaError_t launch_ga_evolve(const KProblem &pb, const KGa &ga, int dtype, const
                              uint16_t *best_genes, cudaStream_t st, KSeed sd, KSub sub)
 {
     if (npix <= 0) return cudaSuccess;
+    if (pb.fill) return launch_ga_evolve_fill(pb, ga, dtype, obs, w, mu_px, npix, best, best_genes, st, sd, sub);
     const bool pat = has_pattern(pb);
 #define GENESIS_EVOLVE(R, NL, MAXT, PAT) \
     launch_evolve_t<R, NL, MAXT, false, PAT>(pb, ga, obs, w, mu_px, npix, best, best_genes, st, nullptr, sd, sub)
@@ -632,7 +127,7 @@ cudaError_t launch_ga_count(const KProblem &pb, const KGa &ga, int dtype, const 
                             unsigned long long *counts, cudaStream_t st)
 {
     if (npix <= 0) return cudaSuccess;
-    if (dtype == ME_F32 && ga.npop <= 256) {
+    if (dtype == ME_F32 && ga.npop <= 256 && !pb.fill) {
         if (has_pattern(pb))
             return launch_evolve_t<float, 0, 256, true, true>(pb, ga, obs, w, mu_px, npix, best, nullptr, st, counts);
         if (pb.n_lines == 2)
@@ -642,20 +137,26 @@ cudaError_t launch_ga_count(const KProblem &pb, const KGa &ga, int dtype, const 
     return cudaErrorNotSupported;
 }
 
-cudaError_t launch_ga_breed(const KGa &ga, const uint16_t *genes, const double *fit, int nprob,
+cudaError_t launch_ga_breed(const KGa &ga, int npar, const uint16_t *genes, const double *fit, int nprob,
                             int gen, uint16_t *child, int *elite, cudaStream_t st)
 {
     if (nprob <= 0) return cudaSuccess;
-    const int smem = ga.npop * 8 + 32 * 8 + 32 * 4 + 2 * ga.npop * ME_NPAR * 2;
-    k_ga_breed<<<nprob, ga.npop, smem, st>>>(ga, genes, fit, gen, child, elite);
+    const int smem = ga.npop * 8 + 32 * 8 + 32 * 4 + 2 * ga.npop * npar * 2;
+    if (npar == ME_NPAR_MAX)
+        k_ga_breed<ME_NPAR_MAX><<<nprob, ga.npop, smem, st>>>(ga, genes, fit, gen, child, elite);
+    else
+        k_ga_breed<ME_NPAR><<<nprob, ga.npop, smem, st>>>(ga, genes, fit, gen, child, elite);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ga_restart(int npop, uint16_t *genes, const double *fit, int nprob,
+cudaError_t launch_ga_restart(int npop, int npar, uint16_t *genes, const double *fit, int nprob,
                               uint64_t sobol_next, cudaStream_t st)
 {
     if (nprob <= 0) return cudaSuccess;
-    k_ga_restart<<<nprob, npop, npop * 8, st>>>(npop, genes, fit, sobol_next);
+    if (npar == ME_NPAR_MAX)
+        k_ga_restart<ME_NPAR_MAX><<<nprob, npop, npop * 8, st>>>(npop, genes, fit, sobol_next);
+    else
+        k_ga_restart<ME_NPAR><<<nprob, npop, npop * 8, st>>>(npop, genes, fit, sobol_next);
     return cudaGetLastError();
 }
 

@@ -15,8 +15,11 @@ struct KGa {
     uint64_t seed, pixel_id0;
     uint64_t t_cross;       // crossover iff u32 < t_cross
     uint64_t t_mut[16];     // flip bit b (0 = MSB) iff u32 < t_mut[b]
-    double lo[ME_NPAR], hi[ME_NPAR];
+    double lo[ME_NPAR_MAX], hi[ME_NPAR_MAX];
 };
+
+// Parameters per model: 9, or 10 with the fill fraction of Section 4.2.
+template <bool FILL> constexpr int kNpar = ME_NPAR + (FILL ? 1 : 0);
 
 // Section 4.5 seeds and polarity restriction: seeds [npix][nseed][3] of
 // (B, psi, chi), NaN = keep the Sobol gene; polarity [npix] of -1, 0, +1;
@@ -39,12 +42,13 @@ struct KLm {
     int iters;
     double lambda0;
     unsigned free_mask;  // bit k set: parameter k is fitted, else held
-    double lo[ME_NPAR], hi[ME_NPAR];
+    double lo[ME_NPAR_MAX], hi[ME_NPAR_MAX];
 };
 
 // Section 4.3 bound rule around a prefit (margins per parameter).
 struct KPrefitBounds {
-    double lo[ME_NPAR], hi[ME_NPAR], lower[ME_NPAR], upper[ME_NPAR];
+    int npar;
+    double lo[ME_NPAR_MAX], hi[ME_NPAR_MAX], lower[ME_NPAR_MAX], upper[ME_NPAR_MAX];
 };
 
 // Coefficient tables, computed once on the host.
@@ -59,17 +63,22 @@ const HostTables &host_tables();
 cudaError_t upload_tables_ga(const HostTables &t);
 cudaError_t upload_tables_synth(const HostTables &t);
 cudaError_t upload_tables_lm(const HostTables &t);
+cudaError_t upload_tables_ga_fill(const HostTables &t);
 
 // ga_kernels.cu
 cudaError_t launch_ga_evolve(const KProblem &pb, const KGa &ga, int dtype, const void *obs,
                              const double *w, const double *mu_px, int npix, double *best,
                              uint16_t *best_genes, cudaStream_t st, KSeed sd = {}, KSub sub = {});
+// ga_fill_kernels.cu: the same for problems with the fill fraction
+cudaError_t launch_ga_evolve_fill(const KProblem &pb, const KGa &ga, int dtype, const void *obs,
+                                  const double *w, const double *mu_px, int npix, double *best,
+                                  uint16_t *best_genes, cudaStream_t st, KSeed sd, KSub sub);
 cudaError_t launch_ga_count(const KProblem &pb, const KGa &ga, int dtype, const void *obs,
                             const double *w, const double *mu_px, int npix, double *best,
                             unsigned long long *counts, cudaStream_t st);
-cudaError_t launch_ga_breed(const KGa &ga, const uint16_t *genes, const double *fit, int nprob,
+cudaError_t launch_ga_breed(const KGa &ga, int npar, const uint16_t *genes, const double *fit, int nprob,
                             int gen, uint16_t *child, int *elite, cudaStream_t st);
-cudaError_t launch_ga_restart(int npop, uint16_t *genes, const double *fit, int nprob,
+cudaError_t launch_ga_restart(int npop, int npar, uint16_t *genes, const double *fit, int nprob,
                               uint64_t sobol_next, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t *ctr, int n, uint64_t key, uint32_t *out, cudaStream_t st);
 cudaError_t launch_sobol(uint64_t first, int n, int ndim, uint32_t *out, cudaStream_t st);
@@ -88,7 +97,7 @@ cudaError_t launch_chi2_f64(const KProblem &pb, int dtype, const void *obs, cons
 // Section 2 selection, weak-field estimate and Section 4.5 seeds.
 struct KClassify {
     double p_thresh, kz;  // kz = 4.6686e-13 g lambda0^2 of the chosen line
-    int q_lo, q_hi, c_lo, c_hi;
+    int q_lo, q_hi, c_lo, c_hi, npar;
     int *flag, *polarity;
     double *pol, *weak, *seeds, *best;
 };
@@ -121,8 +130,9 @@ int set_error(int code, const std::string &msg);
 int cuda_error(cudaError_t e, const char *where);
 int ensure_device();
 int make_problem(const me_problem *pb, KProblem &k);
-int check_bounds(const me_bounds *b);
-int make_ga(const ga_config *cfg, const me_bounds *b, uint64_t pid0, KGa &g);
+int npar_of(const me_problem *pb);  // 9, or 10 with the fill fraction
+int check_bounds(const me_bounds *b, int npar);
+int make_ga(const ga_config *cfg, const me_bounds *b, uint64_t pid0, KGa &g, int npar);
 cudaStream_t as_stream(void *s);
 
 // Decode of Eq. decode in FP64 without contraction, the same expression the

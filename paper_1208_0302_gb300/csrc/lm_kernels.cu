@@ -19,7 +19,6 @@ cudaError_t upload_tables_lm(const HostTables &t)
 namespace {
 
 constexpr int kLmWarps = 4;
-constexpr int kNT = ME_NPAR * (ME_NPAR + 1) / 2;  // packed lower triangle
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -38,20 +37,20 @@ template <class R> __device__ __forceinline__ void kahan_sq(R &s, R &c, R r)
 
 // chi2 (Eq. chisq) of parameters p: synthesis in R, per-lane compensated sums,
 // warp sum in FP64.  Every lane returns the same value.
-template <class R, class RO, int NL>
+template <class R, class RO, int NL, int M = ME_NPAR>
 __device__ double lm_chi2(const KProblem &pb, int nlines, int nl, const double *p, double mu,
                           const RO *o, const R *s_doff, const R *he, const double *w2)
 {
-    R pr[ME_NPAR];
+    R pr[M];
 #pragma unroll
-    for (int d = 0; d < ME_NPAR; ++d) pr[d] = R(p[d]);
-    const Geo<R> g = make_geo<R, NL>(pb, nlines, pr, R(mu));
+    for (int d = 0; d < M; ++d) pr[d] = R(p[d]);
+    const Geo<R> g = make_geo<R, NL, (M > ME_NPAR)>(pb, nlines, pr, R(mu));
     R s[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
     for (int j = threadIdx.x & 31; j < nl; j += 32) {
         R doff[ME_MAX_LINES];
 #pragma unroll
         for (int l = 0; l < ME_MAX_LINES; ++l) doff[l] = l < nlines ? s_doff[l * nl + j] : R(0);
-        const Stokes4<R> m = me_point<R, NL>(g, doff, he, nlines, pb.line);
+        const Stokes4<R> m = me_point<R, NL, true, (M > ME_NPAR)>(g, doff, he, nlines, pb.line);
         kahan_sq(s[0], c[0], R(o[j]) - m.I);
         kahan_sq(s[1], c[1], R(o[nl + j]) - m.Q);
         kahan_sq(s[2], c[2], R(o[2 * nl + j]) - m.U);
@@ -60,50 +59,51 @@ __device__ double lm_chi2(const KProblem &pb, int nlines, int nl, const double *
     double tot = 0.0;
 #pragma unroll
     for (int st = 0; st < 4; ++st) tot += w2[st] * warp_sum((double)s[st]);
-    return tot / (double)(4 * nl - ME_NPAR);
+    return tot / (double)(4 * nl - M);
 }
 
 // Solve (A + lam D) x = g by Cholesky (row-major 9x9 in N), D = diag(max(A_jj,
 // 1e-12 max A_kk)).  Returns false if a pivot is not positive.
+template <int M>
 __device__ bool damped_cholesky(const double *A, const double *g, double lam, double *N, double *x)
 {
     double dmax = 0.0;
-    for (int a = 0; a < ME_NPAR; ++a) dmax = fmax(dmax, A[a * ME_NPAR + a]);
-    for (int a = 0; a < ME_NPAR * ME_NPAR; ++a) N[a] = A[a];
-    for (int a = 0; a < ME_NPAR; ++a) {
-        const double d = A[a * ME_NPAR + a] > 1e-12 * dmax ? A[a * ME_NPAR + a] : 1e-12 * dmax;
-        N[a * ME_NPAR + a] += lam * d;
+    for (int a = 0; a < M; ++a) dmax = fmax(dmax, A[a * M + a]);
+    for (int a = 0; a < M * M; ++a) N[a] = A[a];
+    for (int a = 0; a < M; ++a) {
+        const double d = A[a * M + a] > 1e-12 * dmax ? A[a * M + a] : 1e-12 * dmax;
+        N[a * M + a] += lam * d;
     }
-    for (int j = 0; j < ME_NPAR; ++j) {
-        double d = N[j * ME_NPAR + j];
-        for (int k = 0; k < j; ++k) d -= N[j * ME_NPAR + k] * N[j * ME_NPAR + k];
+    for (int j = 0; j < M; ++j) {
+        double d = N[j * M + j];
+        for (int k = 0; k < j; ++k) d -= N[j * M + k] * N[j * M + k];
         if (!(d > 0.0)) return false;
         const double ljj = sqrt(d);
-        N[j * ME_NPAR + j] = ljj;
-        for (int i = j + 1; i < ME_NPAR; ++i) {
-            double s = N[i * ME_NPAR + j];
-            for (int k = 0; k < j; ++k) s -= N[i * ME_NPAR + k] * N[j * ME_NPAR + k];
-            N[i * ME_NPAR + j] = s / ljj;
+        N[j * M + j] = ljj;
+        for (int i = j + 1; i < M; ++i) {
+            double s = N[i * M + j];
+            for (int k = 0; k < j; ++k) s -= N[i * M + k] * N[j * M + k];
+            N[i * M + j] = s / ljj;
         }
     }
-    for (int i = 0; i < ME_NPAR; ++i) {
+    for (int i = 0; i < M; ++i) {
         double s = g[i];
-        for (int k = 0; k < i; ++k) s -= N[i * ME_NPAR + k] * x[k];
-        x[i] = s / N[i * ME_NPAR + i];
+        for (int k = 0; k < i; ++k) s -= N[i * M + k] * x[k];
+        x[i] = s / N[i * M + i];
     }
-    for (int i = ME_NPAR - 1; i >= 0; --i) {
+    for (int i = M - 1; i >= 0; --i) {
         double s = x[i];
-        for (int k = i + 1; k < ME_NPAR; ++k) s -= N[k * ME_NPAR + i] * x[k];
-        x[i] = s / N[i * ME_NPAR + i];
+        for (int k = i + 1; k < M; ++k) s -= N[k * M + i] * x[k];
+        x[i] = s / N[i * M + i];
     }
     return true;
 }
 
-struct LmWarpSmem {
-    double A[ME_NPAR * ME_NPAR];
-    double N[ME_NPAR * ME_NPAR];
-    double g[ME_NPAR];
-    double x[ME_NPAR];
+struct LmWarpSmem {  // M x M matrices stored with row stride M
+    double A[ME_NPAR_MAX * ME_NPAR_MAX];
+    double N[ME_NPAR_MAX * ME_NPAR_MAX];
+    double g[ME_NPAR_MAX];
+    double x[ME_NPAR_MAX];
     double w2[4];
     double lam;
     int ok;
@@ -155,34 +155,35 @@ __device__ void lm_weights(const RO *o, int nl, const double *w_user, int pix, L
 
 // Normal equations at p: W.A = J^T W^2 J (full 9x9) and W.g = J^T W^2 r,
 // per-lane partial sums in R over the lane's wavelengths, warp sums in FP64.
-template <class R, class RO, int NL>
+template <class R, class RO, int NL, int M = ME_NPAR>
 __device__ void lm_normal(const KProblem &pb, int nlines, int nl, const double *p, double mu,
                           const RO *o, const R *s_doff, const R *he, const R *w2r, LmWarpSmem &W)
 {
     const int lane = threadIdx.x & 31;
-    R pr[ME_NPAR];
+    R pr[M];
 #pragma unroll
-    for (int d = 0; d < ME_NPAR; ++d) pr[d] = R(p[d]);
-    const GeoJ<R> G = make_geoj<R, NL>(pb, nlines, pr, R(mu));
-    R Aacc[kNT], gacc[ME_NPAR];
+    for (int d = 0; d < M; ++d) pr[d] = R(p[d]);
+    const GeoJ<R> G = make_geoj<R, NL, (M > ME_NPAR)>(pb, nlines, pr, R(mu));
+    constexpr int kNT = M * (M + 1) / 2;  // packed lower triangle
+    R Aacc[kNT], gacc[M];
 #pragma unroll
     for (int a = 0; a < kNT; ++a) Aacc[a] = R(0);
 #pragma unroll
-    for (int a = 0; a < ME_NPAR; ++a) gacc[a] = R(0);
+    for (int a = 0; a < M; ++a) gacc[a] = R(0);
     for (int j = lane; j < nl; j += 32) {
         R doff[ME_MAX_LINES];
 #pragma unroll
         for (int l = 0; l < ME_MAX_LINES; ++l) doff[l] = l < nlines ? s_doff[l * nl + j] : R(0);
         Stokes4<R> m;
-        R J[4][ME_NPAR];
-        me_point_jac<R, NL>(G, doff, he, nlines, pb.line, m, J);
+        R J[4][M];
+        me_point_jac<R, NL, (M > ME_NPAR)>(G, doff, he, nlines, pb.line, m, J);
         const R r[4] = {R(o[j]) - m.I, R(o[nl + j]) - m.Q, R(o[2 * nl + j]) - m.U,
                         R(o[3 * nl + j]) - m.V};
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             int t = 0;
 #pragma unroll
-            for (int a = 0; a < ME_NPAR; ++a) {
+            for (int a = 0; a < M; ++a) {
                 const R wa = w2r[s] * J[s][a];
                 gacc[a] += wa * r[s];
 #pragma unroll
@@ -192,22 +193,22 @@ __device__ void lm_normal(const KProblem &pb, int nlines, int nl, const double *
     }
     int t = 0;
 #pragma unroll
-    for (int a = 0; a < ME_NPAR; ++a) {
+    for (int a = 0; a < M; ++a) {
         const double gv = warp_sum((double)gacc[a]);
         if (lane == 0) W.g[a] = gv;
 #pragma unroll
         for (int b = 0; b <= a; ++b) {
             const double v = warp_sum((double)Aacc[t++]);
             if (lane == 0) {
-                W.A[a * ME_NPAR + b] = v;
-                W.A[b * ME_NPAR + a] = v;
+                W.A[a * M + b] = v;
+                W.A[b * M + a] = v;
             }
         }
     }
     __syncwarp();
 }
 
-template <class R, class RO, int NL>
+template <class R, class RO, int NL, int M = ME_NPAR>
 __global__ void __launch_bounds__(kLmWarps * 32)
 k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const RO *__restrict__ obs,
      const double *__restrict__ w_user, const double *__restrict__ mu_px, int npix,
@@ -244,30 +245,30 @@ k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const 
     for (int s = 0; s < 4; ++s) w2r[s] = R(w2[s]);
 
     const double mu = mu_px ? mu_px[pix] : pb.mu;
-    double p[ME_NPAR];
+    double p[M];
 #pragma unroll
-    for (int d = 0; d < ME_NPAR; ++d) p[d] = params[(size_t)pix * ME_NPAR + d];
-    double chi2 = lm_chi2<R, RO, NL>(pb, nlines, nl, p, mu, o, s_doff, he, w2);
+    for (int d = 0; d < M; ++d) p[d] = params[(size_t)pix * M + d];
+    double chi2 = lm_chi2<R, RO, NL, M>(pb, nlines, nl, p, mu, o, s_doff, he, w2);
     double lam = lm.lambda0;
     bool need = true;
     for (int it = 0; it < lm.iters; ++it) {
         if (need) {
-            lm_normal<R, RO, NL>(pb, nlines, nl, p, mu, o, s_doff, he, w2r, W);
+            lm_normal<R, RO, NL, M>(pb, nlines, nl, p, mu, o, s_doff, he, w2r, W);
             need = false;
         }
         if (lane == 0) {
             // held parameters: zero rows and columns, so their step is 0
-            for (int a = 0; a < ME_NPAR; ++a) {
+            for (int a = 0; a < M; ++a) {
                 if ((lm.free_mask >> a) & 1u) continue;
                 W.g[a] = 0.0;
-                for (int b = 0; b < ME_NPAR; ++b) {
-                    W.A[a * ME_NPAR + b] = 0.0;
-                    W.A[b * ME_NPAR + a] = 0.0;
+                for (int b = 0; b < M; ++b) {
+                    W.A[a * M + b] = 0.0;
+                    W.A[b * M + a] = 0.0;
                 }
             }
             bool ok = false;
             for (int tries = 0; tries < 30 && !ok; ++tries) {
-                ok = damped_cholesky(W.A, W.g, lam, W.N, W.x);
+                ok = damped_cholesky<M>(W.A, W.g, lam, W.N, W.x);
                 if (!ok) lam *= 10.0;
             }
             W.ok = ok ? 1 : 0;
@@ -276,9 +277,9 @@ k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const 
         __syncwarp();
         lam = W.lam;
         if (!W.ok) break;
-        double q[ME_NPAR];
+        double q[M];
 #pragma unroll
-        for (int d = 0; d < ME_NPAR; ++d) q[d] = p[d] + W.x[d];
+        for (int d = 0; d < M; ++d) q[d] = p[d] + W.x[d];
         {
             double c = fmod(q[2], 180.0);
             if (c < 0.0) c += 180.0;
@@ -286,12 +287,12 @@ k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const 
             q[2] = c;
         }
 #pragma unroll
-        for (int d = 0; d < ME_NPAR; ++d) q[d] = fmin(fmax(q[d], lm.lo[d]), lm.hi[d]);
-        const double c2 = lm_chi2<R, RO, NL>(pb, nlines, nl, q, mu, o, s_doff, he, w2);
+        for (int d = 0; d < M; ++d) q[d] = fmin(fmax(q[d], lm.lo[d]), lm.hi[d]);
+        const double c2 = lm_chi2<R, RO, NL, M>(pb, nlines, nl, q, mu, o, s_doff, he, w2);
         __syncwarp();
         if (c2 < chi2) {
 #pragma unroll
-            for (int d = 0; d < ME_NPAR; ++d) p[d] = q[d];
+            for (int d = 0; d < M; ++d) p[d] = q[d];
             chi2 = c2;
             lam /= 10.0;
             need = true;
@@ -299,11 +300,11 @@ k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const 
             lam *= 10.0;
         }
     }
-    if (lane < ME_NPAR) {
+    if (lane < M) {
         double v = p[0];
 #pragma unroll
-        for (int d = 1; d < ME_NPAR; ++d) v = (lane == d) ? p[d] : v;
-        params[(size_t)pix * ME_NPAR + lane] = v;
+        for (int d = 1; d < M; ++d) v = (lane == d) ? p[d] : v;
+        params[(size_t)pix * M + lane] = v;
     }
 }
 
@@ -312,7 +313,7 @@ k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const 
 // H = (2/nu) J^T W^2 J.  Warp per pixel; J in the problem precision, sums in
 // FP64, Cholesky inverse diagonal in FP64 (lane 0).  A parameter without
 // influence (singular H) gets +infinity.
-template <class R, class RO, int NL>
+template <class R, class RO, int NL, int M = ME_NPAR>
 __global__ void __launch_bounds__(kLmWarps * 32)
 k_lm_sigma(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
            const double *__restrict__ w_user, const double *__restrict__ mu_px, int npix,
@@ -344,55 +345,55 @@ k_lm_sigma(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
 #pragma unroll
     for (int s = 0; s < 4; ++s) w2r[s] = R(w2[s]);
     const double mu = mu_px ? mu_px[pix] : pb.mu;
-    double p[ME_NPAR];
+    double p[M];
 #pragma unroll
-    for (int d = 0; d < ME_NPAR; ++d) p[d] = params[(size_t)pix * ME_NPAR + d];
-    const double chi2 = lm_chi2<R, RO, NL>(pb, nlines, nl, p, mu, o, s_doff, he, w2);
-    lm_normal<R, RO, NL>(pb, nlines, nl, p, mu, o, s_doff, he, w2r, W);
+    for (int d = 0; d < M; ++d) p[d] = params[(size_t)pix * M + d];
+    const double chi2 = lm_chi2<R, RO, NL, M>(pb, nlines, nl, p, mu, o, s_doff, he, w2);
+    lm_normal<R, RO, NL, M>(pb, nlines, nl, p, mu, o, s_doff, he, w2r, W);
     if (lane == 0) {
-        const double nu = (double)(4 * nl - ME_NPAR);
+        const double nu = (double)(4 * nl - M);
         // H = (2/nu) A;  [H^-1]_ii = (nu/2) [A^-1]_ii
         double *N = W.N;
-        for (int a = 0; a < ME_NPAR * ME_NPAR; ++a) N[a] = W.A[a];
+        for (int a = 0; a < M * M; ++a) N[a] = W.A[a];
         bool ok = true;
-        for (int j = 0; j < ME_NPAR && ok; ++j) {
-            double d = N[j * ME_NPAR + j];
-            for (int k = 0; k < j; ++k) d -= N[j * ME_NPAR + k] * N[j * ME_NPAR + k];
+        for (int j = 0; j < M && ok; ++j) {
+            double d = N[j * M + j];
+            for (int k = 0; k < j; ++k) d -= N[j * M + k] * N[j * M + k];
             if (!(d > 0.0)) { ok = false; break; }
             const double ljj = sqrt(d);
-            N[j * ME_NPAR + j] = ljj;
-            for (int i = j + 1; i < ME_NPAR; ++i) {
-                double t = N[i * ME_NPAR + j];
-                for (int k = 0; k < j; ++k) t -= N[i * ME_NPAR + k] * N[j * ME_NPAR + k];
-                N[i * ME_NPAR + j] = t / ljj;
+            N[j * M + j] = ljj;
+            for (int i = j + 1; i < M; ++i) {
+                double t = N[i * M + j];
+                for (int k = 0; k < j; ++k) t -= N[i * M + k] * N[j * M + k];
+                N[i * M + j] = t / ljj;
             }
         }
-        for (int i = 0; i < ME_NPAR; ++i) {
+        for (int i = 0; i < M; ++i) {
             double v = INFINITY;
             if (ok) {
                 // [A^-1]_ii = || L^-1 e_i ||^2 (forward substitution of e_i)
-                double y[ME_NPAR];
+                double y[M];
                 double acc = 0.0;
-                for (int r = 0; r < ME_NPAR; ++r) {
+                for (int r = 0; r < M; ++r) {
                     double t = (r == i) ? 1.0 : 0.0;
-                    for (int k = 0; k < r; ++k) t -= N[r * ME_NPAR + k] * y[k];
-                    y[r] = t / N[r * ME_NPAR + r];
+                    for (int k = 0; k < r; ++k) t -= N[r * M + k] * y[k];
+                    y[r] = t / N[r * M + r];
                     acc += y[r] * y[r];
                 }
-                v = sqrt(0.5 * nu * acc * chi2 / (double)ME_NPAR);
+                v = sqrt(0.5 * nu * acc * chi2 / (double)M);
             }
-            sigma[(size_t)pix * ME_NPAR + i] = v;
+            sigma[(size_t)pix * M + i] = v;
         }
     }
 }
 
-template <class R, class RO, int NL>
+template <class R, class RO, int NL, int M = ME_NPAR>
 cudaError_t sigma_t(const KProblem &pb, const void *obs, const double *w, const double *mu_px, int npix,
                     const double *params, double *sigma, cudaStream_t st)
 {
     const int nlines = NL > 0 ? NL : pb.n_lines;
     const size_t smem = sizeof(LmWarpSmem) * kLmWarps + sizeof(R) * (ME_MAX_LINES + (size_t)nlines * pb.n_lambda);
-    auto kern = k_lm_sigma<R, RO, NL>;
+    auto kern = k_lm_sigma<R, RO, NL, M>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<(npix + kLmWarps - 1) / kLmWarps, kLmWarps * 32, smem, st>>>(pb, (const RO *)obs, w, mu_px, npix,
@@ -400,13 +401,13 @@ cudaError_t sigma_t(const KProblem &pb, const void *obs, const double *w, const 
     return cudaGetLastError();
 }
 
-template <class R, class RO, int NL>
+template <class R, class RO, int NL, int M = ME_NPAR>
 cudaError_t lm_t(const KProblem &pb, const KLm &lm, const void *obs, const double *w,
                  const double *mu_px, int npix, double *params, cudaStream_t st, KSub sub)
 {
     const int nlines = NL > 0 ? NL : pb.n_lines;
     const size_t smem = sizeof(LmWarpSmem) * kLmWarps + sizeof(R) * (ME_MAX_LINES + (size_t)nlines * pb.n_lambda);
-    auto kern = k_lm<R, RO, NL>;
+    auto kern = k_lm<R, RO, NL, M>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<(npix + kLmWarps - 1) / kLmWarps, kLmWarps * 32, smem, st>>>(pb, lm, (const RO *)obs, w, mu_px,
@@ -421,6 +422,9 @@ cudaError_t launch_lm_sigma(const KProblem &pb, int dtype, const void *obs, cons
                             cudaStream_t st)
 {
     if (npix <= 0) return cudaSuccess;
+    if (pb.fill)
+        return dtype == ME_F32 ? sigma_t<float, float, 0, ME_NPAR_MAX>(pb, obs, w, mu_px, npix, params, sigma, st)
+                               : sigma_t<double, double, 0, ME_NPAR_MAX>(pb, obs, w, mu_px, npix, params, sigma, st);
     if (dtype == ME_F32) {
         if (pb.n_lines == 1) return sigma_t<float, float, 1>(pb, obs, w, mu_px, npix, params, sigma, st);
         if (pb.n_lines == 2) return sigma_t<float, float, 2>(pb, obs, w, mu_px, npix, params, sigma, st);
@@ -434,6 +438,9 @@ cudaError_t launch_lm(const KProblem &pb, const KLm &lm, int dtype, const void *
                       cudaStream_t st, KSub sub)
 {
     if (npix <= 0 || lm.iters <= 0) return cudaSuccess;
+    if (pb.fill)
+        return dtype == ME_F32 ? lm_t<float, float, 0, ME_NPAR_MAX>(pb, lm, obs, w, mu_px, npix, params, st, sub)
+                               : lm_t<double, double, 0, ME_NPAR_MAX>(pb, lm, obs, w, mu_px, npix, params, st, sub);
     if (dtype == ME_F32) {
         if (pb.n_lines == 1) return lm_t<float, float, 1>(pb, lm, obs, w, mu_px, npix, params, st, sub);
         if (pb.n_lines == 2) return lm_t<float, float, 2>(pb, lm, obs, w, mu_px, npix, params, st, sub);

@@ -44,6 +44,7 @@ template <> __device__ __forceinline__ double comp_str<double>(const KLine &ln, 
 struct KProblem {
     int n_lines;
     int n_lambda;
+    int fill;                   // 1: parameter 9 is the fill fraction alpha
     double mu;
     KLine line[ME_MAX_LINES];
     double lam[ME_MAX_LAMBDA];  // wavelength grid [A]
@@ -250,6 +251,7 @@ template <class R> struct Geo {
     R kIp2, kV2;        // kIp^2, kV^2
     R kUV, kQV;         // kU kV, kQ kV
     R S0, muS1;
+    R eta0, alpha;          // line strength; fill fraction (1 without one)
     R shift[ME_MAX_LINES];  // lambda0 v_LOS / c [A]
     R invD[ME_MAX_LINES];   // 1 / Doppler width [1/A]
     R vB[ME_MAX_LINES];     // Zeeman splitting in Doppler units
@@ -267,7 +269,8 @@ __device__ __forceinline__ void sincos_deg(double d, double *s, double *c)
 }
 
 // Geometry of one parameter vector p (Section 4 model vector), in R.
-template <class R, int NL>
+// FILL: p[9] is the fill fraction alpha of Section 4.2.
+template <class R, int NL, bool FILL = false>
 __device__ __forceinline__ Geo<R> make_geo(const KProblem &pb, int nlines, const R *p, R mu)
 {
     Geo<R> g;
@@ -289,6 +292,9 @@ __device__ __forceinline__ Geo<R> make_geo(const KProblem &pb, int nlines, const
     g.kQV = g.kQ * g.kV;
     g.S0 = p[7];
     g.muS1 = mu * p[8];
+    g.eta0 = eta0;
+    if constexpr (FILL) g.alpha = p[9];
+    else g.alpha = R(1);
     const int nl = NL > 0 ? NL : nlines;
 #pragma unroll
     for (int l = 0; l < (NL > 0 ? NL : ME_MAX_LINES); ++l) {
@@ -305,6 +311,19 @@ __device__ __forceinline__ Geo<R> make_geo(const KProblem &pb, int nlines, const
 }
 
 template <class R> struct Stokes4 { R I, Q, U, V; };
+
+// Section 4.2 fill fraction: Stokes <- alpha Stokes + (1 - alpha) I_nm e with
+// the field-free I_nm = S0 + mu S1 / (1 + eta0 sum_l eta_ratio_l Re w0_l)
+// (w0 the unshifted profile); P0 = sum_l (eta_ratio_l / 2) Re w0_l.
+template <class R>
+__device__ __forceinline__ void fill_mix(Stokes4<R> &s, const Geo<R> &g, R P0)
+{
+    const R inm = g.muS1 * fast_rcp(R(1) + R(2) * g.eta0 * P0);
+    s.I = g.S0 + g.alpha * (s.I - g.S0) + (R(1) - g.alpha) * inm;
+    s.Q *= g.alpha;
+    s.U *= g.alpha;
+    s.V *= g.alpha;
+}
 
 // Group profiles (sigma_b, pi, sigma_r) of a line with a full Zeeman pattern:
 // each is the strength-weighted sum of its components' w(x_i + i a), with
@@ -337,11 +356,12 @@ __device__ __forceinline__ void pattern_profiles(const KLine &ln, R dinv, R cp, 
 // FP64, rounded to R), half_eta[l] = eta_ratio_l / 2.
 // PAT = false compiles out full-pattern lines (problems with effective
 // triplets only); PAT = true checks each line at run time.
-template <class R, int NL, bool PAT = true>
+// FILL mixes in the field-free profile with the fill fraction g.alpha.
+template <class R, int NL, bool PAT = true, bool FILL = false>
 __device__ __forceinline__ Stokes4<R> me_point(const Geo<R> &g, const R *doff, const R *half_eta,
                                                int nlines, const KLine *lines)
 {
-    R P = 0, Sg = 0, T = 0, Dd = 0, Ti = 0, Di = 0;
+    R P = 0, Sg = 0, T = 0, Dd = 0, Ti = 0, Di = 0, P0 = 0;
     const int nl = NL > 0 ? NL : nlines;
 #pragma unroll
     for (int l = 0; l < (NL > 0 ? NL : ME_MAX_LINES); ++l) {
@@ -352,8 +372,10 @@ __device__ __forceinline__ Stokes4<R> me_point(const Geo<R> &g, const R *doff, c
                 const R xb = doff[l] * g.invD[l] + (g.cp[l] + g.vB[l]);
                 const R xr = doff[l] * g.invD[l] + (g.cp[l] - g.vB[l]);
                 faddeeva_triplet<R>(xb, v, xr, g.vB[l], g.a, g.a2, wb, wp, wr);
+                if (FILL) P0 += half_eta[l] * wp.x;  // the pi profile is unshifted
             } else {
                 pattern_profiles<R>(lines[l], doff[l] * g.invD[l], g.cp[l], g.vL[l], g.a, g.a2, wb, wp, wr);
+                if (FILL) P0 += half_eta[l] * faddeeva<R>(doff[l] * g.invD[l] + g.cp[l], g.a).x;
             }
             const R q = half_eta[l];
             const R sx = wb.x + wr.x, sy = wb.y + wr.y;
@@ -387,6 +409,7 @@ __device__ __forceinline__ Stokes4<R> me_point(const Geo<R> &g, const R *doff, c
     s.Q = -f * (g.kQ * A + g.kUV * eIC);
     s.U = -f * (g.kU * A - g.kQV * eIC);
     s.V = -f * g.kV * (eI2 * Dd + Di * Pi);
+    if (FILL) fill_mix(s, g, P0);
     return s;
 }
 

@@ -21,11 +21,11 @@ template <class R> struct GeoJ {
     R kL[ME_MAX_LINES];              // d v_L / d B (Larmor displacement, full patterns)
 };
 
-template <class R, int NL>
+template <class R, int NL, bool FILL = false>
 __device__ __forceinline__ GeoJ<R> make_geoj(const KProblem &pb, int nlines, const R *p, R mu)
 {
     GeoJ<R> G;
-    G.g = make_geo<R, NL>(pb, nlines, p, mu);
+    G.g = make_geo<R, NL, FILL>(pb, nlines, p, mu);
     R st, ct, s2c, c2c;
     sincos_deg(p[1], &st, &ct);
     sincos_deg(R(2) * p[2], &s2c, &c2c);
@@ -65,16 +65,20 @@ template <class R> struct Sums {
 };
 
 // Stokes vector and J[s][k] = d Stokes_s / d p_k at one wavelength.
-template <class R, int NL>
+// FILL: Section 4.2 fill fraction, p[9] = alpha, J has a 10th column.
+template <class R, int NL, bool FILL = false>
 __device__ __forceinline__ void me_point_jac(const GeoJ<R> &G, const R *doff, const R *half_eta,
                                              int nlines, const KLine *lines, Stokes4<R> &out,
-                                             R J[4][ME_NPAR])
+                                             R J[4][ME_NPAR + (FILL ? 1 : 0)])
 {
     const Geo<R> &g = G.g;
     Sums<R> S;
     S.P = S.Sg = S.T = S.Ti = S.Dd = S.Di = R(0);
 #pragma unroll
     for (int d = 0; d < 4; ++d) S.dP[d] = S.dSg[d] = S.dT[d] = S.dTi[d] = S.dDd[d] = S.dDi[d] = R(0);
+    // field-free profile sum P0 = sum (eta_ratio / 2) Re w0 and its
+    // derivatives along v_LOS, D, a (FILL only)
+    R P0 = R(0), dP0[4] = {R(0), R(0), R(0), R(0)};
     const R two_isp = R(1.12837916709551257390);  // 2 / sqrt(pi)
     const int nl = NL > 0 ? NL : nlines;
 #pragma unroll
@@ -99,6 +103,11 @@ __device__ __forceinline__ void me_point_jac(const GeoJ<R> &G, const R *doff, co
                     wd[c][1] = {dx * sv, dy * sv};   // d/dv_LOS
                     wd[c][2] = {dx * sD, dy * sD};   // d/dD
                     wd[c][3] = {-dy, dx};            // d/da = i w'
+                }
+                if (FILL) {  // the pi component is unshifted
+                    P0 += q * w[1].x;
+#pragma unroll
+                    for (int d = 1; d < 4; ++d) dP0[d] += q * wd[1][d].x;
                 }
             } else {
                 // full pattern: strength-weighted sums over each group's
@@ -125,6 +134,16 @@ __device__ __forceinline__ void me_point_jac(const GeoJ<R> &G, const R *doff, co
                         wd[c][3].x -= st * dy;
                         wd[c][3].y += st * dx;
                     }
+                }
+                if (FILL) {  // the field-free profile needs its own, unshifted evaluation
+                    const R x = dinv + g.cp[l];
+                    const C2<R> w0 = faddeeva<R>(x, g.a);
+                    const R dx = R(-2) * (x * w0.x - g.a * w0.y);
+                    const R dy = R(-2) * (x * w0.y + g.a * w0.x) + two_isp;
+                    P0 += q * w0.x;
+                    dP0[1] += q * dx * sv;
+                    dP0[2] += q * dx * (-x * G.invDpar);
+                    dP0[3] -= q * dy;
                 }
             }
             const R sx = w[0].x + w[2].x, sy = w[0].y + w[2].y;
@@ -258,6 +277,28 @@ __device__ __forceinline__ void me_point_jac(const GeoJ<R> &G, const R *doff, co
     J[1][8] = -G.mu * xQ;
     J[2][8] = -G.mu * xU;
     J[3][8] = -G.mu * xV;
+    if constexpr (FILL) {
+        // Stokes = alpha S_mag + (1 - alpha) I_nm e, I_nm = S0 + mu S1 / eta_nm,
+        // eta_nm = 1 + 2 eta0 P0
+        const R inv = R(1) / (R(1) + R(2) * G.eta0 * P0);
+        const R inm = g.muS1 * inv;
+        const R c = -g.muS1 * inv * inv * R(2);  // d I_nm / d (eta0 P0)
+        const R al = g.alpha, om = R(1) - g.alpha;
+        R dnm[ME_NPAR] = {R(0), R(0), R(0), c * G.eta0 * dP0[1], c * G.eta0 * dP0[2], c * G.eta0 * dP0[3],
+                          c * P0, R(1), G.mu * inv};
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int k = 0; k < ME_NPAR; ++k) J[s][k] = al * J[s][k] + (s == 0 ? om * dnm[k] : R(0));
+        J[0][ME_NPAR] = (out.I - g.S0) - inm;  // I_mag - I_nm
+        J[1][ME_NPAR] = out.Q;
+        J[2][ME_NPAR] = out.U;
+        J[3][ME_NPAR] = out.V;
+        out.I = g.S0 + al * (out.I - g.S0) + om * inm;
+        out.Q *= al;
+        out.U *= al;
+        out.V *= al;
+    }
 }
 
 }  // namespace genesis

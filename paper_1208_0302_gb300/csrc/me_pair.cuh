@@ -146,13 +146,15 @@ __device__ __forceinline__ void pattern_profiles_x2(const KLine &ln, float2 dinv
 }
 
 // Stokes vectors at two wavelength points.  doff2[l] holds (lambda_j -
-// lambda0_l, lambda_{j+1} - lambda0_l).
-template <int NL, bool COUNT, bool PAT>
+// lambda0_l, lambda_{j+1} - lambda0_l).  FILL mixes in the field-free
+// profile with the fill fraction (Section 4.2, see fill_mix).
+template <int NL, bool COUNT, bool PAT, bool FILL = false>
 __device__ __forceinline__ Stokes4x2 me_point_x2(const Geo<float> &g, const float2 *doff2,
                                                  const float *half_eta, int nlines, unsigned &ncount,
                                                  const KLine *lines)
 {
     float2 P = f2(0.f), Sg = f2(0.f), T = f2(0.f), Ti = f2(0.f), Dd = f2(0.f), Di = f2(0.f);
+    float2 P0 = f2(0.f);
     const int nl = NL > 0 ? NL : nlines;
 #pragma unroll
     for (int l = 0; l < (NL > 0 ? NL : ME_MAX_LINES); ++l) {
@@ -160,6 +162,11 @@ __device__ __forceinline__ Stokes4x2 me_point_x2(const Geo<float> &g, const floa
             float2 w[6];
             pattern_profiles_x2<COUNT>(lines[l], mul2(doff2[l], f2(g.invD[l])), g.cp[l], g.vL[l], g.a, g.a2,
                                        w, ncount);
+            if (FILL) {
+                float2 ux, uy;
+                fad_pair(fma2(doff2[l], f2(g.invD[l]), f2(g.cp[l])), g.a, g.a2, ux, uy);
+                P0 = fma2(f2(half_eta[l]), ux, P0);
+            }
             const float2 q = f2(half_eta[l]);
             const float2 sx = add2(w[0], w[4]), sy = add2(w[1], w[5]);
             P = fma2(q, w[2], P);
@@ -186,6 +193,7 @@ __device__ __forceinline__ Stokes4x2 me_point_x2(const Geo<float> &g, const floa
             }
             const float2 q = f2(half_eta[l]);
             const float2 sx = add2(bx, rx), sy = add2(by, ry);
+            if (FILL) P0 = fma2(q, px, P0);  // the pi profile is unshifted
             P = fma2(q, px, P);
             Sg = fma2(q, sx, Sg);
             T = fma2(q, fma2(f2(-0.5f), sx, px), T);
@@ -211,6 +219,14 @@ __device__ __forceinline__ Stokes4x2 me_point_x2(const Geo<float> &g, const floa
     s.Q = mul2(neg2(f), fma2(f2(g.kQ), A, mul2(f2(g.kUV), eIC)));
     s.U = mul2(neg2(f), fma2(f2(g.kU), A, neg2(mul2(f2(g.kQV), eIC))));
     s.V = mul2(mul2(neg2(f), f2(g.kV)), fma2(eI2, Dd, mul2(Di, Pi)));
+    if (FILL) {
+        const float2 inm = mul2(f2(g.muS1), rcp2(fma2(f2(2.0f * g.eta0), P0, f2(1.0f))));
+        const float2 al = f2(g.alpha), om = f2(1.0f - g.alpha);
+        s.I = fma2(al, sub2(s.I, f2(g.S0)), fma2(om, inm, f2(g.S0)));
+        s.Q = mul2(al, s.Q);
+        s.U = mul2(al, s.U);
+        s.V = mul2(al, s.V);
+    }
     return s;
 }
 

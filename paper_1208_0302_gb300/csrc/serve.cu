@@ -44,7 +44,7 @@ struct Layout {
     size_t obs, w, mu, pw, best, chi2, total;
 };
 
-Layout layout_for(int npix, int n_lambda, size_t elem, bool has_w, bool has_mu, bool has_pw)
+Layout layout_for(int npix, int n_lambda, int npar, size_t elem, bool has_w, bool has_mu, bool has_pw)
 {
     Layout L;
     size_t at = 0;
@@ -57,7 +57,7 @@ Layout layout_for(int npix, int n_lambda, size_t elem, bool has_w, bool has_mu, 
     L.w = has_w ? take((size_t)npix * 4 * 8) : 0;
     L.mu = has_mu ? take((size_t)npix * 8) : 0;
     L.pw = has_pw ? take((size_t)npix * 4 * 8) : 0;
-    L.best = take((size_t)npix * ME_NPAR * 8);
+    L.best = take((size_t)npix * npar * 8);
     L.chi2 = take((size_t)npix * 8);
     L.total = at;
     return L;
@@ -124,7 +124,8 @@ int launch_request(serve_handle *h, Request *r)
     cudaError_t e = cudaMemcpyAsync(db, hb, L.best, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_error(e, "serve H2D");
     KGa g;
-    int rc = make_ga(&q.ga, &q.bounds, q.pixel_id0, g);
+    const int npar = npar_of(&h->pb);
+    int rc = make_ga(&q.ga, &q.bounds, q.pixel_id0, g, npar);
     if (rc) return rc;
     const double *dw = r->w.empty() ? nullptr : (const double *)(db + L.w);
     const double *dmu = r->mu.empty() ? nullptr : (const double *)(db + L.mu);
@@ -139,8 +140,8 @@ int launch_request(serve_handle *h, Request *r)
         std::memset(&lm, 0, sizeof lm);
         lm.iters = q.polish_iters;
         lm.lambda0 = q.lambda0;
-        lm.free_mask = (1u << ME_NPAR) - 1u;
-        for (int d = 0; d < ME_NPAR; ++d) {
+        lm.free_mask = (1u << npar) - 1u;
+        for (int d = 0; d < npar; ++d) {
             lm.lo[d] = q.bounds.lo[d];
             lm.hi[d] = q.bounds.hi[d];
         }
@@ -167,7 +168,7 @@ void finish(serve_handle *h, Request *r, int status)
         if (status == ME_OK) {
             const unsigned char *hb = h->h_arena + r->off;
             r->best.assign((const double *)(hb + r->lay.best),
-                           (const double *)(hb + r->lay.best) + (size_t)r->rq.npix * ME_NPAR);
+                           (const double *)(hb + r->lay.best) + (size_t)r->rq.npix * npar_of(&h->pb));
             r->chi2.assign((const double *)(hb + r->lay.chi2),
                            (const double *)(hb + r->lay.chi2) + r->rq.npix);
         }
@@ -310,15 +311,16 @@ int serve_submit(serve_handle *h, const serve_request *rq, uint64_t *ticket)
     if (!h || !rq || !ticket) return set_error(ME_EINVAL, "NULL argument");
     if (rq->npix < 1) return set_error(ME_EINVAL, "npix must be >= 1");
     if (!rq->obs) return set_error(ME_EINVAL, "obs is NULL");
-    int rc = check_bounds(&rq->bounds);
+    const int npar = npar_of(&h->pb);
+    int rc = check_bounds(&rq->bounds, npar);
     if (rc) return rc;
     KGa g;
-    if ((rc = make_ga(&rq->ga, &rq->bounds, rq->pixel_id0, g))) return rc;
+    if ((rc = make_ga(&rq->ga, &rq->bounds, rq->pixel_id0, g, npar))) return rc;
     if (rq->ga.weight_mode == ME_W_USER && !rq->w) return set_error(ME_EINVAL, "ME_W_USER needs w");
     if (rq->polish_iters < 0) return set_error(ME_EINVAL, "polish_iters must be >= 0");
     if (rq->polish_iters > 0 && !(rq->lambda0 > 0.0)) return set_error(ME_EINVAL, "lambda0 must be > 0");
     if (rq->pixel_id0 + (uint64_t)rq->npix < rq->pixel_id0) return set_error(ME_EINVAL, "pixel id overflow");
-    const Layout lay = layout_for(rq->npix, h->pb.n_lambda, h->elem, rq->w != nullptr,
+    const Layout lay = layout_for(rq->npix, h->pb.n_lambda, npar, h->elem, rq->w != nullptr,
                                   rq->mu_px != nullptr, rq->polish_w != nullptr);
     if (lay.total > h->arena.size()) return set_error(ME_EINVAL, "request larger than the serving arena");
     Request *r = new (std::nothrow) Request();

@@ -29,7 +29,7 @@ __device__ __forceinline__ void stage_offsets(const KProblem &pb, int nlines, R 
 }
 
 // One thread per (model, wavelength).
-template <class R, int NL>
+template <class R, int NL, bool FILL = false>
 __global__ void __launch_bounds__(kSynthBlock)
 k_synth(const __grid_constant__ KProblem pb, const double *__restrict__ params,
         const double *__restrict__ mu_px, int n, R *__restrict__ stokes)
@@ -43,18 +43,19 @@ k_synth(const __grid_constant__ KProblem pb, const double *__restrict__ params,
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)n * nl) return;
     const int m = (int)(i / nl), j = (int)(i - (long long)m * nl);
-    R p[ME_NPAR];
+    constexpr int M = kNpar<FILL>;
+    R p[M];
 #pragma unroll
-    for (int d = 0; d < ME_NPAR; ++d) p[d] = R(params[(size_t)m * ME_NPAR + d]);
+    for (int d = 0; d < M; ++d) p[d] = R(params[(size_t)m * M + d]);
     const R mu = mu_px ? R(mu_px[m]) : R(pb.mu);
-    const Geo<R> g = make_geo<R, NL>(pb, nlines, p, mu);
+    const Geo<R> g = make_geo<R, NL, FILL>(pb, nlines, p, mu);
     R doff[ME_MAX_LINES], he[ME_MAX_LINES];
 #pragma unroll
     for (int l = 0; l < ME_MAX_LINES; ++l) {
         doff[l] = l < nlines ? s_doff[l * nl + j] : R(0);
         he[l] = s_he[l];
     }
-    const Stokes4<R> s = me_point<R, NL>(g, doff, he, nlines, pb.line);
+    const Stokes4<R> s = me_point<R, NL, true, FILL>(g, doff, he, nlines, pb.line);
     R *o = stokes + (size_t)m * 4 * nl;
     o[j] = s.I;
     o[nl + j] = s.Q;
@@ -62,7 +63,7 @@ k_synth(const __grid_constant__ KProblem pb, const double *__restrict__ params,
     o[3 * nl + j] = s.V;
 }
 
-template <class R, int NL>
+template <class R, int NL, bool FILL = false>
 __global__ void __launch_bounds__(kSynthBlock)
 k_jac(const __grid_constant__ KProblem pb, const double *__restrict__ params,
       const double *__restrict__ mu_px, int n, R *__restrict__ stokes, R *__restrict__ jac)
@@ -76,11 +77,12 @@ k_jac(const __grid_constant__ KProblem pb, const double *__restrict__ params,
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)n * nl) return;
     const int m = (int)(i / nl), j = (int)(i - (long long)m * nl);
-    R p[ME_NPAR];
+    constexpr int M = kNpar<FILL>;
+    R p[M];
 #pragma unroll
-    for (int d = 0; d < ME_NPAR; ++d) p[d] = R(params[(size_t)m * ME_NPAR + d]);
+    for (int d = 0; d < M; ++d) p[d] = R(params[(size_t)m * M + d]);
     const R mu = mu_px ? R(mu_px[m]) : R(pb.mu);
-    const GeoJ<R> G = make_geoj<R, NL>(pb, nlines, p, mu);
+    const GeoJ<R> G = make_geoj<R, NL, FILL>(pb, nlines, p, mu);
     R doff[ME_MAX_LINES], he[ME_MAX_LINES];
 #pragma unroll
     for (int l = 0; l < ME_MAX_LINES; ++l) {
@@ -88,8 +90,8 @@ k_jac(const __grid_constant__ KProblem pb, const double *__restrict__ params,
         he[l] = s_he[l];
     }
     Stokes4<R> s;
-    R J[4][ME_NPAR];
-    me_point_jac<R, NL>(G, doff, he, nlines, pb.line, s, J);
+    R J[4][M];
+    me_point_jac<R, NL, FILL>(G, doff, he, nlines, pb.line, s, J);
     if (stokes) {
         R *o = stokes + (size_t)m * 4 * nl;
         o[j] = s.I;
@@ -99,14 +101,14 @@ k_jac(const __grid_constant__ KProblem pb, const double *__restrict__ params,
     }
 #pragma unroll
     for (int st = 0; st < 4; ++st) {
-        R *o = jac + (((size_t)m * 4 + st) * nl + j) * ME_NPAR;
+        R *o = jac + (((size_t)m * 4 + st) * nl + j) * M;
 #pragma unroll
-        for (int k = 0; k < ME_NPAR; ++k) o[k] = J[st][k];
+        for (int k = 0; k < M; ++k) o[k] = J[st][k];
     }
 }
 
 // One warp per model: grad_params[m] = sum_{s, j} J[s][j][:] * grad_stokes[m][s][j].
-template <class R, int NL>
+template <class R, int NL, bool FILL = false>
 __global__ void __launch_bounds__(kSynthBlock)
 k_vjp(const __grid_constant__ KProblem pb, const double *__restrict__ params,
       const double *__restrict__ mu_px, int n, const R *__restrict__ gs, double *__restrict__ gp)
@@ -120,45 +122,46 @@ k_vjp(const __grid_constant__ KProblem pb, const double *__restrict__ params,
     const int lane = threadIdx.x & 31;
     const int m = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (m >= n) return;
-    R p[ME_NPAR];
+    constexpr int M = kNpar<FILL>;
+    R p[M];
 #pragma unroll
-    for (int d = 0; d < ME_NPAR; ++d) p[d] = R(params[(size_t)m * ME_NPAR + d]);
+    for (int d = 0; d < M; ++d) p[d] = R(params[(size_t)m * M + d]);
     const R mu = mu_px ? R(mu_px[m]) : R(pb.mu);
-    const GeoJ<R> G = make_geoj<R, NL>(pb, nlines, p, mu);
+    const GeoJ<R> G = make_geoj<R, NL, FILL>(pb, nlines, p, mu);
     R he[ME_MAX_LINES];
 #pragma unroll
     for (int l = 0; l < ME_MAX_LINES; ++l) he[l] = s_he[l];
-    R acc[ME_NPAR];
+    R acc[M];
 #pragma unroll
-    for (int k = 0; k < ME_NPAR; ++k) acc[k] = R(0);
+    for (int k = 0; k < M; ++k) acc[k] = R(0);
     const R *g = gs + (size_t)m * 4 * nl;
     for (int j = lane; j < nl; j += 32) {
         R doff[ME_MAX_LINES];
 #pragma unroll
         for (int l = 0; l < ME_MAX_LINES; ++l) doff[l] = l < nlines ? s_doff[l * nl + j] : R(0);
         Stokes4<R> s;
-        R J[4][ME_NPAR];
-        me_point_jac<R, NL>(G, doff, he, nlines, pb.line, s, J);
+        R J[4][M];
+        me_point_jac<R, NL, FILL>(G, doff, he, nlines, pb.line, s, J);
 #pragma unroll
         for (int st = 0; st < 4; ++st) {
             const R gv = g[st * nl + j];
 #pragma unroll
-            for (int k = 0; k < ME_NPAR; ++k) acc[k] += J[st][k] * gv;
+            for (int k = 0; k < M; ++k) acc[k] += J[st][k] * gv;
         }
     }
 #pragma unroll
-    for (int k = 0; k < ME_NPAR; ++k) {
+    for (int k = 0; k < M; ++k) {
         double v = (double)acc[k];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (lane == 0) gp[(size_t)m * ME_NPAR + k] = v;
+        if (lane == 0) gp[(size_t)m * M + k] = v;
     }
 }
 
 // FP64 chi-square (Eq. chisq) of given parameters, one block per pixel,
 // threads over wavelengths.  Inverse-max weights (Section 4.5) are formed in
 // FP64 from the observed values when w is NULL.
-template <class RO>
+template <class RO, bool FILL = false>
 __global__ void __launch_bounds__(kSynthBlock)
 k_chi2_f64(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
            const double *__restrict__ w_user, const double *__restrict__ mu_px, int npix,
@@ -205,11 +208,12 @@ k_chi2_f64(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
             }
         }
     }
-    double p[ME_NPAR];
+    constexpr int M = kNpar<FILL>;
+    double p[M];
 #pragma unroll
-    for (int d = 0; d < ME_NPAR; ++d) p[d] = params[(size_t)pix * ME_NPAR + d];
+    for (int d = 0; d < M; ++d) p[d] = params[(size_t)pix * M + d];
     const double mu = mu_px ? mu_px[pix] : pb.mu;
-    const Geo<double> g = make_geo<double, 0>(pb, nlines, p, mu);
+    const Geo<double> g = make_geo<double, 0, FILL>(pb, nlines, p, mu);
     double he[ME_MAX_LINES];
 #pragma unroll
     for (int l = 0; l < ME_MAX_LINES; ++l) he[l] = l < nlines ? pb.line[l].half_eta : 0.0;
@@ -218,7 +222,7 @@ k_chi2_f64(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
         double doff[ME_MAX_LINES];
 #pragma unroll
         for (int l = 0; l < ME_MAX_LINES; ++l) doff[l] = l < nlines ? pb.lam[j] - pb.line[l].lam0 : 0.0;
-        const Stokes4<double> s = me_point<double, 0>(g, doff, he, nlines, pb.line);
+        const Stokes4<double> s = me_point<double, 0, true, FILL>(g, doff, he, nlines, pb.line);
         const double r0 = (double)o[j] - s.I, r1 = (double)o[nl + j] - s.Q;
         const double r2 = (double)o[2 * nl + j] - s.U, r3 = (double)o[3 * nl + j] - s.V;
         ss[0] += r0 * r0;
@@ -241,7 +245,7 @@ k_chi2_f64(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += s_red[w][s];
             tot += s_w2[s] * a;
         }
-        chi2[pix] = tot / (double)(4 * nl - ME_NPAR);
+        chi2[pix] = tot / (double)(4 * nl - M);
     }
 }
 
@@ -301,33 +305,33 @@ template <class R> size_t offsets_smem(const KProblem &pb)
     return sizeof(R) * (ME_MAX_LINES + (size_t)pb.n_lines * pb.n_lambda);
 }
 
-template <class R, int NL>
+template <class R, int NL, bool FILL = false>
 cudaError_t synth_t(const KProblem &pb, const double *params, const double *mu_px, int n,
                     void *stokes, cudaStream_t st)
 {
     const long long tot = (long long)n * pb.n_lambda;
     const int blocks = (int)((tot + kSynthBlock - 1) / kSynthBlock);
-    k_synth<R, NL><<<blocks, kSynthBlock, offsets_smem<R>(pb), st>>>(pb, params, mu_px, n, (R *)stokes);
+    k_synth<R, NL, FILL><<<blocks, kSynthBlock, offsets_smem<R>(pb), st>>>(pb, params, mu_px, n, (R *)stokes);
     return cudaGetLastError();
 }
 
-template <class R, int NL>
+template <class R, int NL, bool FILL = false>
 cudaError_t jac_t(const KProblem &pb, const double *params, const double *mu_px, int n,
                   void *stokes, void *jac, cudaStream_t st)
 {
     const long long tot = (long long)n * pb.n_lambda;
     const int blocks = (int)((tot + kSynthBlock - 1) / kSynthBlock);
-    k_jac<R, NL><<<blocks, kSynthBlock, offsets_smem<R>(pb), st>>>(pb, params, mu_px, n, (R *)stokes,
+    k_jac<R, NL, FILL><<<blocks, kSynthBlock, offsets_smem<R>(pb), st>>>(pb, params, mu_px, n, (R *)stokes,
                                                                   (R *)jac);
     return cudaGetLastError();
 }
 
-template <class R, int NL>
+template <class R, int NL, bool FILL = false>
 cudaError_t vjp_t(const KProblem &pb, const double *params, const double *mu_px, int n,
                   const void *gs, double *gp, cudaStream_t st)
 {
     const int per = kSynthBlock / 32;
-    k_vjp<R, NL><<<(n + per - 1) / per, kSynthBlock, offsets_smem<R>(pb), st>>>(pb, params, mu_px, n,
+    k_vjp<R, NL, FILL><<<(n + per - 1) / per, kSynthBlock, offsets_smem<R>(pb), st>>>(pb, params, mu_px, n,
                                                                                (const R *)gs, gp);
     return cudaGetLastError();
 }
@@ -338,6 +342,9 @@ cudaError_t launch_synth(const KProblem &pb, int dtype, const double *params, co
                          int n, void *stokes, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
+    if (pb.fill)
+        return dtype == ME_F32 ? synth_t<float, 0, true>(pb, params, mu_px, n, stokes, st)
+                               : synth_t<double, 0, true>(pb, params, mu_px, n, stokes, st);
     if (dtype == ME_F32) {
         if (pb.n_lines == 1) return synth_t<float, 1>(pb, params, mu_px, n, stokes, st);
         if (pb.n_lines == 2) return synth_t<float, 2>(pb, params, mu_px, n, stokes, st);
@@ -350,6 +357,9 @@ cudaError_t launch_jac(const KProblem &pb, int dtype, const double *params, cons
                        int n, void *stokes, void *jac, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
+    if (pb.fill)
+        return dtype == ME_F32 ? jac_t<float, 0, true>(pb, params, mu_px, n, stokes, jac, st)
+                               : jac_t<double, 0, true>(pb, params, mu_px, n, stokes, jac, st);
     if (dtype == ME_F32) {
         if (pb.n_lines == 1) return jac_t<float, 1>(pb, params, mu_px, n, stokes, jac, st);
         if (pb.n_lines == 2) return jac_t<float, 2>(pb, params, mu_px, n, stokes, jac, st);
@@ -362,6 +372,9 @@ cudaError_t launch_vjp(const KProblem &pb, int dtype, const double *params, cons
                        int n, const void *gs, double *gp, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
+    if (pb.fill)
+        return dtype == ME_F32 ? vjp_t<float, 0, true>(pb, params, mu_px, n, gs, gp, st)
+                               : vjp_t<double, 0, true>(pb, params, mu_px, n, gs, gp, st);
     if (dtype == ME_F32) {
         if (pb.n_lines == 1) return vjp_t<float, 1>(pb, params, mu_px, n, gs, gp, st);
         if (pb.n_lines == 2) return vjp_t<float, 2>(pb, params, mu_px, n, gs, gp, st);
@@ -389,9 +402,15 @@ cudaError_t launch_chi2_f64(const KProblem &pb, int dtype, const void *obs, cons
                             cudaStream_t st, KSub sub)
 {
     if (npix <= 0) return cudaSuccess;
-    if (dtype == ME_F32)
+    if (dtype == ME_F32 && pb.fill)
+        k_chi2_f64<float, true><<<npix, kSynthBlock, 0, st>>>(pb, (const float *)obs, w, mu_px, npix, params,
+                                                              chi2, sub);
+    else if (dtype == ME_F32)
         k_chi2_f64<float><<<npix, kSynthBlock, 0, st>>>(pb, (const float *)obs, w, mu_px, npix, params, chi2,
                                                         sub);
+    else if (pb.fill)
+        k_chi2_f64<double, true><<<npix, kSynthBlock, 0, st>>>(pb, (const double *)obs, w, mu_px, npix, params,
+                                                               chi2, sub);
     else
         k_chi2_f64<double><<<npix, kSynthBlock, 0, st>>>(pb, (const double *)obs, w, mu_px, npix, params,
                                                          chi2, sub);
