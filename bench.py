@@ -40,7 +40,7 @@ KERNELS_PER_STEP = 4  # GA evolve, FP64 chi2, L-M, FP64 chi2
 # dram__bytes_write.sum 1536, divided by 1024; traffic grows in proportion to
 # pixels: each block reads its pixel's cube row once).  Set to None whenever
 # the kernel changes, until it is captured again.
-GA_DRAM_BYTES_PER_PIXEL = (2213888 + 1536) / 1024
+GA_DRAM_BYTES_PER_PIXEL = None  # kernel changed since the last capture
 
 
 def parse():
@@ -131,13 +131,17 @@ def make_map(api, torch, pb, side, rank, device):
 
 def flop_model(nlines):
     """Algorithmic FP32 flops (FMA = 2, reciprocal = 1) of one synthesis + chi2,
-    counted from the source of faddeeva_interior/faddeeva_exterior and
-    me_point, per unit: interior (Weideman N = 16 by real-quadratic synthetic
-    division) evaluation, exterior (3rd continued-fraction convergent)
-    evaluation, and per wavelength point (26 per line for the component
-    arguments and profile sums, 49 for K and its closed-form inverse, 24 for
-    the Kahan chi2 of four residuals).  Branch tests are not counted."""
-    return {"weideman": 94.0, "cf": 32.0, "point": 26.0 * nlines + 73.0}
+    counted from the source of the GA's fitness path, per unit: an evaluation
+    of w(z) in the interior region (Weideman N = 16 by real-quadratic
+    synthetic division, 94), in the continued-fraction region (3rd convergent,
+    32) and in the far field (two-node approximant, 17); and per wavelength
+    point 26 per line for the component arguments and profile sums, 49 for K
+    and its closed-form inverse, 12.25 for the chi2 of four residuals (a
+    subtraction and an FMA each, plus a block addition per 16 points and
+    Stokes parameter).  Each point's evaluations are classified by its own region;
+    branch tests, votes and work a pair or warp does beyond that are not
+    counted."""
+    return {"weideman": 94.0, "cf": 32.0, "far": 17.0, "point": 26.0 * nlines + 61.25}
 
 
 def run_ours(args):
@@ -236,7 +240,8 @@ def run_ours(args):
         # algorithmic flops of one GA launch from exact branch counts
         counts = api.ga_count_evaluations(pb32, obs, lo, hi, ga, pixel_id0=pid0)
         fm = flop_model(len(spec.lines))
-        flops = counts["weideman"] * fm["weideman"] + counts["cf"] * fm["cf"] + counts["points"] * fm["point"]
+        flops = (counts["weideman"] * fm["weideman"] + counts["cf"] * fm["cf"] + counts["far"] * fm["far"] +
+                 counts["points"] * fm["point"])
         props = torch.cuda.get_device_properties(dev)
         sms = props.multi_processor_count
         max_mhz = clk.get("sm_max_mhz") or 2070.0

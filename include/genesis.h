@@ -225,9 +225,11 @@ int ga_invert_batch(const me_problem *pb, const void *obs, const double *w,
 /*
  * ga_count_evaluations - the same GA as ga_invert_batch (float cubes,
  * npop <= 256) run by a separate instantiation that also counts work:
- * counts dev uint64[3] receives (added to its contents) the number of
- * syntheses (fitness evaluations), of Faddeeva evaluations that took the
- * interior branch and of all Faddeeva evaluations.
+ * counts dev uint64[4] receives (added to its contents) the number of
+ * syntheses (fitness evaluations), of Faddeeva evaluations in the interior
+ * region (|z|^2 <= 36), of all Faddeeva evaluations and of those in the far
+ * field (|z|^2 > 484), each real wavelength point classified by its own
+ * region (the algorithm's work, whatever branch a point's pair or warp took).
  * The arithmetic and the result `best` are those of ga_invert_batch; the
  * counts turn into algorithmic flops for roofline reporting.
  */

@@ -107,27 +107,24 @@ __device__ __forceinline__ R fitness_rows(const KProblem &pb, int nlines, int nl
     return (s_w2[0] * sI + s_w2[1] * sQ + s_w2[2] * sU + s_w2[3] * sV) * inv_nu;
 }
 
-__device__ __forceinline__ void kahan_sq2(float2 &s, float2 &c, float2 r)
-{
-    const float2 y = fma2(r, r, neg2(c));
-    const float2 t = add2(s, y);
-    c = sub2(sub2(t, s), y);
-    s = t;
-}
 
 // Eq. chisq for one individual with the FP32 pair path (two wavelengths per
-// step, packed FP32x2 arithmetic).
+// step, packed FP32x2 arithmetic).  The squared residuals are summed in two
+// levels: FMA partial sums over blocks of 8 pairs, added into a running total
+// per block (relative error about (8 + n/16) u, u = 2^-24, instead of the n u
+// of a single running sum; the best individual's chi2 is re-evaluated in
+// FP64 afterwards).
 template <int NL, bool COUNT, bool PAT, bool FILL>
 __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, int nl, const float *p,
                                                float mu, const float *s_obs, const float *s_doff,
                                                const float *he, const float *s_w2, float inv_nu,
-                                               unsigned long long &ninterior)
+                                               unsigned long long &ninterior, unsigned long long &nfar)
 {
     const Geo<float> geo = make_geo<float, NL, FILL>(pb, nlines, p, mu);
     float2 sI = f2(0.f), sQ = f2(0.f), sU = f2(0.f), sV = f2(0.f);
-    float2 cI = f2(0.f), cQ = f2(0.f), cU = f2(0.f), cV = f2(0.f);
+    float2 bI = f2(0.f), bQ = f2(0.f), bU = f2(0.f), bV = f2(0.f);
     const int npair = (nl + 1) >> 1;
-    unsigned cnt = 0;
+    EvalCount cnt{0u, 0u};
     for (int q = 0; q < npair; ++q) {
         const float4 o0 = *(const float4 *)(s_obs + 8 * q), o1 = *(const float4 *)(s_obs + 8 * q + 4);
         const float4 d0 = *(const float4 *)(s_doff + 8 * q);
@@ -139,16 +136,27 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
             doff2[2] = make_float2(d1.x, d1.y);
             doff2[3] = make_float2(d1.z, d1.w);
         }
-        const Stokes4x2 m = me_point_x2<NL, COUNT, PAT, FILL>(geo, doff2, he, nlines, cnt, pb.line);
+        const bool y_real = 2 * q + 1 < nl;
+        const Stokes4x2 m = me_point_x2<NL, COUNT, PAT, FILL>(geo, doff2, he, nlines, y_real, cnt, pb.line);
         float2 rI = sub2(make_float2(o0.x, o0.y), m.I), rQ = sub2(make_float2(o0.z, o0.w), m.Q);
         float2 rU = sub2(make_float2(o1.x, o1.y), m.U), rV = sub2(make_float2(o1.z, o1.w), m.V);
-        if (2 * q + 1 >= nl) rI.y = rQ.y = rU.y = rV.y = 0.f;  // padded partner
-        kahan_sq2(sI, cI, rI);
-        kahan_sq2(sQ, cQ, rQ);
-        kahan_sq2(sU, cU, rU);
-        kahan_sq2(sV, cV, rV);
+        if (!y_real) rI.y = rQ.y = rU.y = rV.y = 0.f;  // padded partner
+        bI = fma2(rI, rI, bI);
+        bQ = fma2(rQ, rQ, bQ);
+        bU = fma2(rU, rU, bU);
+        bV = fma2(rV, rV, bV);
+        if ((q & 7) == 7 || q == npair - 1) {
+            sI = add2(sI, bI);
+            sQ = add2(sQ, bQ);
+            sU = add2(sU, bU);
+            sV = add2(sV, bV);
+            bI = bQ = bU = bV = f2(0.f);
+        }
     }
-    if (COUNT) ninterior += cnt;
+    if (COUNT) {
+        ninterior += cnt.interior;
+        nfar += cnt.far;
+    }
     return (s_w2[0] * (sI.x + sI.y) + s_w2[1] * (sQ.x + sQ.y) + s_w2[2] * (sU.x + sU.y) +
             s_w2[3] * (sV.x + sV.y)) * inv_nu;
 }
@@ -156,11 +164,12 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
 template <class R, int NL, bool COUNT, bool PAT, bool FILL>
 __device__ __forceinline__ R fitness(const KProblem &pb, int nlines, int nl, const R *p, R mu,
                                      const R *s_obs, const R *s_doff, const R *he,
-                                     const R *s_w2, R inv_nu, unsigned long long &ninterior)
+                                     const R *s_w2, R inv_nu, unsigned long long &ninterior,
+                                     unsigned long long &nfar)
 {
     if constexpr (std::is_same<R, float>::value)
         return fitness_pairs<NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu,
-                                                   ninterior);
+                                                   ninterior, nfar);
     else
         return fitness_rows<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu,
                                                      ninterior);
@@ -347,7 +356,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
             const KSeed sd, const KSub sub)
 {
     constexpr bool FILL = M > ME_NPAR;  // parameter 9: the fill fraction (Section 4.2)
-    unsigned long long nfit = 0, ninterior = 0;
+    unsigned long long nfit = 0, ninterior = 0, nfar = 0;
     extern __shared__ __align__(16) unsigned char smem[];
     const int nl = pb.n_lambda;
     const int nlines = NL > 0 ? NL : pb.n_lines;
@@ -448,7 +457,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
         int cur = 0;
 #pragma unroll
         for (int d = 0; d < M; ++d) s_genes[k * M + d] = g[d];
-        s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior));
+        s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior, nfar));
         if (COUNT) ++nfit;
         uint64_t sobol_next = (uint64_t)npop + 1;
 
@@ -465,7 +474,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
                 p[d] = GaDecode<R>::get(D, d, g[d]);
             }
             cur ^= 1;
-            s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior));
+            s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior, nfar));
             if (COUNT) ++nfit;
             // a13: worst-half Sobol restart
             if (ga.nsamp > 0 && t % ga.nsamp == 0 && t < ga.ngen) {
@@ -482,7 +491,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
                         p[d] = GaDecode<R>::get(D, d, g[d]);
                     }
                     s_fit[k] = clean_fit(
-                        fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior));
+                        fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior, nfar));
                     if (COUNT) ++nfit;
                 }
                 sobol_next += (uint64_t)(npop / 2);
@@ -500,8 +509,8 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
         __syncthreads();  // shared memory is reused by the next pixel
     }
     if (COUNT) {
-        // evaluations per synthesis: every (padded) wavelength point runs each
-        // line's components
+        // evaluations per synthesis: every real wavelength point runs each
+        // line's components (three for an effective triplet)
         unsigned long long per_point = 0;
         for (int l = 0; l < nlines; ++l) {
             const int nc = pb.line[l].ncomp[0] + pb.line[l].ncomp[1] + pb.line[l].ncomp[2];
@@ -509,7 +518,8 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
         }
         atomicAdd(counts + 0, nfit);
         atomicAdd(counts + 1, ninterior);
-        atomicAdd(counts + 2, nfit * (unsigned long long)padded_lambda<R>(nl) * per_point);
+        atomicAdd(counts + 2, nfit * (unsigned long long)nl * per_point);
+        atomicAdd(counts + 3, nfar);
     }
 }
 

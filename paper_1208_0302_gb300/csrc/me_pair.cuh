@@ -4,10 +4,14 @@
 // instruction does the work of two scalar ones, which halves the issue slots
 // of the GA's fitness loop (an issue-bound loop of FP32 arithmetic).
 //
-// Branches are taken per pair: a Zeeman component uses the continued fraction
-// when both points are exterior and Weideman's series otherwise (the series is
-// accurate everywhere, |error| <= 5e-8 for |x| <= 150), so a point's value can
-// depend on its partner's region, always within the FP32 error budget.
+// Branches are uniform across the warp: a Zeeman component takes the far-field
+// approximant when every lane's pair of points is beyond |z|^2 = 484, the
+// continued fraction when every pair is beyond |z|^2 = 36, and Weideman's
+// series otherwise (each branch is accurate wherever it is taken: the series
+// everywhere, |error| <= 5e-8 for |x| <= 150), so a point's value can depend
+// on its partner's and its warp's regions, always within the FP32 error budget.
+// A warp-uniform choice costs one branch where a per-lane choice would run
+// both for a mixed warp.
 #pragma once
 
 #include "me_device.cuh"
@@ -57,6 +61,20 @@ __device__ __forceinline__ void fad_ext2(float2 x, float y, float a2, float2 &wx
     wy = mul2(fma2(nx, ax, mul2(ny, ay)), inv);
 }
 
+// Far field (|z|^2 > kFarR2): the first non-trivial convergent of the Laplace
+// continued fraction (the two-node Gauss-Hermite rule), w = (i/sqrt(pi)) z /
+// (z^2 - 1/2); |error| <= 6e-8 in FP32 there.
+constexpr float kFarR2 = 484.0f;
+__device__ __forceinline__ void fad_far2(float2 x, float y, float a2, float2 &wx, float2 &wy)
+{
+    const float2 ux = fma2(x, x, f2(-a2));
+    const float2 uy = mul2(x, f2(2.0f * y));
+    const float2 dx = add2(ux, f2(-0.5f));
+    const float2 inv = mul2(rcp2(fma2(dx, dx, mul2(uy, uy))), f2(0.56418958354775628695f));
+    wx = mul2(fma2(x, uy, neg2(mul2(f2(y), dx))), inv);
+    wy = mul2(fma2(x, dx, mul2(f2(y), uy)), inv);
+}
+
 // Interior branch (Weideman N = 16, real-quadratic synthetic division) for a
 // pair of real arguments x and common damping y.
 __device__ __forceinline__ void fad_int2(float2 x, float y, float2 &wx, float2 &wy)
@@ -96,25 +114,45 @@ __device__ __forceinline__ bool ext3(float v, float vB, float a2)
 }
 
 __device__ __forceinline__ bool ext1(float x, float a2) { return x * x + a2 > FadCfg<float>::R2; }
+__device__ __forceinline__ bool far1(float x, float a2) { return x * x + a2 > kFarR2; }
+// A predicate that holds for every currently active lane.  The vote only
+// chooses among branches that are each accurate for every lane they are taken
+// by (a lane takes a cheaper branch only if its own points qualify), so it is
+// correct for any set of voting lanes; voting over the active mask also keeps
+// it safe where the caller runs divergent (the GA's restarts evaluate only
+// part of a warp).
+__device__ __forceinline__ bool warp_all(bool p) { return __all_sync(__activemask(), p); }
 
-// One component for the pair: continued fraction if both exterior.
+// One component for the pair, the branch chosen uniformly across the warp.
 __device__ __forceinline__ void fad_pair(float2 x, float y, float a2, float2 &wx, float2 &wy)
 {
-    if (ext1(x.x, a2) && ext1(x.y, a2)) fad_ext2(x, y, a2, wx, wy);
+    if (warp_all(far1(x.x, a2) && far1(x.y, a2))) fad_far2(x, y, a2, wx, wy);
+    else if (warp_all(ext1(x.x, a2) && ext1(x.y, a2))) fad_ext2(x, y, a2, wx, wy);
     else fad_int2(x, y, wx, wy);
 }
-
-// Number of interior (Weideman) evaluations the pair path performs for one
-// line at a pair of points: 0 on the all-exterior fast path, else 2 per
-// component that needs the interior branch at either point.
-__device__ __forceinline__ unsigned count_interior_pair(float2 xb, float2 v, float2 xr, float vB, float a2)
+// The same when every lane's component is already known to be exterior.
+__device__ __forceinline__ void fad_pair_ext(float2 x, float y, float a2, float2 &wx, float2 &wy)
 {
-    if (ext3(v.x, vB, a2) && ext3(v.y, vB, a2)) return 0u;
-    unsigned c = 0;
-    c += (ext1(xb.x, a2) && ext1(xb.y, a2)) ? 0u : 2u;
-    c += (ext1(v.x, a2) && ext1(v.y, a2)) ? 0u : 2u;
-    c += (ext1(xr.x, a2) && ext1(xr.y, a2)) ? 0u : 2u;
-    return c;
+    if (warp_all(far1(x.x, a2) && far1(x.y, a2))) fad_far2(x, y, a2, wx, wy);
+    else fad_ext2(x, y, a2, wx, wy);
+}
+
+// Work counts of the algorithm proper: each real point's evaluation classified
+// by its own region (interior, continued fraction, far field), whatever branch
+// its pair and warp took.
+struct EvalCount {
+    unsigned interior, far;
+};
+__device__ __forceinline__ void count_point(float x, float a2, EvalCount &n)
+{
+    const float r = x * x + a2;
+    n.interior += r > FadCfg<float>::R2 ? 0u : 1u;
+    n.far += r > kFarR2 ? 1u : 0u;
+}
+__device__ __forceinline__ void count_pair(float2 x, float a2, bool y_real, EvalCount &n)
+{
+    count_point(x.x, a2, n);
+    if (y_real) count_point(x.y, a2, n);
 }
 
 struct Stokes4x2 {
@@ -125,7 +163,7 @@ struct Stokes4x2 {
 // of components (see pattern_profiles).
 template <bool COUNT>
 __device__ __forceinline__ void pattern_profiles_x2(const KLine &ln, float2 dinv, float cp, float vL,
-                                                    float a, float a2, float2 w[6], unsigned &ncount)
+                                                    float a, float a2, float2 w[6], bool y_real, EvalCount &ncount)
 {
 #pragma unroll
     for (int g = 0; g < 3; ++g) {
@@ -133,7 +171,7 @@ __device__ __forceinline__ void pattern_profiles_x2(const KLine &ln, float2 dinv
         const int n = ln.ncomp[g];
         for (int i = 0; i < n; ++i) {
             const float2 x = add2(dinv, f2(cp - vL * ln.cshift32[g][i]));
-            if (COUNT) ncount += (ext1(x.x, a2) && ext1(x.y, a2)) ? 0u : 2u;
+            if (COUNT) count_pair(x, a2, y_real, ncount);
             float2 wx, wy;
             fad_pair(x, a, a2, wx, wy);
             const float2 st = f2(ln.cstr32[g][i]);
@@ -150,8 +188,8 @@ __device__ __forceinline__ void pattern_profiles_x2(const KLine &ln, float2 dinv
 // profile with the fill fraction (Section 4.2, see fill_mix).
 template <int NL, bool COUNT, bool PAT, bool FILL = false>
 __device__ __forceinline__ Stokes4x2 me_point_x2(const Geo<float> &g, const float2 *doff2,
-                                                 const float *half_eta, int nlines, unsigned &ncount,
-                                                 const KLine *lines)
+                                                 const float *half_eta, int nlines, bool y_real,
+                                                 EvalCount &ncount, const KLine *lines)
 {
     float2 P = f2(0.f), Sg = f2(0.f), T = f2(0.f), Ti = f2(0.f), Dd = f2(0.f), Di = f2(0.f);
     float2 P0 = f2(0.f);
@@ -161,7 +199,7 @@ __device__ __forceinline__ Stokes4x2 me_point_x2(const Geo<float> &g, const floa
         if (PAT && l < nl && lines[l].ncomp[0] != 0) {
             float2 w[6];
             pattern_profiles_x2<COUNT>(lines[l], mul2(doff2[l], f2(g.invD[l])), g.cp[l], g.vL[l], g.a, g.a2,
-                                       w, ncount);
+                                       w, y_real, ncount);
             if (FILL) {
                 float2 ux, uy;
                 fad_pair(fma2(doff2[l], f2(g.invD[l]), f2(g.cp[l])), g.a, g.a2, ux, uy);
@@ -180,12 +218,16 @@ __device__ __forceinline__ Stokes4x2 me_point_x2(const Geo<float> &g, const floa
             const float2 v = fma2(doff2[l], id, f2(g.cp[l]));
             const float2 xb = fma2(doff2[l], id, f2(g.cp[l] + g.vB[l]));
             const float2 xr = fma2(doff2[l], id, f2(g.cp[l] - g.vB[l]));
-            if (COUNT) ncount += count_interior_pair(xb, v, xr, g.vB[l], g.a2);
+            if (COUNT) {
+                count_pair(xb, g.a2, y_real, ncount);
+                count_pair(v, g.a2, y_real, ncount);
+                count_pair(xr, g.a2, y_real, ncount);
+            }
             float2 bx, by, px, py, rx, ry;
-            if (ext3(v.x, g.vB[l], g.a2) && ext3(v.y, g.vB[l], g.a2)) {
-                fad_ext2(xb, g.a, g.a2, bx, by);
-                fad_ext2(v, g.a, g.a2, px, py);
-                fad_ext2(xr, g.a, g.a2, rx, ry);
+            if (warp_all(ext3(v.x, g.vB[l], g.a2) && ext3(v.y, g.vB[l], g.a2))) {
+                fad_pair_ext(xb, g.a, g.a2, bx, by);
+                fad_pair_ext(v, g.a, g.a2, px, py);
+                fad_pair_ext(xr, g.a, g.a2, rx, ry);
             } else {
                 fad_pair(xb, g.a, g.a2, bx, by);
                 fad_pair(v, g.a, g.a2, px, py);
