@@ -131,17 +131,19 @@ def make_map(api, torch, pb, side, rank, device):
 
 def flop_model(nlines):
     """Algorithmic FP32 flops (FMA = 2, reciprocal = 1) of one synthesis + chi2,
-    counted from the source of the GA's fitness path, per unit: an evaluation
-    of w(z) in the interior region (Weideman N = 16 by real-quadratic
-    synthetic division, 94), in the continued-fraction region (3rd convergent,
-    32) and in the far field (two-node approximant, 17); and per wavelength
+    counted from the source of the GA's fitness path (per call, without the
+    per-individual invariants such as 2a or (L + a)^2), per unit: an
+    evaluation of w(z) in the interior (Weideman N = 16 by real-quadratic
+    synthetic division, 95), in the middle shell (5th convergent, 45), in the
+    continued-fraction region (3rd convergent, 31) and in the far field
+    (two-node approximant, 17); and per wavelength
     point 26 per line for the component arguments and profile sums, 49 for K
     and its closed-form inverse, 12.25 for the chi2 of four residuals (a
     subtraction and an FMA each, plus a block addition per 16 points and
     Stokes parameter).  Each point's evaluations are classified by its own region;
     branch tests, votes and work a pair or warp does beyond that are not
     counted."""
-    return {"weideman": 94.0, "cf": 32.0, "far": 17.0, "point": 26.0 * nlines + 61.25}
+    return {"weideman": 95.0, "mid": 45.0, "cf": 31.0, "far": 17.0, "point": 26.0 * nlines + 61.25}
 
 
 def run_ours(args):
@@ -240,8 +242,8 @@ def run_ours(args):
         # algorithmic flops of one GA launch from exact branch counts
         counts = api.ga_count_evaluations(pb32, obs, lo, hi, ga, pixel_id0=pid0)
         fm = flop_model(len(spec.lines))
-        flops = (counts["weideman"] * fm["weideman"] + counts["cf"] * fm["cf"] + counts["far"] * fm["far"] +
-                 counts["points"] * fm["point"])
+        flops = (counts["weideman"] * fm["weideman"] + counts["mid"] * fm["mid"] + counts["cf"] * fm["cf"] +
+                 counts["far"] * fm["far"] + counts["points"] * fm["point"])
         props = torch.cuda.get_device_properties(dev)
         sms = props.multi_processor_count
         max_mhz = clk.get("sm_max_mhz") or 2070.0

@@ -118,13 +118,14 @@ template <int NL, bool COUNT, bool PAT, bool FILL>
 __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, int nl, const float *p,
                                                float mu, const float *s_obs, const float *s_doff,
                                                const float *he, const float *s_w2, float inv_nu,
-                                               unsigned long long &ninterior, unsigned long long &nfar)
+                                               unsigned long long &ninterior, unsigned long long &nmid,
+                                               unsigned long long &nfar)
 {
     const Geo<float> geo = make_geo<float, NL, FILL>(pb, nlines, p, mu);
     float2 sI = f2(0.f), sQ = f2(0.f), sU = f2(0.f), sV = f2(0.f);
     float2 bI = f2(0.f), bQ = f2(0.f), bU = f2(0.f), bV = f2(0.f);
     const int npair = (nl + 1) >> 1;
-    EvalCount cnt{0u, 0u};
+    EvalCount cnt{0u, 0u, 0u};
     for (int q = 0; q < npair; ++q) {
         const float4 o0 = *(const float4 *)(s_obs + 8 * q), o1 = *(const float4 *)(s_obs + 8 * q + 4);
         const float4 d0 = *(const float4 *)(s_doff + 8 * q);
@@ -155,6 +156,7 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
     }
     if (COUNT) {
         ninterior += cnt.interior;
+        nmid += cnt.mid;
         nfar += cnt.far;
     }
     return (s_w2[0] * (sI.x + sI.y) + s_w2[1] * (sQ.x + sQ.y) + s_w2[2] * (sU.x + sU.y) +
@@ -165,11 +167,11 @@ template <class R, int NL, bool COUNT, bool PAT, bool FILL>
 __device__ __forceinline__ R fitness(const KProblem &pb, int nlines, int nl, const R *p, R mu,
                                      const R *s_obs, const R *s_doff, const R *he,
                                      const R *s_w2, R inv_nu, unsigned long long &ninterior,
-                                     unsigned long long &nfar)
+                                     unsigned long long &nmid, unsigned long long &nfar)
 {
     if constexpr (std::is_same<R, float>::value)
         return fitness_pairs<NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu,
-                                                   ninterior, nfar);
+                                                   ninterior, nmid, nfar);
     else
         return fitness_rows<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu,
                                                      ninterior);
@@ -356,7 +358,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
             const KSeed sd, const KSub sub)
 {
     constexpr bool FILL = M > ME_NPAR;  // parameter 9: the fill fraction (Section 4.2)
-    unsigned long long nfit = 0, ninterior = 0, nfar = 0;
+    unsigned long long nfit = 0, ninterior = 0, nmid = 0, nfar = 0;
     extern __shared__ __align__(16) unsigned char smem[];
     const int nl = pb.n_lambda;
     const int nlines = NL > 0 ? NL : pb.n_lines;
@@ -457,7 +459,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
         int cur = 0;
 #pragma unroll
         for (int d = 0; d < M; ++d) s_genes[k * M + d] = g[d];
-        s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior, nfar));
+        s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior, nmid, nfar));
         if (COUNT) ++nfit;
         uint64_t sobol_next = (uint64_t)npop + 1;
 
@@ -474,7 +476,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
                 p[d] = GaDecode<R>::get(D, d, g[d]);
             }
             cur ^= 1;
-            s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior, nfar));
+            s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior, nmid, nfar));
             if (COUNT) ++nfit;
             // a13: worst-half Sobol restart
             if (ga.nsamp > 0 && t % ga.nsamp == 0 && t < ga.ngen) {
@@ -491,7 +493,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
                         p[d] = GaDecode<R>::get(D, d, g[d]);
                     }
                     s_fit[k] = clean_fit(
-                        fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior, nfar));
+                        fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior, nmid, nfar));
                     if (COUNT) ++nfit;
                 }
                 sobol_next += (uint64_t)(npop / 2);
@@ -520,6 +522,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
         atomicAdd(counts + 1, ninterior);
         atomicAdd(counts + 2, nfit * (unsigned long long)nl * per_point);
         atomicAdd(counts + 3, nfar);
+        atomicAdd(counts + 4, nmid);
     }
 }
 
