@@ -252,6 +252,11 @@ template <class R> struct Geo {
     R kUV, kQV;         // kU kV, kQ kV
     R S0, muS1;
     R eta0, alpha;          // line strength; fill fraction (1 without one)
+    // FP32 pair path: |x| thresholds of the far, continued-fraction and middle
+    // regions (|x| > t <=> x^2 + a^2 > R^2; -1 when a^2 >= R^2) and, per line,
+    // the all-exterior test of a triplet |v| > t_ext + |v_B|
+    R tfar, text, tmid;
+    R t3[ME_MAX_LINES];
     R shift[ME_MAX_LINES];  // lambda0 v_LOS / c [A]
     R invD[ME_MAX_LINES];   // 1 / Doppler width [1/A]
     R vB[ME_MAX_LINES];     // Zeeman splitting in Doppler units

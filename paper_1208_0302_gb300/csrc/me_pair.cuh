@@ -112,17 +112,20 @@ __device__ __forceinline__ void fad_int2(float2 x, float y, float2 &wx, float2 &
     wy = fma2(f2(2.0f), fma2(px, r2y, mul2(py, r2x)), mul2(ry, s));
 }
 
-// All three components of a line outside |z| = R at one point (the same test
-// as triplet_exterior<float>).
-__device__ __forceinline__ bool ext3(float v, float vB, float a2)
-{
-    const float m = fabsf(v) - fabsf(vB);
-    return m > 0.0f && m * m + a2 > FadCfg<float>::R2;
-}
 
-__device__ __forceinline__ bool ext1(float x, float a2) { return x * x + a2 > FadCfg<float>::R2; }
-__device__ __forceinline__ bool far1(float x, float a2) { return x * x + a2 > kFarR2; }
-__device__ __forceinline__ bool mid1(float x, float a2) { return x * x + a2 > kMidR2; }
+// |x| threshold of a region x^2 + a^2 > R2 (once per individual).
+__device__ __forceinline__ float region_threshold(float R2, float a2) { return a2 >= R2 ? -1.0f : sqrtf(R2 - a2); }
+// Fill the pair path's thresholds of a geometry (once per individual).
+__device__ __forceinline__ void pair_thresholds(Geo<float> &g, int nlines)
+{
+    g.tfar = region_threshold(kFarR2, g.a2);
+    g.text = region_threshold(FadCfg<float>::R2, g.a2);
+    g.tmid = region_threshold(kMidR2, g.a2);
+#pragma unroll
+    for (int l = 0; l < ME_MAX_LINES; ++l)
+        g.t3[l] = (l < nlines && g.text >= 0.0f) ? g.text + fabsf(g.vB[l]) : -1.0f;
+}
+__device__ __forceinline__ bool beyond(float2 x, float t) { return fabsf(x.x) > t && fabsf(x.y) > t; }
 // A predicate that holds for every currently active lane.  The vote only
 // chooses among branches that are each accurate for every lane they are taken
 // by (a lane takes a cheaper branch only if its own points qualify), so it is
@@ -132,18 +135,18 @@ __device__ __forceinline__ bool mid1(float x, float a2) { return x * x + a2 > kM
 __device__ __forceinline__ bool warp_all(bool p) { return __all_sync(__activemask(), p); }
 
 // One component for the pair, the branch chosen uniformly across the warp.
-__device__ __forceinline__ void fad_pair(float2 x, float y, float a2, float2 &wx, float2 &wy)
+__device__ __forceinline__ void fad_pair(float2 x, const Geo<float> &g, float2 &wx, float2 &wy)
 {
-    if (warp_all(far1(x.x, a2) && far1(x.y, a2))) fad_far2(x, y, a2, wx, wy);
-    else if (warp_all(ext1(x.x, a2) && ext1(x.y, a2))) fad_ext2(x, y, a2, wx, wy);
-    else if (warp_all(mid1(x.x, a2) && mid1(x.y, a2))) fad_cf2<5>(x, y, a2, wx, wy);
-    else fad_int2(x, y, wx, wy);
+    if (warp_all(beyond(x, g.tfar))) fad_far2(x, g.a, g.a2, wx, wy);
+    else if (warp_all(beyond(x, g.text))) fad_ext2(x, g.a, g.a2, wx, wy);
+    else if (warp_all(beyond(x, g.tmid))) fad_cf2<5>(x, g.a, g.a2, wx, wy);
+    else fad_int2(x, g.a, wx, wy);
 }
 // The same when every lane's component is already known to be exterior.
-__device__ __forceinline__ void fad_pair_ext(float2 x, float y, float a2, float2 &wx, float2 &wy)
+__device__ __forceinline__ void fad_pair_ext(float2 x, const Geo<float> &g, float2 &wx, float2 &wy)
 {
-    if (warp_all(far1(x.x, a2) && far1(x.y, a2))) fad_far2(x, y, a2, wx, wy);
-    else fad_ext2(x, y, a2, wx, wy);
+    if (warp_all(beyond(x, g.tfar))) fad_far2(x, g.a, g.a2, wx, wy);
+    else fad_ext2(x, g.a, g.a2, wx, wy);
 }
 
 // Work counts of the algorithm proper: each real point's evaluation classified
@@ -173,7 +176,8 @@ struct Stokes4x2 {
 // of components (see pattern_profiles).
 template <bool COUNT>
 __device__ __forceinline__ void pattern_profiles_x2(const KLine &ln, float2 dinv, float cp, float vL,
-                                                    float a, float a2, float2 w[6], bool y_real, EvalCount &ncount)
+                                                    const Geo<float> &geo, float2 w[6], bool y_real,
+                                                    EvalCount &ncount)
 {
 #pragma unroll
     for (int g = 0; g < 3; ++g) {
@@ -181,9 +185,9 @@ __device__ __forceinline__ void pattern_profiles_x2(const KLine &ln, float2 dinv
         const int n = ln.ncomp[g];
         for (int i = 0; i < n; ++i) {
             const float2 x = add2(dinv, f2(cp - vL * ln.cshift32[g][i]));
-            if (COUNT) count_pair(x, a2, y_real, ncount);
+            if (COUNT) count_pair(x, geo.a2, y_real, ncount);
             float2 wx, wy;
-            fad_pair(x, a, a2, wx, wy);
+            fad_pair(x, geo, wx, wy);
             const float2 st = f2(ln.cstr32[g][i]);
             px = fma2(st, wx, px);
             py = fma2(st, wy, py);
@@ -208,11 +212,11 @@ __device__ __forceinline__ Stokes4x2 me_point_x2(const Geo<float> &g, const floa
     for (int l = 0; l < (NL > 0 ? NL : ME_MAX_LINES); ++l) {
         if (PAT && l < nl && lines[l].ncomp[0] != 0) {
             float2 w[6];
-            pattern_profiles_x2<COUNT>(lines[l], mul2(doff2[l], f2(g.invD[l])), g.cp[l], g.vL[l], g.a, g.a2,
-                                       w, y_real, ncount);
+            pattern_profiles_x2<COUNT>(lines[l], mul2(doff2[l], f2(g.invD[l])), g.cp[l], g.vL[l], g, w, y_real,
+                                       ncount);
             if (FILL) {
                 float2 ux, uy;
-                fad_pair(fma2(doff2[l], f2(g.invD[l]), f2(g.cp[l])), g.a, g.a2, ux, uy);
+                fad_pair(fma2(doff2[l], f2(g.invD[l]), f2(g.cp[l])), g, ux, uy);
                 P0 = fma2(f2(half_eta[l]), ux, P0);
             }
             const float2 q = f2(half_eta[l]);
@@ -234,14 +238,14 @@ __device__ __forceinline__ Stokes4x2 me_point_x2(const Geo<float> &g, const floa
                 count_pair(xr, g.a2, y_real, ncount);
             }
             float2 bx, by, px, py, rx, ry;
-            if (warp_all(ext3(v.x, g.vB[l], g.a2) && ext3(v.y, g.vB[l], g.a2))) {
-                fad_pair_ext(xb, g.a, g.a2, bx, by);
-                fad_pair_ext(v, g.a, g.a2, px, py);
-                fad_pair_ext(xr, g.a, g.a2, rx, ry);
+            if (warp_all(beyond(v, g.t3[l]))) {
+                fad_pair_ext(xb, g, bx, by);
+                fad_pair_ext(v, g, px, py);
+                fad_pair_ext(xr, g, rx, ry);
             } else {
-                fad_pair(xb, g.a, g.a2, bx, by);
-                fad_pair(v, g.a, g.a2, px, py);
-                fad_pair(xr, g.a, g.a2, rx, ry);
+                fad_pair(xb, g, bx, by);
+                fad_pair(v, g, px, py);
+                fad_pair(xr, g, rx, ry);
             }
             const float2 q = f2(half_eta[l]);
             const float2 sx = add2(bx, rx), sy = add2(by, ry);
