@@ -137,13 +137,13 @@ def flop_model(nlines):
     synthetic division, 95), in the middle shell (5th convergent, 45), in the
     continued-fraction region (3rd convergent, 31) and in the far field
     (two-node approximant, 17); and per wavelength
-    point 26 per line for the component arguments and profile sums, 49 for K
+    point 22 per line for the component arguments and profile sums, 52 for K
     and its closed-form inverse, 12.25 for the chi2 of four residuals (a
     subtraction and an FMA each, plus a block addition per 16 points and
     Stokes parameter).  Each point's evaluations are classified by its own region;
     branch tests, votes and work a pair or warp does beyond that are not
     counted."""
-    return {"weideman": 95.0, "mid": 45.0, "cf": 31.0, "far": 17.0, "point": 26.0 * nlines + 61.25}
+    return {"weideman": 95.0, "mid": 45.0, "cf": 31.0, "far": 17.0, "point": 22.0 * nlines + 64.25}
 
 
 def run_ours(args):

@@ -205,7 +205,10 @@ __device__ __forceinline__ Stokes4x2 me_point_x2(const Geo<float> &g, const floa
                                                  const float *half_eta, int nlines, bool y_real,
                                                  EvalCount &ncount, const KLine *lines)
 {
-    float2 P = f2(0.f), Sg = f2(0.f), T = f2(0.f), Ti = f2(0.f), Dd = f2(0.f), Di = f2(0.f);
+    // per-line profile sums: P, Pi = sum q phi_p, q psi_p; Sg, Sgi = sum q (phi_b
+    // + phi_r), q (psi_b + psi_r); Dd, Di = sum q (phi_r - phi_b), q (psi_r - psi_b);
+    // T = P - Sg/2 and Ti = Pi - Sgi/2 follow once per point
+    float2 P = f2(0.f), Sg = f2(0.f), Pim = f2(0.f), Sgi = f2(0.f), Dd = f2(0.f), Di = f2(0.f);
     float2 P0 = f2(0.f);
     const int nl = NL > 0 ? NL : nlines;
 #pragma unroll
@@ -220,11 +223,10 @@ __device__ __forceinline__ Stokes4x2 me_point_x2(const Geo<float> &g, const floa
                 P0 = fma2(f2(half_eta[l]), ux, P0);
             }
             const float2 q = f2(half_eta[l]);
-            const float2 sx = add2(w[0], w[4]), sy = add2(w[1], w[5]);
             P = fma2(q, w[2], P);
-            Sg = fma2(q, sx, Sg);
-            T = fma2(q, fma2(f2(-0.5f), sx, w[2]), T);
-            Ti = fma2(q, fma2(f2(-0.5f), sy, w[3]), Ti);
+            Pim = fma2(q, w[3], Pim);
+            Sg = fma2(q, add2(w[0], w[4]), Sg);
+            Sgi = fma2(q, add2(w[1], w[5]), Sgi);
             Dd = fma2(q, sub2(w[4], w[0]), Dd);
             Di = fma2(q, sub2(w[5], w[1]), Di);
         } else if (l < nl) {
@@ -248,17 +250,18 @@ __device__ __forceinline__ Stokes4x2 me_point_x2(const Geo<float> &g, const floa
                 fad_pair(xr, g, rx, ry);
             }
             const float2 q = f2(half_eta[l]);
-            const float2 sx = add2(bx, rx), sy = add2(by, ry);
             if (FILL) P0 = fma2(q, px, P0);  // the pi profile is unshifted
             P = fma2(q, px, P);
-            Sg = fma2(q, sx, Sg);
-            T = fma2(q, fma2(f2(-0.5f), sx, px), T);
-            Ti = fma2(q, fma2(f2(-0.5f), sy, py), Ti);
+            Pim = fma2(q, py, Pim);
+            Sg = fma2(q, add2(bx, rx), Sg);
+            Sgi = fma2(q, add2(by, ry), Sgi);
             Dd = fma2(q, sub2(rx, bx), Dd);
             Di = fma2(q, sub2(ry, by), Di);
         }
     }
-    // closed form of K^-1 e (see me_point)
+    // closed form of K^-1 e (see me_point), with G = eI^2 + rho^2 shared by
+    // Delta = eI^2 (G - E2) - Pi^2 and I = S0 + f eI G
+    const float2 T = fma2(f2(-0.5f), Sg, P), Ti = fma2(f2(-0.5f), Sgi, Pim);
     const float2 eI = fma2(f2(g.kIs), Sg, fma2(f2(g.kIp), P, f2(1.0f)));
     const float2 pT = mul2(f2(g.kIp2), T), pTi = mul2(f2(g.kIp2), Ti);
     const float2 vD = mul2(f2(g.kV2), Dd), vDi = mul2(f2(g.kV2), Di);
@@ -266,12 +269,13 @@ __device__ __forceinline__ Stokes4x2 me_point_x2(const Geo<float> &g, const floa
     const float2 rho2 = fma2(pTi, Ti, mul2(vDi, Di));
     const float2 Pi = fma2(pT, Ti, mul2(vD, Di));
     const float2 eI2 = mul2(eI, eI);
-    const float2 Delta = fma2(eI2, add2(sub2(eI2, E2), rho2), neg2(mul2(Pi, Pi)));
+    const float2 G = add2(eI2, rho2);
+    const float2 Delta = fma2(eI2, sub2(G, E2), neg2(mul2(Pi, Pi)));
     const float2 f = mul2(f2(g.muS1), rcp2(Delta));
     const float2 A = fma2(eI2, T, mul2(Ti, Pi));
     const float2 eIC = mul2(eI, fma2(Dd, Ti, neg2(mul2(T, Di))));
     Stokes4x2 s;
-    s.I = fma2(mul2(f, eI), add2(eI2, rho2), f2(g.S0));
+    s.I = fma2(mul2(f, eI), G, f2(g.S0));
     s.Q = mul2(neg2(f), fma2(f2(g.kQ), A, mul2(f2(g.kUV), eIC)));
     s.U = mul2(neg2(f), fma2(f2(g.kU), A, neg2(mul2(f2(g.kQV), eIC))));
     s.V = mul2(mul2(neg2(f), f2(g.kV)), fma2(eI2, Dd, mul2(Di, Pi)));
