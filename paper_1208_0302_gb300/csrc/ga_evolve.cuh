@@ -349,9 +349,16 @@ __device__ __forceinline__ void weights_invmax_w2(const R *s_obs, int nl, R *s_w
 #ifndef GENESIS_GA_MINB
 #define GENESIS_GA_MINB 3
 #endif
+// Build option: GENESIS_GA_MAXNREG=N caps every instantiation at N registers
+// per thread instead (for tuning the cap; the two qualifiers exclude each other).
+#ifdef GENESIS_GA_MAXNREG
+#define GENESIS_GA_BOUNDS(MAXT, R) __maxnreg__(GENESIS_GA_MAXNREG)
+#else
+#define GENESIS_GA_BOUNDS(MAXT, R) __launch_bounds__(MAXT, ((MAXT) <= 256 && sizeof(R) == 4) ? GENESIS_GA_MINB : 1)
+#endif
 
 template <class R, int NL, int MAXT, bool COUNT, bool PAT, int M>
-__global__ void __launch_bounds__(MAXT, (MAXT <= 256 && sizeof(R) == 4) ? GENESIS_GA_MINB : 1)
+__global__ void GENESIS_GA_BOUNDS(MAXT, R)
 k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
             const R *__restrict__ obs, const double *__restrict__ w_user,
             const double *__restrict__ mu_px, int npix, double *__restrict__ best,
