@@ -49,8 +49,10 @@ def test_adjoint_against_central_differences_1000_vectors(gpu, orc):
     assert worst < 2e-3, (worst, int(i), int(k), P[i].tolist())
 
 
-def test_float32_map_with_polish_at_full_size(gpu):
-    """512x512 float32 two-line map, FP32 GA + 10 L-M, in one launch each."""
+def test_float32_map_with_polish_at_full_size(gpu, orc):
+    """512x512 float32 two-line map, FP32 GA + 10 L-M, in one launch each;
+    on a sample of pixels the oracle recomputes the reported FP64 chi2 of the
+    output parameters one by one."""
     spec = gi.two_line_spec()
     pb = gpu.Problem.from_spec(spec, "f32")
     npix = 512 * 512
@@ -71,6 +73,14 @@ def test_float32_map_with_polish_at_full_size(gpu):
     assert torch.equal(c2, gpu.me_chi2(pb, obs, p, w=w))
     med = float(np.median(c2n))
     assert 0.9 < med < 1.3, med
+    # sampled parity: the oracle's FP64 chi2 of the GPU's answers
+    idx = np.random.default_rng(12).choice(npix, 16, replace=False)
+    idx[-1] = npix - 1
+    o_s = obs[idx].double().cpu().numpy()
+    w_s = w[idx].cpu().numpy()
+    for k, i in enumerate(idx):
+        ref = orc.chi2(o_s[k], orc.synth(spec, pn[i])[0], w_s[k])
+        assert abs(c2n[i] / ref - 1) < 1e-10, (i, c2n[i], ref)
     # batch invariance at full size: a sampled slice run on its own
     for a in [0, 131072, npix - 300]:
         b2, _ = gpu.ga_invert_batch(pb, obs[a:a + 300].contiguous(), gi.PRIOR_LO, gi.PRIOR_HI, ga,
