@@ -8,7 +8,7 @@
 // approximant when every lane's pair of points is beyond |z|^2 = 484, the
 // continued fraction when every pair is beyond |z|^2 = 36, and Weideman's
 // series otherwise (each branch is accurate wherever it is taken: the series
-// everywhere, |error| <= 5e-8 for |x| <= 150), so a point's value can depend
+// everywhere: |error| <= 4.3e-8 for |x| <= 1e4, 0 <= y <= 1), so a point's value can depend
 // on its partner's and its warp's regions, always within the FP32 error budget.
 // A warp-uniform choice costs one branch where a per-lane choice would run
 // both for a mixed warp.
