@@ -61,3 +61,28 @@ def test_lm_fp32_never_worse_and_in_bounds(gpu, orc):
     pn = p.cpu().numpy()
     assert np.all(pn >= gi.PRIOR_LO) and np.all(pn <= gi.PRIOR_HI)
     assert np.all((pn[:, 2] >= 0) & (pn[:, 2] < 180.0 + 1e-12))
+
+
+def test_fp32_served_form_against_fp64_oracle_per_parameter(gpu, orc):
+    """The FP32 GA + FP32 L-M answer against the FP64 oracle's L-M from the
+    same GA best: the same chi2 and, per parameter, differences far below the
+    noise-set uncertainties (the error of the FP32 path stated per parameter)."""
+    spec = gi.two_line_spec()
+    n = 96
+    truth, obs = make_obs(orc, spec, n, seed=60)
+    obs32 = obs.astype(np.float32)
+    sig = 1e-3 * (truth[:, 7] + truth[:, 8])
+    w = np.repeat((1 / sig)[:, None], 4, 1)
+    pb = gpu.Problem.from_spec(spec, "f32")
+    ob = torch.tensor(obs32, device="cuda")
+    best, _ = gpu.ga_invert_batch(pb, ob, gi.PRIOR_LO, gi.PRIOR_HI, gpu.GaSettings(npop=128, ngen=100, seed=3))
+    p32, c32 = gpu.lm_polish(pb, ob, best, gi.PRIOR_LO, gi.PRIOR_HI, iters=10, w=torch.tensor(w, device="cuda"))
+    p64, c64 = orc.lm_polish(spec, obs32.astype(np.float64), best.cpu().numpy(), gi.PRIOR_LO, gi.PRIOR_HI,
+                             iters=10, w=w)
+    p32, c32 = p32.cpu().numpy(), c32.cpu().numpy()
+    ratio = c32 / c64
+    assert abs(np.median(ratio) - 1) < 1e-6 and np.quantile(np.abs(ratio - 1), 0.9) < 1e-4
+    d = np.abs(p32 - p64)
+    d[:, 2] = np.abs((p32[:, 2] - p64[:, 2] + 90) % 180 - 90)
+    rel = np.median(d, 0) / (gi.PRIOR_HI - gi.PRIOR_LO)
+    assert np.all(rel < 1e-5), rel
