@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving sample")
+    ap.add_argument("--no-pipeline", action="store_true", help="skip the full-disc pipeline sample")
     ap.add_argument("--serve", action="store_true",
                     help="run only the serving benchmark (Poisson arrivals at 0.7x and 1.2x capacity)")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
@@ -277,12 +278,53 @@ def run_ours(args):
             result["fp64_plain_ga"] = fp64_comparator(api, torch, pb64, obs, w, lo, hi, rank)
         if not args.no_serve:
             result["serving"] = serving(api, torch, pb32, dev, args.serve_seconds, loads=(0.7,))
+        if not args.no_pipeline:
+            result["pipeline"] = pipeline_sample(api, torch, dev)
         if not args.no_cpu and world == 1:
             result["cpu_baseline"] = cpu_baseline(spec, obs, w, lo, hi)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     return result
+
+
+def pipeline_sample(api, torch, device, n=512, n_spots=10, thresh=10.0):
+    """The Section 2 pipeline (api.invert_map) on a synthetic full disc of an
+    n x n grid: classification with the weak-field answer below the
+    polarization threshold, selection, the Section 4.3 prefit bounds, the
+    seeded polarity-restricted FP32 GA and the L-M polish on the selected
+    pixels, all on one stream.  Every on-disc pixel is answered, so pixels/s
+    counts all of them."""
+    truth, mu, _ = gi.draw_full_disc(n=n, seed=7, n_spots=n_spots)
+    npix = len(mu)
+    spec = gi.two_line_spec()
+    pb = api.Problem.from_spec(spec, "f32")
+    tp = torch.tensor(truth, device=device)
+    mp = torch.tensor(mu, device=device)
+    clean = api.me_synth(pb, tp, mp)
+    g = torch.Generator(device=device).manual_seed(17)
+    sig = 1e-3 * (tp[:, 7] + mp * tp[:, 8])
+    obs = (clean + sig.to(clean.dtype)[:, None, None] * torch.randn(clean.shape, generator=g, device=device,
+                                                                   dtype=clean.dtype)).contiguous()
+    w = (1.0 / sig)[:, None].repeat(1, 4).contiguous()
+    lo = gi.PRIOR_LO.copy()
+    lo[7] = lo[8] = 0.05
+    ga = api.GaSettings(npop=NPOP, ngen=NGEN, seed=3)
+    kw = dict(nseed=4, prefit=True, polish_iters=LM_ITERS, polish_w=w, mu_px=mp)
+    api.invert_map(pb, obs[:4096].contiguous(), lo, gi.PRIOR_HI, ga, thresh, (0, 8), 1, (80, 110),
+                   **dict(kw, polish_w=w[:4096].contiguous(), mu_px=mp[:4096].contiguous()))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    r = api.invert_map(pb, obs, lo, gi.PRIOR_HI, ga, thresh, (0, 8), 1, (80, 110), **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    flagged = int(r["count"].item())
+    chi2 = r["chi2"][r["flag"] == 1]
+    return {"grid": f"{n}x{n} disc", "pixels": npix, "flagged": flagged, "p_thresh": thresh, "ms": ms,
+            "pixels_per_s": npix / (ms / 1e3), "median_chi2_flagged": float(chi2.median().item()) if flagged else None,
+            "steps": "classify, select, prefit (40 L-M, Stokes I), bounds, seeded GA, 10 L-M"}
 
 
 def _request_obs(api, torch, pb, rq, device):
