@@ -2,9 +2,11 @@
 //
 // One warp per pixel, lanes over wavelengths.  Per iteration: analytic
 // Jacobian in the problem's precision (FP32 for float cubes), per-lane partial
-// sums of J^T W^2 J and J^T W^2 r, a warp reduction in FP64, the damped
-// Cholesky solve in FP64 (lane 0, in shared memory), and a trial synthesis
-// whose chi2 decides acceptance (Levenberg 1944, Marquardt 1963).
+// sums of J^T W^2 J and J^T W^2 r and their warp reduction in the same
+// precision (the FP32 Jacobian bounds their accuracy; GB300's FP64 rate is a
+// small fraction of its FP32 rate), the damped Cholesky solve in FP64 (lane 0,
+// in shared memory), and a trial synthesis whose FP64-summed chi2 decides
+// acceptance (Levenberg 1944, Marquardt 1963).
 #include "kernels.h"
 #include "me_jac.cuh"
 #include "rng_device.cuh"
@@ -21,6 +23,12 @@ namespace {
 constexpr int kLmWarps = 4;
 
 __device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -153,8 +161,9 @@ __device__ void lm_weights(const RO *o, int nl, const double *w_user, int pix, L
     for (int s = 0; s < 4; ++s) w2[s] = W.w2[s];
 }
 
-// Normal equations at p: W.A = J^T W^2 J (full 9x9) and W.g = J^T W^2 r,
-// per-lane partial sums in R over the lane's wavelengths, warp sums in FP64.
+// Normal equations at p: W.A = J^T W^2 J (full M x M) and W.g = J^T W^2 r,
+// per-lane partial sums in R over the lane's wavelengths, warp sums in R,
+// stored in FP64 for the solve.
 template <class R, class RO, int NL, int M = ME_NPAR>
 __device__ void lm_normal(const KProblem &pb, int nlines, int nl, const double *p, double mu,
                           const RO *o, const R *s_doff, const R *he, const R *w2r, LmWarpSmem &W)
@@ -194,11 +203,11 @@ __device__ void lm_normal(const KProblem &pb, int nlines, int nl, const double *
     int t = 0;
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-        const double gv = warp_sum((double)gacc[a]);
+        const double gv = (double)warp_sum(gacc[a]);
         if (lane == 0) W.g[a] = gv;
 #pragma unroll
         for (int b = 0; b <= a; ++b) {
-            const double v = warp_sum((double)Aacc[t++]);
+            const double v = (double)warp_sum(Aacc[t++]);
             if (lane == 0) {
                 W.A[a * M + b] = v;
                 W.A[b * M + a] = v;
