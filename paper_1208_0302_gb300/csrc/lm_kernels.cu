@@ -70,52 +70,89 @@ __device__ double lm_chi2(const KProblem &pb, int nlines, int nl, const double *
     return tot / (double)(4 * nl - M);
 }
 
-// Solve (A + lam D) x = g by Cholesky (row-major 9x9 in N), D = diag(max(A_jj,
-// 1e-12 max A_kk)).  Returns false if a pivot is not positive.
-template <int M>
-__device__ bool damped_cholesky(const double *A, const double *g, double lam, double *N, double *x)
-{
-    double dmax = 0.0;
-    for (int a = 0; a < M; ++a) dmax = fmax(dmax, A[a * M + a]);
-    for (int a = 0; a < M * M; ++a) N[a] = A[a];
-    for (int a = 0; a < M; ++a) {
-        const double d = A[a * M + a] > 1e-12 * dmax ? A[a * M + a] : 1e-12 * dmax;
-        N[a * M + a] += lam * d;
-    }
-    for (int j = 0; j < M; ++j) {
-        double d = N[j * M + j];
-        for (int k = 0; k < j; ++k) d -= N[j * M + k] * N[j * M + k];
-        if (!(d > 0.0)) return false;
-        const double ljj = sqrt(d);
-        N[j * M + j] = ljj;
-        for (int i = j + 1; i < M; ++i) {
-            double s = N[i * M + j];
-            for (int k = 0; k < j; ++k) s -= N[i * M + k] * N[j * M + k];
-            N[i * M + j] = s / ljj;
-        }
-    }
-    for (int i = 0; i < M; ++i) {
-        double s = g[i];
-        for (int k = 0; k < i; ++k) s -= N[i * M + k] * x[k];
-        x[i] = s / N[i * M + i];
-    }
-    for (int i = M - 1; i >= 0; --i) {
-        double s = x[i];
-        for (int k = i + 1; k < M; ++k) s -= N[k * M + i] * x[k];
-        x[i] = s / N[i * M + i];
-    }
-    return true;
-}
-
 struct LmWarpSmem {  // M x M matrices stored with row stride M
     double A[ME_NPAR_MAX * ME_NPAR_MAX];
     double N[ME_NPAR_MAX * ME_NPAR_MAX];
     double g[ME_NPAR_MAX];
     double x[ME_NPAR_MAX];
     double w2[4];
-    double lam;
-    int ok;
 };
+
+// Solve (A + lam D) x = g with Marquardt's diagonal D = diag(max(A_jj,
+// 1e-12 max_k A_kk)), the rows and columns of held parameters zeroed, by a
+// warp-cooperative Cholesky factorisation in FP64: lane i < M keeps row i of
+// the factor L in registers and column j is formed on all rows at once (the
+// left-looking order), with the row of L_j broadcast by shuffles and one
+// reciprocal square root of the pivot per column in place of a division per
+// element.  Forward substitution runs on the same rows; back substitution
+// reads L^T through the warp's shared matrix N.  A pivot that is not positive
+// multiplies lam by 10 and retries (up to 30 times).  Returns false, on every
+// lane, if no step was found (also when A has no positive diagonal); the
+// step lands in W.x.  All lanes of the warp must call it together.
+template <int M>
+__device__ bool warp_damped_solve(LmWarpSmem &W, unsigned free_mask, double &lam)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int row = lane < M ? lane : 0;
+    const bool free_row = lane < M && ((free_mask >> row) & 1u);
+    const double aii = free_row ? W.A[row * M + row] : 0.0;
+    double dmax = aii;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) dmax = fmax(dmax, __shfl_xor_sync(full, dmax, off));
+    if (!(dmax > 0.0)) return false;
+    const double floor_d = 1e-12 * dmax;
+    const double dscale = aii > floor_d ? aii : floor_d;
+    const double grow = free_row ? W.g[row] : 0.0;
+    for (int tries = 0; tries < 30; ++tries) {
+        const double drow = fma(lam, dscale, aii);  // this row's damped diagonal
+        double L[M], rinv[M];
+        bool ok = true;
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            const bool fj = free_row && ((free_mask >> j) & 1u);
+            double s = (lane == j) ? drow : (fj ? W.A[row * M + j] : 0.0);
+#pragma unroll
+            for (int k = 0; k < j; ++k) s = fma(-L[k], __shfl_sync(full, L[k], j), s);
+            const double dj = __shfl_sync(full, s, j);
+            if (!(dj > 0.0)) {
+                ok = false;
+                break;
+            }
+            rinv[j] = rsqrt(dj);
+            L[j] = s * rinv[j];
+        }
+        if (!ok) {
+            lam *= 10.0;
+            continue;
+        }
+        // L y = g, then L^T x = y
+        double t = grow, y = 0.0;
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const double yk = __shfl_sync(full, t, k) * rinv[k];
+            if (lane == k) y = yk;
+            t = fma(-L[k], yk, t);
+        }
+        if (lane < M) {
+#pragma unroll
+            for (int k = 0; k < M; ++k) W.N[row * M + k] = L[k];
+        }
+        __syncwarp();
+        double u = y, x = 0.0;
+#pragma unroll
+        for (int k = M - 1; k >= 0; --k) {
+            const double xk = __shfl_sync(full, u, k) * rinv[k];
+            if (lane == k) x = xk;
+            u = fma(-W.N[k * M + row], xk, u);
+        }
+        if (lane < M) W.x[row] = x;
+        __syncwarp();
+        return true;
+    }
+    return false;
+}
+
 
 // Weights of one pixel into w2 (squared): the caller's, or Section 4.5
 // inverse-max in FP64.  Every lane gets the result.
@@ -265,27 +302,7 @@ k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const 
             lm_normal<R, RO, NL, M>(pb, nlines, nl, p, mu, o, s_doff, he, w2r, W);
             need = false;
         }
-        if (lane == 0) {
-            // held parameters: zero rows and columns, so their step is 0
-            for (int a = 0; a < M; ++a) {
-                if ((lm.free_mask >> a) & 1u) continue;
-                W.g[a] = 0.0;
-                for (int b = 0; b < M; ++b) {
-                    W.A[a * M + b] = 0.0;
-                    W.A[b * M + a] = 0.0;
-                }
-            }
-            bool ok = false;
-            for (int tries = 0; tries < 30 && !ok; ++tries) {
-                ok = damped_cholesky<M>(W.A, W.g, lam, W.N, W.x);
-                if (!ok) lam *= 10.0;
-            }
-            W.ok = ok ? 1 : 0;
-            W.lam = lam;
-        }
-        __syncwarp();
-        lam = W.lam;
-        if (!W.ok) break;
+        if (!warp_damped_solve<M>(W, lm.free_mask, lam)) break;
         double q[M];
 #pragma unroll
         for (int d = 0; d < M; ++d) q[d] = p[d] + W.x[d];
