@@ -78,17 +78,38 @@ struct LmWarpSmem {  // M x M matrices stored with row stride M
     double w2[4];
 };
 
-// Solve (A + lam D) x = g with Marquardt's diagonal D = diag(max(A_jj,
-// 1e-12 max_k A_kk)), the rows and columns of held parameters zeroed, by a
-// warp-cooperative Cholesky factorisation in FP64: lane i < M keeps row i of
+// Warp-cooperative Cholesky factorisation in FP64 of an M x M symmetric
+// matrix whose row i lane i < M supplies through a(j): lane i keeps row i of
 // the factor L in registers and column j is formed on all rows at once (the
 // left-looking order), with the row of L_j broadcast by shuffles and one
-// reciprocal square root of the pivot per column in place of a division per
-// element.  Forward substitution runs on the same rows; back substitution
-// reads L^T through the warp's shared matrix N.  A pivot that is not positive
-// multiplies lam by 10 and retries (up to 30 times).  Returns false, on every
-// lane, if no step was found (also when A has no positive diagonal); the
-// step lands in W.x.  All lanes of the warp must call it together.
+// reciprocal square root of the pivot per column (rinv, the same on every
+// lane) in place of a division per element.  Entries above the diagonal of
+// L are left unspecified.  Returns false, on every lane, at the first pivot
+// that is not positive.  All lanes of the warp must call it together.
+template <int M, class RowFn>
+__device__ __forceinline__ bool warp_cholesky(RowFn a, double (&L)[M], double (&rinv)[M])
+{
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        double s = a(j);
+#pragma unroll
+        for (int k = 0; k < j; ++k) s = fma(-L[k], __shfl_sync(0xffffffffu, L[k], j), s);
+        const double dj = __shfl_sync(0xffffffffu, s, j);
+        if (!(dj > 0.0)) return false;
+        rinv[j] = rsqrt(dj);
+        L[j] = s * rinv[j];
+    }
+    return true;
+}
+
+// Solve (A + lam D) x = g with Marquardt's diagonal D = diag(max(A_jj,
+// 1e-12 max_k A_kk)), the rows and columns of held parameters zeroed, with
+// warp_cholesky; forward substitution runs on the same rows, back
+// substitution reads L^T through the warp's shared matrix N.  A pivot that
+// is not positive multiplies lam by 10 and retries (up to 30 times).
+// Returns false, on every lane, if no step was found (also when A has no
+// positive diagonal); the step lands in W.x.  All lanes of the warp must
+// call it together.
 template <int M>
 __device__ bool warp_damped_solve(LmWarpSmem &W, unsigned free_mask, double &lam)
 {
@@ -107,21 +128,11 @@ __device__ bool warp_damped_solve(LmWarpSmem &W, unsigned free_mask, double &lam
     for (int tries = 0; tries < 30; ++tries) {
         const double drow = fma(lam, dscale, aii);  // this row's damped diagonal
         double L[M], rinv[M];
-        bool ok = true;
-#pragma unroll
-        for (int j = 0; j < M; ++j) {
-            const bool fj = free_row && ((free_mask >> j) & 1u);
-            double s = (lane == j) ? drow : (fj ? W.A[row * M + j] : 0.0);
-#pragma unroll
-            for (int k = 0; k < j; ++k) s = fma(-L[k], __shfl_sync(full, L[k], j), s);
-            const double dj = __shfl_sync(full, s, j);
-            if (!(dj > 0.0)) {
-                ok = false;
-                break;
-            }
-            rinv[j] = rsqrt(dj);
-            L[j] = s * rinv[j];
-        }
+        const bool ok = warp_cholesky<M>(
+            [&](int j) {
+                return lane == j ? drow : ((free_row && ((free_mask >> j) & 1u)) ? W.A[row * M + j] : 0.0);
+            },
+            L, rinv);
         if (!ok) {
             lam *= 10.0;
             continue;
@@ -336,9 +347,10 @@ k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const 
 
 // Section 5 uncertainty estimate at given parameters: sigma_i^2 =
 // [H^-1]_ii chi2 / M with H the Gauss-Newton Hessian of Eq. chisq,
-// H = (2/nu) J^T W^2 J.  Warp per pixel; J in the problem precision, sums in
-// FP64, Cholesky inverse diagonal in FP64 (lane 0).  A parameter without
-// influence (singular H) gets +infinity.
+// H = (2/nu) J^T W^2 J.  Warp per pixel; J and its sums in the problem
+// precision, the Cholesky factor and the inverse diagonal in FP64 (lane i
+// forms [H^-1]_ii).  A parameter without influence (singular H) gets
+// +infinity on every parameter of the pixel.
 template <class R, class RO, int NL, int M = ME_NPAR>
 __global__ void __launch_bounds__(kLmWarps * 32)
 k_lm_sigma(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
@@ -376,40 +388,33 @@ k_lm_sigma(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
     for (int d = 0; d < M; ++d) p[d] = params[(size_t)pix * M + d];
     const double chi2 = lm_chi2<R, RO, NL, M>(pb, nlines, nl, p, mu, o, s_doff, he, w2);
     lm_normal<R, RO, NL, M>(pb, nlines, nl, p, mu, o, s_doff, he, w2r, W);
-    if (lane == 0) {
-        const double nu = (double)(4 * nl - M);
-        // H = (2/nu) A;  [H^-1]_ii = (nu/2) [A^-1]_ii
-        double *N = W.N;
-        for (int a = 0; a < M * M; ++a) N[a] = W.A[a];
-        bool ok = true;
-        for (int j = 0; j < M && ok; ++j) {
-            double d = N[j * M + j];
-            for (int k = 0; k < j; ++k) d -= N[j * M + k] * N[j * M + k];
-            if (!(d > 0.0)) { ok = false; break; }
-            const double ljj = sqrt(d);
-            N[j * M + j] = ljj;
-            for (int i = j + 1; i < M; ++i) {
-                double t = N[i * M + j];
-                for (int k = 0; k < j; ++k) t -= N[i * M + k] * N[j * M + k];
-                N[i * M + j] = t / ljj;
+    // H = (2/nu) A;  [H^-1]_ii = (nu/2) [A^-1]_ii = (nu/2) || L^-1 e_i ||^2
+    double L[M], rinv[M];
+    const int row = lane < M ? lane : 0;
+    const bool ok = warp_cholesky<M>([&](int j) { return lane < M ? W.A[row * M + j] : 0.0; }, L, rinv);
+    if (ok && lane < M) {
+#pragma unroll
+        for (int k = 0; k < M; ++k) W.N[row * M + k] = L[k];
+    }
+    __syncwarp();
+    if (lane < M) {
+        double v = INFINITY;
+        if (ok) {
+            // lane i: forward substitution of e_i against L (broadcast reads)
+            double y[M];
+            double acc = 0.0;
+#pragma unroll
+            for (int r = 0; r < M; ++r) {
+                double t = (r == lane) ? 1.0 : 0.0;
+#pragma unroll
+                for (int k = 0; k < r; ++k) t = fma(-W.N[r * M + k], y[k], t);
+                y[r] = t * rinv[r];
+                acc = fma(y[r], y[r], acc);
             }
+            const double nu = (double)(4 * nl - M);
+            v = sqrt(0.5 * nu * acc * chi2 / (double)M);
         }
-        for (int i = 0; i < M; ++i) {
-            double v = INFINITY;
-            if (ok) {
-                // [A^-1]_ii = || L^-1 e_i ||^2 (forward substitution of e_i)
-                double y[M];
-                double acc = 0.0;
-                for (int r = 0; r < M; ++r) {
-                    double t = (r == i) ? 1.0 : 0.0;
-                    for (int k = 0; k < r; ++k) t -= N[r * M + k] * y[k];
-                    y[r] = t / N[r * M + r];
-                    acc += y[r] * y[r];
-                }
-                v = sqrt(0.5 * nu * acc * chi2 / (double)M);
-            }
-            sigma[(size_t)pix * M + i] = v;
-        }
+        sigma[(size_t)pix * M + lane] = v;
     }
 }
 
