@@ -75,3 +75,4 @@ def test_full_pattern_ga_fp32_and_polish(gpu, orc):
                                       gpu.GaSettings(npop=64, ngen=4, seed=3))
     # 12 components for 6301.5 + 3 for 6302.5 per wavelength point
     assert counts["weideman"] + counts["mid"] + counts["cf"] + counts["far"] == counts["points"] * 15
+    assert min(counts["weideman"], counts["mid"], counts["cf"], counts["far"]) > 0
