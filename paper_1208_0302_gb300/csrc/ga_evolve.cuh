@@ -123,6 +123,7 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
 {
     Geo<float> geo = make_geo<float, NL, FILL>(pb, nlines, p, mu);
     pair_thresholds(geo, nlines);
+    geo.vmask = __activemask();
     float2 sI = f2(0.f), sQ = f2(0.f), sU = f2(0.f), sV = f2(0.f);
     float2 bI = f2(0.f), bQ = f2(0.f), bU = f2(0.f), bV = f2(0.f);
     const int npair = (nl + 1) >> 1;

@@ -11,7 +11,9 @@
 // everywhere: |error| <= 4.3e-8 for |x| <= 1e4, 0 <= y <= 1), so a point's value can depend
 // on its partner's and its warp's regions, always within the FP32 error budget.
 // A warp-uniform choice costs one branch where a per-lane choice would run
-// both for a mixed warp.
+// both for a mixed warp.  A region test is one comparison of the pair's nearer
+// |x| with a per-individual threshold, and the vote reuses the fitness call's
+// lane mask: the loop's issue slots, not its flops, set its speed.
 #pragma once
 
 #include "me_device.cuh"
@@ -125,27 +127,31 @@ __device__ __forceinline__ void pair_thresholds(Geo<float> &g, int nlines)
     for (int l = 0; l < ME_MAX_LINES; ++l)
         g.t3[l] = (l < nlines && g.text >= 0.0f) ? g.text + fabsf(g.vB[l]) : -1.0f;
 }
-__device__ __forceinline__ bool beyond(float2 x, float t) { return fabsf(x.x) > t && fabsf(x.y) > t; }
-// A predicate that holds for every currently active lane.  The vote only
-// chooses among branches that are each accurate for every lane they are taken
-// by (a lane takes a cheaper branch only if its own points qualify), so it is
-// correct for any set of voting lanes; voting over the active mask also keeps
-// it safe where the caller runs divergent (the GA's restarts evaluate only
-// part of a warp).
-__device__ __forceinline__ bool warp_all(bool p) { return __all_sync(__activemask(), p); }
+// Nearer |x| of a pair: the pair is beyond a threshold t when this is.
+__device__ __forceinline__ float pair_min_abs(float2 x) { return fminf(fabsf(x.x), fabsf(x.y)); }
+// A predicate that holds for every lane of mask, the lanes that evaluate
+// together.  The vote only chooses among branches that are each accurate for
+// every lane they are taken by (a lane takes a cheaper branch only if its own
+// points qualify), so it is correct for any set of voting lanes.  The fitness
+// loop takes the mask once per call (__activemask() on entry): its branches
+// are all warp-uniform, so the set of lanes does not change inside it, and a
+// caller that runs divergent (the GA's restarts evaluate only part of a
+// warp) votes over just its active lanes.
+__device__ __forceinline__ bool warp_all(bool p, unsigned mask) { return __all_sync(mask, p); }
 
 // One component for the pair, the branch chosen uniformly across the warp.
 __device__ __forceinline__ void fad_pair(float2 x, const Geo<float> &g, float2 &wx, float2 &wy)
 {
-    if (warp_all(beyond(x, g.tfar))) fad_far2(x, g.a, g.a2, wx, wy);
-    else if (warp_all(beyond(x, g.text))) fad_ext2(x, g.a, g.a2, wx, wy);
-    else if (warp_all(beyond(x, g.tmid))) fad_cf2<5>(x, g.a, g.a2, wx, wy);
+    const float m = pair_min_abs(x);
+    if (warp_all(m > g.tfar, g.vmask)) fad_far2(x, g.a, g.a2, wx, wy);
+    else if (warp_all(m > g.text, g.vmask)) fad_ext2(x, g.a, g.a2, wx, wy);
+    else if (warp_all(m > g.tmid, g.vmask)) fad_cf2<5>(x, g.a, g.a2, wx, wy);
     else fad_int2(x, g.a, wx, wy);
 }
 // The same when every lane's component is already known to be exterior.
 __device__ __forceinline__ void fad_pair_ext(float2 x, const Geo<float> &g, float2 &wx, float2 &wy)
 {
-    if (warp_all(beyond(x, g.tfar))) fad_far2(x, g.a, g.a2, wx, wy);
+    if (warp_all(pair_min_abs(x) > g.tfar, g.vmask)) fad_far2(x, g.a, g.a2, wx, wy);
     else fad_ext2(x, g.a, g.a2, wx, wy);
 }
 
@@ -240,7 +246,7 @@ __device__ __forceinline__ Stokes4x2 me_point_x2(const Geo<float> &g, const floa
                 count_pair(xr, g.a2, y_real, ncount);
             }
             float2 bx, by, px, py, rx, ry;
-            if (warp_all(beyond(v, g.t3[l]))) {
+            if (warp_all(pair_min_abs(v) > g.t3[l], g.vmask)) {
                 fad_pair_ext(xb, g, bx, by);
                 fad_pair_ext(v, g, px, py);
                 fad_pair_ext(xr, g, rx, ry);
