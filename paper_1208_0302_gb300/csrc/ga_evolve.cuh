@@ -109,11 +109,11 @@ __device__ __forceinline__ R fitness_rows(const KProblem &pb, int nlines, int nl
 
 
 // Eq. chisq for one individual with the FP32 pair path (two wavelengths per
-// step, packed FP32x2 arithmetic).  The squared residuals are summed in two
-// levels: FMA partial sums over blocks of 8 pairs, added into a running total
-// per block (relative error about (8 + n/16) u, u = 2^-24, instead of the n u
-// of a single running sum; the best individual's chi2 is re-evaluated in
-// FP64 afterwards).
+// step, packed FP32x2 arithmetic).  The squared residuals of each Stokes
+// parameter go into one FMA running sum per lane of the pair (relative error
+// at most about (n/2) u, u = 2^-24, for n wavelengths; the fitness only ranks
+// individuals, and the best individual's chi2 is re-evaluated in FP64
+// afterwards).  Fewer live accumulators keep the loop's state in registers.
 template <int NL, bool COUNT, bool PAT, bool FILL>
 __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, int nl, const float *p,
                                                float mu, const float *s_obs, const float *s_doff,
@@ -125,7 +125,6 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
     pair_thresholds(geo, nlines);
     geo.vmask = __activemask();
     float2 sI = f2(0.f), sQ = f2(0.f), sU = f2(0.f), sV = f2(0.f);
-    float2 bI = f2(0.f), bQ = f2(0.f), bU = f2(0.f), bV = f2(0.f);
     const int npair = (nl + 1) >> 1;
     EvalCount cnt{0u, 0u, 0u};
     for (int q = 0; q < npair; ++q) {
@@ -144,17 +143,10 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
         float2 rI = sub2(make_float2(o0.x, o0.y), m.I), rQ = sub2(make_float2(o0.z, o0.w), m.Q);
         float2 rU = sub2(make_float2(o1.x, o1.y), m.U), rV = sub2(make_float2(o1.z, o1.w), m.V);
         if (!y_real) rI.y = rQ.y = rU.y = rV.y = 0.f;  // padded partner
-        bI = fma2(rI, rI, bI);
-        bQ = fma2(rQ, rQ, bQ);
-        bU = fma2(rU, rU, bU);
-        bV = fma2(rV, rV, bV);
-        if ((q & 7) == 7 || q == npair - 1) {
-            sI = add2(sI, bI);
-            sQ = add2(sQ, bQ);
-            sU = add2(sU, bU);
-            sV = add2(sV, bV);
-            bI = bQ = bU = bV = f2(0.f);
-        }
+        sI = fma2(rI, rI, sI);
+        sQ = fma2(rQ, rQ, sQ);
+        sU = fma2(rU, rU, sU);
+        sV = fma2(rV, rV, sV);
     }
     if (COUNT) {
         ninterior += cnt.interior;

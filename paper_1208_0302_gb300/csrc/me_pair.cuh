@@ -203,6 +203,31 @@ __device__ __forceinline__ void pattern_profiles_x2(const KLine &ln, float2 dinv
     }
 }
 
+// One effective triplet's contribution to a pair's profile sums, each
+// component added as soon as it is evaluated (EXT: every lane's triplet is
+// already exterior).
+template <bool EXT, bool FILL>
+__device__ __forceinline__ void triplet_acc(float2 xb, float2 v, float2 xr, const Geo<float> &g, float2 q,
+                                            float2 &P, float2 &Pim, float2 &Sg, float2 &Sgi, float2 &Dd,
+                                            float2 &Di, float2 &P0)
+{
+    float2 wx, wy;
+    if (EXT) fad_pair_ext(xb, g, wx, wy); else fad_pair(xb, g, wx, wy);
+    Sg = fma2(q, wx, Sg);
+    Sgi = fma2(q, wy, Sgi);
+    Dd = fma2(neg2(q), wx, Dd);
+    Di = fma2(neg2(q), wy, Di);
+    if (EXT) fad_pair_ext(v, g, wx, wy); else fad_pair(v, g, wx, wy);
+    if (FILL) P0 = fma2(q, wx, P0);  // the pi profile is unshifted
+    P = fma2(q, wx, P);
+    Pim = fma2(q, wy, Pim);
+    if (EXT) fad_pair_ext(xr, g, wx, wy); else fad_pair(xr, g, wx, wy);
+    Sg = fma2(q, wx, Sg);
+    Sgi = fma2(q, wy, Sgi);
+    Dd = fma2(q, wx, Dd);
+    Di = fma2(q, wy, Di);
+}
+
 // Stokes vectors at two wavelength points.  doff2[l] holds (lambda_j -
 // lambda0_l, lambda_{j+1} - lambda0_l).  FILL mixes in the field-free
 // profile with the fill fraction (Section 4.2, see fill_mix).
@@ -245,24 +270,11 @@ __device__ __forceinline__ Stokes4x2 me_point_x2(const Geo<float> &g, const floa
                 count_pair(v, g.a2, y_real, ncount);
                 count_pair(xr, g.a2, y_real, ncount);
             }
-            float2 bx, by, px, py, rx, ry;
-            if (warp_all(pair_min_abs(v) > g.t3[l], g.vmask)) {
-                fad_pair_ext(xb, g, bx, by);
-                fad_pair_ext(v, g, px, py);
-                fad_pair_ext(xr, g, rx, ry);
-            } else {
-                fad_pair(xb, g, bx, by);
-                fad_pair(v, g, px, py);
-                fad_pair(xr, g, rx, ry);
-            }
             const float2 q = f2(half_eta[l]);
-            if (FILL) P0 = fma2(q, px, P0);  // the pi profile is unshifted
-            P = fma2(q, px, P);
-            Pim = fma2(q, py, Pim);
-            Sg = fma2(q, add2(bx, rx), Sg);
-            Sgi = fma2(q, add2(by, ry), Sgi);
-            Dd = fma2(q, sub2(rx, bx), Dd);
-            Di = fma2(q, sub2(ry, by), Di);
+            if (warp_all(pair_min_abs(v) > g.t3[l], g.vmask))
+                triplet_acc<true, FILL>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
+            else
+                triplet_acc<false, FILL>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
         }
     }
     // closed form of K^-1 e (see me_point), with G = eI^2 + rho^2 shared by
