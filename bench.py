@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="run only the serving benchmark (Poisson arrivals at 0.7x and 1.2x capacity)")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--configs", action="store_true",
+                    help="time the FP64 oracle and the GPU FP64 GA on C1 (256 px) and a 256-px C2 subset")
     return ap.parse_args()
 
 
@@ -434,6 +436,15 @@ def fp64_comparator(api, torch, pb64, obs32, w, lo, hi, rank, n=1024):
             "median_chi2": float(chi.median().item())}
 
 
+def syntheses_per_pixel(npop, ngen, nsamp=None):
+    """GA fitness evaluations per pixel: the initial population, every child
+    of every generation, and the restarted worst half at each N_samp-th
+    generation before the last (Section 4.6)."""
+    nsamp = ngen // 4 if nsamp is None else nsamp
+    restarts = sum(1 for t in range(1, ngen) if nsamp > 0 and t % nsamp == 0)
+    return npop * (ngen + 1) + restarts * (npop // 2)
+
+
 def cpu_baseline(spec, obs, w, lo, hi, n=None):
     """The FP64 oracle (GA + L-M) on a bounded pixel sample, all host cores."""
     import oracle
@@ -448,7 +459,57 @@ def cpu_baseline(spec, obs, w, lo, hi, n=None):
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": "pixels/s", "cores": nth, "kind": "oracle",
             "sample": f"first {n} pixels of the map, FP64 GA (npop {NPOP}, {NGEN} gen) + {LM_ITERS} L-M",
-            "seconds": dt, "median_chi2": float(np.median(c2))}
+            "seconds": dt, "median_chi2": float(np.median(c2)),
+            "ga_syntheses_per_s": n * syntheses_per_pixel(NPOP, NGEN) / dt}
+
+
+def run_configs(args):
+    """FP64 GA on C1 (all 256 pixels) and on a seeded 256-pixel subset of C2:
+    the oracle on all host cores and the GPU on the same inputs (inverse-max
+    weights, no polish).  Reports pixels/s, syntheses/s and the fraction of
+    pixels whose best parameters are identical on both sides."""
+    import torch
+
+    import oracle
+    from paper_1208_0302_gb300 import _lib, api
+    torch.cuda.set_device(0)
+    _lib.load()
+    dev = torch.device("cuda", 0)
+    nth = os.cpu_count() or 1
+    out = {}
+    for name in ("c1", "c2"):
+        wl = gi.workload(name)
+        n = 256
+        truth = gi.draw_truth(n, seed=wl.seed + 11)
+        sig = 1e-3 * (truth[:, 7] + truth[:, 8])
+        obs = oracle.synth(wl.spec, truth) + sig[:, None, None] * gi.draw_noise(n, wl.spec.n_lambda, wl.seed + 11)
+        spp = syntheses_per_pixel(wl.npop, wl.ngen)
+        t0 = time.perf_counter()
+        r = oracle.ga_invert(wl.spec, obs, wl.lo, wl.hi, oracle.ga_config(wl.npop, wl.ngen, seed=0), nthreads=nth)
+        dt = time.perf_counter() - t0
+        pb = api.Problem.from_spec(wl.spec, "f64")
+        ob = torch.tensor(obs, device=dev)
+        ga = api.GaSettings(npop=wl.npop, ngen=wl.ngen, seed=0)
+        api.ga_invert_batch(pb, ob[:8].contiguous(), wl.lo, wl.hi, api.GaSettings(npop=wl.npop, ngen=2))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        best, chi2 = api.ga_invert_batch(pb, ob, wl.lo, wl.hi, ga)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        same = np.all(best.cpu().numpy() == r["best"], axis=1)
+        c_gpu = chi2.cpu().numpy()
+        out[name] = {"pixels": n, "npop": wl.npop, "ngen": wl.ngen, "n_lambda": wl.spec.n_lambda,
+                     "lines": len(wl.spec.lines), "syntheses_per_pixel": spp,
+                     "oracle": {"pixels_per_s": n / dt, "syntheses_per_s": n * spp / dt, "cores": nth,
+                                "seconds": dt, "median_chi2": float(np.median(r["chi2"]))},
+                     "gpu_fp64": {"pixels_per_s": n / (ms / 1e3), "syntheses_per_s": n * spp / (ms / 1e3),
+                                  "ms": ms, "median_chi2": float(np.median(c_gpu)),
+                                  "note": "one launch of 256 blocks (under one wave of the GPU)"},
+                     "identical_best_fraction": float(same.mean()),
+                     "max_rel_chi2_diff": float(np.max(np.abs(c_gpu - r["chi2"]) / r["chi2"]))}
+    return {"configs": out, "data": "synthetic (seeded truth from the priors, oracle ME synthesis + 1e-3 Ic noise)"}
 
 
 def run_reference(args):
@@ -507,6 +568,8 @@ def main():
     args = parse()
     if args.serve:
         res = run_serve(args)
+    elif args.configs:
+        res = run_configs(args)
     else:
         res = run_reference(args) if args.impl == "reference" else run_ours(args)
     if res is not None:
