@@ -279,6 +279,7 @@ int make_ga(const ga_config *cfg, const me_bounds *b, uint64_t pid0, KGa &g, int
     g.weight_mode = cfg->weight_mode;
     g.seed = cfg->seed;
     g.pixel_id0 = pid0;
+    philox_round_keys(cfg->seed, g.rk);
     g.t_cross = prob_threshold(cfg->pc);
     for (int bit = 0; bit < 16; ++bit) {
         double r = 1.0;

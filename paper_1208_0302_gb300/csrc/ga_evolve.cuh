@@ -217,7 +217,7 @@ __device__ __forceinline__ void breed_one(const KGa &ga, uint64_t pid, int t, in
                                           const R *s_fit, const uint16_t *s_cur, int elite,
                                           uint16_t *s_row, uint16_t g[M])
 {
-    const U4 u = ga_random(ga.seed, pid, t, (uint32_t)k, kPurposeSelect);
+    const U4 u = ga_random_rk(ga.rk, pid, t, (uint32_t)k, kPurposeSelect);
     const int i = (int)(((uint64_t)u.x * (uint64_t)npop) >> 32);
     const int j = (i + 1 + (int)(((uint64_t)u.y * (uint64_t)(npop - 1)) >> 32)) % npop;
     const R fi = s_fit[i], fj = s_fit[j];
@@ -225,7 +225,7 @@ __device__ __forceinline__ void breed_one(const KGa &ga, uint64_t pid, int t, in
 #pragma unroll
     for (int d = 0; d < M; ++d) g[d] = s_cur[win * M + d];
 
-    const U4 uc = ga_random(ga.seed, pid, t, (uint32_t)(k >> 1), kPurposeCross);
+    const U4 uc = ga_random_rk(ga.rk, pid, t, (uint32_t)(k >> 1), kPurposeCross);
     const bool cross = (uint64_t)uc.x < ga.t_cross;
     const int c = 1 + (int)(((uint64_t)uc.y * (uint64_t)(16 * M - 1)) >> 32);
 #pragma unroll
@@ -251,7 +251,7 @@ __device__ __forceinline__ void breed_one(const KGa &ga, uint64_t pid, int t, in
         uint32_t word = s_row[d];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const U4 um = ga_random(ga.seed, pid, t, (uint32_t)k, kPurposeMutate + (uint32_t)(4 * d + q));
+            const U4 um = ga_random_rk(ga.rk, pid, t, (uint32_t)k, kPurposeMutate + (uint32_t)(4 * d + q));
             const uint32_t uu[4] = {um.x, um.y, um.z, um.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {

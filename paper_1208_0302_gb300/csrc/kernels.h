@@ -15,8 +15,22 @@ struct KGa {
     uint64_t seed, pixel_id0;
     uint64_t t_cross;       // crossover iff u32 < t_cross
     uint64_t t_mut[16];     // flip bit b (0 = MSB) iff u32 < t_mut[b]
+    uint32_t rk[10][2];     // Philox4x32-10 round keys of seed: (k0, k1) + r (W0, W1)
     double lo[ME_NPAR_MAX], hi[ME_NPAR_MAX];
 };
+
+// Round keys of Philox4x32-10 for a 64-bit seed (k0 = low word, k1 = high):
+// round r uses (k0 + r 0x9E3779B9, k1 + r 0xBB67AE85) mod 2^32.
+inline void philox_round_keys(uint64_t seed, uint32_t rk[10][2])
+{
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        rk[r][0] = k0;
+        rk[r][1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
 
 // Parameters per model: 9, or 10 with the fill fraction of Section 4.2.
 template <bool FILL> constexpr int kNpar = ME_NPAR + (FILL ? 1 : 0);
