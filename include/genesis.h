@@ -243,8 +243,8 @@ int ga_count_evaluations(const me_problem *pb, const void *obs, const double *w,
 /*
  * lm_polish - Levenberg-Marquardt refinement of each pixel's parameters
  * (Levenberg 1944, Marquardt 1963): FP32 analytic Jacobian, normal equations
- * (J^T W^2 J + lambda D) delta = J^T W^2 r reduced and solved by Cholesky in
- * FP64, trial step with the azimuth wrapped into [0, 180) and clamped to the
+ * (J^T W^2 J + lambda D) delta = J^T W^2 r summed in the cube's precision
+ * and solved by Cholesky in FP64, trial step with the azimuth wrapped into [0, 180) and clamped to the
  * bounds, accepted when chi2 decreases.  iters trial steps are taken.
  *   params_inout  dev double [npix][M]
  *   chi2_out      dev double [npix]: FP64 chi2 of the final parameters

@@ -4,9 +4,9 @@
 // Jacobian in the problem's precision (FP32 for float cubes), per-lane partial
 // sums of J^T W^2 J and J^T W^2 r and their warp reduction in the same
 // precision (the FP32 Jacobian bounds their accuracy; GB300's FP64 rate is a
-// small fraction of its FP32 rate), the damped Cholesky solve in FP64 (lane 0,
-// in shared memory), and a trial synthesis whose FP64-summed chi2 decides
-// acceptance (Levenberg 1944, Marquardt 1963).
+// small fraction of its FP32 rate), the damped Cholesky solve in FP64 shared
+// by the warp (lane i holds row i of the factor), and a trial synthesis whose
+// FP64-summed chi2 decides acceptance (Levenberg 1944, Marquardt 1963).
 #include "kernels.h"
 #include "me_jac.cuh"
 #include "rng_device.cuh"
