@@ -479,21 +479,27 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
             cur ^= 1;
             s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior, nmid, nfar));
             if (COUNT) ++nfit;
-            // a13: worst-half Sobol restart
+            // a13: worst-half Sobol restart.  The individual of rank npop/2 + i
+            // takes Sobol point sobol_next + i; thread i evaluates it, so the
+            // new half fills whole warps (the idle half of the gene double
+            // buffer carries the individuals' indices).
             if (ga.nsamp > 0 && t % ga.nsamp == 0 && t < ga.ngen) {
                 __syncthreads();
                 const int rank = stable_rank<R>(s_fit, npop, k);
+                int *s_ridx = (int *)(s_genes + (cur ^ 1) * npop * M);
+                if (rank >= npop / 2) s_ridx[rank - npop / 2] = k;
                 __syncthreads();
-                if (rank >= npop / 2) {
-                    const uint64_t n = sobol_next + (uint64_t)(rank - npop / 2);
+                if (k < npop / 2) {
+                    const int kr = s_ridx[k];
+                    const uint64_t n = sobol_next + (uint64_t)k;
                     uint16_t *s_c = s_genes + cur * npop * M;
 #pragma unroll
                     for (int d = 0; d < M; ++d) {
                         g[d] = (uint16_t)(sobol_point(n, d) >> 16);
-                        s_c[k * M + d] = g[d];
+                        s_c[kr * M + d] = g[d];
                         p[d] = GaDecode<R>::get(D, d, g[d]);
                     }
-                    s_fit[k] = clean_fit(
+                    s_fit[kr] = clean_fit(
                         fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior, nmid, nfar));
                     if (COUNT) ++nfit;
                 }
