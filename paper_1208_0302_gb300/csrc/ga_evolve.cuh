@@ -139,9 +139,10 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
             doff2[3] = make_float2(d1.z, d1.w);
         }
         const bool y_real = 2 * q + 1 < nl;
-        const Stokes4x2 m = me_point_x2<NL, COUNT, PAT, FILL>(geo, doff2, he, nlines, y_real, cnt, pb.line);
-        float2 rI = sub2(make_float2(o0.x, o0.y), m.I), rQ = sub2(make_float2(o0.z, o0.w), m.Q);
-        float2 rU = sub2(make_float2(o1.x, o1.y), m.U), rV = sub2(make_float2(o1.z, o1.w), m.V);
+        const Stokes4x2 ob = {make_float2(o0.x, o0.y), make_float2(o0.z, o0.w), make_float2(o1.x, o1.y),
+                              make_float2(o1.z, o1.w)};
+        const Stokes4x2 rr = resid_x2<NL, COUNT, PAT, FILL>(geo, doff2, ob, he, nlines, y_real, cnt, pb.line);
+        float2 rI = rr.I, rQ = rr.Q, rU = rr.U, rV = rr.V;
         if (!y_real) rI.y = rQ.y = rU.y = rV.y = 0.f;  // padded partner
         sI = fma2(rI, rI, sI);
         sQ = fma2(rQ, rQ, sQ);

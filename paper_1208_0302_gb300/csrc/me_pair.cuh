@@ -228,13 +228,14 @@ __device__ __forceinline__ void triplet_acc(float2 xb, float2 v, float2 xr, cons
     Di = fma2(q, wy, Di);
 }
 
-// Stokes vectors at two wavelength points.  doff2[l] holds (lambda_j -
+// Residuals o - Stokes at two wavelength points (the synthesis of Section
+// 4.1 and the difference of Eq. chisq).  doff2[l] holds (lambda_j -
 // lambda0_l, lambda_{j+1} - lambda0_l).  FILL mixes in the field-free
 // profile with the fill fraction (Section 4.2, see fill_mix).
 template <int NL, bool COUNT, bool PAT, bool FILL = false>
-__device__ __forceinline__ Stokes4x2 me_point_x2(const Geo<float> &g, const float2 *doff2,
-                                                 const float *half_eta, int nlines, bool y_real,
-                                                 EvalCount &ncount, const KLine *lines)
+__device__ __forceinline__ Stokes4x2 resid_x2(const Geo<float> &g, const float2 *doff2, const Stokes4x2 &o,
+                                              const float *half_eta, int nlines, bool y_real,
+                                              EvalCount &ncount, const KLine *lines)
 {
     // per-line profile sums: P, Pi = sum q phi_p, q psi_p; Sg, Sgi = sum q (phi_b
     // + phi_r), q (psi_b + psi_r); Dd, Di = sum q (phi_r - phi_b), q (psi_r - psi_b);
@@ -292,20 +293,21 @@ __device__ __forceinline__ Stokes4x2 me_point_x2(const Geo<float> &g, const floa
     const float2 f = mul2(f2(g.muS1), rcp2(Delta));
     const float2 A = fma2(eI2, T, mul2(Ti, Pi));
     const float2 eIC = mul2(eI, fma2(Dd, Ti, neg2(mul2(T, Di))));
-    Stokes4x2 s;
-    s.I = fma2(mul2(f, eI), G, f2(g.S0));
-    s.Q = mul2(neg2(f), fma2(f2(g.kQ), A, mul2(f2(g.kUV), eIC)));
-    s.U = mul2(neg2(f), fma2(f2(g.kU), A, neg2(mul2(f2(g.kQV), eIC))));
-    s.V = mul2(mul2(neg2(f), f2(g.kV)), fma2(eI2, Dd, mul2(Di, Pi)));
+    // Q, U, V = -f X: the residual o - (-f X) is one FMA, f X + o.  FILL
+    // scales the polarised model by alpha and mixes the field-free I.
+    const float2 fq = FILL ? mul2(f, f2(g.alpha)) : f;
+    Stokes4x2 r;
     if (FILL) {
         const float2 inm = mul2(f2(g.muS1), rcp2(fma2(f2(2.0f * g.eta0), P0, f2(1.0f))));
-        const float2 al = f2(g.alpha), om = f2(1.0f - g.alpha);
-        s.I = fma2(al, sub2(s.I, f2(g.S0)), fma2(om, inm, f2(g.S0)));
-        s.Q = mul2(al, s.Q);
-        s.U = mul2(al, s.U);
-        s.V = mul2(al, s.V);
+        const float2 base = fma2(f2(1.0f - g.alpha), inm, f2(g.S0));
+        r.I = sub2(o.I, fma2(mul2(fq, eI), G, base));
+    } else {
+        r.I = sub2(o.I, fma2(mul2(f, eI), G, f2(g.S0)));
     }
-    return s;
+    r.Q = fma2(fq, fma2(f2(g.kQ), A, mul2(f2(g.kUV), eIC)), o.Q);
+    r.U = fma2(fq, fma2(f2(g.kU), A, neg2(mul2(f2(g.kQV), eIC))), o.U);
+    r.V = fma2(mul2(fq, f2(g.kV)), fma2(eI2, Dd, mul2(Di, Pi)), o.V);
+    return r;
 }
 
 }  // namespace genesis

@@ -109,6 +109,15 @@ def test_ga_fp64_two_line_matches_oracle(gpu, orc):
     _ga_compare(gpu, orc, gi.two_line_spec(), "f64", 37, 128, 24, 1e-10, seed=2, pid0=65000)
 
 
+@pytest.mark.parametrize("npop", [32, 512, 1024])
+def test_ga_fp64_population_sizes_match_oracle(gpu, orc, npop):
+    """The smallest population (the restarted half is 16 threads of one warp)
+    and the large-population instantiation (npop > 256), FP64, with three
+    restarts (ngen 12, N_samp 3)."""
+    spec = gi.one_line_spec(n_lambda=48)
+    _ga_compare(gpu, orc, spec, "f64", 12, npop, 12, 1e-10, seed=6, pid0=7)
+
+
 def test_ga_fp32_short_runs_match_oracle(gpu, orc):
     """FP32 evaluation: decisions separated by > 1e-4 relative are exact."""
     _ga_compare(gpu, orc, gi.two_line_spec(), "f32", 64, 64, 0, 1e-4, seed=3, frac_min=0.7)
