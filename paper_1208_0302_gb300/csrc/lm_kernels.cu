@@ -70,12 +70,15 @@ __device__ double lm_chi2(const KProblem &pb, int nlines, int nl, const double *
     return tot / (double)(4 * nl - M);
 }
 
-struct LmWarpSmem {  // M x M matrices stored with row stride M
-    double A[ME_NPAR_MAX * ME_NPAR_MAX];
+// One warp's shared state; M x M matrices stored with row stride M.  The
+// normal equations A, g keep the precision R they were summed in (the solve
+// widens each element as it reads it).
+template <class R> struct LmWarpSmem {
     double N[ME_NPAR_MAX * ME_NPAR_MAX];
-    double g[ME_NPAR_MAX];
     double x[ME_NPAR_MAX];
     double w2[4];
+    R A[ME_NPAR_MAX * ME_NPAR_MAX];
+    R g[ME_NPAR_MAX];
 };
 
 // Warp-cooperative Cholesky factorisation in FP64 of an M x M symmetric
@@ -110,27 +113,27 @@ __device__ __forceinline__ bool warp_cholesky(RowFn a, double (&L)[M], double (&
 // Returns false, on every lane, if no step was found (also when A has no
 // positive diagonal); the step lands in W.x.  All lanes of the warp must
 // call it together.
-template <int M>
-__device__ bool warp_damped_solve(LmWarpSmem &W, unsigned free_mask, double &lam)
+template <int M, class R>
+__device__ bool warp_damped_solve(LmWarpSmem<R> &W, unsigned free_mask, double &lam)
 {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int row = lane < M ? lane : 0;
     const bool free_row = lane < M && ((free_mask >> row) & 1u);
-    const double aii = free_row ? W.A[row * M + row] : 0.0;
+    const double aii = free_row ? (double)W.A[row * M + row] : 0.0;
     double dmax = aii;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) dmax = fmax(dmax, __shfl_xor_sync(full, dmax, off));
     if (!(dmax > 0.0)) return false;
     const double floor_d = 1e-12 * dmax;
     const double dscale = aii > floor_d ? aii : floor_d;
-    const double grow = free_row ? W.g[row] : 0.0;
+    const double grow = free_row ? (double)W.g[row] : 0.0;
     for (int tries = 0; tries < 30; ++tries) {
         const double drow = fma(lam, dscale, aii);  // this row's damped diagonal
         double L[M], rinv[M];
         const bool ok = warp_cholesky<M>(
             [&](int j) {
-                return lane == j ? drow : ((free_row && ((free_mask >> j) & 1u)) ? W.A[row * M + j] : 0.0);
+                return lane == j ? drow : ((free_row && ((free_mask >> j) & 1u)) ? (double)W.A[row * M + j] : 0.0);
             },
             L, rinv);
         if (!ok) {
@@ -167,8 +170,8 @@ __device__ bool warp_damped_solve(LmWarpSmem &W, unsigned free_mask, double &lam
 
 // Weights of one pixel into w2 (squared): the caller's, or Section 4.5
 // inverse-max in FP64.  Every lane gets the result.
-template <class RO>
-__device__ void lm_weights(const RO *o, int nl, const double *w_user, int pix, LmWarpSmem &W, double w2[4])
+template <class RO, class R>
+__device__ void lm_weights(const RO *o, int nl, const double *w_user, int pix, LmWarpSmem<R> &W, double w2[4])
 {
     const int lane = threadIdx.x & 31;
     if (w_user) {
@@ -211,10 +214,10 @@ __device__ void lm_weights(const RO *o, int nl, const double *w_user, int pix, L
 
 // Normal equations at p: W.A = J^T W^2 J (full M x M) and W.g = J^T W^2 r,
 // per-lane partial sums in R over the lane's wavelengths, warp sums in R,
-// stored in FP64 for the solve.
+// stored in R (the solve widens them to FP64).
 template <class R, class RO, int NL, int M = ME_NPAR>
 __device__ void lm_normal(const KProblem &pb, int nlines, int nl, const double *p, double mu,
-                          const RO *o, const R *s_doff, const R *he, const R *w2r, LmWarpSmem &W)
+                          const RO *o, const R *s_doff, const R *he, const R *w2r, LmWarpSmem<R> &W)
 {
     const int lane = threadIdx.x & 31;
     R pr[M];
@@ -251,11 +254,11 @@ __device__ void lm_normal(const KProblem &pb, int nlines, int nl, const double *
     int t = 0;
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-        const double gv = (double)warp_sum(gacc[a]);
+        const R gv = warp_sum(gacc[a]);
         if (lane == 0) W.g[a] = gv;
 #pragma unroll
         for (int b = 0; b <= a; ++b) {
-            const double v = (double)warp_sum(Aacc[t++]);
+            const R v = warp_sum(Aacc[t++]);
             if (lane == 0) {
                 W.A[a * M + b] = v;
                 W.A[b * M + a] = v;
@@ -272,8 +275,8 @@ k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const 
      double *__restrict__ params, const KSub sub)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    LmWarpSmem *s_w = (LmWarpSmem *)smem;
-    R *s_he = (R *)(smem + sizeof(LmWarpSmem) * kLmWarps);
+    LmWarpSmem<R> *s_w = (LmWarpSmem<R> *)smem;
+    R *s_he = (R *)(smem + sizeof(LmWarpSmem<R>) * kLmWarps);
     R *s_doff = s_he + ME_MAX_LINES;
     const int nl = pb.n_lambda, nlines = NL > 0 ? NL : pb.n_lines;
     for (int i = threadIdx.x; i < nlines * nl; i += blockDim.x) {
@@ -289,7 +292,7 @@ k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const 
     if (b >= (sub.count ? min(*sub.count, npix) : npix)) return;
     const int pix = sub.index ? sub.index[b] : b;
     if (pix < 0 || pix >= npix) return;  // a bad index skips the warp, uniformly
-    LmWarpSmem &W = s_w[warp];
+    LmWarpSmem<R> &W = s_w[warp];
     const RO *o = obs + (size_t)pix * 4 * nl;
     R he[ME_MAX_LINES];
 #pragma unroll
@@ -314,17 +317,24 @@ k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const 
             need = false;
         }
         if (!warp_damped_solve<M>(W, lm.free_mask, lam)) break;
+        // trial point: lane d forms parameter d (the azimuth wrapped into
+        // [0, 180), then the bounds), and the warp gathers the vector
         double q[M];
-#pragma unroll
-        for (int d = 0; d < M; ++d) q[d] = p[d] + W.x[d];
         {
-            double c = fmod(q[2], 180.0);
-            if (c < 0.0) c += 180.0;
-            if (c >= 180.0) c -= 180.0;
-            q[2] = c;
-        }
+            const int row = lane < M ? lane : 0;
+            double pl = p[0];
 #pragma unroll
-        for (int d = 0; d < M; ++d) q[d] = fmin(fmax(q[d], lm.lo[d]), lm.hi[d]);
+            for (int d = 1; d < M; ++d) pl = (lane == d) ? p[d] : pl;
+            double qv = pl + W.x[row];
+            if (lane == 2 && !(qv >= 0.0 && qv < 180.0)) {
+                qv = fmod(qv, 180.0);
+                if (qv < 0.0) qv += 180.0;
+                if (qv >= 180.0) qv -= 180.0;
+            }
+            qv = fmin(fmax(qv, lm.lo[row]), lm.hi[row]);
+#pragma unroll
+            for (int d = 0; d < M; ++d) q[d] = __shfl_sync(0xffffffffu, qv, d);
+        }
         const double c2 = lm_chi2<R, RO, NL, M>(pb, nlines, nl, q, mu, o, s_doff, he, w2);
         __syncwarp();
         if (c2 < chi2) {
@@ -358,8 +368,8 @@ k_lm_sigma(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
            const double *__restrict__ params, double *__restrict__ sigma)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    LmWarpSmem *s_w = (LmWarpSmem *)smem;
-    R *s_he = (R *)(smem + sizeof(LmWarpSmem) * kLmWarps);
+    LmWarpSmem<R> *s_w = (LmWarpSmem<R> *)smem;
+    R *s_he = (R *)(smem + sizeof(LmWarpSmem<R>) * kLmWarps);
     R *s_doff = s_he + ME_MAX_LINES;
     const int nl = pb.n_lambda, nlines = NL > 0 ? NL : pb.n_lines;
     for (int i = threadIdx.x; i < nlines * nl; i += blockDim.x) {
@@ -372,7 +382,7 @@ k_lm_sigma(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int pix = blockIdx.x * kLmWarps + warp;
     if (pix >= npix) return;
-    LmWarpSmem &W = s_w[warp];
+    LmWarpSmem<R> &W = s_w[warp];
     const RO *o = obs + (size_t)pix * 4 * nl;
     R he[ME_MAX_LINES];
 #pragma unroll
@@ -391,7 +401,7 @@ k_lm_sigma(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
     // H = (2/nu) A;  [H^-1]_ii = (nu/2) [A^-1]_ii = (nu/2) || L^-1 e_i ||^2
     double L[M], rinv[M];
     const int row = lane < M ? lane : 0;
-    const bool ok = warp_cholesky<M>([&](int j) { return lane < M ? W.A[row * M + j] : 0.0; }, L, rinv);
+    const bool ok = warp_cholesky<M>([&](int j) { return lane < M ? (double)W.A[row * M + j] : 0.0; }, L, rinv);
     if (ok && lane < M) {
 #pragma unroll
         for (int k = 0; k < M; ++k) W.N[row * M + k] = L[k];
@@ -423,7 +433,7 @@ cudaError_t sigma_t(const KProblem &pb, const void *obs, const double *w, const 
                     const double *params, double *sigma, cudaStream_t st)
 {
     const int nlines = NL > 0 ? NL : pb.n_lines;
-    const size_t smem = sizeof(LmWarpSmem) * kLmWarps + sizeof(R) * (ME_MAX_LINES + (size_t)nlines * pb.n_lambda);
+    const size_t smem = sizeof(LmWarpSmem<R>) * kLmWarps + sizeof(R) * (ME_MAX_LINES + (size_t)nlines * pb.n_lambda);
     auto kern = k_lm_sigma<R, RO, NL, M>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -437,7 +447,7 @@ cudaError_t lm_t(const KProblem &pb, const KLm &lm, const void *obs, const doubl
                  const double *mu_px, int npix, double *params, cudaStream_t st, KSub sub)
 {
     const int nlines = NL > 0 ? NL : pb.n_lines;
-    const size_t smem = sizeof(LmWarpSmem) * kLmWarps + sizeof(R) * (ME_MAX_LINES + (size_t)nlines * pb.n_lambda);
+    const size_t smem = sizeof(LmWarpSmem<R>) * kLmWarps + sizeof(R) * (ME_MAX_LINES + (size_t)nlines * pb.n_lambda);
     auto kern = k_lm<R, RO, NL, M>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
