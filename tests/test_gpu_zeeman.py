@@ -76,3 +76,7 @@ def test_full_pattern_ga_fp32_and_polish(gpu, orc):
     # 12 components for 6301.5 + 3 for 6302.5 per wavelength point
     assert counts["weideman"] + counts["mid"] + counts["cf"] + counts["far"] == counts["points"] * 15
     assert min(counts["weideman"], counts["mid"], counts["cf"], counts["far"]) > 0
+    # syntheses: the initial population, every child of every generation and
+    # the restarted half at each generation t < ngen with t % nsamp == 0
+    # (nsamp = ngen // 4 = 1 here, so t = 1, 2, 3)
+    assert counts["syntheses"] == 32 * (64 * (4 + 1) + 3 * 32)
