@@ -209,11 +209,19 @@ k_chi2_f64(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
         }
     }
     constexpr int M = kNpar<FILL>;
-    double p[M];
+    // the pixel's geometry, built once per block (FP64 trigonometry and
+    // divisions) and read by every thread from shared memory
+    __shared__ __align__(16) unsigned char s_geo_raw[sizeof(Geo<double>)];
+    Geo<double> &s_geo = *reinterpret_cast<Geo<double> *>(s_geo_raw);
+    if (threadIdx.x == 0) {
+        double p[M];
 #pragma unroll
-    for (int d = 0; d < M; ++d) p[d] = params[(size_t)pix * M + d];
-    const double mu = mu_px ? mu_px[pix] : pb.mu;
-    const Geo<double> g = make_geo<double, 0, FILL>(pb, nlines, p, mu);
+        for (int d = 0; d < M; ++d) p[d] = params[(size_t)pix * M + d];
+        const double mu = mu_px ? mu_px[pix] : pb.mu;
+        s_geo = make_geo<double, 0, FILL>(pb, nlines, p, mu);
+    }
+    __syncthreads();
+    const Geo<double> &g = s_geo;
     double he[ME_MAX_LINES];
 #pragma unroll
     for (int l = 0; l < ME_MAX_LINES; ++l) he[l] = l < nlines ? pb.line[l].half_eta : 0.0;
