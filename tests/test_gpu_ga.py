@@ -124,6 +124,24 @@ def test_ga_fp32_short_runs_match_oracle(gpu, orc):
     _ga_compare(gpu, orc, gi.two_line_spec(), "f32", 64, 64, 2, 1e-4, seed=4, frac_min=0.3)
 
 
+def test_ga_fp32_partial_warp_restarts(gpu, orc):
+    """FP32, npop 32: each restart evaluates 16 individuals, so the w(z)
+    branch votes run over half a warp.  Results stay in bounds, finite,
+    consistent with me_chi2 and independent of the batch."""
+    spec = gi.two_line_spec()
+    truth, obs = make_obs(orc, spec, 40, seed=12)
+    pb = gpu.Problem.from_spec(spec, "f32")
+    ob = torch.tensor(obs, device="cuda", dtype=torch.float32)
+    ga = gpu.GaSettings(npop=32, ngen=16, seed=4)   # restarts at t = 4, 8, 12
+    best, chi2 = gpu.ga_invert_batch(pb, ob, gi.PRIOR_LO, gi.PRIOR_HI, ga, pixel_id0=50)
+    b2, c2 = gpu.ga_invert_batch(pb, ob[7:19].contiguous(), gi.PRIOR_LO, gi.PRIOR_HI, ga, pixel_id0=57)
+    assert torch.equal(best[7:19], b2) and torch.equal(chi2[7:19], c2)
+    bn = best.cpu().numpy()
+    assert np.all(np.isfinite(chi2.cpu().numpy()))
+    assert np.all(bn >= gi.PRIOR_LO) and np.all(bn <= gi.PRIOR_HI)
+    assert torch.equal(gpu.me_chi2(pb, ob, best), chi2)
+
+
 def test_ga_batch_invariance_and_consistency(gpu, orc):
     """A pixel's result depends only on (obs, pixel id, seed), not on the batch."""
     spec = gi.two_line_spec()
