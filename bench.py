@@ -40,7 +40,7 @@ KERNELS_PER_STEP = 4  # GA evolve, FP64 chi2, L-M, FP64 chi2
 # dram__bytes_write.sum 0, divided by 1024; traffic grows in proportion to
 # pixels: each block reads its pixel's cube row once).  Set to None whenever
 # the kernel changes, until it is captured again.
-GA_DRAM_BYTES_PER_PIXEL = (2252544 + 0) / 1024
+GA_DRAM_BYTES_PER_PIXEL = None  # re-measure after a kernel change
 
 
 def parse():
@@ -140,13 +140,12 @@ def flop_model(nlines):
     synthetic division, 95), in the middle shell (5th convergent, 45), in the
     continued-fraction region (3rd convergent, 31) and in the far field
     (two-node approximant, 17); and per wavelength
-    point 22 per line for the component arguments and profile sums, 52 for K
-    and its closed-form inverse, 12.25 for the chi2 of four residuals (a
-    subtraction and an FMA each, plus a block addition per 16 points and
-    Stokes parameter).  Each point's evaluations are classified by its own region;
+    point 22 per line for the component arguments and profile sums, 36 for K
+    and its closed-form inverse, 20 for the four Stokes values formed into
+    their residuals and 8 for the residuals' squares in the running sums.  Each point's evaluations are classified by its own region;
     branch tests, votes and work a pair or warp does beyond that are not
     counted."""
-    return {"weideman": 95.0, "mid": 45.0, "cf": 31.0, "far": 17.0, "point": 22.0 * nlines + 64.25}
+    return {"weideman": 95.0, "mid": 45.0, "cf": 31.0, "far": 17.0, "point": 22.0 * nlines + 64.0}
 
 
 def run_ours(args):

@@ -228,8 +228,8 @@ int ga_invert_batch(const me_problem *pb, const void *obs, const double *w,
  * counts dev uint64[5] receives (added to its contents) the number of
  * syntheses (fitness evaluations), of Faddeeva evaluations by Weideman's
  * series (|z|^2 <= 22), of all Faddeeva evaluations, of those in the far
- * field (|z|^2 > 484) and of those in the middle shell (22 < |z|^2 <= 36;
- * the rest, 36 < |z|^2 <= 484, use the 3rd convergent), each real wavelength
+ * field (|z|^2 > 360) and of those in the middle shell (22 < |z|^2 <= 36;
+ * the rest, 36 < |z|^2 <= 360, use the 3rd convergent), each real wavelength
  * point classified by its own region (the algorithm's work, whatever branch a
  * point's pair or warp took).
  * The arithmetic and the result `best` are those of ga_invert_batch; the

@@ -5,7 +5,7 @@
 // of the GA's fitness loop (an issue-bound loop of FP32 arithmetic).
 //
 // Branches are uniform across the warp: a Zeeman component takes the far-field
-// approximant when every lane's pair of points is beyond |z|^2 = 484, the
+// approximant when every lane's pair of points is beyond |z|^2 = 360, the
 // continued fraction when every pair is beyond |z|^2 = 36, and Weideman's
 // series otherwise (each branch is accurate wherever it is taken: the series
 // everywhere: |error| <= 4.3e-8 for |x| <= 1e4, 0 <= y <= 1), so a point's value can depend
@@ -72,8 +72,9 @@ constexpr float kMidR2 = 22.0f;
 
 // Far field (|z|^2 > kFarR2): the first non-trivial convergent of the Laplace
 // continued fraction (the two-node Gauss-Hermite rule), w = (i/sqrt(pi)) z /
-// (z^2 - 1/2); |error| <= 6e-8 in FP32 there.
-constexpr float kFarR2 = 484.0f;
+// (z^2 - 1/2); |error| <= 1.23e-7 in FP32 there (at the boundary; it falls
+// as |z|^-5 outward), within the 1.3e-7 of the 3rd convergent at |z|^2 = 36.
+constexpr float kFarR2 = 360.0f;
 __device__ __forceinline__ void fad_far2(float2 x, float y, float a2, float2 &wx, float2 &wy)
 {
     const float2 ux = fma2(x, x, f2(-a2));
