@@ -21,6 +21,15 @@ cudaError_t upload_tables_lm(const HostTables &t)
 namespace {
 
 constexpr int kLmWarps = 4;
+// Blocks per SM the register allocation of the FP32 instantiations must
+// allow: 4 (128 registers) spills a little of the Jacobian's partial sums
+// but gives the latency-bound warps twice the company of the unbounded 255
+// registers (10-iteration polish 5 % faster, 40-iteration prefit 7 %, the
+// uncertainty 20 % on GB300).  FP64 instantiations keep the compiler's
+// choice.  Build option: GENESIS_LM_MINB.
+#ifndef GENESIS_LM_MINB
+#define GENESIS_LM_MINB 4
+#endif
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -269,7 +278,7 @@ __device__ void lm_normal(const KProblem &pb, int nlines, int nl, const double *
 }
 
 template <class R, class RO, int NL, int M = ME_NPAR>
-__global__ void __launch_bounds__(kLmWarps * 32)
+__global__ void __launch_bounds__(kLmWarps * 32, sizeof(R) == 4 ? GENESIS_LM_MINB : 1)
 k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const RO *__restrict__ obs,
      const double *__restrict__ w_user, const double *__restrict__ mu_px, int npix,
      double *__restrict__ params, const KSub sub)
@@ -362,7 +371,7 @@ k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const 
 // forms [H^-1]_ii).  A parameter without influence (singular H) gets
 // +infinity on every parameter of the pixel.
 template <class R, class RO, int NL, int M = ME_NPAR>
-__global__ void __launch_bounds__(kLmWarps * 32)
+__global__ void __launch_bounds__(kLmWarps * 32, sizeof(R) == 4 ? GENESIS_LM_MINB : 1)
 k_lm_sigma(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
            const double *__restrict__ w_user, const double *__restrict__ mu_px, int npix,
            const double *__restrict__ params, double *__restrict__ sigma)
