@@ -257,6 +257,7 @@ template <class R> struct Geo {
     // the all-exterior test of a triplet |v| > t_ext + |v_B|
     R tfar, text, tmid;
     R t3[ME_MAX_LINES];
+    R t3far[ME_MAX_LINES];  // pair path: the all-far test of a triplet |v| > t_far + |v_B|
     unsigned vmask;     // pair path: the lanes that evaluate together (votes)
     R shift[ME_MAX_LINES];  // lambda0 v_LOS / c [A]
     R invD[ME_MAX_LINES];   // 1 / Doppler width [1/A]

@@ -127,6 +127,9 @@ __device__ __forceinline__ void pair_thresholds(Geo<float> &g, int nlines)
 #pragma unroll
     for (int l = 0; l < ME_MAX_LINES; ++l)
         g.t3[l] = (l < nlines && g.text >= 0.0f) ? g.text + fabsf(g.vB[l]) : -1.0f;
+#pragma unroll
+    for (int l = 0; l < ME_MAX_LINES; ++l)
+        g.t3far[l] = (l < nlines && g.tfar >= 0.0f) ? g.tfar + fabsf(g.vB[l]) : -1.0f;
 }
 // Nearer |x| of a pair: the pair is beyond a threshold t when this is.
 __device__ __forceinline__ float pair_min_abs(float2 x) { return fminf(fabsf(x.x), fabsf(x.y)); }
@@ -204,25 +207,35 @@ __device__ __forceinline__ void pattern_profiles_x2(const KLine &ln, float2 dinv
     }
 }
 
+// One component at a known level: 2 = every lane's pair is in the far
+// field, 1 = beyond the continued-fraction threshold, 0 = anywhere.
+template <int LEVEL>
+__device__ __forceinline__ void fad_level(float2 x, const Geo<float> &g, float2 &wx, float2 &wy)
+{
+    if (LEVEL == 2) fad_far2(x, g.a, g.a2, wx, wy);
+    else if (LEVEL == 1) fad_pair_ext(x, g, wx, wy);
+    else fad_pair(x, g, wx, wy);
+}
+
 // One effective triplet's contribution to a pair's profile sums, each
 // component added as soon as it is evaluated (EXT: every lane's triplet is
-// already exterior).
-template <bool EXT, bool FILL>
+// exterior, 2 when it is in the far field as a whole).
+template <int EXT, bool FILL>
 __device__ __forceinline__ void triplet_acc(float2 xb, float2 v, float2 xr, const Geo<float> &g, float2 q,
                                             float2 &P, float2 &Pim, float2 &Sg, float2 &Sgi, float2 &Dd,
                                             float2 &Di, float2 &P0)
 {
     float2 wx, wy;
-    if (EXT) fad_pair_ext(xb, g, wx, wy); else fad_pair(xb, g, wx, wy);
+    fad_level<EXT>(xb, g, wx, wy);
     Sg = fma2(q, wx, Sg);
     Sgi = fma2(q, wy, Sgi);
     Dd = fma2(neg2(q), wx, Dd);
     Di = fma2(neg2(q), wy, Di);
-    if (EXT) fad_pair_ext(v, g, wx, wy); else fad_pair(v, g, wx, wy);
+    fad_level<EXT>(v, g, wx, wy);
     if (FILL) P0 = fma2(q, wx, P0);  // the pi profile is unshifted
     P = fma2(q, wx, P);
     Pim = fma2(q, wy, Pim);
-    if (EXT) fad_pair_ext(xr, g, wx, wy); else fad_pair(xr, g, wx, wy);
+    fad_level<EXT>(xr, g, wx, wy);
     Sg = fma2(q, wx, Sg);
     Sgi = fma2(q, wy, Sgi);
     Dd = fma2(q, wx, Dd);
@@ -273,10 +286,15 @@ __device__ __forceinline__ Stokes4x2 resid_x2(const Geo<float> &g, const float2 
                 count_pair(xr, g.a2, y_real, ncount);
             }
             const float2 q = f2(half_eta[l]);
-            if (warp_all(pair_min_abs(v) > g.t3[l], g.vmask))
-                triplet_acc<true, FILL>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
-            else
-                triplet_acc<false, FILL>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
+            const float mv = pair_min_abs(v);
+            if (warp_all(mv > g.t3[l], g.vmask)) {
+                if (warp_all(mv > g.t3far[l], g.vmask))
+                    triplet_acc<2, FILL>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
+                else
+                    triplet_acc<1, FILL>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
+            } else {
+                triplet_acc<0, FILL>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
+            }
         }
     }
     // closed form of K^-1 e (see me_point), with G = eI^2 + rho^2 shared by
