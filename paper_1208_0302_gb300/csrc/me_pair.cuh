@@ -5,9 +5,12 @@
 // of the GA's fitness loop (an issue-bound loop of FP32 arithmetic).
 //
 // Branches are uniform across the warp: a Zeeman component takes the far-field
-// approximant when every lane's pair of points is beyond |z|^2 = 360, the
-// continued fraction when every pair is beyond |z|^2 = 36, and Weideman's
-// series otherwise (each branch is accurate wherever it is taken: the series
+// approximant when every lane's pair of points is beyond |z|^2 = 360, the 3rd
+// convergent of the continued fraction when every pair is beyond |z|^2 = 36,
+// the 5th beyond 22, and Weideman's series otherwise.  An effective triplet
+// is tested as a whole first: wholly far, all three take the far field;
+// wholly beyond 36, all three take the 3rd convergent (each branch is
+// accurate wherever it is taken: the series
 // everywhere: |error| <= 4.3e-8 for |x| <= 1e4, 0 <= y <= 1), so a point's value can depend
 // on its partner's and its warp's regions, always within the FP32 error budget.
 // A warp-uniform choice costs one branch where a per-lane choice would run
@@ -152,12 +155,6 @@ __device__ __forceinline__ void fad_pair(float2 x, const Geo<float> &g, float2 &
     else if (warp_all(m > g.tmid, g.vmask)) fad_cf2<5>(x, g.a, g.a2, wx, wy);
     else fad_int2(x, g.a, wx, wy);
 }
-// The same when every lane's component is already known to be exterior.
-__device__ __forceinline__ void fad_pair_ext(float2 x, const Geo<float> &g, float2 &wx, float2 &wy)
-{
-    if (warp_all(pair_min_abs(x) > g.tfar, g.vmask)) fad_far2(x, g.a, g.a2, wx, wy);
-    else fad_ext2(x, g.a, g.a2, wx, wy);
-}
 
 // Work counts of the algorithm proper: each real point's evaluation classified
 // by its own region (Weideman interior, middle shell, continued fraction, far
@@ -208,12 +205,14 @@ __device__ __forceinline__ void pattern_profiles_x2(const KLine &ln, float2 dinv
 }
 
 // One component at a known level: 2 = every lane's pair is in the far
-// field, 1 = beyond the continued-fraction threshold, 0 = anywhere.
+// field, 1 = beyond the continued-fraction threshold (the 3rd convergent,
+// accurate there, also where a component is already far: cheaper than
+// testing each component), 0 = anywhere.
 template <int LEVEL>
 __device__ __forceinline__ void fad_level(float2 x, const Geo<float> &g, float2 &wx, float2 &wy)
 {
     if (LEVEL == 2) fad_far2(x, g.a, g.a2, wx, wy);
-    else if (LEVEL == 1) fad_pair_ext(x, g, wx, wy);
+    else if (LEVEL == 1) fad_ext2(x, g.a, g.a2, wx, wy);
     else fad_pair(x, g, wx, wy);
 }
 
