@@ -9,7 +9,8 @@
 // convergent of the continued fraction when every pair is beyond |z|^2 = 36,
 // the 5th beyond 22, and Weideman's series otherwise.  An effective triplet
 // is tested as a whole first: wholly far, all three take the far field;
-// wholly beyond 36, all three take the 3rd convergent (each branch is
+// wholly beyond 36, all three take the 3rd convergent; otherwise (near a
+// line core) each component tests the regions from the inside out (each branch is
 // accurate wherever it is taken: the series
 // everywhere: |error| <= 4.3e-8 for |x| <= 1e4, 0 <= y <= 1), so a point's value can depend
 // on its partner's and its warp's regions, always within the FP32 error budget.
@@ -204,6 +205,17 @@ __device__ __forceinline__ void pattern_profiles_x2(const KLine &ln, float2 dinv
     }
 }
 
+// One component near a line core: the same branches tested from the inside
+// out, for components that mostly need the inner ones.
+__device__ __forceinline__ void fad_pair_in(float2 x, const Geo<float> &g, float2 &wx, float2 &wy)
+{
+    const float m = pair_min_abs(x);
+    if (!warp_all(m > g.tmid, g.vmask)) fad_int2(x, g.a, wx, wy);
+    else if (!warp_all(m > g.text, g.vmask)) fad_cf2<5>(x, g.a, g.a2, wx, wy);
+    else if (warp_all(m > g.tfar, g.vmask)) fad_far2(x, g.a, g.a2, wx, wy);
+    else fad_ext2(x, g.a, g.a2, wx, wy);
+}
+
 // One component at a known level: 2 = every lane's pair is in the far
 // field, 1 = beyond the continued-fraction threshold (the 3rd convergent,
 // accurate there, also where a component is already far: cheaper than
@@ -213,7 +225,7 @@ __device__ __forceinline__ void fad_level(float2 x, const Geo<float> &g, float2 
 {
     if (LEVEL == 2) fad_far2(x, g.a, g.a2, wx, wy);
     else if (LEVEL == 1) fad_ext2(x, g.a, g.a2, wx, wy);
-    else fad_pair(x, g, wx, wy);
+    else fad_pair_in(x, g, wx, wy);
 }
 
 // One effective triplet's contribution to a pair's profile sums, each
