@@ -227,8 +227,8 @@ int ga_invert_batch(const me_problem *pb, const void *obs, const double *w,
  * npop <= 256) run by a separate instantiation that also counts work:
  * counts dev uint64[5] receives (added to its contents) the number of
  * syntheses (fitness evaluations), of Faddeeva evaluations by Weideman's
- * series (|z|^2 <= 22), of all Faddeeva evaluations, of those in the far
- * field (|z|^2 > 360) and of those in the middle shell (22 < |z|^2 <= 36;
+ * series (|z|^2 <= 21), of all Faddeeva evaluations, of those in the far
+ * field (|z|^2 > 360) and of those in the middle shell (21 < |z|^2 <= 36;
  * the rest, 36 < |z|^2 <= 360, use the 3rd convergent), each real wavelength
  * point classified by its own region (the algorithm's work, whatever branch a
  * point's pair or warp took).

@@ -7,7 +7,7 @@
 // Branches are uniform across the warp: a Zeeman component takes the far-field
 // approximant when every lane's pair of points is beyond |z|^2 = 360, the 3rd
 // convergent of the continued fraction when every pair is beyond |z|^2 = 36,
-// the 5th beyond 22, and Weideman's series otherwise.  An effective triplet
+// the 5th beyond 21, and Weideman's series otherwise.  An effective triplet
 // is tested as a whole first: wholly far, all three take the far field;
 // wholly beyond 36, all three take the 3rd convergent; otherwise (near a
 // line core) each component tests the regions from the inside out (each branch is
@@ -71,8 +71,9 @@ __device__ __forceinline__ void fad_ext2(float2 x, float y, float a2, float2 &wx
     fad_cf2<FadCfg<float>::K>(x, y, a2, wx, wy);
 }
 // Middle shell kMidR2 < |z|^2 <= R2: the 5th convergent (six-node rule),
-// |error| <= 8e-8 there, about half the work of Weideman's series.
-constexpr float kMidR2 = 22.0f;
+// |error| <= 1.04e-7 there (at the boundary), about half the work of
+// Weideman's series.
+constexpr float kMidR2 = 21.0f;
 
 // Far field (|z|^2 > kFarR2): the first non-trivial convergent of the Laplace
 // continued fraction (the two-node Gauss-Hermite rule), w = (i/sqrt(pi)) z /
@@ -212,7 +213,6 @@ __device__ __forceinline__ void fad_pair_in(float2 x, const Geo<float> &g, float
     const float m = pair_min_abs(x);
     if (!warp_all(m > g.tmid, g.vmask)) fad_int2(x, g.a, wx, wy);
     else if (!warp_all(m > g.text, g.vmask)) fad_cf2<5>(x, g.a, g.a2, wx, wy);
-    else if (warp_all(m > g.tfar, g.vmask)) fad_far2(x, g.a, g.a2, wx, wy);
     else fad_ext2(x, g.a, g.a2, wx, wy);
 }
 
