@@ -4,20 +4,22 @@
 // instruction does the work of two scalar ones, which halves the issue slots
 // of the GA's fitness loop (an issue-bound loop of FP32 arithmetic).
 //
-// Branches are uniform across the warp: a Zeeman component takes the far-field
-// approximant when every lane's pair of points is beyond |z|^2 = 360, the 3rd
-// convergent of the continued fraction when every pair is beyond |z|^2 = 36,
-// the 5th beyond 21, and Weideman's series otherwise.  An effective triplet
-// is tested as a whole first: wholly far, all three take the far field;
-// wholly beyond 36, all three take the 3rd convergent; otherwise (near a
-// line core) each component tests the regions from the inside out (each branch is
-// accurate wherever it is taken: the series
-// everywhere: |error| <= 4.3e-8 for |x| <= 1e4, 0 <= y <= 1), so a point's value can depend
-// on its partner's and its warp's regions, always within the FP32 error budget.
-// A warp-uniform choice costs one branch where a per-lane choice would run
-// both for a mixed warp.  A region test is one comparison of the pair's nearer
-// |x| with a per-individual threshold, and the vote reuses the fitness call's
-// lane mask: the loop's issue slots, not its flops, set its speed.
+// Branches are uniform across the warp.  A Zeeman component takes the
+// far-field approximant when every lane's pair of points is beyond
+// |z|^2 = 360, the 3rd convergent of the continued fraction when every pair
+// is beyond |z|^2 = 36, the 5th beyond 21, and Weideman's series otherwise.
+// Each branch is accurate wherever it is taken: the convergents and the far
+// field to 1.3e-7 or better beyond their thresholds, the series everywhere
+// (4.3e-8 for |x| <= 1e4, 0 <= y <= 1).  A point's value can therefore depend
+// on its partner's and its warp's regions, always within that budget.
+// An effective triplet is tested as a whole first: wholly far, all three
+// components take the far field; wholly beyond 36, all three take the 3rd
+// convergent; otherwise (near a line core) each component tests the regions
+// from the inside out.  A warp-uniform choice costs one branch where a
+// per-lane choice would run both for a mixed warp.  A region test is one
+// comparison of the pair's nearer |x| with a per-individual threshold, and
+// the vote reuses the fitness call's lane mask: the loop's issue slots, not
+// its flops, set its speed.
 #pragma once
 
 #include "me_device.cuh"
