@@ -40,7 +40,7 @@ KERNELS_PER_STEP = 4  # GA evolve, FP64 chi2, L-M, FP64 chi2
 # dram__bytes_write.sum 0, divided by 1024; traffic grows in proportion to
 # pixels: each block reads its pixel's cube row once).  Set to None whenever
 # the kernel changes, until it is captured again.
-GA_DRAM_BYTES_PER_PIXEL = (2731008 + 0) / 1024
+GA_DRAM_BYTES_PER_PIXEL = None  # re-measure after a kernel change
 
 
 def parse():

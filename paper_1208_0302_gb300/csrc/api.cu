@@ -95,7 +95,7 @@ HostTables build_tables()
         const std::vector<double> a = weideman_coefficients(16, L);
         for (int n = 0; n <= 16; ++n) {
             t.fad.w32[n] = (float)a[n];
-            t.fad.w32x2[n] = make_float2((float)a[n], (float)a[n]);
+            t.fad.w32x2[n] = make_float2(2.0f * (float)a[n], 2.0f * (float)a[n]);
         }
         t.fad.L32 = (float)L;
     }

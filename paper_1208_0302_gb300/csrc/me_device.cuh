@@ -53,7 +53,7 @@ struct KProblem {
 // Weideman coefficient tables (filled per device at library initialisation).
 struct FaddeevaTables {
     float w32[17];     // Weideman a_1..a_16 (index n = 1..16), N = 16
-    float2 w32x2[17];  // the same, duplicated into both lanes for packed FP32x2 use
+    float2 w32x2[17];  // the same doubled (the series' factor 2, exact), in both lanes for packed FP32x2 use
     float L32;
     double w64[37];    // Weideman N = 36
     double L64;

@@ -10,8 +10,10 @@
 // is beyond |z|^2 = 36, the 5th beyond 21, and Weideman's series otherwise.
 // Each branch is accurate wherever it is taken: the convergents and the far
 // field to 1.3e-7 or better beyond their thresholds, the series everywhere
-// (4.3e-8 for |x| <= 1e4, 0 <= y <= 1).  A point's value can therefore depend
-// on its partner's and its warp's regions, always within that budget.
+// (truncation error 4.3e-8 for |x| <= 1e4, 0 <= y <= 1; near the line centre,
+// where |w| is about 1, FP32 rounding of the series is the larger term, about
+// 1e-6 relative).  A point's value can therefore depend on its partner's and
+// its warp's regions, always within that budget.
 // An effective triplet is tested as a whole first: wholly far, all three
 // components take the far field; wholly beyond 36, all three take the 3rd
 // convergent; otherwise (near a line core) each component tests the regions
@@ -102,10 +104,9 @@ __device__ __forceinline__ void fad_int2(float2 x, float y, float2 &wx, float2 &
     const float dx = L + y;
     const float2 inv = rcp2(fma2(x, x, f2(dx * dx)));
     const float2 rx = mul2(f2(dx), inv), ry = mul2(x, inv);
-    // Z = ((L - y) + i x) (rx + i ry)
-    const float mx = L - y;
-    const float2 Zx = fma2(f2(mx), rx, neg2(mul2(x, ry)));
-    const float2 Zy = fma2(f2(mx), ry, mul2(x, rx));
+    // Z = ((L - y) + i x) / ((L + y) - i x) = ((L^2 - y^2 - x^2) + i 2 L x) inv
+    const float2 Zx = mul2(fma2(neg2(x), x, f2((L - y) * dx)), inv);
+    const float2 Zy = mul2(ry, f2(2.0f * L));
     const float2 r = add2(Zx, Zx), sq = neg2(fma2(Zx, Zx, mul2(Zy, Zy)));
     float2 b2 = c_fad.w32x2[N];
     float2 b1 = fma2(r, b2, c_fad.w32x2[N - 1]);
@@ -118,8 +119,8 @@ __device__ __forceinline__ void fad_int2(float2 x, float y, float2 &wx, float2 &
     const float2 px = fma2(sq, b2, fma2(b1, Zx, c_fad.w32x2[1])), py = mul2(b1, Zy);
     const float2 r2x = fma2(rx, rx, neg2(mul2(ry, ry))), r2y = mul2(add2(rx, rx), ry);
     const float2 s = f2(0.56418958354775628695f);
-    wx = fma2(f2(2.0f), fma2(px, r2x, neg2(mul2(py, r2y))), mul2(rx, s));
-    wy = fma2(f2(2.0f), fma2(px, r2y, mul2(py, r2x)), mul2(ry, s));
+    wx = fma2(px, r2x, fma2(neg2(py), r2y, mul2(rx, s)));
+    wy = fma2(px, r2y, fma2(py, r2x, mul2(ry, s)));
 }
 
 
