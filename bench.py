@@ -36,11 +36,11 @@ WORKLOAD = "two-line Fe I 6301.5+6302.5 ME inversion, 256x256 px, 128 lambda, np
 NPOP, NGEN, LM_ITERS = 128, 200, 10
 KERNELS_PER_STEP = 4  # GA evolve, FP64 chi2, L-M, FP64 chi2
 # DRAM bytes (read + write) per pixel of one GA launch, from an ncu capture of
-# k_ga_evolve on the 1024-pixel two-line case (dram__bytes_read.sum 2731008 +
+# k_ga_evolve on the 1024-pixel two-line case (dram__bytes_read.sum 2524160 +
 # dram__bytes_write.sum 0, divided by 1024; traffic grows in proportion to
 # pixels: each block reads its pixel's cube row once).  Set to None whenever
 # the kernel changes, until it is captured again.
-GA_DRAM_BYTES_PER_PIXEL = None  # re-measure after a kernel change
+GA_DRAM_BYTES_PER_PIXEL = (2524160 + 0) / 1024
 
 
 def parse():
