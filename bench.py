@@ -137,7 +137,7 @@ def flop_model(nlines):
     counted from the source of the GA's fitness path (per call, without the
     per-individual invariants such as 2a or (L + a)^2), per unit: an
     evaluation of w(z) in the interior (Weideman N = 16 by real-quadratic
-    synthetic division, 95), in the middle shell (5th convergent, 45), in the
+    synthetic division, 91), in the middle shell (5th convergent, 45), in the
     continued-fraction region (3rd convergent, 31) and in the far field
     (two-node approximant, 17); and per wavelength
     point 22 per line for the component arguments and profile sums, 36 for K
@@ -145,7 +145,7 @@ def flop_model(nlines):
     their residuals and 8 for the residuals' squares in the running sums.  Each point's evaluations are classified by its own region;
     branch tests, votes and work a pair or warp does beyond that are not
     counted."""
-    return {"weideman": 95.0, "mid": 45.0, "cf": 31.0, "far": 17.0, "point": 22.0 * nlines + 64.0}
+    return {"weideman": 91.0, "mid": 45.0, "cf": 31.0, "far": 17.0, "point": 22.0 * nlines + 64.0}
 
 
 def run_ours(args):
