@@ -6,7 +6,10 @@ pessimistic) beyond its threshold, and compared with scipy's wofz: the far
 field, the 3rd convergent and the 5th convergent of the Laplace continued
 fraction w = (i/sqrt(pi)) / (z - (1/2) / (z - 1 / (z - (3/2) / ...))) must stay
 within 1.5e-7 absolute (1.3e-7 with the kernel's FMAs).  Moving a threshold
-inward past the budget fails here."""
+inward past the budget fails here.  Weideman's series, the branch a mixed
+warp may take anywhere, is checked the same way in the pair path's
+algebraic form (coefficients from their defining integral, N and L read
+from the host code)."""
 import os
 import re
 
@@ -101,3 +104,56 @@ def test_fifth_convergent_within_budget():
 def test_budget_is_tight_enough_to_fail():
     """The check has teeth: the far field a little further in exceeds it."""
     assert worst_beyond(far32, 0.8 * thresholds()["far"]) > BUDGET
+
+
+def _weideman_setup():
+    with open(os.path.join(CSRC, "api.cu")) as fh:
+        src = fh.read()
+    m = re.search(r"const double L = ([0-9.]+);\s*const std::vector<double> a = weideman_coefficients\((\d+), L\);", src)
+    assert m, "FP32 Weideman parameters"
+    L, n = float(m.group(1)), int(m.group(2))
+    # a_k = (1/K) sum over the midpoint rule of exp(-t^2) (L^2 + t^2) cos(k theta), t = L tan(theta/2)
+    kk = 8192
+    th = -np.pi + 2 * np.pi * (np.arange(kk) + 0.5) / kk
+    t = L * np.tan(0.5 * th)
+    g = np.exp(-t * t) * (L * L + t * t)
+    a = np.array([np.mean(g * np.cos(k * th)) for k in range(n + 1)])
+    return L, n, a
+
+
+def weideman32(x, y, L, n, a):
+    """The pair path's interior branch in float32: Z = ((L^2 - y^2 - x^2) + 2iLx)
+    / ((L+y)^2 + x^2), p(Z) by real-quadratic synthetic division with the
+    doubled coefficients, w = p (r^2) + r / sqrt(pi), r = 1/(L - iz)."""
+    x, y = x.astype(f32), f32(y)
+    Lf = f32(L)
+    dx = Lf + y
+    inv = f32(1) / (x * x + dx * dx)
+    rx, ry = dx * inv, x * inv
+    zx = (-(x * x) + (Lf - y) * dx) * inv
+    zy = ry * (f32(2) * Lf)
+    w = [f32(2 * c) for c in a]
+    r, sq = zx + zx, -(zx * zx + zy * zy)
+    b2 = np.full_like(x, w[n])
+    b1 = r * b2 + w[n - 1]
+    for j in range(n - 3, 0, -1):
+        b2, b1 = b1, r * b1 + (sq * b2 + w[j + 1])
+    px, py = sq * b2 + (b1 * zx + w[1]), b1 * zy
+    r2x, r2y = rx * rx - ry * ry, (rx + rx) * ry
+    s = f32(0.56418958354775628695)
+    wx = px * r2x + (-py * r2y + rx * s)
+    wy = px * r2y + (py * r2x + ry * s)
+    return wx.astype(float) + 1j * wy.astype(float)
+
+
+def test_weideman_series_fp32():
+    """Everywhere (the branch a mixed warp may take): within the FP32 floor at
+    the line centre, where |w| is about 1, and at truncation level beyond."""
+    L, n, a = _weideman_setup()
+    xs = np.concatenate([np.linspace(0.0, 6.0, 3001), np.geomspace(6.0, 1e4, 2000)])
+    near, far = 0.0, 0.0
+    for y in np.concatenate([[0.0], np.geomspace(1e-4, 1.0, 25)]):
+        e = np.abs(weideman32(xs, y, L, n, a) - special.wofz(xs + 1j * y))
+        near = max(near, float(np.max(e[xs < 6.0])))
+        far = max(far, float(np.max(e[xs >= 6.0])))
+    assert near < 1.0e-6 and far < 5.0e-8, (near, far)
