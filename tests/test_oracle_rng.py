@@ -119,3 +119,64 @@ def test_sobol_direction_numbers_odd(orc):
         v = orc.sobol_directions(dim)
         for k in range(32):
             assert (int(v[k]) >> (31 - k)) & 1 == 1   # m_k odd
+
+
+# The first primitive polynomials over GF(2), ordered by degree and then by
+# their encoding (bit i = coefficient of x^i): x + 1; x^2 + x + 1; x^3 + x + 1,
+# x^3 + x^2 + 1; x^4 + x + 1, x^4 + x^3 + 1; x^5 + x^2 + 1, x^5 + x^3 + 1,
+# x^5 + x^3 + x^2 + x + 1, x^5 + x^4 + x^2 + x + 1, x^5 + x^4 + x^3 + x + 1,
+# x^5 + x^4 + x^3 + x^2 + 1 (a textbook table; phi(2^s - 1) / s of degree s).
+PRIMITIVE = [0b11, 0b111, 0b1011, 0b1101, 0b10011, 0b11001, 0b100101, 0b101001, 0b101111, 0b110111,
+             0b111011, 0b111101]
+
+
+def _gf2_mod(a, b):
+    db = b.bit_length() - 1
+    while a and a.bit_length() - 1 >= db:
+        a ^= b << (a.bit_length() - 1 - db)
+    return a
+
+
+def _irreducible(p):
+    """No factor of degree 1..deg/2 (trial division by every polynomial)."""
+    d = p.bit_length() - 1
+    return all(_gf2_mod(p, q) != 0 for q in range(2, 1 << (d // 2 + 1)) if q.bit_length() - 1 >= 1)
+
+
+def test_primitive_polynomial_table():
+    """The table is what it says: each entry irreducible with x of order
+    2^s - 1, and no primitive polynomial of the same degree is missing or out
+    of order."""
+    for p in PRIMITIVE:
+        s = p.bit_length() - 1
+        assert _irreducible(p), bin(p)
+        order = next(e for e in range(1, 1 << s) if _gf2_mod(1 << e, p) == 1)
+        assert order == (1 << s) - 1, bin(p)
+    by_deg = {}
+    for p in PRIMITIVE:
+        by_deg.setdefault(p.bit_length() - 1, []).append(p)
+    for s, ps in by_deg.items():
+        if s == 5:   # complete for degree <= 5: phi(31) / 5 = 6 entries
+            assert len(ps) == 6
+        assert ps == sorted(ps)
+    assert [len(by_deg[s]) for s in (1, 2, 3, 4)] == [1, 1, 2, 2]   # phi(2^s - 1) / s
+
+
+@pytest.mark.parametrize("dim", range(1, 12))
+def test_sobol_direction_numbers_follow_the_primitive_polynomials(orc, dim):
+    """Dimension d >= 1 uses the d-th primitive polynomial: its direction
+    integers m_k start at 2^k - 1 (k <= s) and obey Sobol's recurrence
+    m_k = 2 a_1 m_{k-1} ^ ... ^ 2^(s-1) a_(s-1) m_(k-s+1) ^ 2^s m_(k-s) ^ m_(k-s)
+    for the polynomial x^s + a_1 x^(s-1) + ... + a_(s-1) x + 1."""
+    p = PRIMITIVE[dim - 1]
+    s = p.bit_length() - 1
+    v = orc.sobol_directions(dim)
+    m = [None] + [int(v[k]) >> (31 - k) for k in range(32)]   # m[1..32]
+    for k in range(1, s + 1):
+        assert m[k] == (1 << k) - 1, (dim, k)
+    for k in range(s + 1, 33):
+        x = m[k - s] ^ (m[k - s] << s)
+        for j in range(1, s):
+            if (p >> (s - j)) & 1:
+                x ^= m[k - j] << j
+        assert m[k] == x, (dim, k)
