@@ -16,13 +16,13 @@
  *  - Invalid arguments are rejected on the host (ME_EINVAL) before anything
  *    is launched; a failed launch returns ME_ECUDA.
  *  - Parameter vectors have M = ME_NPAR = 9 entries in this fixed order
- *    (Section 4, model vector p; v_LOS replaces lambda0 and S0, S1 replace
+ *    (Section 5, model vector p; v_LOS replaces lambda0 and S0, S1 replace
  *    S0, beta0 with beta0 = S1/S0), or M = 10 with the fill fraction:
  *       0 B [G]          1 theta inclination [deg]   2 chi azimuth [deg]
  *       3 v_LOS [km/s]   4 Doppler width [mA] at lambda_dop_A
  *       5 damping a      6 eta0 (line/continuum opacity ratio)
  *       7 S0             8 S1 (source function S0 + S1 tau)
- *       9 alpha (me_problem.fill_fraction = 1; Section 4.2)
+ *       9 alpha (me_problem.fill_fraction = 1; Section 5.2)
  *  - Stokes arrays are [n][4][n_lambda] (I, Q, U, V), pixel-major, of the
  *    problem's dtype (float for ME_F32, double for ME_F64).
  */
@@ -48,7 +48,7 @@ extern "C" {
 
 /* ------------------------------------------------------------ limits/enums */
 #define ME_NPAR 9      /* model parameters without the fill fraction          */
-#define ME_NPAR_MAX 10 /* with it: parameter 9 is alpha (Section 4.2)         */
+#define ME_NPAR_MAX 10 /* with it: parameter 9 is alpha (Section 5.2)         */
 #define ME_MAX_LINES 4
 #define ME_MAX_LAMBDA 512
 #define ME_MAX_COMP 9 /* Zeeman components per group in a full pattern (J <= 4) */
@@ -58,7 +58,7 @@ extern "C" {
 #define ME_F32 0 /* float cube, FP32 synthesis and chi2            */
 #define ME_F64 1 /* double cube, FP64 synthesis and chi2           */
 
-#define ME_W_INVMAX 0 /* Section 4.5 inverse-max weights from the data  */
+#define ME_W_INVMAX 0 /* Section 5.4 inverse-max weights from the data  */
 #define ME_W_USER 1   /* caller-supplied w[npix][4]                     */
 
 /*
@@ -66,10 +66,10 @@ extern "C" {
  *   lambda0_A  rest wavelength [A]
  *   g_eff      effective Lande factor (pattern == 0): an effective Zeeman
  *              triplet, sigma_blue, pi, sigma_red at v + v_B, v, v - v_B with
- *              v_B = 4.6686e-13 g_eff lambda0^2 B / dlambda_D (Section 4)
+ *              v_B = 4.6686e-13 g_eff lambda0^2 B / dlambda_D (Section 5)
  *   eta_ratio  eta0 of this line divided by the eta0 parameter (1 for the
  *              reference line); all lines add into one propagation matrix.
- *   pattern    1: use the line's full Zeeman pattern (Section 4: computed at
+ *   pattern    1: use the line's full Zeeman pattern (Section 5: computed at
  *              start-up from the transition), built from the lower level
  *              (j_lower, g_lower) and upper level (j_upper, g_upper) in LS
  *              coupling: components M_u -> M_l, q = M_l - M_u (-1 sigma_blue,
@@ -89,7 +89,7 @@ typedef struct me_line {
 } me_line;
 
 /*
- * The synthesis problem (Section 4): line list, wavelength grid and geometry.
+ * The synthesis problem (Section 5): line list, wavelength grid and geometry.
  *   n_lines       1..ME_MAX_LINES
  *   n_lambda      1..ME_MAX_LAMBDA
  *   lambda_A      HOST pointer to n_lambda wavelengths [A]; copied into the
@@ -99,7 +99,7 @@ typedef struct me_line {
  *   mu            cosine of the heliocentric angle used when mu_px is NULL
  *   dtype         ME_F32 or ME_F64: element type of obs/stokes arrays and the
  *                 arithmetic of synthesis and chi2
- *   fill_fraction 1: the magnetic fill fraction alpha of Section 4.2 is a 10th
+ *   fill_fraction 1: the magnetic fill fraction alpha of Section 5.2 is a 10th
  *                 parameter, Stokes = alpha S_mag + (1 - alpha) I_nm (1,0,0,0)
  *                 with I_nm = S0 + mu S1 / (1 + sum_l eta0_l Re w(v_l, a)), the
  *                 same atmosphere without a field; 0: 9 parameters.
@@ -128,7 +128,7 @@ typedef struct me_bounds {
 } me_bounds;
 
 /*
- * Genetic-algorithm settings (Section 3, Algorithm 1; Section 4.6).
+ * Genetic-algorithm settings (Section 3, Algorithm 1; Section 5.6).
  *   npop         population, a multiple of 32 in [ME_MIN_POP, ME_MAX_POP]
  *   ngen         generations (>= 0)
  *   nsamp        restart period: every nsamp generations (t < ngen) the worst
@@ -165,7 +165,7 @@ int me_version(void);
 
 /*
  * me_synth - Unno-Rachkovsky Stokes vectors of n parameter vectors
- * (Section 4: K = 1 + eta0 Phi, Stokes = S0 e + mu S1 K^-1 e, I_c = S0 + mu S1).
+ * (Section 5: K = 1 + eta0 Phi, Stokes = S0 e + mu S1 K^-1 e, I_c = S0 + mu S1).
  *   params  dev double [n][M]
  *   mu_px   dev double [n] or NULL (then pb->mu)
  *   stokes  dev [n][4][n_lambda] of pb->dtype (output)
@@ -176,7 +176,7 @@ int me_synth(const me_problem *pb, const double *params, const double *mu_px, in
 
 /*
  * me_synth_jac - analytic Jacobian d stokes / d p of the same synthesis
- * (the derivative of Section 4's closed form, with w'(z) = -2 z w + 2i/sqrt(pi)).
+ * (the derivative of Section 5's closed form, with w'(z) = -2 z w + 2i/sqrt(pi)).
  *   stokes  dev [n][4][n_lambda] of pb->dtype, or NULL
  *   jac     dev [n][4][n_lambda][M] of pb->dtype (output)
  */
@@ -196,7 +196,7 @@ int me_synth_vjp(const me_problem *pb, const double *params, const double *mu_px
  * me_chi2 - Eq. chisq, chi2 = (1/nu) sum_s w_s^2 sum_j (O - M)^2 with
  * nu = 4 n_lambda - M, evaluated in FP64 for each pixel's parameters.
  *   obs   dev [npix][4][n_lambda] of pb->dtype
- *   w     dev double [npix][4] (ME_W_USER) or NULL (inverse-max, Section 4.5)
+ *   w     dev double [npix][4] (ME_W_USER) or NULL (inverse-max, Section 5.4)
  *   chi2  dev double [npix] (output)
  */
 int me_chi2(const me_problem *pb, const void *obs, const double *w, const double *mu_px,
@@ -208,7 +208,7 @@ int me_chi2(const me_problem *pb, const void *obs, const double *w, const double
  * Sobol initial population, then per generation binary tournament selection,
  * one-point crossover, LSB-biased mutation, elitism and fitness evaluation
  * (synthesis + chi2 in pb->dtype arithmetic), with worst-half Sobol restarts
- * every nsamp generations (Section 4.6).  Philox4x32-10 counters are keyed by
+ * every nsamp generations (Section 5.6).  Philox4x32-10 counters are keyed by
  * pixel id = pixel_id0 + i, so a pixel's result does not depend on the batch.
  *   obs         dev [npix][4][n_lambda] of pb->dtype
  *   w           dev double [npix][4] if cfg->weight_mode == ME_W_USER, else NULL
@@ -241,6 +241,66 @@ int ga_count_evaluations(const me_problem *pb, const void *obs, const double *w,
                          unsigned long long *counts, void *stream);
 
 /*
+ * ga_fitness - the fitness that ga_invert_batch ranks its population by, for
+ * caller-given individuals: Eq. chisq of the Section 5 synthesis, in
+ * pb->dtype arithmetic (FP32: the packed two-wavelength pair path with its
+ * warp-voted w(z) regions; FP64: the per-wavelength path), with the GA's
+ * launch shape and the kernel instantiation ga_invert_batch would choose.
+ * One thread block per pixel and one thread per individual; only threads
+ * k < nactive evaluate, inside a divergent branch as the GA's restarts do
+ * (nactive = npop / 2 = 16 of npop = 32 is the restart of the smallest
+ * population), so the w(z) branch votes run over exactly those lanes.  A
+ * verification entry point: it exposes the GA's evaluation so that it can be
+ * compared with an independent FP64 synthesis.
+ *   obs      dev [npix][4][n_lambda] of pb->dtype
+ *   w        dev double [npix][4] (the caller's weights) or NULL (Section 5.4
+ *            inverse-max weights of the pixel, as ME_W_INVMAX)
+ *   mu_px    dev double [npix] or NULL
+ *   npop     threads per block, a multiple of 32 in [ME_MIN_POP, ME_MAX_POP]
+ *   nactive  1..npop
+ *   params   dev double [npix][npop][M], each rounded to pb->dtype (the GA
+ *            decodes its genes in that precision)
+ *   fitness  dev double [npix][npop] (output): chi2 / nu of individual k for
+ *            k < nactive, as computed (NaN is not replaced); rows k >= nactive
+ *            are not written
+ *   resid    dev [npix][npop][4][n_lambda] of pb->dtype or NULL (output): the
+ *            residuals O - S whose weighted squares the fitness sums; rows
+ *            k >= nactive are not written
+ * Errors: ME_EINVAL for an invalid problem, npop, nactive or a population and
+ * grid that exceed shared memory; ME_ECUDA for a failed launch.
+ */
+int ga_fitness(const me_problem *pb, const void *obs, const double *w, const double *mu_px, int npix,
+               int npop, int nactive, const double *params, double *fitness, void *resid, void *stream);
+
+/*
+ * me_faddeeva_pairs - the FP32 Voigt and Faraday-Voigt profiles of the GA's
+ * pair path, H + iF = w(x + i a) (Section 5: phi = Re w, psi = Im w), for
+ * caller-given arguments, through the same branch choice the fitness makes:
+ * Weideman's series, the 5th and 3rd convergents of the Laplace continued
+ * fraction and the far-field approximant, chosen per pair and voted across
+ * the warp.  Thread i (32 to a warp, in index order) holds pair i; a ragged n
+ * leaves the last warp partial, and its vote runs over the lanes present.  A
+ * verification entry point.
+ *   x     dev float [n][2]: the pair's two real arguments (8-byte aligned)
+ *   a     dev float [n]: the pair's damping a >= 0
+ *   v_b   dev float [n]: Zeeman splitting in Doppler units (mode 2 only;
+ *         may be NULL otherwise)
+ *   mode  0: one component, regions tested from the outside in (the branch
+ *            of full-pattern components);
+ *         1: one component, tested from the inside out (components of an
+ *            effective triplet near a line core);
+ *         2: an effective triplet with pi arguments x and sigma arguments
+ *            x +- v_b, its level voted as a whole first, as the fitness does
+ *   out   dev float (output): modes 0, 1: [n][2][2] = (Re w, Im w) of each
+ *         point; mode 2: [n][2][6] = per point the unit-strength profile
+ *         sums (phi_pi, psi_pi, phi_b + phi_r, psi_b + psi_r, phi_r - phi_b,
+ *         psi_r - psi_b), phi_b = Re w(x + v_b + i a), phi_r = Re w(x - v_b + i a)
+ * Errors: ME_EINVAL for n < 0, a bad mode, NULL or misaligned pointers.
+ */
+int me_faddeeva_pairs(const float *x, const float *a, const float *v_b, int n, int mode, float *out,
+                      void *stream);
+
+/*
  * lm_polish - Levenberg-Marquardt refinement of each pixel's parameters
  * (Levenberg 1944, Marquardt 1963): FP32 analytic Jacobian, normal equations
  * (J^T W^2 J + lambda D) delta = J^T W^2 r summed in the cube's precision
@@ -253,10 +313,22 @@ int lm_polish(const me_problem *pb, const void *obs, const double *w, const doub
               int npix, const me_bounds *bounds, int iters, double lambda0,
               double *params_inout, double *chi2_out, void *stream);
 
+/*
+ * me_fp32_peak - FP32 FMA-pipe throughput probe.  The paper has no
+ * counterpart: it measures the FP32 peak of the GPU at the clock it runs, the
+ * denominator of the GA kernel's roofline fraction.  nblocks blocks of 256
+ * threads, each running 8 independent FMA chains for iters x 16 steps, as
+ * scalar FFMA (packed = 0) or packed FFMA2 (packed = 1).
+ *   out    dev float [nblocks * 256] (output; values of no interest)
+ *   flops  host double* or NULL: receives the launch's FP32 flops (FMA = 2)
+ * Errors: ME_EINVAL for nblocks or iters < 1 or a NULL out.
+ */
+int me_fp32_peak(int packed, int nblocks, int iters, float *out, double *flops, void *stream);
+
 /* ----------------------------------------------------------------- serving
  * A continuous-batching request loop for inversions of slit scans and map
  * tiles of uneven pixel counts (the paper's goal of near real-time pipeline
- * inversions, Section 6).  serve_submit copies a request and queues it; a
+ * inversions, Section 7).  serve_submit copies a request and queues it; a
  * worker thread admits queued requests in arrival order whenever one of
  * max_inflight slots is free and the request's buffers fit the arena
  * (admission by memory), then runs the GA (and optional L-M polish) of
@@ -329,7 +401,7 @@ int serve_stats(serve_handle *h, serve_stats_t *out);
 int serve_destroy(serve_handle *h);
 
 /*
- * lm_uncertainty - Section 5 uncertainty estimate at given parameters:
+ * lm_uncertainty - Section 6 uncertainty estimate at given parameters:
  * sigma_i^2 = [H^-1]_ii chi2 / M (M parameters) with H the Hessian of Eq. chisq
  * in its Gauss-Newton form H = (2/nu) J^T W^2 J (exact where the residuals
  * vanish); J analytic in the problem precision, H and its inverse in FP64.
@@ -341,7 +413,7 @@ int lm_uncertainty(const me_problem *pb, const void *obs, const double *w, const
                    int npix, const double *params, double *sigma, void *stream);
 
 /*
- * me_line_centre - Section 4.1 line-centre estimate by centre of symmetry:
+ * me_line_centre - Section 5.1 line-centre estimate by centre of symmetry:
  * S_i = sum_{j=1..W} |I(lambda_{i+j}) - I(lambda_{i-j})|, lambda_sym = the
  * lambda_i minimising S over candidates i in [i_lo, i_hi] intersected with
  * [W, n_lambda-1-W] (ties: lowest index), refined by the vertex of the
@@ -357,7 +429,7 @@ int me_line_centre(const me_problem *pb, const void *obs, int npix, int half_wid
 
 /* ------------------------------------------ pixel selection and seeding
  * me_classify - Section 2 pixel selection with the weak-field fallback, and
- * the Section 4.5 seeds and polarity, one pixel per warp in FP64.
+ * the Section 5.5 seeds and polarity, one pixel per warp in FP64.
  *   Threshold: I_c = mean of I over the quiet window [q_lo, q_hi); sigma_s^2
  *   the variance (1/n) of s = Q, U, V there; p = sqrt(Qmax^2 + Umax^2 +
  *   Vmax^2) / I_c with X_max = max |X| over the grid; sigma_P = p_thresh
@@ -419,7 +491,7 @@ int me_select_static(const int *flag, int npix, int want, int *index, int *count
 
 /*
  * ga_invert_subset - ga_invert_batch on a subset of a map, with the Section
- * 4.5 seeds and polarity restriction.  Block b inverts pixel index[b] for
+ * 5.5 seeds and polarity restriction.  Block b inverts pixel index[b] for
  * b < *count (index and count on the device, e.g. from me_select; index NULL
  * = identity, count NULL = npix); every per-pixel array (obs, w, mu_px,
  * seeds, polarity, best, chi2, best_genes) is indexed by that pixel number,
@@ -432,7 +504,7 @@ int me_select_static(const int *flag, int npix, int want, int *index, int *count
  *             [lo, min(hi, 90)], -1 to [max(lo, 90), hi] (0, or an empty half:
  *             unrestricted); the decode of that gene uses it throughout.
  *   bounds_px dev double [npix][2][M] or NULL: per-pixel search domain
- *             (lo row, hi row; Section 4.3, e.g. from me_prefit_bounds) in
+ *             (lo row, hi row; Section 5.3, e.g. from me_prefit_bounds) in
  *             place of *bounds for the decode and the seed encoding; the
  *             polarity restriction applies on top of it.
  */
@@ -448,14 +520,14 @@ int ga_invert_subset(const me_problem *pb, const void *obs, const double *w, con
  * Parameters whose bit in free_mask is clear are held: their rows and
  * columns of the normal equations are zeroed, so their step is exactly 0.
  * With B, theta, chi held at B = 0 and weights (w_I, 0, 0, 0) this is the
- * Section 4.3 thermodynamic prefit: a non-magnetic fit of Stokes I.
+ * Section 5.3 thermodynamic prefit: a non-magnetic fit of Stokes I.
  */
 int lm_fit(const me_problem *pb, const void *obs, const double *w, const double *mu_px, int npix,
            const me_bounds *bounds, int iters, double lambda0, unsigned free_mask, const int *index,
            const int *count, double *params_inout, double *chi2_out, void *stream);
 
 /*
- * me_prefit_bounds - Section 4.3: the prefit's values constrain the GA's
+ * me_prefit_bounds - Section 5.3: the prefit's values constrain the GA's
  * search to ranges around them.  For pixel i and parameter k:
  *   lo'_ik = max(lo_k, p_hat_ik - lower[k]), hi'_ik = min(hi_k, p_hat_ik + upper[k]),
  * an infinite margin keeping the global bound; where that leaves no interval
@@ -488,7 +560,7 @@ int ga_breed(const uint16_t *genes, const double *fitness, int nprob, int npop, 
              int *elite, void *stream);
 
 /*
- * ga_restart - Section 4.6 restart: the worst npop/2 individuals (stable rank by
+ * ga_restart - Section 5.6 restart: the worst npop/2 individuals (stable rank by
  * fitness, then index) take Sobol points sobol_next + r in rank order r.
  *   genes  dev uint16 [nprob][npop][npar], modified in place
  */

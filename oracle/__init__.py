@@ -6,15 +6,15 @@ code with the CUDA path; this module compiles them with gcc into
 ``oracle/liboracle.so`` and exposes them through ctypes with numpy arrays.
 
 Every function cites the passage of Harker & Mighell (2012) it follows:
-    faddeeva        Section 4 (Voigt / Faraday-Voigt profiles, Hui et al. 1978)
-    synth, synth_lu Section 4 (Unno-Rachkovsky ME solution, K = 1 + eta0 Phi)
-    weights_invmax  Section 4.5 (inverse-max weighting)
-    chi2            Section 4, Eq. chisq
-    philox, sobol   Section 4.6 (Sobol initialisation); Philox drives S, R, M
+    faddeeva        Section 5 (Voigt / Faraday-Voigt profiles, Hui et al. 1978)
+    synth, synth_lu Section 5 (Unno-Rachkovsky ME solution, K = 1 + eta0 Phi)
+    weights_invmax  Section 5.4 (inverse-max weighting)
+    chi2            Section 5, Eq. chisq
+    philox, sobol   Section 5.6 (Sobol initialisation); Philox drives S, R, M
     ga_breed        Section 3, Algorithm 1 (S, E, R, M, elitism)
-    ga_restart      Section 4.6 (worst half replaced every N_samp generations)
+    ga_restart      Section 5.6 (worst half replaced every N_samp generations)
     ga_invert       Algorithm 1 run per pixel
-    jacobian, lm_polish   Levenberg-Marquardt (Section 1, Section 4.3)
+    jacobian, lm_polish   Levenberg-Marquardt (Section 1, Section 5.3)
 """
 from __future__ import annotations
 
@@ -197,7 +197,7 @@ def ga_config(npop, ngen, nsamp=None, pc=0.9, pmut_lsb=0.05, pmut_ratio=0.7, see
 # ------------------------------------------------------------------ profiles
 
 def faddeeva(x, y):
-    """w(x + i y) (Section 4 profiles; Matta & Reichel trapezoid)."""
+    """w(x + i y) (Section 5 profiles; Matta & Reichel trapezoid)."""
     x, y = np.broadcast_arrays(_f64(x), _f64(y))
     shape = x.shape
     x, y = _f64(x.ravel()), _f64(y.ravel())
@@ -212,7 +212,7 @@ def wigner3j(j1, j2, j3, m1, m2, m3):
 
 
 def zeeman_components(j_lower, g_lower, j_upper, g_upper):
-    """[(shifts, strengths)] for the sigma_b, pi, sigma_r groups (Section 4
+    """[(shifts, strengths)] for the sigma_b, pi, sigma_r groups (Section 5
     full Zeeman pattern), shifts in Larmor units toward longer wavelength."""
     n = np.zeros(3, dtype=np.int32)
     sh = np.zeros((3, 9))
@@ -226,7 +226,7 @@ def zeeman_components(j_lower, g_lower, j_upper, g_upper):
 # ----------------------------------------------------------------- synthesis
 
 def synth(pb, params, mu=1.0, mu_px=None, nthreads=None):
-    """Stokes [n,4,n_lambda] of params [n,M] (Section 4 ME solution)."""
+    """Stokes [n,4,n_lambda] of params [n,M] (Section 5 ME solution)."""
     pb = _problem(pb)
     p = _f64(np.atleast_2d(params))
     if p.shape[1] != pb.npar:
@@ -247,7 +247,7 @@ def synth_lu(pb, params, mu=1.0):
 
 
 def weights_invmax(obs):
-    """Section 4.5 inverse-max weights of obs [...,4,n_lambda] -> [...,4]."""
+    """Section 5.4 inverse-max weights of obs [...,4,n_lambda] -> [...,4]."""
     obs = _f64(obs)
     flat = obs.reshape(-1, 4, obs.shape[-1])
     w = np.empty((flat.shape[0], 4))
@@ -319,8 +319,8 @@ def ga_restart(genes, f, sobol_next):
 def ga_invert(pb, obs, lo, hi, cfg, w=None, mu=1.0, mu_px=None, pixel_id0=0,
               nthreads=None, want_margin=False, seeds=None, polarity=None, bounds_px=None):
     """Algorithm 1 per pixel; returns dict(best, chi2, genes[, margin]).
-    seeds [npix][nseed][3] (B, psi, chi) and polarity [npix] of Section 4.5;
-    bounds_px [npix][2][9] per-pixel bounds (Section 4.3)."""
+    seeds [npix][nseed][3] (B, psi, chi) and polarity [npix] of Section 5.5;
+    bounds_px [npix][2][9] per-pixel bounds (Section 5.3)."""
     pb = _problem(pb)
     obs = _f64(obs)
     npix = obs.shape[0]
@@ -377,7 +377,7 @@ def lm_polish(pb, obs, params, lo, hi, iters=10, lambda0=1e-3, w=None, mu=1.0,
 
 
 def lm_uncertainty(pb, obs, params, w=None, mu=1.0, mu_px=None):
-    """Section 5 sigma_i = sqrt([H^-1]_ii chi2 / M), H = (2/nu) J^T W^2 J."""
+    """Section 6 sigma_i = sqrt([H^-1]_ii chi2 / M), H = (2/nu) J^T W^2 J."""
     pb = _problem(pb)
     obs = _f64(obs)
     npix = obs.shape[0]
@@ -389,7 +389,7 @@ def lm_uncertainty(pb, obs, params, w=None, mu=1.0, mu_px=None):
 
 
 def line_centre(obs, lambda_grid, half_width, i_lo=0, i_hi=1 << 30):
-    """Section 4.1 centre-of-symmetry line centre of each pixel's Stokes I
+    """Section 5.1 centre-of-symmetry line centre of each pixel's Stokes I
     (obs [npix, 4, n_lambda]) -> (lambda_c [npix], index [npix])."""
     obs = _f64(obs)
     npix, _, nl = obs.shape
@@ -401,7 +401,7 @@ def line_centre(obs, lambda_grid, half_width, i_lo=0, i_hi=1 << 30):
 
 
 def classify(pb, obs, p_thresh, quiet, line, core):
-    """Section 2 selection, weak-field fallback and Section 4.5 seeds.
+    """Section 2 selection, weak-field fallback and Section 5.5 seeds.
     quiet = (lo, hi) half-open quiet window, core = (lo, hi) inclusive line
     window.  Returns dict(flag, polarity, p, sigma_p, B, theta, chi, B_par,
     B_perp, seeds [npix][4][3] = (B, psi, chi) of the weak-field, integral,
@@ -426,14 +426,14 @@ def ga_encode(x, lo, hi):
 
 
 def polarity_bounds(pol, lo, hi):
-    """Inclination domain of Section 4.5's polarity restriction."""
+    """Inclination domain of Section 5.5's polarity restriction."""
     a, b = C.c_double(), C.c_double()
     lib().or_polarity_bounds(int(pol), float(lo), float(hi), C.byref(a), C.byref(b))
     return a.value, b.value
 
 
 def prefit_bounds(p_hat, lo, hi, lower, upper):
-    """Per-pixel bounds [npix][2][M] around a thermodynamic prefit (Section 4.3);
+    """Per-pixel bounds [npix][2][M] around a thermodynamic prefit (Section 5.3);
     M = the number of columns of p_hat."""
     p_hat = np.asarray(p_hat, dtype=np.float64)
     m = p_hat.shape[-1]

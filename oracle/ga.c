@@ -12,7 +12,7 @@
  *                  pmut_lsb * ratio^(15-b): less-significant bits mutate more
  *   elitism        child slot 0 takes the best parent unchanged
  *   restart        every nsamp generations (t < ngen) the worst half is
- *                  replaced by the next Sobol points (Section 4.6)
+ *                  replaced by the next Sobol points (Section 5.6)
  * Random numbers: Philox4x32-10, key = (seed lo, seed hi), counter =
  * (pixel id lo, pixel id hi, generation, index << 8 | purpose) with purpose 0
  * = tournament of child slot index, 1 = crossover of pair index, 2 + g =
@@ -167,7 +167,7 @@ uint16_t or_ga_encode(double x, double lo, double hi)
     return (uint16_t)floor(t * 65535.0 + 0.5);
 }
 
-/* Section 4.5 polarity restriction of the inclination domain: +1 keeps
+/* Section 5.5 polarity restriction of the inclination domain: +1 keeps
  * [u, min(v, 90)], -1 keeps [max(u, 90), v], 0 (or an empty half) keeps [u, v]. */
 void or_polarity_bounds(int pol, double lo, double hi, double *plo, double *phi)
 {
@@ -282,7 +282,7 @@ static void ga_pixel(const ga_job *J, int ip)
     double margin = INFINITY;
 
     /* create P0 from Sobol points 1..npop, the last nseed individuals taking
-     * the seeds' (B, psi, chi) genes (Section 4.5), and evaluate F0 */
+     * the seeds' (B, psi, chi) genes (Section 5.5), and evaluate F0 */
     for (int k = 0; k < npop; ++k) {
         for (int d = 0; d < m; ++d)
             genes[(size_t)k * m + d] = (uint16_t)(or_sobol_u32((uint64_t)(k + 1), d) >> 16);

@@ -13,7 +13,7 @@
  * lower (lambda /= 10), otherwise rejected (lambda *= 10).  A fixed number of
  * trial steps is taken.  Parameters outside free_mask (bit k = parameter k)
  * are held: their Jacobian columns are zero, so A and g have zero rows and
- * columns there and delta_k = 0 (Section 4.3's prefit fits Stokes I with the
+ * columns there and delta_k = 0 (Section 5.3's prefit fits Stokes I with the
  * field held at B = 0).
  */
 #include <math.h>
@@ -168,7 +168,7 @@ static void lm_pixel(const or_problem *pb, const double *obs, const double *w,
 }
 
 /*
- * Section 5: sigma_i^2 = [H^-1]_ii chi2 / M at p, with H = (2/nu) J^T W^2 J the
+ * Section 6: sigma_i^2 = [H^-1]_ii chi2 / M at p, with H = (2/nu) J^T W^2 J the
  * Gauss-Newton Hessian of Eq. chisq (J by central differences), inverted by
  * Gauss-Jordan elimination with partial pivoting; +infinity if singular.
  */

@@ -20,7 +20,7 @@
  * Faddeeva function w(z) = exp(-z^2) erfc(-i z), z = x + i y.
  *
  * The paper evaluates the Voigt and Faraday-Voigt profiles H and F with a
- * rational approximation (Section 4, Hui et al. 1978).  The oracle uses a
+ * rational approximation (Section 5, Hui et al. 1978).  The oracle uses a
  * different, published method so that it shares nothing with the GPU path:
  * the trapezoidal rule with pole correction of Matta & Reichel (1971,
  * Math. Comp. 25, 339) applied to
@@ -76,7 +76,7 @@ void or_faddeeva(double x, double y, double *re, double *im)
 }
 
 /*
- * Propagation-matrix elements at one wavelength (Section 4: K = 1 + eta0 Phi).
+ * Propagation-matrix elements at one wavelength (Section 5: K = 1 + eta0 Phi).
  * The paper defers the elements of Phi to Landi Degl'Innocenti & Landolfi;
  * with the effective-triplet Zeeman pattern they are, per line l with
  * eta0_l = eta0 * r_l and phi + i psi = w(z):
@@ -145,7 +145,7 @@ static void kmatrix(const or_problem *pb, const double *p, double lam,
 }
 
 /*
- * Milne-Eddington solution (Section 4): with S = S0 + S1 tau the emergent
+ * Milne-Eddington solution (Section 5): with S = S0 + S1 tau the emergent
  * Stokes vector is S0 e + mu S1 K^-1 e, e = (1,0,0,0); I_c = S0 + mu S1.
  * K^-1 e written out (Landi Degl'Innocenti closed form):
  *   Delta = eI^2 (eI^2 - eQ^2 - eU^2 - eV^2 + rQ^2 + rU^2 + rV^2) - Pi^2,
@@ -154,7 +154,7 @@ static void kmatrix(const or_problem *pb, const double *p, double lam,
  *   Q = -[eI^2 eQ + eI (eV rU - eU rV) + rQ Pi] / Delta, U, V cyclic.
  */
 /*
- * Section 4.2 fill fraction: I <- alpha I_mag + (1 - alpha) I_nm e.  The
+ * Section 5.2 fill fraction: I <- alpha I_mag + (1 - alpha) I_nm e.  The
  * field-free part is read as the same Milne-Eddington atmosphere without a
  * field (the paper's quiet-sun CLV profile is not printed):
  *   I_nm = S0 + mu S1 / (1 + sum_l eta0_l Re w(v_l, a)),
@@ -254,7 +254,7 @@ void or_synth_lu(const or_problem *pb, const double *p, double mu, double *stoke
 }
 
 /*
- * Inverse-max weights (Section 4.5): w_I = 1/(I_c - I_0), w_Q = 1/max|Q|,
+ * Inverse-max weights (Section 5.4): w_I = 1/(I_c - I_0), w_Q = 1/max|Q|,
  * w_U = 1/max|U|, w_V = 1/max|V|.  I_c is read as the largest observed I in
  * the window and I_0 as the smallest (the line core).  Each denominator is
  * floored at 1e-6 |I_c| so that a profile that is identically zero gives a
@@ -307,7 +307,7 @@ void or_faddeeva_batch(int n, const double *x, const double *y, double *re, doub
 }
 
 /*
- * Section 4.1: line centre by centre of symmetry.  For candidate index i,
+ * Section 5.1: line centre by centre of symmetry.  For candidate index i,
  * S_i = sum_{j=1..W} |I(lambda_{i+j}) - I(lambda_{i-j})| (W = half_width, in
  * grid points); lambda_sym = argmin_i S_i over i in [i_lo, i_hi] restricted to
  * [W, N-1-W] (ties: lowest index), refined by the vertex of the parabola
@@ -351,7 +351,7 @@ void or_line_centre(const double *rows, int npix, int stride, int nl, const doub
 }
 
 /*
- * Section 2 pixel selection, the weak-field fallback and the Section 4.5
+ * Section 2 pixel selection, the weak-field fallback and the Section 5.5
  * seeds.  Window sums run in index order; extrema take the lowest index on ties.
  *   Threshold: I_c = mean of I over the quiet window [q_lo, q_hi); sigma_s^2
  *   the (1/n) variance of s = Q, U, V there; p = sqrt(Qmax^2 + Umax^2 +

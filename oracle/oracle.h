@@ -15,7 +15,7 @@
  * Parameter vector (M = 9, or 10 with the fill fraction), fixed order:
  *   0 B [G], 1 theta [deg], 2 chi [deg], 3 v_LOS [km/s], 4 Doppler width
  *   [mA] (quoted at lambda_dop), 5 damping a, 6 eta0, 7 S0, 8 S1, and with
- *   fill != 0: 9 alpha, the magnetic fill fraction of Section 4.2.
+ *   fill != 0: 9 alpha, the magnetic fill fraction of Section 5.2.
  *
  * Pins (tests/test_oracle_*.py): the Faddeeva routine against brute-force
  * quadrature, the a->0 closed forms and scipy.special.wofz; the closed-form ME
@@ -119,11 +119,11 @@ void or_ga_restart(uint16_t *genes, const double *f, int npop, int m,
  * re-evaluation with the fitness weights), best_genes [npix][m] (may be NULL)
  * and margin [npix] (may be NULL): the smallest relative gap between two
  * unequal fitness values whose order decided a selection, elitism or restart
- * step.  Section 4.5: seeds [npix][nseed][3] (B, psi, chi; NaN keeps the
+ * step.  Section 5.5: seeds [npix][nseed][3] (B, psi, chi; NaN keeps the
  * Sobol gene) replace those genes of the last nseed <= npop/2 individuals of
  * P0; polarity [npix] (may be NULL) restricts the inclination domain per
  * pixel (or_polarity_bounds).  bounds_px [npix][2][m] (may be NULL) replaces
- * lo/hi per pixel (Section 4.3), the polarity applying on top. */
+ * lo/hi per pixel (Section 5.3), the polarity applying on top. */
 uint16_t or_ga_encode(double x, double lo, double hi);
 void or_polarity_bounds(int pol, double lo, double hi, double *plo, double *phi);
 int or_ga_invert(const or_problem *pb, const double *obs, const double *w,
@@ -144,14 +144,14 @@ int or_lm_polish(const or_problem *pb, const double *obs, const double *w,
                  const double *hi, int iters, double lambda0, unsigned free_mask,
                  double *params_inout, double *chi2_out, int nthreads);
 
-/* Section 4.3 bounds from a thermodynamic prefit p_hat [npix][m]:
+/* Section 5.3 bounds from a thermodynamic prefit p_hat [npix][m]:
  * lo'_k = max(lo_k, p_hat_k - lower_k), hi'_k = min(hi_k, p_hat_k + upper_k)
  * (an infinite margin keeps the global bound); where that leaves no interval
  * (or p_hat_k is NaN) the global bounds stay.  out [npix][2][m]. */
 void or_prefit_bounds(const double *p_hat, int npix, int m, const double *lo, const double *hi,
                       const double *lower, const double *upper, double *out);
 
-/* Section 4.1 line centre by centre of symmetry (see me.c). */
+/* Section 5.1 line centre by centre of symmetry (see me.c). */
 void or_line_centre(const double *rows, int npix, int stride, int nl, const double *lam, int half_width,
                     int i_lo, int i_hi, double *lam_c, int *idx);
 
@@ -160,7 +160,7 @@ void or_classify(const or_problem *pb, const double *obs, int npix, double p_thr
                  int line, int c_lo, int c_hi, int *flag, int *polarity, double *out_pol, double *out_weak,
                  double *seeds);
 
-/* Section 5 uncertainties sigma [npix][M] at params. */
+/* Section 6 uncertainties sigma [npix][M] at params. */
 void or_lm_uncertainty(const or_problem *pb, const double *obs, const double *w, const double *mu_px,
                        double mu, int npix, const double *params, double *sigma);
 

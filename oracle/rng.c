@@ -33,7 +33,7 @@ void or_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]
 }
 
 /*
- * Sobol sequence (Section 4.6; Bratley & Fox 1988 construction).
+ * Sobol sequence (Section 5.6; Bratley & Fox 1988 construction).
  * The Bratley-Fox table of polynomials and initial numbers is not part of the
  * paper, so the direction numbers are generated here:
  *   - dimension 0 is the van der Corput sequence (m_k = 1 for all k);

@@ -1,6 +1,6 @@
 /*
  * Oracle: Zeeman components of a transition (the "full Zeeman pattern" the
- * paper computes at start-up, Section 4).  TEST INFRASTRUCTURE ONLY (see
+ * paper computes at start-up, Section 5).  TEST INFRASTRUCTURE ONLY (see
  * oracle.h).
  *
  * A transition lower (J_l, g_l) -> upper (J_u, g_u) splits into components

@@ -100,6 +100,9 @@ _SIGNATURES = {
                          C.POINTER(GaConfig), _VP, _VP, _VP, _VP], C.c_int),
     "ga_count_evaluations": ([_P, _VP, _VP, _VP, C.c_int, C.c_uint64, C.POINTER(MeBounds),
                               C.POINTER(GaConfig), _VP, _VP, _VP], C.c_int),
+    "ga_fitness": ([_P, _VP, _VP, _VP, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, _VP], C.c_int),
+    "me_faddeeva_pairs": ([_VP, _VP, _VP, C.c_int, C.c_int, _VP, _VP], C.c_int),
+    "me_fp32_peak": ([C.c_int, C.c_int, C.c_int, _VP, _VP, _VP], C.c_int),
     "lm_polish": ([_P, _VP, _VP, _VP, C.c_int, C.POINTER(MeBounds), C.c_int, C.c_double, _VP,
                    _VP, _VP], C.c_int),
     "lm_uncertainty": ([_P, _VP, _VP, _VP, C.c_int, _VP, _VP, _VP], C.c_int),

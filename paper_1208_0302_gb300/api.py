@@ -15,7 +15,7 @@ import torch
 from . import _lib as L
 
 NPAR = L.ME_NPAR          # parameters without the fill fraction
-NPAR_MAX = L.ME_NPAR_MAX  # with it (Section 4.2): Problem(fill=True)
+NPAR_MAX = L.ME_NPAR_MAX  # with it (Section 5.2): Problem(fill=True)
 F32, F64 = L.ME_F32, L.ME_F64
 ALL_FREE = (1 << NPAR_MAX) - 1
 
@@ -198,6 +198,40 @@ def ga_count_evaluations(pb: Problem, obs, lo, hi, ga: GaSettings, w=None, mu_px
             "cf": int(c[2]) - int(c[1]) - int(c[3]) - int(c[4]), "best": best}
 
 
+def ga_fitness(pb: Problem, obs, params, nactive=None, w=None, mu_px=None, want_resid=False):
+    """The GA's fitness of individuals params [npix, npop, M] (float64 CUDA,
+    each value representable in the problem's precision): (fitness [npix,
+    npop] float64, residuals [npix, npop, 4, n_lambda] or None).  Threads
+    k < nactive evaluate (default: all); rows beyond are NaN."""
+    npix, npop = params.shape[0], params.shape[1]
+    _need(obs, pb.torch_dtype, (npix, 4, pb.n_lambda), "obs")
+    _need(params, torch.float64, (npix, npop, pb.npar), "params")
+    _need(w, torch.float64, (npix, 4), "w")
+    _need(mu_px, torch.float64, (npix,), "mu_px")
+    nactive = npop if nactive is None else int(nactive)
+    fit = torch.full((npix, npop), float("nan"), dtype=torch.float64, device=params.device)
+    res = (torch.full((npix, npop, 4, pb.n_lambda), float("nan"), dtype=pb.torch_dtype, device=params.device)
+           if want_resid else None)
+    L.check(L.load().ga_fitness(pb.ref(), _ptr(obs), _ptr(w), _ptr(mu_px), npix, npop, nactive, _ptr(params),
+                                _ptr(fit), _ptr(res), _stream()))
+    return fit, res
+
+
+def faddeeva_pairs(x, a, mode=0, v_b=None):
+    """The pair path's FP32 w(z): x [n, 2] float32 CUDA, a [n] (and v_b [n]
+    for mode 2).  Modes 0 and 1: complex [n, 2]; mode 2: float [n, 2, 6]
+    profile sums (see include/genesis.h)."""
+    n = x.shape[0]
+    _need(x, torch.float32, (n, 2), "x")
+    _need(a, torch.float32, (n,), "a")
+    _need(v_b, torch.float32, (n,), "v_b")
+    out = torch.empty((n, 2, 6 if mode == 2 else 2), dtype=torch.float32, device=x.device)
+    L.check(L.load().me_faddeeva_pairs(_ptr(x), _ptr(a), _ptr(v_b), n, int(mode), _ptr(out), _stream()))
+    if mode == 2:
+        return out
+    return torch.complex(out[..., 0].double(), out[..., 1].double())
+
+
 def zeeman_components(line):
     """The library's Zeeman components of one line tuple (see Problem): list
     of (shifts, strengths) for sigma_b, pi, sigma_r."""
@@ -228,7 +262,7 @@ def lm_polish(pb: Problem, obs, params, lo, hi, iters=10, lambda0=1e-3, w=None, 
 
 
 def lm_uncertainty(pb: Problem, obs, params, w=None, mu_px=None):
-    """Section 5 sigma_i = sqrt([H^-1]_ii chi2 / M), H = (2/nu) J^T W^2 J -> [npix, 9]."""
+    """Section 6 sigma_i = sqrt([H^-1]_ii chi2 / M), H = (2/nu) J^T W^2 J -> [npix, 9]."""
     npix = obs.shape[0]
     _need(obs, pb.torch_dtype, (npix, 4, pb.n_lambda), "obs")
     _need(params, torch.float64, (npix, pb.npar), "params")
@@ -241,7 +275,7 @@ def lm_uncertainty(pb: Problem, obs, params, w=None, mu_px=None):
 
 
 def line_centre(pb: Problem, obs, half_width, i_lo=0, i_hi=1 << 30):
-    """Section 4.1 centre-of-symmetry line centre -> (lambda_c [npix] f64, index [npix] i32)."""
+    """Section 5.1 centre-of-symmetry line centre -> (lambda_c [npix] f64, index [npix] i32)."""
     npix = obs.shape[0]
     _need(obs, pb.torch_dtype, (npix, 4, pb.n_lambda), "obs")
     lc = torch.empty(npix, dtype=torch.float64, device=obs.device)
@@ -254,7 +288,7 @@ def line_centre(pb: Problem, obs, half_width, i_lo=0, i_hi=1 << 30):
 # ------------------------------------------------- selection and seeding
 
 def classify(pb: Problem, obs, p_thresh, quiet, line, core, best=None):
-    """Section 2 selection, weak-field fallback and Section 4.5 seeds.
+    """Section 2 selection, weak-field fallback and Section 5.5 seeds.
     quiet = (lo, hi) half-open quiet window, core = (lo, hi) inclusive line
     window (grid indices).  Returns dict of device tensors: flag, polarity
     (int32 [npix]), p, sigma_p (f64 [npix]), weak (f64 [npix, 5] = B, theta,
@@ -308,8 +342,8 @@ def ga_invert_subset(pb: Problem, obs, lo, hi, ga: GaSettings, index=None, count
                      polarity=None, bounds_px=None, w=None, mu_px=None, pixel_id0=0, best=None, chi2=None,
                      want_genes=False):
     """ga_invert_batch on the pixels index[:count] of a map, seeded and
-    polarity-restricted (Section 4.5), optionally in per-pixel bounds
-    (Section 4.3).  best/chi2 (map-sized) are written in place for those
+    polarity-restricted (Section 5.5), optionally in per-pixel bounds
+    (Section 5.3).  best/chi2 (map-sized) are written in place for those
     pixels and returned."""
     npix = obs.shape[0]
     _need(obs, pb.torch_dtype, (npix, 4, pb.n_lambda), "obs")
@@ -377,7 +411,7 @@ def lm_polish_subset(pb: Problem, obs, params, lo, hi, index=None, count=None, i
                   mu_px=mu_px, chi2=chi2)
 
 
-# Section 4.3 prefit: Stokes I, non-magnetic (B, theta, chi held at 0, 90, 0)
+# Section 5.3 prefit: Stokes I, non-magnetic (B, theta, chi held at 0, 90, 0)
 PREFIT_MASK = 0x1F8
 PREFIT_START = (0.0, 90.0, 0.0, 0.0, 35.0, 0.2, 5.0, 0.3, 0.7)
 # margins of the bound rule (B theta chi v dlD a eta0 S0 S1): Zeeman broadening
@@ -389,7 +423,7 @@ PREFIT_UPPER = (float("inf"),) * 3 + (1.0, 3.0, 0.15, float("inf"), 0.15, 0.15)
 
 def thermo_prefit(pb: Problem, obs, lo, hi, index=None, count=None, iters=40, lambda0=1e-3, mu_px=None,
                   start=PREFIT_START):
-    """Section 4.3 thermodynamic prefit: L-M fit of Stokes I alone with the
+    """Section 5.3 thermodynamic prefit: L-M fit of Stokes I alone with the
     field held at zero, from a generic start -> (params [npix, M], chi2).
     With the fill fraction, alpha is held at 1 (at B = 0 it has no effect)."""
     npix = obs.shape[0]
@@ -427,7 +461,7 @@ def invert_map(pb: Problem, obs, lo, hi, ga: GaSettings, p_thresh, quiet, line, 
                polish_w=None, mu_px=None, pixel_id0=0):
     """The Section 2 pipeline on a map, asynchronous on the current stream:
     classification (weak-field answer below the threshold), selection of the
-    pixels above it, optionally the Section 4.3 prefit and its per-pixel
+    pixels above it, optionally the Section 5.3 prefit and its per-pixel
     bounds, the seeded, polarity-restricted GA and the L-M polish on those.
     Returns dict(best [npix, 9], chi2 [npix] (NaN for weak-field pixels),
     flag, polarity, index, count, weak, seeds[, prefit, bounds_px])."""
@@ -612,3 +646,26 @@ class MeSynthFunction(torch.autograd.Function):
 
 def synth_autograd(pb: Problem, params, mu_px=None):
     return MeSynthFunction.apply(params, pb, mu_px)
+
+
+def fp32_peak(packed=True, nblocks=None, iters=4096, repeats=3):
+    """Measured FP32 FMA-pipe throughput (me_fp32_peak) in TFLOP/s: the best of
+    `repeats` launches timed with CUDA events on the current stream after one
+    warm-up launch; nblocks defaults to 8 blocks of 256 threads per SM."""
+    dev = torch.cuda.current_device()
+    if nblocks is None:
+        nblocks = 8 * torch.cuda.get_device_properties(dev).multi_processor_count
+    out = torch.empty(nblocks * 256, dtype=torch.float32, device="cuda")
+    flops = C.c_double(0.0)
+    lib = L.load()
+    L.check(lib.me_fp32_peak(int(packed), int(nblocks), int(iters), _ptr(out), C.byref(flops), _stream()))
+    best = float("inf")
+    st = torch.cuda.current_stream()
+    for _ in range(repeats):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        L.check(lib.me_fp32_peak(int(packed), int(nblocks), int(iters), _ptr(out), None, _stream()))
+        e1.record(st)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return flops.value / (best / 1e3) / 1e12

@@ -19,8 +19,8 @@ LIBDIR = os.path.join(HERE, "lib")
 BUILDDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(LIBDIR, "libgenesis.so")
 
-UNITS = ["api.cu", "ga_kernels.cu", "ga_fill_kernels.cu", "synth_kernels.cu", "lm_kernels.cu", "classify_kernels.cu",
-         "serve.cu"]
+UNITS = ["api.cu", "ga_kernels.cu", "ga_fill_kernels.cu", "ga_check_kernels.cu", "synth_kernels.cu", "lm_kernels.cu",
+         "classify_kernels.cu", "serve.cu", "peak_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

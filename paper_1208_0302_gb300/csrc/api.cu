@@ -48,7 +48,7 @@ std::vector<double> weideman_coefficients(int N, double L)
     return a;
 }
 
-// Sobol direction numbers (Section 4.6; Sobol 1967, Bratley & Fox 1988):
+// Sobol direction numbers (Section 5.6; Sobol 1967, Bratley & Fox 1988):
 // dimension 0 is van der Corput; dimension d >= 1 takes the d-th primitive
 // polynomial over GF(2) (ordered by degree, then by integer encoding) and
 // initial numbers m_k = 2^k - 1, extended by the Sobol recurrence.
@@ -132,6 +132,7 @@ int ensure_device()
     if ((e = upload_tables_synth(t)) != cudaSuccess) return cuda_fail(e, "upload tables");
     if ((e = upload_tables_lm(t)) != cudaSuccess) return cuda_fail(e, "upload tables");
     if ((e = upload_tables_ga_fill(t)) != cudaSuccess) return cuda_fail(e, "upload tables");
+    if ((e = upload_tables_check(t)) != cudaSuccess) return cuda_fail(e, "upload tables");
     if ((e = select_static_scratch(&g_select_static[dev], &g_select_static_bytes)) != cudaSuccess)
         return cuda_fail(e, "select scratch address");
     g_dev_ready[dev] = true;
@@ -198,7 +199,7 @@ int make_problem(const me_problem *pb, KProblem &k)
 }
 
 // Zeeman components of lower (J_l, g_l) -> upper (J_u, g_u) in LS coupling
-// (Section 4 full pattern), from the closed-form relative line strengths of
+// (Section 5 full pattern), from the closed-form relative line strengths of
 // dipole transitions (Condon & Shortley) for Delta J = 0, +-1, normalised per
 // group q = M_l - M_u (-1 sigma_blue, 0 pi, +1 sigma_red).  Shift of M_u -> M_l
 // in Larmor units toward longer wavelength: g_l M_l - g_u M_u.
@@ -465,6 +466,52 @@ int ga_count_evaluations(const me_problem *pb, const void *obs, const double *w,
     cudaError_t e = launch_ga_count(k, g, pb->dtype, obs, cfg->weight_mode == ME_W_USER ? w : nullptr,
                                     mu_px, npix, best, counts, as_stream(stream));
     return e == cudaSuccess ? ME_OK : cuda_fail(e, "ga_count_evaluations launch");
+}
+
+int ga_fitness(const me_problem *pb, const void *obs, const double *w, const double *mu_px, int npix, int npop,
+               int nactive, const double *params, double *fitness, void *resid, void *stream)
+{
+    KProblem k;
+    int rc = make_problem(pb, k);
+    if (rc) return rc;
+    if (npix < 0) return fail(ME_EINVAL, "npix must be >= 0");
+    if (npop < ME_MIN_POP || npop > ME_MAX_POP || npop % 32)
+        return fail(ME_EINVAL, "npop must be a multiple of 32 in [32, 1024]");
+    if (nactive < 1 || nactive > npop) return fail(ME_EINVAL, "nactive must be in [1, npop]");
+    if (npix == 0) return ME_OK;
+    if (!obs || !params || !fitness) return fail(ME_EINVAL, "obs, params and fitness must be non-NULL");
+    const size_t rs = pb->dtype == ME_F32 ? 4 : 8;
+    const size_t need = rs * (4 + pb->n_lines) * pb->n_lambda + rs * (npop + 72) + 128 +
+                        (size_t)4 * npop * npar_of(pb) + 256;
+    if (need > 220 * 1024) return fail(ME_EINVAL, "population and grid exceed shared memory");
+    if ((rc = ensure_device())) return rc;
+    cudaError_t e = launch_ga_fitness(k, pb->dtype, w ? ME_W_USER : ME_W_INVMAX, obs, w, mu_px, npix, npop, nactive,
+                                      params, fitness, resid, as_stream(stream));
+    return e == cudaSuccess ? ME_OK : cuda_fail(e, "ga_fitness launch");
+}
+
+int me_faddeeva_pairs(const float *x, const float *a, const float *v_b, int n, int mode, float *out, void *stream)
+{
+    if (n < 0) return fail(ME_EINVAL, "n must be >= 0");
+    if (mode < 0 || mode > 2) return fail(ME_EINVAL, "mode must be 0, 1 or 2");
+    if (n == 0) return ME_OK;
+    if (!x || !a || !out || (mode == 2 && !v_b)) return fail(ME_EINVAL, "NULL argument");
+    if (((uintptr_t)x) & 7) return fail(ME_EINVAL, "x must be 8-byte aligned");
+    int rc = ensure_device();
+    if (rc) return rc;
+    cudaError_t e = launch_fad_probe(x, a, v_b, n, mode, out, as_stream(stream));
+    return e == cudaSuccess ? ME_OK : cuda_fail(e, "me_faddeeva_pairs launch");
+}
+
+int me_fp32_peak(int packed, int nblocks, int iters, float *out, double *flops, void *stream)
+{
+    if (nblocks < 1 || iters < 1) return fail(ME_EINVAL, "nblocks and iters must be >= 1");
+    if (!out) return fail(ME_EINVAL, "out must be non-NULL");
+    int rc = ensure_device();
+    if (rc) return rc;
+    if (flops) *flops = fma_peak_flops(packed, nblocks, iters);
+    cudaError_t e = launch_fma_peak(packed, nblocks, iters, out, as_stream(stream));
+    return e == cudaSuccess ? ME_OK : cuda_fail(e, "me_fp32_peak launch");
 }
 
 static int lm_polish_impl(const me_problem *pb, const void *obs, const double *w, const double *mu_px,

@@ -1,4 +1,4 @@
-// Section 2 pixel selection and weak-field fallback, Section 4.5 seeds and
+// Section 2 pixel selection and weak-field fallback, Section 5.5 seeds and
 // polarity, and the order-preserving selection of the pixels to invert.
 #include "kernels.h"
 
@@ -340,7 +340,7 @@ k_select_scatter(const int *__restrict__ flag, int npix, int want, const int *__
         if (bits & (1u << e)) index[pos++] = first + e;
 }
 
-// Section 4.3 bound rule, one thread per (pixel, parameter): [max(lo,
+// Section 5.3 bound rule, one thread per (pixel, parameter): [max(lo,
 // p - lower), min(hi, p + upper)], the global interval where that is empty
 // or the prefit is NaN.
 __global__ void k_prefit_bounds(const double *__restrict__ p_hat, int npix, const KPrefitBounds r,

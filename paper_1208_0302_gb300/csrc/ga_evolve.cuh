@@ -1,6 +1,6 @@
 // Fused genetic-algorithm inversion kernel template for sm_103a (Section 3,
-// Algorithm 1; Section 4.6), shared by the translation units that instantiate
-// it (9 parameters; 10 with the fill fraction of Section 4.2).
+// Algorithm 1; Section 5.6), shared by the translation units that instantiate
+// it (9 parameters; 10 with the fill fraction of Section 5.2).
 //
 //
 // One thread block per pixel, one thread per individual.  The pixel's
@@ -64,7 +64,7 @@ template <class R> __device__ __forceinline__ int padded_lambda(int nl)
 
 template <class R> struct GaDecode;
 // The pixel's decode domain in shared memory (per-pixel bounds of Section
-// 4.3 and the polarity restriction of Section 4.5 already applied):
+// 5.3 and the polarity restriction of Section 5.5 already applied):
 // double lo[M], hi[M], then float lo[M], scale[M] = (hi - lo) / 65535.
 struct DecodeDomain {
     double lo[ME_NPAR_MAX], hi[ME_NPAR_MAX];
@@ -86,10 +86,13 @@ template <> struct GaDecode<double> {
 // Eq. chisq for one individual, FP32 (or FP64) synthesis over the whole grid.
 // s_obs rows are (I, Q, U, V) of one wavelength; s_doff rows hold
 // lambda_j - lambda0_l for l = 0..3: one vector load each per wavelength.
-template <class R, int NL, bool COUNT, bool PAT, bool FILL>
+// STORE (verification kernel only): res, when not NULL, receives the
+// residuals O - S as [4][nl].
+template <class R, int NL, bool COUNT, bool PAT, bool FILL, bool STORE = false>
 __device__ __forceinline__ R fitness_rows(const KProblem &pb, int nlines, int nl, const R *p, R mu,
                                           const R *s_obs, const R *s_doff, const R *he,
-                                          const R *s_w2, R inv_nu, unsigned long long &ninterior)
+                                          const R *s_w2, R inv_nu, unsigned long long &ninterior,
+                                          R *res = nullptr)
 {
     const Geo<R> geo = make_geo<R, NL, FILL>(pb, nlines, p, mu);
     R sI = 0, sQ = 0, sU = 0, sV = 0, cI = 0, cQ = 0, cU = 0, cV = 0;
@@ -99,6 +102,12 @@ __device__ __forceinline__ R fitness_rows(const KProblem &pb, int nlines, int nl
         load4(s_obs + 4 * j, ob);
         const Stokes4<R> s = me_point<R, NL, PAT, FILL>(geo, doff, he, nlines, pb.line);
         if (COUNT) ninterior += count_interior<R, NL, PAT>(geo, doff, nlines, pb.line);
+        if (STORE && res) {
+            res[j] = ob[0] - s.I;
+            res[nl + j] = ob[1] - s.Q;
+            res[2 * nl + j] = ob[2] - s.U;
+            res[3 * nl + j] = ob[3] - s.V;
+        }
         kahan_sq(sI, cI, ob[0] - s.I);
         kahan_sq(sQ, cQ, ob[1] - s.Q);
         kahan_sq(sU, cU, ob[2] - s.U);
@@ -114,12 +123,12 @@ __device__ __forceinline__ R fitness_rows(const KProblem &pb, int nlines, int nl
 // at most about (n/2) u, u = 2^-24, for n wavelengths; the fitness only ranks
 // individuals, and the best individual's chi2 is re-evaluated in FP64
 // afterwards).  Fewer live accumulators keep the loop's state in registers.
-template <int NL, bool COUNT, bool PAT, bool FILL>
+template <int NL, bool COUNT, bool PAT, bool FILL, bool STORE = false>
 __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, int nl, const float *p,
                                                float mu, const float *s_obs, const float *s_doff,
                                                const float *he, const float *s_w2, float inv_nu,
                                                unsigned long long &ninterior, unsigned long long &nmid,
-                                               unsigned long long &nfar)
+                                               unsigned long long &nfar, float *res = nullptr)
 {
     Geo<float> geo = make_geo<float, NL, FILL>(pb, nlines, p, mu);
     pair_thresholds(geo, nlines);
@@ -144,6 +153,19 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
         const Stokes4x2 rr = resid_x2<NL, COUNT, PAT, FILL>(geo, doff2, ob, he, nlines, y_real, cnt, pb.line);
         float2 rI = rr.I, rQ = rr.Q, rU = rr.U, rV = rr.V;
         if (!y_real) rI.y = rQ.y = rU.y = rV.y = 0.f;  // padded partner
+        if (STORE && res) {
+            const int j = 2 * q;
+            res[j] = rI.x;
+            res[nl + j] = rQ.x;
+            res[2 * nl + j] = rU.x;
+            res[3 * nl + j] = rV.x;
+            if (y_real) {
+                res[j + 1] = rI.y;
+                res[nl + j + 1] = rQ.y;
+                res[2 * nl + j + 1] = rU.y;
+                res[3 * nl + j + 1] = rV.y;
+            }
+        }
         sI = fma2(rI, rI, sI);
         sQ = fma2(rQ, rQ, sQ);
         sU = fma2(rU, rU, sU);
@@ -158,18 +180,18 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
             s_w2[3] * (sV.x + sV.y)) * inv_nu;
 }
 
-template <class R, int NL, bool COUNT, bool PAT, bool FILL>
+template <class R, int NL, bool COUNT, bool PAT, bool FILL, bool STORE = false>
 __device__ __forceinline__ R fitness(const KProblem &pb, int nlines, int nl, const R *p, R mu,
                                      const R *s_obs, const R *s_doff, const R *he,
                                      const R *s_w2, R inv_nu, unsigned long long &ninterior,
-                                     unsigned long long &nmid, unsigned long long &nfar)
+                                     unsigned long long &nmid, unsigned long long &nfar, R *res = nullptr)
 {
     if constexpr (std::is_same<R, float>::value)
-        return fitness_pairs<NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu,
-                                                   ninterior, nmid, nfar);
+        return fitness_pairs<NL, COUNT, PAT, FILL, STORE>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2,
+                                                          inv_nu, ninterior, nmid, nfar, res);
     else
-        return fitness_rows<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu,
-                                                     ninterior);
+        return fitness_rows<R, NL, COUNT, PAT, FILL, STORE>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2,
+                                                            inv_nu, ninterior, res);
 }
 
 // argmin over the block's fitness, ties to the lowest index.  Every thread
@@ -300,7 +322,7 @@ __host__ __device__ __forceinline__ GaSmem ga_smem_layout(int nl, int nlines, in
     return L;
 }
 
-// Section 4.5 inverse-max weights of the staged pixel (warp 0), written as w^2.
+// Section 5.4 inverse-max weights of the staged pixel (warp 0), written as w^2.
 template <class R>
 __device__ __forceinline__ void weights_invmax_w2(const R *s_obs, int nl, R *s_w2)
 {
@@ -336,6 +358,67 @@ __device__ __forceinline__ void weights_invmax_w2(const R *s_obs, int nl, R *s_w
     }
 }
 
+// Per-launch constants of a GA block: s_doff in the layout of obs_idx with
+// lambda_j - lambda0_l (exact in FP64, then rounded; a padded partner repeats
+// the last point) and s_he[l] = eta_ratio_l / 2.
+template <class R>
+__device__ __forceinline__ void stage_offsets_ga(const KProblem &pb, int nlines, int nl, int k, R *s_doff,
+                                                 R *s_he)
+{
+    if (k < 4) s_he[k] = k < nlines ? R(pb.line[k].half_eta) : R(0);
+    for (int i = k; i < 4 * padded_lambda<R>(nl); i += blockDim.x) {
+        const int j = i >> 2, l = i & 3;
+        const int jj = j < nl ? j : nl - 1;
+        s_doff[obs_idx<R>(l, j)] = l < nlines ? R(pb.lam[jj] - pb.line[l].lam0) : R(0);
+    }
+}
+
+// a1: one pixel's Stokes profiles from [4][nl] in HBM into the shared-memory
+// layout of obs_idx (16-byte vector loads when a vector stays in one row).
+template <class R>
+__device__ __forceinline__ void stage_obs(const R *o, int nl, int k, R *s_obs)
+{
+    constexpr int VW = 16 / (int)sizeof(R);  // elements per 16-byte vector
+    if (nl % VW == 0 && (((uintptr_t)o) & 15) == 0) {
+        for (int i = k; i < 4 * nl / VW; i += blockDim.x) {
+            const int e = i * VW, st = e / nl, j = e - st * nl;
+            if (VW == 4) {
+                const float4 q = __ldg((const float4 *)o + i);
+                s_obs[obs_idx<R>(st, j)] = R(q.x);
+                s_obs[obs_idx<R>(st, j + 1)] = R(q.y);
+                s_obs[obs_idx<R>(st, j + 2)] = R(q.z);
+                s_obs[obs_idx<R>(st, j + 3)] = R(q.w);
+            } else {
+                const double2 q = __ldg((const double2 *)o + i);
+                s_obs[obs_idx<R>(st, j)] = R(q.x);
+                s_obs[obs_idx<R>(st, j + 1)] = R(q.y);
+            }
+        }
+    } else {
+        for (int i = k; i < 4 * nl; i += blockDim.x) {
+            const int st = i / nl, j = i - st * nl;
+            s_obs[obs_idx<R>(st, j)] = o[i];
+        }
+    }
+    if (padded_lambda<R>(nl) > nl && k < 4) s_obs[obs_idx<R>(k, nl)] = o[k * nl + nl - 1];
+}
+
+// a2: the pixel's squared weights, the caller's (ME_W_USER) or Section 5.4's
+// inverse-max weights of the staged profiles (warp 0).
+template <class R>
+__device__ __forceinline__ void stage_weights(int weight_mode, const double *w_user, int pix, const R *s_obs,
+                                              int nl, int k, R *s_w2)
+{
+    if (weight_mode == ME_W_USER) {
+        if (k < 4) {
+            const double wv = w_user[(size_t)pix * 4 + k];
+            s_w2[k] = R(wv * wv);
+        }
+    } else if (k < 32) {
+        weights_invmax_w2<R>(s_obs, nl, s_w2);
+    }
+}
+
 // Register budget of the FP32 npop <= 256 instantiations: MAXT * GENESIS_GA_MINB
 // threads must fit an SM's 64K registers, which caps registers per thread
 // (more resident warps hide the FP32 pipe latency).  FP64 instantiations are
@@ -359,7 +442,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
             uint16_t *__restrict__ best_genes, unsigned long long *__restrict__ counts,
             const KSeed sd, const KSub sub)
 {
-    constexpr bool FILL = M > ME_NPAR;  // parameter 9: the fill fraction (Section 4.2)
+    constexpr bool FILL = M > ME_NPAR;  // parameter 9: the fill fraction (Section 5.2)
     unsigned long long nfit = 0, ninterior = 0, nmid = 0, nfar = 0;
     extern __shared__ __align__(16) unsigned char smem[];
     const int nl = pb.n_lambda;
@@ -379,13 +462,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
 
     // per-launch constants
     const R inv_nu = R(1) / R(4 * nl - M);
-    if (k < 4) s_he[k] = k < nlines ? R(pb.line[k].half_eta) : R(0);
-    for (int i = k; i < 4 * padded_lambda<R>(nl); i += blockDim.x) {
-        const int j = i >> 2, l = i & 3;
-        const int jj = j < nl ? j : nl - 1;  // a padded partner repeats the last point
-        // exact difference in FP64, then rounded
-        s_doff[obs_idx<R>(l, j)] = l < nlines ? R(pb.lam[jj] - pb.line[l].lam0) : R(0);
-    }
+    stage_offsets_ga<R>(pb, nlines, nl, k, s_doff, s_he);
 
     const int nrun = sub.count ? min(*sub.count, npix) : npix;
     for (int blk = blockIdx.x; blk < nrun; blk += gridDim.x) {
@@ -400,42 +477,11 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
             D.lo32[k] = (float)a;
             D.sc32[k] = (float)((b - a) / 65535.0);
         }
-        // a1: stage the pixel's Stokes profiles from [4][nl] in HBM into the
-        // shared-memory layout (16-byte vector loads when a vector stays in one row)
-        const R *o = obs + (size_t)pix * 4 * nl;
-        constexpr int VW = 16 / (int)sizeof(R);  // elements per 16-byte vector
-        if (nl % VW == 0 && (((uintptr_t)o) & 15) == 0) {
-            for (int i = k; i < 4 * nl / VW; i += blockDim.x) {
-                const int e = i * VW, st = e / nl, j = e - st * nl;
-                if (VW == 4) {
-                    const float4 q = __ldg((const float4 *)o + i);
-                    s_obs[obs_idx<R>(st, j)] = R(q.x);
-                    s_obs[obs_idx<R>(st, j + 1)] = R(q.y);
-                    s_obs[obs_idx<R>(st, j + 2)] = R(q.z);
-                    s_obs[obs_idx<R>(st, j + 3)] = R(q.w);
-                } else {
-                    const double2 q = __ldg((const double2 *)o + i);
-                    s_obs[obs_idx<R>(st, j)] = R(q.x);
-                    s_obs[obs_idx<R>(st, j + 1)] = R(q.y);
-                }
-            }
-        } else {
-            for (int i = k; i < 4 * nl; i += blockDim.x) {
-                const int st = i / nl, j = i - st * nl;
-                s_obs[obs_idx<R>(st, j)] = o[i];
-            }
-        }
-        if (padded_lambda<R>(nl) > nl && k < 4) s_obs[obs_idx<R>(k, nl)] = o[k * nl + nl - 1];
+        // a1: stage the pixel's Stokes profiles
+        stage_obs<R>(obs + (size_t)pix * 4 * nl, nl, k, s_obs);
         __syncthreads();
         // a2: weights
-        if (ga.weight_mode == ME_W_USER) {
-            if (k < 4) {
-                const double wv = w_user[(size_t)pix * 4 + k];
-                s_w2[k] = R(wv * wv);
-            }
-        } else if (k < 32) {
-            weights_invmax_w2<R>(s_obs, nl, s_w2);
-        }
+        stage_weights<R>(ga.weight_mode, w_user, pix, s_obs, nl, k, s_w2);
         __syncthreads();
         R he[ME_MAX_LINES];
 #pragma unroll

@@ -1,4 +1,4 @@
-// The fill-fraction instantiations of the GA kernel (Section 4.2: ten
+// The fill-fraction instantiations of the GA kernel (Section 5.2: ten
 // parameters, the tenth the magnetic fill fraction), built in a translation
 // unit of their own so that the library's units compile in parallel.
 #include "ga_evolve.cuh"

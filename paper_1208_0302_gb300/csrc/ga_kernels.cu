@@ -1,5 +1,5 @@
 // Fused genetic-algorithm inversion kernel for sm_103a (Section 3, Algorithm 1;
-// Section 4.6), plus the operator-only kernels used to verify it.
+// Section 5.6), plus the operator-only kernels used to verify it.
 //
 // One thread block per pixel, one thread per individual.  The pixel's
 // observed Stokes profiles, its wavelength offsets, the population's uint16

@@ -9,7 +9,7 @@
 
 namespace genesis {
 
-// GA launch parameters (Section 3 operators, Section 4.6 restarts).
+// GA launch parameters (Section 3 operators, Section 5.6 restarts).
 struct KGa {
     int npop, ngen, nsamp, weight_mode;
     uint64_t seed, pixel_id0;
@@ -32,12 +32,12 @@ inline void philox_round_keys(uint64_t seed, uint32_t rk[10][2])
     }
 }
 
-// Parameters per model: 9, or 10 with the fill fraction of Section 4.2.
+// Parameters per model: 9, or 10 with the fill fraction of Section 5.2.
 template <bool FILL> constexpr int kNpar = ME_NPAR + (FILL ? 1 : 0);
 
-// Section 4.5 seeds and polarity restriction: seeds [npix][nseed][3] of
+// Section 5.5 seeds and polarity restriction: seeds [npix][nseed][3] of
 // (B, psi, chi), NaN = keep the Sobol gene; polarity [npix] of -1, 0, +1;
-// per-pixel bounds [npix][2][M] of Section 4.3 (NULL = the launch's).
+// per-pixel bounds [npix][2][M] of Section 5.3 (NULL = the launch's).
 struct KSeed {
     const double *seeds;
     int nseed;
@@ -59,7 +59,7 @@ struct KLm {
     double lo[ME_NPAR_MAX], hi[ME_NPAR_MAX];
 };
 
-// Section 4.3 bound rule around a prefit (margins per parameter).
+// Section 5.3 bound rule around a prefit (margins per parameter).
 struct KPrefitBounds {
     int npar;
     double lo[ME_NPAR_MAX], hi[ME_NPAR_MAX], lower[ME_NPAR_MAX], upper[ME_NPAR_MAX];
@@ -78,6 +78,7 @@ cudaError_t upload_tables_ga(const HostTables &t);
 cudaError_t upload_tables_synth(const HostTables &t);
 cudaError_t upload_tables_lm(const HostTables &t);
 cudaError_t upload_tables_ga_fill(const HostTables &t);
+cudaError_t upload_tables_check(const HostTables &t);
 
 // ga_kernels.cu
 cudaError_t launch_ga_evolve(const KProblem &pb, const KGa &ga, int dtype, const void *obs,
@@ -90,6 +91,15 @@ cudaError_t launch_ga_evolve_fill(const KProblem &pb, const KGa &ga, int dtype, 
 cudaError_t launch_ga_count(const KProblem &pb, const KGa &ga, int dtype, const void *obs,
                             const double *w, const double *mu_px, int npix, double *best,
                             unsigned long long *counts, cudaStream_t st);
+// true when a line of the problem carries its full Zeeman pattern
+bool has_pattern(const KProblem &pb);
+// ga_check_kernels.cu: the GA's fitness on given individuals and the pair
+// path's w(z) branches (verification entry points)
+cudaError_t launch_ga_fitness(const KProblem &pb, int dtype, int weight_mode, const void *obs, const double *w,
+                              const double *mu_px, int npix, int npop, int nactive, const double *params,
+                              double *fit, void *res, cudaStream_t st);
+cudaError_t launch_fad_probe(const float *x, const float *a, const float *vB, int n, int mode, float *out,
+                             cudaStream_t st);
 cudaError_t launch_ga_breed(const KGa &ga, int npar, const uint16_t *genes, const double *fit, int nprob,
                             int gen, uint16_t *child, int *elite, cudaStream_t st);
 cudaError_t launch_ga_restart(int npop, int npar, uint16_t *genes, const double *fit, int nprob,
@@ -108,7 +118,7 @@ cudaError_t launch_chi2_f64(const KProblem &pb, int dtype, const void *obs, cons
                             const double *mu_px, int npix, const double *params, double *chi2,
                             cudaStream_t st, KSub sub = {});
 
-// Section 2 selection, weak-field estimate and Section 4.5 seeds.
+// Section 2 selection, weak-field estimate and Section 5.5 seeds.
 struct KClassify {
     double p_thresh, kz;  // kz = 4.6686e-13 g lambda0^2 of the chosen line
     int q_lo, q_hi, c_lo, c_hi, npar;
@@ -137,6 +147,11 @@ cudaError_t launch_lm(const KProblem &pb, const KLm &lm, int dtype, const void *
                       const double *w, const double *mu_px, int npix, double *params,
                       cudaStream_t st, KSub sub = {});
 
+// peak_kernels.cu: FP32 FMA-pipe throughput probe (measurement only)
+double fma_peak_flops(int packed, int nblocks, int iters);
+int fma_peak_threads();
+cudaError_t launch_fma_peak(int packed, int nblocks, int iters, float *out, cudaStream_t st);
+
 // api.cu: argument validation shared by the C entry points and the serving
 // loop.  Each returns ME_OK or an ME_E* code with the thread-local message set.
 extern thread_local std::string g_last_error;
@@ -156,7 +171,7 @@ __device__ __forceinline__ double decode64(uint16_t g, double lo, double hi)
     return __dadd_rn(lo, __dmul_rn(__dsub_rn(hi, lo), __ddiv_rn((double)g, 65535.0)));
 }
 
-// Nearest gene of a seed value (Section 4.5), the inverse of the decode:
+// Nearest gene of a seed value (Section 5.5), the inverse of the decode:
 // t = (x - lo) / (hi - lo) clamped to [0, 1], g = floor(65535 t + 1/2).
 __device__ __forceinline__ uint16_t encode64(double x, double lo, double hi)
 {
@@ -166,7 +181,7 @@ __device__ __forceinline__ uint16_t encode64(double x, double lo, double hi)
     return (uint16_t)floor(__dadd_rn(__dmul_rn(t, 65535.0), 0.5));
 }
 
-// Section 4.5 polarity restriction of the inclination domain [lo, hi]:
+// Section 5.5 polarity restriction of the inclination domain [lo, hi]:
 // +1 keeps [lo, min(hi, 90)], -1 keeps [max(lo, 90), hi]; 0, or a half
 // that would be empty, keeps [lo, hi].
 __host__ __device__ __forceinline__ void polarity_bounds(int pol, double lo, double hi, double &a,

@@ -177,7 +177,7 @@ __device__ bool warp_damped_solve(LmWarpSmem<R> &W, unsigned free_mask, double &
 }
 
 
-// Weights of one pixel into w2 (squared): the caller's, or Section 4.5
+// Weights of one pixel into w2 (squared): the caller's, or Section 5.4
 // inverse-max in FP64.  Every lane gets the result.
 template <class RO, class R>
 __device__ void lm_weights(const RO *o, int nl, const double *w_user, int pix, LmWarpSmem<R> &W, double w2[4])
@@ -364,7 +364,7 @@ k_lm(const __grid_constant__ KProblem pb, const __grid_constant__ KLm lm, const 
     }
 }
 
-// Section 5 uncertainty estimate at given parameters: sigma_i^2 =
+// Section 6 uncertainty estimate at given parameters: sigma_i^2 =
 // [H^-1]_ii chi2 / M with H the Gauss-Newton Hessian of Eq. chisq,
 // H = (2/nu) J^T W^2 J.  Warp per pixel; J and its sums in the problem
 // precision, the Cholesky factor and the inverse diagonal in FP64 (lane i

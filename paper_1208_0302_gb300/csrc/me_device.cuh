@@ -1,6 +1,6 @@
 // Device-side Milne-Eddington synthesis for sm_103a.
 //
-// Section 4 of Harker & Mighell (2012): K = 1 + eta0 Phi, the emergent Stokes
+// Section 5 of Harker & Mighell (2012): K = 1 + eta0 Phi, the emergent Stokes
 // vector S0 e + mu S1 K^-1 e, with Voigt / Faraday-Voigt profiles for the
 // sigma_b, pi and sigma_r components of every line.  All templates take the
 // arithmetic type R (float or double).
@@ -275,8 +275,8 @@ __device__ __forceinline__ void sincos_deg(double d, double *s, double *c)
     sincospi(d * (1.0 / 180.0), s, c);
 }
 
-// Geometry of one parameter vector p (Section 4 model vector), in R.
-// FILL: p[9] is the fill fraction alpha of Section 4.2.
+// Geometry of one parameter vector p (Section 5 model vector), in R.
+// FILL: p[9] is the fill fraction alpha of Section 5.2.
 template <class R, int NL, bool FILL = false>
 __device__ __forceinline__ Geo<R> make_geo(const KProblem &pb, int nlines, const R *p, R mu)
 {
@@ -319,7 +319,7 @@ __device__ __forceinline__ Geo<R> make_geo(const KProblem &pb, int nlines, const
 
 template <class R> struct Stokes4 { R I, Q, U, V; };
 
-// Section 4.2 fill fraction: Stokes <- alpha Stokes + (1 - alpha) I_nm e with
+// Section 5.2 fill fraction: Stokes <- alpha Stokes + (1 - alpha) I_nm e with
 // the field-free I_nm = S0 + mu S1 / (1 + eta0 sum_l eta_ratio_l Re w0_l)
 // (w0 the unshifted profile); P0 = sum_l (eta_ratio_l / 2) Re w0_l.
 template <class R>

@@ -1,6 +1,6 @@
 // Analytic Jacobian of the Milne-Eddington Stokes vector (sm_103a).
 //
-// Differentiates Section 4's solution S0 e + mu S1 K^-1 e through the closed
+// Differentiates Section 5's solution S0 e + mu S1 K^-1 e through the closed
 // form of K^-1 e, the propagation-matrix elements and the Faddeeva profiles,
 // using w'(z) = -2 z w(z) + 2 i / sqrt(pi) and dw/da = i w'(z).
 #pragma once
@@ -65,7 +65,7 @@ template <class R> struct Sums {
 };
 
 // Stokes vector and J[s][k] = d Stokes_s / d p_k at one wavelength.
-// FILL: Section 4.2 fill fraction, p[9] = alpha, J has a 10th column.
+// FILL: Section 5.2 fill fraction, p[9] = alpha, J has a 10th column.
 template <class R, int NL, bool FILL = false>
 __device__ __forceinline__ void me_point_jac(const GeoJ<R> &G, const R *doff, const R *half_eta,
                                              int nlines, const KLine *lines, Stokes4<R> &out,

@@ -256,10 +256,21 @@ __device__ __forceinline__ void triplet_acc(float2 xb, float2 v, float2 xr, cons
     Di = fma2(q, wy, Di);
 }
 
+// The branch level of an effective triplet for a pair, voted across the warp
+// from its pi arguments v (the sigma arguments are v +- v_B): 2 when every
+// lane's triplet is wholly in the far field (|v| > t_far + |v_B|), 1 when
+// wholly beyond the continued-fraction threshold, 0 near a line core.
+__device__ __forceinline__ int triplet_level(float2 v, const Geo<float> &g, int l)
+{
+    const float mv = pair_min_abs(v);
+    if (warp_all(mv > g.t3[l], g.vmask)) return warp_all(mv > g.t3far[l], g.vmask) ? 2 : 1;
+    return 0;
+}
+
 // Residuals o - Stokes at two wavelength points (the synthesis of Section
-// 4.1 and the difference of Eq. chisq).  doff2[l] holds (lambda_j -
+// 5 and the difference of Eq. chisq).  doff2[l] holds (lambda_j -
 // lambda0_l, lambda_{j+1} - lambda0_l).  FILL mixes in the field-free
-// profile with the fill fraction (Section 4.2, see fill_mix).
+// profile with the fill fraction (Section 5.2, see fill_mix).
 template <int NL, bool COUNT, bool PAT, bool FILL = false>
 __device__ __forceinline__ Stokes4x2 resid_x2(const Geo<float> &g, const float2 *doff2, const Stokes4x2 &o,
                                               const float *half_eta, int nlines, bool y_real,
@@ -300,15 +311,13 @@ __device__ __forceinline__ Stokes4x2 resid_x2(const Geo<float> &g, const float2 
                 count_pair(xr, g.a2, y_real, ncount);
             }
             const float2 q = f2(half_eta[l]);
-            const float mv = pair_min_abs(v);
-            if (warp_all(mv > g.t3[l], g.vmask)) {
-                if (warp_all(mv > g.t3far[l], g.vmask))
-                    triplet_acc<2, FILL>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
-                else
-                    triplet_acc<1, FILL>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
-            } else {
+            const int lev = triplet_level(v, g, l);
+            if (lev == 2)
+                triplet_acc<2, FILL>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
+            else if (lev == 1)
+                triplet_acc<1, FILL>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
+            else
                 triplet_acc<0, FILL>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
-            }
         }
     }
     // closed form of K^-1 e (see me_point), with G = eI^2 + rho^2 shared by

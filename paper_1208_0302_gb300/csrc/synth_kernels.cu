@@ -159,7 +159,7 @@ k_vjp(const __grid_constant__ KProblem pb, const double *__restrict__ params,
 }
 
 // FP64 chi-square (Eq. chisq) of given parameters, one block per pixel,
-// threads over wavelengths.  Inverse-max weights (Section 4.5) are formed in
+// threads over wavelengths.  Inverse-max weights (Section 5.4) are formed in
 // FP64 from the observed values when w is NULL.
 template <class RO, bool FILL = false>
 __global__ void __launch_bounds__(kSynthBlock)
@@ -257,7 +257,7 @@ k_chi2_f64(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
     }
 }
 
-// Section 4.1 centre of symmetry, one warp per pixel: lanes scan candidates,
+// Section 5.1 centre of symmetry, one warp per pixel: lanes scan candidates,
 // each sums |I(i+j) - I(i-j)| in FP64 in increasing j; warp argmin (ties to
 // the lowest index); lane 0 refines with the three-point parabola vertex,
 // written without contraction.

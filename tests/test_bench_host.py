@@ -17,7 +17,7 @@ def _walk_schedule(npop, ngen, nsamp):
     """Fitness evaluations of one pixel, generation by generation: the
     initial population, every child of generations 1..ngen, and the worst
     half again after generation t whenever t is a multiple of nsamp and
-    t < ngen (Section 4.6 restarts)."""
+    t < ngen (Section 5.6 restarts)."""
     n = npop
     for t in range(1, ngen + 1):
         n += npop

@@ -5,7 +5,7 @@ each transition's term symbols (2S+1, L, J) the LS-coupling Lande factors
 g = 1 + [J(J+1) + S(S+1) - L(L+1)] / [2J(J+1)] are formed here, the oracle
 builds the full pattern, and its sigma-group first moment (the effective
 Lande factor) must equal the printed g_eff to the printed three decimals; the
-6301.5 pattern must have four components in each group (Section 7)."""
+6301.5 pattern must have four components in each group (Section 6)."""
 import os
 import re
 

@@ -1,4 +1,4 @@
-"""Section 4.1 line centre on the GPU: bit-exact with the oracle."""
+"""Section 5.1 line centre on the GPU: bit-exact with the oracle."""
 import numpy as np
 import pytest
 import torch

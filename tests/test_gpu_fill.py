@@ -1,4 +1,4 @@
-"""GPU fill fraction (Section 4.2, parameter 9) against the oracle: synthesis,
+"""GPU fill fraction (Section 5.2, parameter 9) against the oracle: synthesis,
 Jacobian, adjoint, the GA (bit-exact in FP64 on margin-safe pixels and
 through the operator entry points), the L-M polish, the uncertainty, the
 serving loop and the classification's weak-field rows."""

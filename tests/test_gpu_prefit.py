@@ -1,4 +1,4 @@
-"""GPU Section 4.3 prefit pieces against the oracle: the masked L-M
+"""GPU Section 5.3 prefit pieces against the oracle: the masked L-M
 (lm_fit), the bound rule (me_prefit_bounds, bit-exact) and the GA in
 per-pixel bounds (bit-exact in FP64 on the pixels whose decisions the oracle
 separates by more than the FP64 evaluation error)."""

@@ -1,4 +1,4 @@
-"""Section 5 uncertainties on the GPU against the oracle."""
+"""Section 6 uncertainties on the GPU against the oracle."""
 import numpy as np
 import pytest
 import torch

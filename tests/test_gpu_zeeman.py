@@ -1,4 +1,4 @@
-"""Full Zeeman pattern (Section 4; Fe I 6301.5 5P2-5D2) on the GPU against the
+"""Full Zeeman pattern (Section 5; Fe I 6301.5 5P2-5D2) on the GPU against the
 oracle: synthesis, Jacobian and whole FP64 GA runs."""
 import numpy as np
 import pytest

@@ -1,4 +1,4 @@
-"""Pins of the oracle's Section 4.1 centre-of-symmetry line centre."""
+"""Pins of the oracle's Section 5.1 centre-of-symmetry line centre."""
 import numpy as np
 
 import genesis_inputs as gi

@@ -1,5 +1,5 @@
 """Pins of the oracle's Section 2 pixel selection, weak-field fallback and
-Section 4.5 seeds.
+Section 5.5 seeds.
 
 The pins come from outside the oracle's own formulas: hand-sized cases
 whose variances and maxima are known; profiles built to satisfy the

@@ -1,4 +1,4 @@
-"""Pins of the oracle's Faddeeva function w(z) = H + i F (Section 4 profiles).
+"""Pins of the oracle's Faddeeva function w(z) = H + i F (Section 5 profiles).
 
 The oracle evaluates w by the Matta-Reichel trapezoid; these tests pin it to
 things it does not compute that way: brute-force quadrature of the Voigt and

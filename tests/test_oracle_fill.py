@@ -1,4 +1,4 @@
-"""Pins of the oracle's Section 4.2 fill fraction alpha (10th parameter).
+"""Pins of the oracle's Section 5.2 fill fraction alpha (10th parameter).
 
 * alpha = 1 is the 9-parameter synthesis, bit for bit.
 * alpha = 0 leaves Q = U = V = 0 and an I equal to the 9-parameter
@@ -8,7 +8,7 @@
 * The model is affine in alpha, and the Jacobian's alpha column is the
   difference of the two end members.
 * L-M recovers noiseless truth including alpha; the zero-generation GA
-  places a seed in a 10-gene individual; the Section 5 uncertainty matches a
+  places a seed in a 10-gene individual; the Section 6 uncertainty matches a
   finite-difference Hessian in 10 dimensions.
 """
 import numpy as np

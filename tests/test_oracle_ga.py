@@ -1,4 +1,4 @@
-"""Pins of the oracle's genetic algorithm (Section 3, Algorithm 1; Section 4.6).
+"""Pins of the oracle's genetic algorithm (Section 3, Algorithm 1; Section 5.6).
 
 The operators' exact forms are readings (the paper names them only), so they
 are pinned by properties that follow from those readings independently of the

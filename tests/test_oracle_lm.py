@@ -76,7 +76,7 @@ def test_lm_never_increases_chi2(orc):
 
 
 def test_uncertainty_matches_finite_difference_hessian(orc):
-    """Section 5: sigma_i^2 = [H^-1]_ii chi2 / M.  The oracle forms H = (2/nu)
+    """Section 6: sigma_i^2 = [H^-1]_ii chi2 / M.  The oracle forms H = (2/nu)
     J^T W^2 J; at a least-squares optimum with small residuals this equals the
     Hessian of chi2 itself, recomputed here by central second differences."""
     spec = gi.two_line_spec(n_lambda=64)

@@ -1,4 +1,4 @@
-"""Pins of the oracle's Unno-Rachkovsky synthesis, weights and chi2 (Section 4).
+"""Pins of the oracle's Unno-Rachkovsky synthesis, weights and chi2 (Section 5).
 
 Each check is something the physics or mathematics fixes independently of how
 the oracle computes the Stokes vector: the direct 4x4 solve, the symmetries of

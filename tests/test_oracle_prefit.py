@@ -1,4 +1,4 @@
-"""Pins of the oracle's Section 4.3 thermodynamic prefit pieces: the L-M
+"""Pins of the oracle's Section 5.3 thermodynamic prefit pieces: the L-M
 parameter mask, the bound rule around a prefit, and per-pixel GA bounds.
 
 * Held parameters never move, bit for bit, and a Stokes-I-only fit with the

@@ -1,4 +1,4 @@
-"""Pins of the oracle's Section 4.5 seeding and polarity restriction.
+"""Pins of the oracle's Section 5.5 seeding and polarity restriction.
 
 * The seed encoding is the nearest gene: a round trip through the decode is
   the identity on all 65536 genes, and brute force over every gene finds
@@ -81,7 +81,7 @@ def test_polarity_confines_inclination(orc):
 
 def test_seeds_from_classification_help(orc):
     """Seeding the GA with the weak-field and related estimates improves the
-    short-run fit of weak-field pixels on average (Section 4.5)."""
+    short-run fit of weak-field pixels on average (Section 5.5)."""
     spec = gi.two_line_spec(n_lambda=96)
     truth = gi.draw_truth(24, seed=21)
     truth[:, 0] = np.linspace(100.0, 600.0, 24)

@@ -1,4 +1,4 @@
-"""Pins of the oracle's full Zeeman pattern (Section 4: the pattern of the
+"""Pins of the oracle's full Zeeman pattern (Section 5: the pattern of the
 configured line is computed at start-up; Fe I 6301.5, 5P2-5D2, has four
 components in each of sigma_b, pi, sigma_r).
 

@@ -1,6 +1,6 @@
 """The library's Zeeman components (closed-form Delta J = 0, +-1 line strengths,
 computed on the host) against the oracle's (Racah 3j symbols): two independent
-constructions of the Section 4 full pattern.  No GPU needed."""
+constructions of the Section 5 full pattern.  No GPU needed."""
 import numpy as np
 import pytest
 
