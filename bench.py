@@ -40,11 +40,11 @@ E2E_STEPS_MAX = 5   # the end-to-end leg repeats at most this many steps
 NPOP, NGEN, LM_ITERS = 128, 200, 10
 KERNELS_PER_STEP = 4  # GA evolve, FP64 chi2, L-M, FP64 chi2
 # DRAM bytes (read + write) per pixel of one GA launch, from an ncu capture of
-# k_ga_evolve on the 1024-pixel two-line case (dram__bytes_read.sum 2524160 +
-# dram__bytes_write.sum 0, divided by 1024; traffic grows in proportion to
+# k_ga_evolve on the 4096-pixel two-line case (dram__bytes_read.sum 8579840 +
+# dram__bytes_write.sum 0, divided by 4096; traffic grows in proportion to
 # pixels: each block reads its pixel's cube row once).  Set to None whenever
 # the kernel changes, until it is captured again.
-GA_DRAM_BYTES_PER_PIXEL = (2524160 + 0) / 1024
+GA_DRAM_BYTES_PER_PIXEL = (8579840 + 0) / 4096
 
 
 def parse():
@@ -145,11 +145,12 @@ def flop_model(nlines):
     continued-fraction region (3rd convergent, 31) and in the far field
     (two-node approximant, 17); and per wavelength
     point 22 per line for the component arguments and profile sums, 36 for K
-    and its closed-form inverse, 20 for the four Stokes values formed into
-    their residuals and 8 for the residuals' squares in the running sums.  Each point's evaluations are classified by its own region;
-    branch tests, votes and work a pair or warp does beyond that are not
-    counted."""
-    return {"weideman": 91.0, "mid": 45.0, "cf": 31.0, "far": 17.0, "point": 22.0 * nlines + 64.0}
+    and its closed-form inverse, 21 for the four Stokes values formed into
+    their weighted residuals (w_I by one multiply), 7 for the four squares
+    summed by FMA and 4 for the Kahan-compensated running sum.  Each point's
+    evaluations are classified by its own region; branch tests, votes and work
+    a pair or warp does beyond that are not counted."""
+    return {"weideman": 91.0, "mid": 45.0, "cf": 31.0, "far": 17.0, "point": 22.0 * nlines + 68.0}
 
 
 def run_ours(args):
@@ -295,7 +296,7 @@ def run_ours(args):
         if not args.no_fp64:
             result["fp64_plain_ga"] = fp64_comparator(api, torch, pb64, obs, w, lo, hi, rank)
         if not args.no_serve:
-            result["serving"] = serving(api, torch, pb32, dev, args.serve_seconds, loads=(0.7,))
+            result["serving"] = serving(api, torch, pb32, dev, args.serve_seconds, loads=(0.7, 1.2))
         if not args.no_pipeline:
             result["pipeline"] = pipeline_sample(api, torch, dev)
         if not args.no_cpu and world == 1:

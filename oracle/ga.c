@@ -8,15 +8,24 @@
  *                  toward better fitness)
  *   recombination  one-point crossover of the MSB-first 16M-bit string of a
  *                  pair (2q, 2q+1) with probability pc
- *   mutation M     bit b (0 = MSB) of every word flips with probability
- *                  pmut_lsb * ratio^(15-b): less-significant bits mutate more
+ *   mutation M     bit b (0 = MSB) of every word flips on its own with
+ *                  probability q_b = pmut_lsb * ratio^(15-b): less-significant
+ *                  bits mutate more
  *   elitism        child slot 0 takes the best parent unchanged
  *   restart        every nsamp generations (t < ngen) the worst half is
  *                  replaced by the next Sobol points (Section 5.6)
  * Random numbers: Philox4x32-10, key = (seed lo, seed hi), counter =
- * (pixel id lo, pixel id hi, generation, index << 8 | purpose) with purpose 0
- * = tournament of child slot index, 1 = crossover of pair index, 2 + g =
- * mutation bits 4g .. 4g+3 of child slot index.
+ * (pixel id lo, pixel id hi, generation, index << 8 | purpose).  Purpose 0:
+ * words 0, 1 drive the tournament of child slot index, and for an even index
+ * words 2, 3 drive the crossover of the pair (index, index + 1).  Purposes
+ * 2, 3, ...: the child slot's mutation draws, four per block, used in order.
+ * The mutation places the flips of each word by jumps: with bits 0..b of the
+ * word still open (b = 15, the LSB, first), a draw u at or above
+ * A(b, 0) = floor(2^32 P(a flip among bits 0..b)) leaves them unflipped;
+ * otherwise the next flip is bit c, the largest c <= b with u < A(b, c) =
+ * floor(2^32 (1 - prod_{d=c..b} (1 - q_d))), and bits 0..c-1 remain open.
+ * Each bit thus flips independently with probability q_b (up to the 2^-32
+ * rounding of the thresholds), at about 1 + sum_b q_b draws per word.
  *
  * TEST INFRASTRUCTURE ONLY (see oracle.h).
  */
@@ -47,11 +56,26 @@ static uint64_t prob_threshold(double p)
     return (uint64_t)floor(p * 4294967296.0);
 }
 
-static uint64_t mutation_threshold(const or_ga_config *cfg, int b)
+/* A[b][c] for c <= b: floor(2^32 (1 - prod_{d=c..b} (1 - q_d))), the chance
+ * that a flip falls among bits c..b, with q_d = pmut_lsb ratio^(15-d) clamped
+ * to [0, 1] (ratio^k by repeated multiplication, the product taken from d = b
+ * down to c). */
+static void mutation_table(const or_ga_config *cfg, uint64_t A[16][16])
 {
-    double r = 1.0;
-    for (int k = 0; k < 15 - b; ++k) r *= cfg->pmut_ratio;
-    return prob_threshold(cfg->pmut_lsb * r);
+    double q[16];
+    for (int d = 0; d < 16; ++d) {
+        double r = 1.0;
+        for (int k = 0; k < 15 - d; ++k) r *= cfg->pmut_ratio;
+        const double p = cfg->pmut_lsb * r;
+        q[d] = p > 0.0 ? (p < 1.0 ? p : 1.0) : 0.0;
+    }
+    for (int b = 0; b < 16; ++b) {
+        double none = 1.0;
+        for (int c = b; c >= 0; --c) {
+            none *= 1.0 - q[c];
+            A[b][c] = prob_threshold(1.0 - none);
+        }
+    }
 }
 
 static int argmin_f(const double *f, int n)
@@ -76,14 +100,14 @@ int or_ga_breed(const uint16_t *genes, const double *f, int npop, int m,
         const int win = (fj < fi || (fj == fi && j < i)) ? j : i;
         memcpy(child + (size_t)k * m, genes + (size_t)win * m, sizeof(uint16_t) * m);
     }
-    /* R: one-point crossover of each pair */
+    /* R: one-point crossover of each pair, from words 2, 3 of the even slot's block */
     const uint64_t tc = prob_threshold(cfg->pc);
     const int nbits = 16 * m;
     for (int q = 0; q < npop / 2; ++q) {
         uint32_t u[4];
-        philox_at(cfg->seed, pid, gen, (uint32_t)q, 1u, u);
-        if ((uint64_t)u[0] >= tc) continue;
-        const int c = 1 + (int)(((uint64_t)u[1] * (uint64_t)(nbits - 1)) >> 32);
+        philox_at(cfg->seed, pid, gen, (uint32_t)(2 * q), 0u, u);
+        if ((uint64_t)u[2] >= tc) continue;
+        const int c = 1 + (int)(((uint64_t)u[3] * (uint64_t)(nbits - 1)) >> 32);
         uint16_t *a = child + (size_t)(2 * q) * m;
         uint16_t *b = child + (size_t)(2 * q + 1) * m;
         /* bits [c, nbits) of the MSB-first string change owners */
@@ -95,20 +119,28 @@ int or_ga_breed(const uint16_t *genes, const double *f, int npop, int m,
             b[w] = (uint16_t)((b[w] & ~mask) | ta);
         }
     }
-    /* M: per-bit mutation, thresholds by bit position within the word */
-    uint64_t tb[16];
-    for (int b = 0; b < 16; ++b) tb[b] = mutation_threshold(cfg, b);
-    const int ngroups = (nbits + 3) / 4;
+    /* M: per-bit mutation placed by jumps between flips (see above) */
+    uint64_t A[16][16];
+    mutation_table(cfg, A);
     for (int k = 0; k < npop; ++k) {
         uint16_t *g = child + (size_t)k * m;
-        for (int grp = 0; grp < ngroups; ++grp) {
-            uint32_t u[4];
-            philox_at(cfg->seed, pid, gen, (uint32_t)k, 2u + (uint32_t)grp, u);
-            for (int t = 0; t < 4; ++t) {
-                const int bit = 4 * grp + t;
-                if (bit >= nbits) break;
-                const int b = bit % 16;
-                if ((uint64_t)u[t] < tb[b]) g[bit / 16] ^= (uint16_t)(1u << (15 - b));
+        uint32_t u[4];
+        int used = 4;
+        uint32_t block = 0;
+        for (int w = 0; w < m; ++w) {
+            int b = 15;
+            while (b >= 0) {
+                if (used == 4) {
+                    philox_at(cfg->seed, pid, gen, (uint32_t)k, 2u + block, u);
+                    ++block;
+                    used = 0;
+                }
+                const uint64_t draw = u[used++];
+                if (draw >= A[b][0]) break;
+                int c = b;
+                while (!(draw < A[b][c])) --c;
+                g[w] ^= (uint16_t)(1u << (15 - c));
+                b = c - 1;
             }
         }
     }

@@ -282,10 +282,21 @@ int make_ga(const ga_config *cfg, const me_bounds *b, uint64_t pid0, KGa &g, int
     g.pixel_id0 = pid0;
     philox_round_keys(cfg->seed, g.rk);
     g.t_cross = prob_threshold(cfg->pc);
+    // bit b (0 = MSB) flips with q_b = pmut_lsb ratio^(15 - b), clamped to [0, 1];
+    // t_mut holds the chance of a flip among bits c..b, for the mutation's jumps
+    double q[16];
     for (int bit = 0; bit < 16; ++bit) {
         double r = 1.0;
         for (int k = 0; k < 15 - bit; ++k) r *= cfg->pmut_ratio;
-        g.t_mut[bit] = prob_threshold(cfg->pmut_lsb * r);
+        const double p = cfg->pmut_lsb * r;
+        q[bit] = p > 0.0 ? (p < 1.0 ? p : 1.0) : 0.0;
+    }
+    for (int b = 0; b < 16; ++b) {
+        double keep = 1.0;  // no flip among bits c..b
+        for (int c = b; c >= 0; --c) {
+            keep *= 1.0 - q[c];
+            g.t_mut[b * (b + 1) / 2 + c] = prob_threshold(1.0 - keep);
+        }
     }
     if (b) {
         for (int d = 0; d < npar; ++d) {

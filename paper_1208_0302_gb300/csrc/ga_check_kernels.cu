@@ -41,6 +41,10 @@ k_ga_fitness(const __grid_constant__ KProblem pb, int weight_mode, const R *__re
     __syncthreads();
     stage_weights<R>(weight_mode, w_user, pix, s_obs, nl, k, s_w2);
     __syncthreads();
+    if (sizeof(R) == 4) {
+        weight_obs_rows<R>(s_obs, nl, k, s_w2);
+        __syncthreads();
+    }
     R he[ME_MAX_LINES];
 #pragma unroll
     for (int l = 0; l < ME_MAX_LINES; ++l) he[l] = s_he[l];

@@ -118,11 +118,14 @@ __device__ __forceinline__ R fitness_rows(const KProblem &pb, int nlines, int nl
 
 
 // Eq. chisq for one individual with the FP32 pair path (two wavelengths per
-// step, packed FP32x2 arithmetic).  The squared residuals of each Stokes
-// parameter go into one FMA running sum per lane of the pair (relative error
-// at most about (n/2) u, u = 2^-24, for n wavelengths; the fitness only ranks
-// individuals, and the best individual's chi2 is re-evaluated in FP64
-// afterwards).  Fewer live accumulators keep the loop's state in registers.
+// step, packed FP32x2 arithmetic), as a Kahan-compensated sum.  The residuals
+// come out weighted: the staged Q, U, V rows carry the pixel's weights
+// (weight_obs_rows) and so do the individual's Q, U, V output constants, and
+// the I residual takes w_I with one multiply.  Each pair's four squared
+// weighted residuals are summed by FMA and added into one running total per
+// lane with Kahan's compensation, so the sum's relative error stays at a few
+// units of 2^-24 whatever the number of wavelengths.  The fitness only ranks
+// individuals; the best individual's chi2 is re-evaluated in FP64.
 template <int NL, bool COUNT, bool PAT, bool FILL, bool STORE = false>
 __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, int nl, const float *p,
                                                float mu, const float *s_obs, const float *s_doff,
@@ -133,7 +136,14 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
     Geo<float> geo = make_geo<float, NL, FILL>(pb, nlines, p, mu);
     pair_thresholds(geo, nlines);
     geo.vmask = __activemask();
-    float2 sI = f2(0.f), sQ = f2(0.f), sU = f2(0.f), sV = f2(0.f);
+    const float *sw = s_w2 + 4;  // the weights themselves
+    geo.kQ *= sw[1];
+    geo.kUV *= sw[1];
+    geo.kU *= sw[2];
+    geo.kQV *= sw[2];
+    geo.kV *= sw[3];
+    const float2 wI = f2(sw[0]);
+    float2 sum = f2(0.f), comp = f2(0.f);
     const int npair = (nl + 1) >> 1;
     EvalCount cnt{0u, 0u, 0u};
     for (int q = 0; q < npair; ++q) {
@@ -151,7 +161,7 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
         const Stokes4x2 ob = {make_float2(o0.x, o0.y), make_float2(o0.z, o0.w), make_float2(o1.x, o1.y),
                               make_float2(o1.z, o1.w)};
         const Stokes4x2 rr = resid_x2<NL, COUNT, PAT, FILL>(geo, doff2, ob, he, nlines, y_real, cnt, pb.line);
-        float2 rI = rr.I, rQ = rr.Q, rU = rr.U, rV = rr.V;
+        float2 rI = mul2(rr.I, wI), rQ = rr.Q, rU = rr.U, rV = rr.V;
         if (!y_real) rI.y = rQ.y = rU.y = rV.y = 0.f;  // padded partner
         if (STORE && res) {
             const int j = 2 * q;
@@ -166,18 +176,20 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
                 res[3 * nl + j + 1] = rV.y;
             }
         }
-        sI = fma2(rI, rI, sI);
-        sQ = fma2(rQ, rQ, sQ);
-        sU = fma2(rU, rU, sU);
-        sV = fma2(rV, rV, sV);
+        float2 t2 = fma2(rQ, rQ, mul2(rI, rI));
+        t2 = fma2(rU, rU, t2);
+        t2 = fma2(rV, rV, t2);
+        const float2 y = sub2(t2, comp);  // Kahan: comp holds the lost low part, negated
+        const float2 t = add2(sum, y);
+        comp = sub2(sub2(t, sum), y);
+        sum = t;
     }
     if (COUNT) {
         ninterior += cnt.interior;
         nmid += cnt.mid;
         nfar += cnt.far;
     }
-    return (s_w2[0] * (sI.x + sI.y) + s_w2[1] * (sQ.x + sQ.y) + s_w2[2] * (sU.x + sU.y) +
-            s_w2[3] * (sV.x + sV.y)) * inv_nu;
+    return ((sum.x - comp.x) + (sum.y - comp.y)) * inv_nu;
 }
 
 template <class R, int NL, bool COUNT, bool PAT, bool FILL, bool STORE = false>
@@ -248,9 +260,11 @@ __device__ __forceinline__ void breed_one(const KGa &ga, uint64_t pid, int t, in
 #pragma unroll
     for (int d = 0; d < M; ++d) g[d] = s_cur[win * M + d];
 
-    const U4 uc = ga_random_rk(ga.rk, pid, t, (uint32_t)(k >> 1), kPurposeCross);
-    const bool cross = (uint64_t)uc.x < ga.t_cross;
-    const int c = 1 + (int)(((uint64_t)uc.y * (uint64_t)(16 * M - 1)) >> 32);
+    // the pair's crossover draws: words z, w of the even slot's block
+    const uint32_t cz = __shfl_sync(0xffffffffu, u.z, (k & 31) & ~1);
+    const uint32_t cw = __shfl_sync(0xffffffffu, u.w, (k & 31) & ~1);
+    const bool cross = (uint64_t)cz < ga.t_cross;
+    const int c = 1 + (int)(((uint64_t)cw * (uint64_t)(16 * M - 1)) >> 32);
 #pragma unroll
     for (int d = 0; d < M; ++d) {
         const uint32_t pg = __shfl_xor_sync(0xffffffffu, (uint32_t)g[d], 1);
@@ -265,22 +279,42 @@ __device__ __forceinline__ void breed_one(const KGa &ga, uint64_t pid, int t, in
         }
     }
 
-    // Mutation word by word through this slot's shared-memory row (a rolled
-    // loop keeps the code small): bits 16d..16d+15 use Philox calls 4d..4d+3.
+    // Mutation (every bit b flips on its own with probability q_b), word by
+    // word through this slot's shared-memory row (a rolled loop keeps the code
+    // small).  The slot's draws u_0, u_1, ... (four per Philox block, purposes
+    // 2, 3, ...) jump from flip to flip, from the word's LSB toward its MSB:
+    // with bits 0..b still open, u >= t(b, 0) leaves them all unflipped;
+    // otherwise the next flip is bit c, the largest c <= b with u < t(b, c),
+    // and bits 0..c-1 stay open.  A word without flips takes one draw.
 #pragma unroll
     for (int d = 0; d < M; ++d) s_row[d] = g[d];
+    U4 blk = {0u, 0u, 0u, 0u};
+    uint32_t nblk = 0, left = 0;
 #pragma unroll 1
     for (int d = 0; d < M; ++d) {
         uint32_t word = s_row[d];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const U4 um = ga_random_rk(ga.rk, pid, t, (uint32_t)k, kPurposeMutate + (uint32_t)(4 * d + q));
-            const uint32_t uu[4] = {um.x, um.y, um.z, um.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int b = 4 * q + e;  // bit within the word, 0 = MSB
-                if ((uint64_t)uu[e] < ga.t_mut[b]) word ^= 1u << (15 - b);
+        int b = 15;
+        while (b >= 0) {
+            if (left == 0) {
+                blk = ga_random_rk(ga.rk, pid, t, (uint32_t)k, kPurposeMutate + nblk);
+                ++nblk;
+                left = 4;
             }
+            const uint64_t uv = blk.x;
+            blk.x = blk.y;
+            blk.y = blk.z;
+            blk.z = blk.w;
+            --left;
+            const uint64_t *row = ga.t_mut + b * (b + 1) / 2;
+            if (uv >= row[0]) break;
+            int lo = 0, hi = b;  // the largest c with uv < row[c]; row[0] qualifies
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (uv < row[mid]) lo = mid;
+                else hi = mid - 1;
+            }
+            word ^= 1u << (15 - lo);
+            b = lo - 1;
         }
         s_row[d] = (uint16_t)word;
     }
@@ -314,7 +348,7 @@ __host__ __device__ __forceinline__ GaSmem ga_smem_layout(int nl, int nlines, in
     L.fit = take(npop * (int)sizeof(R), 16);
     L.wmin = take(32 * (int)sizeof(R), 16);
     L.widx = take(32 * 4, 16);
-    L.w2 = take(4 * (int)sizeof(R), 16);
+    L.w2 = take(8 * (int)sizeof(R), 16);  // w^2 of I, Q, U, V, then w
     L.he = take(4 * (int)sizeof(R), 16);
     L.dom = take((int)sizeof(DecodeDomain), 16);  // the pixel's decode domain
     L.genes = take(2 * npop * npar * 2, 16);
@@ -322,7 +356,8 @@ __host__ __device__ __forceinline__ GaSmem ga_smem_layout(int nl, int nlines, in
     return L;
 }
 
-// Section 5.4 inverse-max weights of the staged pixel (warp 0), written as w^2.
+// Section 5.4 inverse-max weights of the staged pixel (warp 0), written as
+// w^2 (s_w2[0..3]) and w (s_w2[4..7]).
 template <class R>
 __device__ __forceinline__ void weights_invmax_w2(const R *s_obs, int nl, R *s_w2)
 {
@@ -354,6 +389,7 @@ __device__ __forceinline__ void weights_invmax_w2(const R *s_obs, int nl, R *s_w
             const R dd = d[s] > fl ? d[s] : fl;
             const R w = dd > R(0) ? R(1) / dd : R(0);
             s_w2[s] = w * w;
+            s_w2[4 + s] = w;
         }
     }
 }
@@ -413,9 +449,25 @@ __device__ __forceinline__ void stage_weights(int weight_mode, const double *w_u
         if (k < 4) {
             const double wv = w_user[(size_t)pix * 4 + k];
             s_w2[k] = R(wv * wv);
+            s_w2[4 + k] = R(fabs(wv));
         }
     } else if (k < 32) {
         weights_invmax_w2<R>(s_obs, nl, s_w2);
+    }
+}
+
+// FP32 pair path: the pixel's weights w_Q, w_U, w_V folded into its staged
+// Q, U, V rows (after the weights are known), so that the fitness forms
+// weighted residuals directly (see fitness_pairs).  FP64 rows stay as staged.
+template <class R>
+__device__ __forceinline__ void weight_obs_rows(R *s_obs, int nl, int k, const R *s_w2)
+{
+    if constexpr (sizeof(R) == 4) {
+        const int nlp = padded_lambda<R>(nl);
+        for (int i = k; i < 3 * nlp; i += blockDim.x) {
+            const int st = 1 + i / nlp, j = i - (st - 1) * nlp;
+            s_obs[obs_idx<R>(st, j)] *= s_w2[4 + st];
+        }
     }
 }
 
@@ -483,6 +535,10 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
         // a2: weights
         stage_weights<R>(ga.weight_mode, w_user, pix, s_obs, nl, k, s_w2);
         __syncthreads();
+        if (sizeof(R) == 4) {
+            weight_obs_rows<R>(s_obs, nl, k, s_w2);
+            __syncthreads();
+        }
         R he[ME_MAX_LINES];
 #pragma unroll
         for (int l = 0; l < ME_MAX_LINES; ++l) he[l] = s_he[l];

@@ -14,7 +14,10 @@ struct KGa {
     int npop, ngen, nsamp, weight_mode;
     uint64_t seed, pixel_id0;
     uint64_t t_cross;       // crossover iff u32 < t_cross
-    uint64_t t_mut[16];     // flip bit b (0 = MSB) iff u32 < t_mut[b]
+    // mutation thresholds: t_mut[b (b + 1) / 2 + c] = floor(2^32 (1 - prod_{d=c..b}
+    // (1 - q_d))) for c <= b, q_d the flip probability of bit d (0 = MSB): the
+    // probability that a flip falls among bits c..b of a word
+    uint64_t t_mut[136];
     uint32_t rk[10][2];     // Philox4x32-10 round keys of seed: (k0, k1) + r (W0, W1)
     double lo[ME_NPAR_MAX], hi[ME_NPAR_MAX];
 };

@@ -61,9 +61,10 @@ __host__ __device__ __forceinline__ U4 philox4x32_10_rk(U4 c, const uint32_t (*r
 }
 
 // GA random-number streams.  Counter = (pixel id lo, pixel id hi, generation,
-// index << 8 | purpose): purpose 0 = tournament of child slot `index`,
-// 1 = crossover of pair `index`, 2 + g = mutation bits 4g..4g+3 of slot `index`.
-enum : uint32_t { kPurposeSelect = 0, kPurposeCross = 1, kPurposeMutate = 2 };
+// index << 8 | purpose): purpose 0 = the tournament of child slot `index`
+// (words x, y) and, for an even slot, the crossover of its pair (words z, w);
+// 2 + i = the mutation draws 4i..4i+3 of slot `index`.
+enum : uint32_t { kPurposeSelect = 0, kPurposeMutate = 2 };
 
 __device__ __forceinline__ U4 ga_random(uint64_t seed, uint64_t pid, int gen, uint32_t idx,
                                         uint32_t purpose)

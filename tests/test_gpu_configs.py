@@ -24,13 +24,28 @@ def _gpu_cube(gpu, pb, truth, seed, mu=None):
 
 
 def test_adjoint_against_central_differences_1000_vectors(gpu, orc):
-    """Analytic FP32 Jacobian vs central differences of the FP64 oracle with a
-    1e-4 relative step on 1000 random parameter vectors (seed 3)."""
+    """Analytic Jacobians vs central differences of the FP64 oracle with a
+    1e-4 relative step on 1000 random parameter vectors (seed 3), per column
+    relative to its scale floored at 1e-3 I_c per unit of the parameter's prior
+    range (columns that nearly vanish, e.g. d/dchi at B ~ 0, keep an absolute
+    bar at the noise level).
+
+    * The differences are a sound reference: they agree with the oracle's
+      Richardson-extrapolated Jacobian to 1e-5 of the floored scale.
+    * FP32: within 2e-4 for every vector with B >= 100 G.  Below 100 G the
+      linear polarization scales as B^2 and its FP32 value, formed from
+      T = P - (phi_b + phi_r) / 2 where the three profiles nearly cancel,
+      keeps a relative precision of about 1e-7 / v_B^2; the azimuth column
+      (d(Q, U)/dchi = 2 pi / 180 (-U, Q)) inherits it, so those vectors are held
+      to 1e-3 (measured: 1.95e-4 at B >= 100 G, 8.9e-4 below; the median
+      over vectors of their worst column is 5.2e-5).
+    * FP64: within 2e-7 against the Richardson Jacobian (measured 6.9e-8)."""
     spec = gi.two_line_spec()
     P = gi.draw_params_uniform(1000, seed=3)
     P[:, 5] = np.maximum(P[:, 5], 1e-3)
-    pb = gpu.Problem.from_spec(spec, "f32")
-    jac = gpu.me_synth_jac(pb, torch.tensor(P, device="cuda")).double().cpu().numpy()
+    pt = torch.tensor(P, device="cuda")
+    jac = gpu.me_synth_jac(gpu.Problem.from_spec(spec, "f32"), pt).double().cpu().numpy()
+    jac64 = gpu.me_synth_jac(gpu.Problem.from_spec(spec, "f64"), pt).cpu().numpy()
     fd = np.empty((1000, 4, 128, 9))
     for k in range(9):
         h = 1e-4 * np.maximum(np.abs(P[:, k]), 1e-2)
@@ -38,15 +53,21 @@ def test_adjoint_against_central_differences_1000_vectors(gpu, orc):
         pp[:, k] += h
         pm[:, k] -= h
         fd[..., k] = (orc.synth(spec, pp) - orc.synth(spec, pm)) / (2 * h[:, None, None])
-    # per-column scale, floored at 1e-3 I_c per unit of the parameter's prior
-    # range (columns that nearly vanish, e.g. d/dchi at B ~ 0, keep an absolute bar)
+    rich = np.stack([orc.jacobian(spec, P[i]) for i in range(1000)])
     ic = (P[:, 7] + P[:, 8])[:, None, None, None]
     floor = 1e-3 * ic / (gi.PRIOR_HI - gi.PRIOR_LO)[None, None, None, :]
-    scale = np.maximum(np.max(np.abs(fd), axis=(1, 2), keepdims=True), floor)
-    err = np.abs(jac - fd) / scale
-    worst = float(err.max())
-    i, s_, j, k = np.unravel_index(np.argmax(err), err.shape)
-    assert worst < 2e-3, (worst, int(i), int(k), P[i].tolist())
+
+    def err(a, ref):
+        scale = np.maximum(np.max(np.abs(ref), axis=(1, 2), keepdims=True), floor)
+        return (np.abs(a - ref) / scale).max(axis=(1, 2, 3))     # worst column of each vector
+
+    assert err(fd, rich).max() < 1e-5
+    e32 = err(jac, fd)
+    strong = P[:, 0] >= 100.0
+    assert e32[strong].max() < 2e-4, (float(e32[strong].max()), int(np.argmax(np.where(strong, e32, 0))))
+    assert e32.max() < 1e-3, float(e32.max())
+    assert np.median(e32) < 1e-4
+    assert err(jac64, rich).max() < 2e-7
 
 
 def test_float32_map_with_polish_at_full_size(gpu, orc):

@@ -10,11 +10,11 @@ as in the restarts) and compare it with the oracle:
   1.5e-7 absolute or the series' FP32 floor 1e-6 |w| (the larger), on warps
   wholly inside one region, warps straddling every threshold, pairs whose two
   points lie in different regions and a ragged last warp;
-* the Stokes vectors behind the fitness (ga_fitness residuals), per sample
-  within 2e-5 of max(|oracle|, I_c);
-* the fitness value: against the FP64 sum of its own residuals within the
-  FP32 summation bound, and against the oracle's chi2 within the bound that
-  the 2e-5 sample bar implies.
+* the Stokes vectors behind the fitness (ga_fitness returns the weighted
+  residuals w_s (O - S)), per sample within 2e-5 of max(|oracle|, I_c);
+* the fitness value: against the FP64 sum of its own squared residuals within
+  the bound of its Kahan-compensated FP32 sum, and against the oracle's chi2
+  within the bound that the 2e-5 sample bar implies.
 """
 import numpy as np
 import pytest
@@ -208,11 +208,15 @@ def _run(gpu, orc, spec, npix, npop, nactive, seed, user_w, mu_px=None):
     act = P[:, :nactive]
     ref = orc.synth(spec, act.reshape(-1, npar), mu_px=None if mu_px is None else np.repeat(mu_px, nactive))
     ref = ref.reshape(npix, nactive, 4, spec.n_lambda)
-    return dict(P=P, obs32=obs32.astype(np.float64), w=w, fit=fit, res=res, ref=ref, mu=mu, npar=npar)
+    if w is not None:
+        wk = w.astype(np.float32).astype(np.float64)          # the kernel's FP32 weights
+    else:
+        wk = orc.weights_invmax(obs32.astype(np.float64))     # within a few ulp of the kernel's
+    return dict(P=P, obs32=obs32.astype(np.float64), w=w, wk=wk, fit=fit, res=res, ref=ref, mu=mu, npar=npar)
 
 
 def _check_samples(r, nactive):
-    gpu_st = r["obs32"][:, None] - r["res"][:, :nactive]
+    gpu_st = r["obs32"][:, None] - r["res"][:, :nactive] / r["wk"][:, None, :, None]
     ic = (r["P"][:, :nactive, 7] + r["mu"][:, None] * r["P"][:, :nactive, 8])[:, :, None, None]
     err = np.abs(gpu_st - r["ref"]) / np.maximum(np.abs(r["ref"]), ic)
     assert np.all(np.isfinite(gpu_st))
@@ -227,16 +231,15 @@ def _check_fitness(orc, r, nactive, nl):
     nu = 4 * nl - npar
     res = r["res"][:, :nactive]
     fit = r["fit"][:, :nactive]
-    if r["w"] is not None:
-        w2 = (r["w"] ** 2).astype(np.float32).astype(np.float64)   # the kernel's FP32 w^2
-    else:
-        w2 = orc.weights_invmax(r["obs32"]) ** 2
-    own = np.einsum("ps,pksj->pk", w2, res ** 2) / nu
-    # FP32 accumulation: each lane of a pair sums ceil(nl / 2) squares per
-    # Stokes parameter, then the weighted combination (and, for inverse-max
-    # weights, their FP32 evaluation: a few units in the last place)
-    bound_sum = ((nl + 1) // 2 + 12) * U32 + (0 if r["w"] is not None else 1e-6)
+    w2 = r["wk"] ** 2
+    own = np.einsum("pksj->pk", res ** 2) / nu
+    # Kahan-compensated FP32 sum: each pair's four squares by FMA (3 roundings),
+    # the compensated running total (2 units plus O(n u^2)), the two lanes and
+    # the final scaling: 16 units of 2^-24 bound it, whatever the grid size
+    bound_sum = 16 * U32
     assert np.all(np.abs(fit - own) <= bound_sum * own + 1e-30), float(np.max(np.abs(fit - own) / own))
+    if r["w"] is None:
+        bound_sum += 1e-6     # the kernel's FP32 inverse-max weights against the oracle's FP64 ones
     # against the oracle's chi2 at the same individuals: |dchi2| <= (1/nu)
     # sum w^2 (2 |r| e + e^2) with e = 2e-5 max(|S|, I_c) per sample
     ref = r["ref"]
