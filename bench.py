@@ -40,11 +40,11 @@ E2E_STEPS_MAX = 5   # the end-to-end leg repeats at most this many steps
 NPOP, NGEN, LM_ITERS = 128, 200, 10
 KERNELS_PER_STEP = 4  # GA evolve, FP64 chi2, L-M, FP64 chi2
 # DRAM bytes (read + write) per pixel of one GA launch, from an ncu capture of
-# k_ga_evolve on the 4096-pixel two-line case (dram__bytes_read.sum 8579840 +
+# k_ga_evolve on the 4096-pixel two-line case (dram__bytes_read.sum 8511744 +
 # dram__bytes_write.sum 0, divided by 4096; traffic grows in proportion to
 # pixels: each block reads its pixel's cube row once).  Set to None whenever
 # the kernel changes, until it is captured again.
-GA_DRAM_BYTES_PER_PIXEL = (8579840 + 0) / 4096
+GA_DRAM_BYTES_PER_PIXEL = (8511744 + 0) / 4096
 
 
 def parse():
@@ -141,16 +141,18 @@ def flop_model(nlines):
     counted from the source of the GA's fitness path (per call, without the
     per-individual invariants such as 2a or (L + a)^2), per unit: an
     evaluation of w(z) in the interior (Weideman N = 16 by real-quadratic
-    synthetic division, 91), in the middle shell (5th convergent, 45), in the
-    continued-fraction region (3rd convergent, 31) and in the far field
-    (two-node approximant, 17); and per wavelength
-    point 22 per line for the component arguments and profile sums, 36 for K
+    synthetic division, 91), in the middle shell (5th convergent, 43), in the
+    continued-fraction region (3rd convergent, 29) and in the far field
+    (two-node approximant, 14), the rational branches leaving their
+    normalisation to the accumulation weight; and per wavelength
+    point 23 per line for the component arguments, the weight q / sqrt(pi)
+    and the profile sums, 35 for K
     and its closed-form inverse, 21 for the four Stokes values formed into
     their weighted residuals (w_I by one multiply), 7 for the four squares
     summed by FMA and 4 for the Kahan-compensated running sum.  Each point's
     evaluations are classified by its own region; branch tests, votes and work
     a pair or warp does beyond that are not counted."""
-    return {"weideman": 91.0, "mid": 45.0, "cf": 31.0, "far": 17.0, "point": 22.0 * nlines + 68.0}
+    return {"weideman": 91.0, "mid": 43.0, "cf": 29.0, "far": 14.0, "point": 23.0 * nlines + 67.0}
 
 
 def run_ours(args):

@@ -115,9 +115,11 @@ __global__ void k_fad_probe(const float2 *__restrict__ x, const float *__restric
         }
         return;
     }
-    float2 wx, wy;
-    if (mode == 0) fad_pair(v, g, wx, wy);
-    else fad_pair_in(v, g, wx, wy);
+    float2 wx, wy, qi;
+    if (mode == 0) fad_pair(v, g, f2(1.0f), f2(kInvSqrtPi), wx, wy, qi);
+    else fad_pair_in(v, g, f2(1.0f), f2(kInvSqrtPi), wx, wy, qi);
+    wx = mul2(qi, wx);  // w itself: the unit-weight profile
+    wy = mul2(qi, wy);
     float *r = out + (size_t)i * 4;
     r[0] = wx.x;
     r[1] = wy.x;

@@ -36,10 +36,17 @@ __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
 __device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(fast_rcp(a.x), fast_rcp(a.y)); }
 
+// Every branch returns a weighted profile value q w(z) as qi (nx + i ny): the
+// caller adds qi nx and qi ny into its sums with one FMA each.  The rational
+// branches leave their numerator unnormalised and put q / (sqrt(pi) |A|^2)
+// into qi (qs = q / sqrt(pi) is passed in), which saves the two multiplies of
+// a normalised w; the series returns w itself with qi = q.
+
 // Continued-fraction branch (K-th convergent, monic a(u), b(u)) for a pair of
 // real arguments x and a common damping y (a2 = y^2).
 template <int K>
-__device__ __forceinline__ void fad_cf2(float2 x, float y, float a2, float2 &wx, float2 &wy)
+__device__ __forceinline__ void fad_cf2(float2 x, float y, float a2, float2 qs, float2 &wx, float2 &wy,
+                                        float2 &qi)
 {
     constexpr int NA = (K + 1) / 2, NB = (K - 1) / 2;
     constexpr CfPoly<K> P{};
@@ -63,16 +70,17 @@ __device__ __forceinline__ void fad_cf2(float2 x, float y, float a2, float2 &wx,
         by = fma2(bx, uy, mul2(by, ux));
         bx = tx;
     }
-    // num = z b(u), z = x + i y;  w = (i/sqrt(pi)) num / a(u)
+    // num = z b(u), z = x + i y;  w = (i/sqrt(pi)) num conj(a(u)) / |a(u)|^2
     const float2 nx = fma2(x, bx, mul2(f2(-y), by));
     const float2 ny = fma2(x, by, mul2(f2(y), bx));
-    const float2 inv = mul2(rcp2(fma2(ax, ax, mul2(ay, ay))), f2(0.56418958354775628695f));
-    wx = mul2(fma2(nx, ay, neg2(mul2(ny, ax))), inv);
-    wy = mul2(fma2(nx, ax, mul2(ny, ay)), inv);
+    qi = mul2(qs, rcp2(fma2(ax, ax, mul2(ay, ay))));
+    wx = fma2(nx, ay, neg2(mul2(ny, ax)));
+    wy = fma2(nx, ax, mul2(ny, ay));
 }
-__device__ __forceinline__ void fad_ext2(float2 x, float y, float a2, float2 &wx, float2 &wy)
+__device__ __forceinline__ void fad_ext2(float2 x, float y, float a2, float2 qs, float2 &wx, float2 &wy,
+                                         float2 &qi)
 {
-    fad_cf2<FadCfg<float>::K>(x, y, a2, wx, wy);
+    fad_cf2<FadCfg<float>::K>(x, y, a2, qs, wx, wy, qi);
 }
 // Middle shell kMidR2 < |z|^2 <= R2: the 5th convergent (six-node rule),
 // |error| <= 1.04e-7 there (at the boundary), about half the work of
@@ -84,20 +92,21 @@ constexpr float kMidR2 = 21.0f;
 // (z^2 - 1/2); |error| <= 1.23e-7 in FP32 there (at the boundary; it falls
 // as |z|^-5 outward), within the 1.3e-7 of the 3rd convergent at |z|^2 = 36.
 constexpr float kFarR2 = 360.0f;
-__device__ __forceinline__ void fad_far2(float2 x, float y, float a2, float2 &wx, float2 &wy)
+__device__ __forceinline__ void fad_far2(float2 x, float y, float a2, float2 qs, float2 &wx, float2 &wy,
+                                         float2 &qi)
 {
-    const float2 ux = fma2(x, x, f2(-a2));
-    const float2 uy = mul2(x, f2(2.0f * y));
-    const float2 dx = add2(ux, f2(-0.5f));
-    const float2 inv = mul2(rcp2(fma2(dx, dx, mul2(uy, uy))), f2(0.56418958354775628695f));
-    wx = mul2(fma2(x, uy, neg2(mul2(f2(y), dx))), inv);
-    wy = mul2(fma2(x, dx, mul2(f2(y), uy)), inv);
+    const float2 dx = fma2(x, x, f2(-a2 - 0.5f));  // Re(z^2 - 1/2)
+    const float2 uy = mul2(x, f2(2.0f * y));       // Im(z^2)
+    qi = mul2(qs, rcp2(fma2(dx, dx, mul2(uy, uy))));
+    wx = fma2(x, uy, neg2(mul2(f2(y), dx)));
+    wy = fma2(x, dx, mul2(f2(y), uy));
 }
 
 // Interior branch (Weideman N = 16, real-quadratic synthetic division) for a
 // pair of real arguments x and common damping y.
-__device__ __forceinline__ void fad_int2(float2 x, float y, float2 &wx, float2 &wy)
+__device__ __forceinline__ void fad_int2(float2 x, float y, float2 q, float2 &wx, float2 &wy, float2 &qi)
 {
+    qi = q;
     constexpr int N = FadCfg<float>::N;
     const float L = c_fad.L32;
     // 1/(L - i z) = (dx + i x) / (dx^2 + x^2), dx = L + y
@@ -151,14 +160,19 @@ __device__ __forceinline__ float pair_min_abs(float2 x) { return fminf(fabsf(x.x
 // warp) votes over just its active lanes.
 __device__ __forceinline__ bool warp_all(bool p, unsigned mask) { return __all_sync(mask, p); }
 
-// One component for the pair, the branch chosen uniformly across the warp.
-__device__ __forceinline__ void fad_pair(float2 x, const Geo<float> &g, float2 &wx, float2 &wy)
+// 1 / sqrt(pi), the factor of the rational branches.
+constexpr float kInvSqrtPi = 0.56418958354775628695f;
+
+// One component for the pair, weighted by q (qs = q / sqrt(pi)), the branch
+// chosen uniformly across the warp.
+__device__ __forceinline__ void fad_pair(float2 x, const Geo<float> &g, float2 q, float2 qs, float2 &wx,
+                                         float2 &wy, float2 &qi)
 {
     const float m = pair_min_abs(x);
-    if (warp_all(m > g.tfar, g.vmask)) fad_far2(x, g.a, g.a2, wx, wy);
-    else if (warp_all(m > g.text, g.vmask)) fad_ext2(x, g.a, g.a2, wx, wy);
-    else if (warp_all(m > g.tmid, g.vmask)) fad_cf2<5>(x, g.a, g.a2, wx, wy);
-    else fad_int2(x, g.a, wx, wy);
+    if (warp_all(m > g.tfar, g.vmask)) fad_far2(x, g.a, g.a2, qs, wx, wy, qi);
+    else if (warp_all(m > g.text, g.vmask)) fad_ext2(x, g.a, g.a2, qs, wx, wy, qi);
+    else if (warp_all(m > g.tmid, g.vmask)) fad_cf2<5>(x, g.a, g.a2, qs, wx, wy, qi);
+    else fad_int2(x, g.a, q, wx, wy, qi);
 }
 
 // Work counts of the algorithm proper: each real point's evaluation classified
@@ -198,11 +212,11 @@ __device__ __forceinline__ void pattern_profiles_x2(const KLine &ln, float2 dinv
         for (int i = 0; i < n; ++i) {
             const float2 x = add2(dinv, f2(cp - vL * ln.cshift32[g][i]));
             if (COUNT) count_pair(x, geo.a2, y_real, ncount);
-            float2 wx, wy;
-            fad_pair(x, geo, wx, wy);
-            const float2 st = f2(ln.cstr32[g][i]);
-            px = fma2(st, wx, px);
-            py = fma2(st, wy, py);
+            const float st = ln.cstr32[g][i];
+            float2 wx, wy, qi;
+            fad_pair(x, geo, f2(st), f2(st * kInvSqrtPi), wx, wy, qi);
+            px = fma2(qi, wx, px);
+            py = fma2(qi, wy, py);
         }
         w[2 * g] = px;
         w[2 * g + 1] = py;
@@ -211,12 +225,13 @@ __device__ __forceinline__ void pattern_profiles_x2(const KLine &ln, float2 dinv
 
 // One component near a line core: the same branches tested from the inside
 // out, for components that mostly need the inner ones.
-__device__ __forceinline__ void fad_pair_in(float2 x, const Geo<float> &g, float2 &wx, float2 &wy)
+__device__ __forceinline__ void fad_pair_in(float2 x, const Geo<float> &g, float2 q, float2 qs, float2 &wx,
+                                            float2 &wy, float2 &qi)
 {
     const float m = pair_min_abs(x);
-    if (!warp_all(m > g.tmid, g.vmask)) fad_int2(x, g.a, wx, wy);
-    else if (!warp_all(m > g.text, g.vmask)) fad_cf2<5>(x, g.a, g.a2, wx, wy);
-    else fad_ext2(x, g.a, g.a2, wx, wy);
+    if (!warp_all(m > g.tmid, g.vmask)) fad_int2(x, g.a, q, wx, wy, qi);
+    else if (!warp_all(m > g.text, g.vmask)) fad_cf2<5>(x, g.a, g.a2, qs, wx, wy, qi);
+    else fad_ext2(x, g.a, g.a2, qs, wx, wy, qi);
 }
 
 // One component at a known level: 2 = every lane's pair is in the far
@@ -224,11 +239,12 @@ __device__ __forceinline__ void fad_pair_in(float2 x, const Geo<float> &g, float
 // accurate there, also where a component is already far: cheaper than
 // testing each component), 0 = anywhere.
 template <int LEVEL>
-__device__ __forceinline__ void fad_level(float2 x, const Geo<float> &g, float2 &wx, float2 &wy)
+__device__ __forceinline__ void fad_level(float2 x, const Geo<float> &g, float2 q, float2 qs, float2 &wx,
+                                          float2 &wy, float2 &qi)
 {
-    if (LEVEL == 2) fad_far2(x, g.a, g.a2, wx, wy);
-    else if (LEVEL == 1) fad_ext2(x, g.a, g.a2, wx, wy);
-    else fad_pair_in(x, g, wx, wy);
+    if (LEVEL == 2) fad_far2(x, g.a, g.a2, qs, wx, wy, qi);
+    else if (LEVEL == 1) fad_ext2(x, g.a, g.a2, qs, wx, wy, qi);
+    else fad_pair_in(x, g, q, qs, wx, wy, qi);
 }
 
 // One effective triplet's contribution to a pair's profile sums, each
@@ -239,21 +255,22 @@ __device__ __forceinline__ void triplet_acc(float2 xb, float2 v, float2 xr, cons
                                             float2 &P, float2 &Pim, float2 &Sg, float2 &Sgi, float2 &Dd,
                                             float2 &Di, float2 &P0)
 {
-    float2 wx, wy;
-    fad_level<EXT>(xb, g, wx, wy);
-    Sg = fma2(q, wx, Sg);
-    Sgi = fma2(q, wy, Sgi);
-    Dd = fma2(neg2(q), wx, Dd);
-    Di = fma2(neg2(q), wy, Di);
-    fad_level<EXT>(v, g, wx, wy);
-    if (FILL) P0 = fma2(q, wx, P0);  // the pi profile is unshifted
-    P = fma2(q, wx, P);
-    Pim = fma2(q, wy, Pim);
-    fad_level<EXT>(xr, g, wx, wy);
-    Sg = fma2(q, wx, Sg);
-    Sgi = fma2(q, wy, Sgi);
-    Dd = fma2(q, wx, Dd);
-    Di = fma2(q, wy, Di);
+    const float2 qs = mul2(q, f2(kInvSqrtPi));
+    float2 wx, wy, qi;
+    fad_level<EXT>(xb, g, q, qs, wx, wy, qi);
+    Sg = fma2(qi, wx, Sg);
+    Sgi = fma2(qi, wy, Sgi);
+    Dd = fma2(neg2(qi), wx, Dd);
+    Di = fma2(neg2(qi), wy, Di);
+    fad_level<EXT>(v, g, q, qs, wx, wy, qi);
+    if (FILL) P0 = fma2(qi, wx, P0);  // the pi profile is unshifted
+    P = fma2(qi, wx, P);
+    Pim = fma2(qi, wy, Pim);
+    fad_level<EXT>(xr, g, q, qs, wx, wy, qi);
+    Sg = fma2(qi, wx, Sg);
+    Sgi = fma2(qi, wy, Sgi);
+    Dd = fma2(qi, wx, Dd);
+    Di = fma2(qi, wy, Di);
 }
 
 // The branch level of an effective triplet for a pair, voted across the warp
@@ -289,9 +306,10 @@ __device__ __forceinline__ Stokes4x2 resid_x2(const Geo<float> &g, const float2 
             pattern_profiles_x2<COUNT>(lines[l], mul2(doff2[l], f2(g.invD[l])), g.cp[l], g.vL[l], g, w, y_real,
                                        ncount);
             if (FILL) {
-                float2 ux, uy;
-                fad_pair(fma2(doff2[l], f2(g.invD[l]), f2(g.cp[l])), g, ux, uy);
-                P0 = fma2(f2(half_eta[l]), ux, P0);
+                float2 ux, uy, qi;
+                fad_pair(fma2(doff2[l], f2(g.invD[l]), f2(g.cp[l])), g, f2(half_eta[l]),
+                         f2(half_eta[l] * kInvSqrtPi), ux, uy, qi);
+                P0 = fma2(qi, ux, P0);
             }
             const float2 q = f2(half_eta[l]);
             P = fma2(q, w[2], P);
@@ -334,20 +352,23 @@ __device__ __forceinline__ Stokes4x2 resid_x2(const Geo<float> &g, const float2 
     const float2 Delta = fma2(eI2, sub2(G, E2), neg2(mul2(Pi, Pi)));
     const float2 f = mul2(f2(g.muS1), rcp2(Delta));
     const float2 A = fma2(eI2, T, mul2(Ti, Pi));
-    const float2 eIC = mul2(eI, fma2(Dd, Ti, neg2(mul2(T, Di))));
-    // Q, U, V = -f X: the residual o - (-f X) is one FMA, f X + o.  FILL
-    // scales the polarised model by alpha and mixes the field-free I.
+    const float2 C = fma2(Dd, Ti, neg2(mul2(T, Di)));
+    // Q, U, V = -f X: the residual o - (-f X) is formed by FMAs on o, with f
+    // applied once to A and to eI C.  FILL scales the polarised model by
+    // alpha and mixes the field-free I.
     const float2 fq = FILL ? mul2(f, f2(g.alpha)) : f;
+    const float2 fqeI = mul2(fq, eI);
+    const float2 fA = mul2(fq, A), fC = mul2(fqeI, C);
     Stokes4x2 r;
     if (FILL) {
         const float2 inm = mul2(f2(g.muS1), rcp2(fma2(f2(2.0f * g.eta0), P0, f2(1.0f))));
         const float2 base = fma2(f2(1.0f - g.alpha), inm, f2(g.S0));
-        r.I = sub2(o.I, fma2(mul2(fq, eI), G, base));
+        r.I = sub2(o.I, fma2(fqeI, G, base));
     } else {
-        r.I = sub2(o.I, fma2(mul2(f, eI), G, f2(g.S0)));
+        r.I = sub2(o.I, fma2(fqeI, G, f2(g.S0)));
     }
-    r.Q = fma2(fq, fma2(f2(g.kQ), A, mul2(f2(g.kUV), eIC)), o.Q);
-    r.U = fma2(fq, fma2(f2(g.kU), A, neg2(mul2(f2(g.kQV), eIC))), o.U);
+    r.Q = fma2(f2(g.kQ), fA, fma2(f2(g.kUV), fC, o.Q));
+    r.U = fma2(f2(g.kU), fA, fma2(f2(-g.kQV), fC, o.U));
     r.V = fma2(mul2(fq, f2(g.kV)), fma2(eI2, Dd, mul2(Di, Pi)), o.V);
     return r;
 }
