@@ -243,24 +243,53 @@ def run_ours(args):
     peak_meas = max(api.fp32_peak(packed=False), api.fp32_peak(packed=True))
     clk = clocks.stop()
 
-    # end to end through the C ABI with host buffers (pinned), copies timed
+    # end to end through the C ABI with host buffers (pinned), copies timed:
+    # every step copies its cube and weights in from pinned host memory and
+    # its parameters and chi2 back out.  Two device buffers let the next
+    # step's input copy run on a copy stream while the current step computes,
+    # and each step's results are read on the host while the next one runs.
     host_obs = obs.cpu().pin_memory()
     host_w = w.cpu().pin_memory()
-    host_out = torch.empty((npix, 9), dtype=torch.float64).pin_memory()
-    host_chi = torch.empty(npix, dtype=torch.float64).pin_memory()
-    dobs = torch.empty_like(obs)
-    dw = torch.empty_like(w)
+    host_out = [torch.empty((npix, 9), dtype=torch.float64).pin_memory() for _ in range(2)]
+    host_chi = [torch.empty(npix, dtype=torch.float64).pin_memory() for _ in range(2)]
+    dobs = [torch.empty_like(obs) for _ in range(2)]
+    dw = [torch.empty_like(w) for _ in range(2)]
+    copy_stream = torch.cuda.Stream(device=dev)
+    copied = [torch.cuda.Event() for _ in range(2)]
+    consumed = [torch.cuda.Event() for _ in range(2)]
+    results = [torch.cuda.Event() for _ in range(2)]
     e2e_steps = max(1, min(args.steps, E2E_STEPS_MAX))
+    checksum = 0.0
+
+    def fetch(i):
+        b = i % 2
+        with torch.cuda.stream(copy_stream):
+            if i >= 2:
+                copy_stream.wait_event(consumed[b])   # step i - 2 is done with this buffer
+            dobs[b].copy_(host_obs, non_blocking=True)
+            dw[b].copy_(host_w, non_blocking=True)
+            copied[b].record(copy_stream)
+
     barrier()
     h0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        dobs.copy_(host_obs, non_blocking=True)
-        dw.copy_(host_w, non_blocking=True)
-        best, _ = api.ga_invert_batch(pb32, dobs, lo, hi, ga, pixel_id0=pid0)
-        p2, c22 = api.lm_polish(pb32, dobs, best, lo, hi, iters=LM_ITERS, w=dw)
-        host_out.copy_(p2, non_blocking=True)
-        host_chi.copy_(c22, non_blocking=True)
-        torch.cuda.synchronize()
+    fetch(0)
+    for i in range(e2e_steps):
+        b = i % 2
+        if i + 1 < e2e_steps:
+            fetch(i + 1)
+        stream.wait_event(copied[b])
+        best, _ = api.ga_invert_batch(pb32, dobs[b], lo, hi, ga, pixel_id0=pid0)
+        p2, c22 = api.lm_polish(pb32, dobs[b], best, lo, hi, iters=LM_ITERS, w=dw[b])
+        consumed[b].record(stream)
+        if i >= 1:   # the previous step's results are on the host by now
+            results[(i - 1) % 2].synchronize()
+            checksum += float(host_chi[(i - 1) % 2][0])
+        host_out[b].copy_(p2, non_blocking=True)
+        host_chi[b].copy_(c22, non_blocking=True)
+        results[b].record(stream)
+    results[(e2e_steps - 1) % 2].synchronize()
+    checksum += float(host_chi[(e2e_steps - 1) % 2][0])
+    assert checksum == checksum
     e2e_ms = (time.perf_counter() - h0) * 1e3 / e2e_steps
     te = torch.tensor([e2e_ms], device=dev)
     if world > 1:
