@@ -44,7 +44,7 @@ KERNELS_PER_STEP = 4  # GA evolve, FP64 chi2, L-M, FP64 chi2
 # dram__bytes_write.sum 0, divided by 4096; traffic grows in proportion to
 # pixels: each block reads its pixel's cube row once).  Set to None whenever
 # the kernel changes, until it is captured again.
-GA_DRAM_BYTES_PER_PIXEL = (8511744 + 0) / 4096
+GA_DRAM_BYTES_PER_PIXEL = None
 
 
 def parse():
@@ -145,8 +145,9 @@ def flop_model(nlines):
     per-individual invariants such as 2a or (L + a)^2), per unit: an
     evaluation of w(z) in the interior (Weideman N = 16 by real-quadratic
     synthetic division, 91), in the middle shell (5th convergent, 43), in the
-    continued-fraction region (3rd convergent, 29) and in the far field
-    (two-node approximant, 14), the rational branches leaving their
+    continued-fraction region (3rd convergent, 29), in the outer shell (the
+    even convergent, 20) and in the far field (two-node approximant, 14), the
+    rational branches leaving their
     normalisation to the accumulation weight; and per wavelength
     point 23 per line for the component arguments, the weight q / sqrt(pi)
     and the profile sums, 35 for K
@@ -155,7 +156,7 @@ def flop_model(nlines):
     summed by FMA and 4 for the Kahan-compensated running sum.  Each point's
     evaluations are classified by its own region; branch tests, votes and work
     a pair or warp does beyond that are not counted."""
-    return {"weideman": 91.0, "mid": 43.0, "cf": 29.0, "far": 14.0, "point": 23.0 * nlines + 67.0}
+    return {"weideman": 91.0, "mid": 43.0, "cf": 29.0, "even2": 20.0, "far": 14.0, "point": 23.0 * nlines + 67.0}
 
 
 def run_ours(args):
@@ -302,7 +303,7 @@ def run_ours(args):
         counts = api.ga_count_evaluations(pb32, obs, lo, hi, ga, pixel_id0=pid0)
         fm = flop_model(len(spec.lines))
         flops = (counts["weideman"] * fm["weideman"] + counts["mid"] * fm["mid"] + counts["cf"] * fm["cf"] +
-                 counts["far"] * fm["far"] + counts["points"] * fm["point"])
+                 counts["even2"] * fm["even2"] + counts["far"] * fm["far"] + counts["points"] * fm["point"])
         props = torch.cuda.get_device_properties(dev)
         sms = props.multi_processor_count
         max_mhz = clk.get("sm_max_mhz") or 2070.0
@@ -310,7 +311,7 @@ def run_ours(args):
         ga_kernel_ms = ga_avg - chi_ms
         achieved = flops / (ga_kernel_ms / 1e3) / 1e12
         syntheses = counts["syntheses"]
-        wz_evals = counts["weideman"] + counts["mid"] + counts["cf"] + counts["far"]
+        wz_evals = counts["weideman"] + counts["mid"] + counts["cf"] + counts["even2"] + counts["far"]
         result = {
             "metric": METRIC, "value": value, "unit": "pixels/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,

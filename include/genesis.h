@@ -225,13 +225,13 @@ int ga_invert_batch(const me_problem *pb, const void *obs, const double *w,
 /*
  * ga_count_evaluations - the same GA as ga_invert_batch (float cubes,
  * npop <= 256) run by a separate instantiation that also counts work:
- * counts dev uint64[5] receives (added to its contents) the number of
+ * counts dev uint64[6] receives (added to its contents) the number of
  * syntheses (fitness evaluations), of Faddeeva evaluations by Weideman's
  * series (|z|^2 <= 21), of all Faddeeva evaluations, of those in the far
- * field (|z|^2 > 360) and of those in the middle shell (21 < |z|^2 <= 36;
- * the rest, 36 < |z|^2 <= 360, use the 3rd convergent), each real wavelength
- * point classified by its own region (the algorithm's work, whatever branch a
- * point's pair or warp took).
+ * field (|z|^2 > 360), of those in the middle shell (21 < |z|^2 <= 36) and
+ * of those in the outer shell (80 < |z|^2 <= 360; the rest, 36 < |z|^2 <= 80,
+ * use the 3rd convergent), each real wavelength point classified by its own
+ * region (the algorithm's work, whatever branch a point's pair or warp took).
  * The arithmetic and the result `best` are those of ga_invert_batch; the
  * counts turn into algorithmic flops for roofline reporting.
  */

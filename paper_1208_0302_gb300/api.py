@@ -185,7 +185,7 @@ def ga_count_evaluations(pb: Problem, obs, lo, hi, ga: GaSettings, w=None, mu_px
     _need(w, torch.float64, (npix, 4), "w")
     _need(mu_px, torch.float64, (npix,), "mu_px")
     best = torch.empty((npix, pb.npar), dtype=torch.float64, device=obs.device)
-    counts = torch.zeros(5, dtype=torch.int64, device=obs.device)
+    counts = torch.zeros(6, dtype=torch.int64, device=obs.device)
     cfg = ga.to_c(L.ME_W_USER if w is not None else L.ME_W_INVMAX)
     b = bounds(lo, hi)
     L.check(L.load().ga_count_evaluations(pb.ref(), _ptr(obs), _ptr(w), _ptr(mu_px), npix,
@@ -195,7 +195,7 @@ def ga_count_evaluations(pb: Problem, obs, lo, hi, ga: GaSettings, w=None, mu_px
     syn = int(c[0])
     points = syn * pb.n_lambda
     return {"syntheses": syn, "points": points, "weideman": int(c[1]), "mid": int(c[4]), "far": int(c[3]),
-            "cf": int(c[2]) - int(c[1]) - int(c[3]) - int(c[4]), "best": best}
+            "even2": int(c[5]), "cf": int(c[2]) - int(c[1]) - int(c[3]) - int(c[4]) - int(c[5]), "best": best}
 
 
 def ga_fitness(pb: Problem, obs, params, nactive=None, w=None, mu_px=None, want_resid=False):

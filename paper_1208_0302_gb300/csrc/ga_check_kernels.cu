@@ -54,9 +54,9 @@ k_ga_fitness(const __grid_constant__ KProblem pb, int weight_mode, const R *__re
         R p[M];
 #pragma unroll
         for (int d = 0; d < M; ++d) p[d] = R(params[ind * M + d]);
-        unsigned long long n0 = 0, n1 = 0, n2 = 0;
+        WorkCount wc{};
         const R f = fitness<R, NL, false, PAT, FILL, true>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu,
-                                                           n0, n1, n2, res ? res + ind * 4 * nl : nullptr);
+                                                           wc, res ? res + ind * 4 * nl : nullptr);
         fit[ind] = double(f);
     }
 }
@@ -100,7 +100,9 @@ __global__ void k_fad_probe(const float2 *__restrict__ x, const float *__restric
         const float2 q = f2(1.0f);
         float2 P = f2(0.f), Pim = f2(0.f), Sg = f2(0.f), Sgi = f2(0.f), Dd = f2(0.f), Di = f2(0.f), P0 = f2(0.f);
         const int lev = triplet_level(v, g, 0);
-        if (lev == 2)
+        if (lev == 3)
+            triplet_acc<3, false>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
+        else if (lev == 2)
             triplet_acc<2, false>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
         else if (lev == 1)
             triplet_acc<1, false>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);

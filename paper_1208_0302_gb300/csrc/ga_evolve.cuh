@@ -22,6 +22,12 @@ namespace genesis {
 namespace {
 
 
+// Per-thread work counts of the counting instantiation: the fitness
+// evaluations' Faddeeva evaluations by region of their own point.
+struct WorkCount {
+    unsigned long long interior, mid, even2, far;
+};
+
 template <class R> __device__ __forceinline__ R clean_fit(R f)
 {
     return f == f ? f : R(INFINITY);  // NaN ranks as +infinity
@@ -91,7 +97,7 @@ template <> struct GaDecode<double> {
 template <class R, int NL, bool COUNT, bool PAT, bool FILL, bool STORE = false>
 __device__ __forceinline__ R fitness_rows(const KProblem &pb, int nlines, int nl, const R *p, R mu,
                                           const R *s_obs, const R *s_doff, const R *he,
-                                          const R *s_w2, R inv_nu, unsigned long long &ninterior,
+                                          const R *s_w2, R inv_nu, WorkCount &wc,
                                           R *res = nullptr)
 {
     const Geo<R> geo = make_geo<R, NL, FILL>(pb, nlines, p, mu);
@@ -101,7 +107,7 @@ __device__ __forceinline__ R fitness_rows(const KProblem &pb, int nlines, int nl
         load4(s_doff + 4 * j, doff);
         load4(s_obs + 4 * j, ob);
         const Stokes4<R> s = me_point<R, NL, PAT, FILL>(geo, doff, he, nlines, pb.line);
-        if (COUNT) ninterior += count_interior<R, NL, PAT>(geo, doff, nlines, pb.line);
+        if (COUNT) wc.interior += count_interior<R, NL, PAT>(geo, doff, nlines, pb.line);
         if (STORE && res) {
             res[j] = ob[0] - s.I;
             res[nl + j] = ob[1] - s.Q;
@@ -130,8 +136,7 @@ template <int NL, bool COUNT, bool PAT, bool FILL, bool STORE = false>
 __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, int nl, const float *p,
                                                float mu, const float *s_obs, const float *s_doff,
                                                const float *he, const float *s_w2, float inv_nu,
-                                               unsigned long long &ninterior, unsigned long long &nmid,
-                                               unsigned long long &nfar, float *res = nullptr)
+                                               WorkCount &wc, float *res = nullptr)
 {
     Geo<float> geo = make_geo<float, NL, FILL>(pb, nlines, p, mu);
     pair_thresholds(geo, nlines);
@@ -145,7 +150,7 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
     const float2 wI = f2(sw[0]);
     float2 sum = f2(0.f), comp = f2(0.f);
     const int npair = (nl + 1) >> 1;
-    EvalCount cnt{0u, 0u, 0u};
+    EvalCount cnt{0u, 0u, 0u, 0u};
     for (int q = 0; q < npair; ++q) {
         const float4 o0 = *(const float4 *)(s_obs + 8 * q), o1 = *(const float4 *)(s_obs + 8 * q + 4);
         const float4 d0 = *(const float4 *)(s_doff + 8 * q);
@@ -185,9 +190,10 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
         sum = t;
     }
     if (COUNT) {
-        ninterior += cnt.interior;
-        nmid += cnt.mid;
-        nfar += cnt.far;
+        wc.interior += cnt.interior;
+        wc.mid += cnt.mid;
+        wc.even2 += cnt.even2;
+        wc.far += cnt.far;
     }
     return ((sum.x - comp.x) + (sum.y - comp.y)) * inv_nu;
 }
@@ -195,15 +201,14 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
 template <class R, int NL, bool COUNT, bool PAT, bool FILL, bool STORE = false>
 __device__ __forceinline__ R fitness(const KProblem &pb, int nlines, int nl, const R *p, R mu,
                                      const R *s_obs, const R *s_doff, const R *he,
-                                     const R *s_w2, R inv_nu, unsigned long long &ninterior,
-                                     unsigned long long &nmid, unsigned long long &nfar, R *res = nullptr)
+                                     const R *s_w2, R inv_nu, WorkCount &wc, R *res = nullptr)
 {
     if constexpr (std::is_same<R, float>::value)
         return fitness_pairs<NL, COUNT, PAT, FILL, STORE>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2,
-                                                          inv_nu, ninterior, nmid, nfar, res);
+                                                          inv_nu, wc, res);
     else
         return fitness_rows<R, NL, COUNT, PAT, FILL, STORE>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2,
-                                                            inv_nu, ninterior, res);
+                                                            inv_nu, wc, res);
 }
 
 // argmin over the block's fitness, ties to the lowest index.  Every thread
@@ -495,7 +500,8 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
             const KSeed sd, const KSub sub)
 {
     constexpr bool FILL = M > ME_NPAR;  // parameter 9: the fill fraction (Section 5.2)
-    unsigned long long nfit = 0, ninterior = 0, nmid = 0, nfar = 0;
+    unsigned long long nfit = 0;
+    WorkCount wc{};
     extern __shared__ __align__(16) unsigned char smem[];
     const int nl = pb.n_lambda;
     const int nlines = NL > 0 ? NL : pb.n_lines;
@@ -563,7 +569,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
         int cur = 0;
 #pragma unroll
         for (int d = 0; d < M; ++d) s_genes[k * M + d] = g[d];
-        s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior, nmid, nfar));
+        s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, wc));
         if (COUNT) ++nfit;
         uint64_t sobol_next = (uint64_t)npop + 1;
 
@@ -580,7 +586,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
                 p[d] = GaDecode<R>::get(D, d, g[d]);
             }
             cur ^= 1;
-            s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior, nmid, nfar));
+            s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, wc));
             if (COUNT) ++nfit;
             // a13: worst-half Sobol restart.  The individual of rank npop/2 + i
             // takes Sobol point sobol_next + i; thread i evaluates it, so the
@@ -603,7 +609,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
                         p[d] = GaDecode<R>::get(D, d, g[d]);
                     }
                     s_fit[kr] = clean_fit(
-                        fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, ninterior, nmid, nfar));
+                        fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, wc));
                     if (COUNT) ++nfit;
                 }
                 sobol_next += (uint64_t)(npop / 2);
@@ -629,10 +635,11 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
             per_point += nc ? nc : 3;
         }
         atomicAdd(counts + 0, nfit);
-        atomicAdd(counts + 1, ninterior);
+        atomicAdd(counts + 1, wc.interior);
         atomicAdd(counts + 2, nfit * (unsigned long long)nl * per_point);
-        atomicAdd(counts + 3, nfar);
-        atomicAdd(counts + 4, nmid);
+        atomicAdd(counts + 3, wc.far);
+        atomicAdd(counts + 4, wc.mid);
+        atomicAdd(counts + 5, wc.even2);
     }
 }
 

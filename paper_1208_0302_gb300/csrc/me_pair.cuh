@@ -6,18 +6,19 @@
 //
 // Branches are uniform across the warp.  A Zeeman component takes the
 // far-field approximant when every lane's pair of points is beyond
-// |z|^2 = 360, the 3rd convergent of the continued fraction when every pair
-// is beyond |z|^2 = 36, the 5th beyond 21, and Weideman's series otherwise.
-// Each branch is accurate wherever it is taken: the convergents and the far
-// field to 1.3e-7 or better beyond their thresholds, the series everywhere
-// (truncation error 4.3e-8 for |x| <= 1e4, 0 <= y <= 1; near the line centre,
-// where |w| is about 1, FP32 rounding of the series is the larger term, about
-// 1e-6 relative).  A point's value can therefore depend on its partner's and
-// its warp's regions, always within that budget.
+// |z|^2 = 360, the even (three-node) convergent of the continued fraction when
+// every pair is beyond |z|^2 = 80, the 3rd convergent beyond 36, the 5th
+// beyond 21, and Weideman's series otherwise.  Each branch is accurate
+// wherever it is taken: the convergents and the far field to 1.3e-7 or better
+// beyond their thresholds, the series everywhere (truncation error 4.3e-8 for
+// |x| <= 1e4, 0 <= y <= 1; near the line centre, where |w| is about 1, FP32
+// rounding of the series is the larger term, about 1e-6 relative).  A point's
+// value can therefore depend on its partner's and its warp's regions, always
+// within that budget.
 // An effective triplet is tested as a whole first: wholly far, all three
-// components take the far field; wholly beyond 36, all three take the 3rd
-// convergent; otherwise (near a line core) each component tests the regions
-// from the inside out.  A warp-uniform choice costs one branch where a
+// components take the far field; wholly beyond 80 the even convergent, wholly
+// beyond 36 the 3rd convergent; otherwise (near a line core) each component
+// tests the regions from the inside out.  A warp-uniform choice costs one branch where a
 // per-lane choice would run both for a mixed warp.  A region test is one
 // comparison of the pair's nearer |x| with a per-individual threshold, and
 // the vote reuses the fitness call's lane mask: the loop's issue slots, not
@@ -87,6 +88,25 @@ __device__ __forceinline__ void fad_ext2(float2 x, float y, float a2, float2 qs,
 // Weideman's series.
 constexpr float kMidR2 = 21.0f;
 
+// Outer shell kEven2R2 < |z|^2 <= kFarR2: the even convergent
+// w = (i/sqrt(pi)) (z^2 - 1) / (z (z^2 - 3/2)) of the Laplace continued fraction
+// (the three-node Gauss-Hermite rule), |error| <= 1.13e-7 in FP32 there (at
+// the boundary; it falls outward), within the 1.3e-7 of the 3rd convergent.
+constexpr float kEven2R2 = 80.0f;
+__device__ __forceinline__ void fad_even2(float2 x, float y, float a2, float2 qs, float2 &wx, float2 &wy,
+                                          float2 &qi)
+{
+    // N = z^2 - 1, D = z^3 - (3/2) z = x (x^2 - 3y^2 - 3/2) + i y (3x^2 - y^2 - 3/2)
+    const float2 Nx = fma2(x, x, f2(-a2 - 1.0f));
+    const float2 Ny = mul2(x, f2(2.0f * y));
+    const float2 Dx = mul2(x, fma2(x, x, f2(-3.0f * a2 - 1.5f)));
+    const float2 Dy = fma2(mul2(x, f2(3.0f * y)), x, f2(y * (-a2 - 1.5f)));
+    qi = mul2(qs, rcp2(fma2(Dx, Dx, mul2(Dy, Dy))));
+    // w = (i/sqrt(pi)) N conj(D) / |D|^2
+    wx = fma2(Nx, Dy, neg2(mul2(Ny, Dx)));
+    wy = fma2(Nx, Dx, mul2(Ny, Dy));
+}
+
 // Far field (|z|^2 > kFarR2): the first non-trivial convergent of the Laplace
 // continued fraction (the two-node Gauss-Hermite rule), w = (i/sqrt(pi)) z /
 // (z^2 - 1/2); |error| <= 1.23e-7 in FP32 there (at the boundary; it falls
@@ -139,6 +159,7 @@ __device__ __forceinline__ float region_threshold(float R2, float a2) { return a
 __device__ __forceinline__ void pair_thresholds(Geo<float> &g, int nlines)
 {
     g.tfar = region_threshold(kFarR2, g.a2);
+    g.t80 = region_threshold(kEven2R2, g.a2);
     g.text = region_threshold(FadCfg<float>::R2, g.a2);
     g.tmid = region_threshold(kMidR2, g.a2);
 #pragma unroll
@@ -147,6 +168,9 @@ __device__ __forceinline__ void pair_thresholds(Geo<float> &g, int nlines)
 #pragma unroll
     for (int l = 0; l < ME_MAX_LINES; ++l)
         g.t3far[l] = (l < nlines && g.tfar >= 0.0f) ? g.tfar + fabsf(g.vB[l]) : -1.0f;
+#pragma unroll
+    for (int l = 0; l < ME_MAX_LINES; ++l)
+        g.t3e2[l] = (l < nlines && g.t80 >= 0.0f) ? g.t80 + fabsf(g.vB[l]) : -1.0f;
 }
 // Nearer |x| of a pair: the pair is beyond a threshold t when this is.
 __device__ __forceinline__ float pair_min_abs(float2 x) { return fminf(fabsf(x.x), fabsf(x.y)); }
@@ -170,22 +194,24 @@ __device__ __forceinline__ void fad_pair(float2 x, const Geo<float> &g, float2 q
 {
     const float m = pair_min_abs(x);
     if (warp_all(m > g.tfar, g.vmask)) fad_far2(x, g.a, g.a2, qs, wx, wy, qi);
+    else if (warp_all(m > g.t80, g.vmask)) fad_even2(x, g.a, g.a2, qs, wx, wy, qi);
     else if (warp_all(m > g.text, g.vmask)) fad_ext2(x, g.a, g.a2, qs, wx, wy, qi);
     else if (warp_all(m > g.tmid, g.vmask)) fad_cf2<5>(x, g.a, g.a2, qs, wx, wy, qi);
     else fad_int2(x, g.a, q, wx, wy, qi);
 }
 
 // Work counts of the algorithm proper: each real point's evaluation classified
-// by its own region (Weideman interior, middle shell, continued fraction, far
-// field), whatever branch its pair and warp took.
+// by its own region (Weideman interior, middle shell, 3rd convergent, outer
+// shell, far field), whatever branch its pair and warp took.
 struct EvalCount {
-    unsigned interior, mid, far;
+    unsigned interior, mid, even2, far;
 };
 __device__ __forceinline__ void count_point(float x, float a2, EvalCount &n)
 {
     const float r = x * x + a2;
     n.interior += r > kMidR2 ? 0u : 1u;
     n.mid += (r > kMidR2 && r <= FadCfg<float>::R2) ? 1u : 0u;
+    n.even2 += (r > kEven2R2 && r <= kFarR2) ? 1u : 0u;
     n.far += r > kFarR2 ? 1u : 0u;
 }
 __device__ __forceinline__ void count_pair(float2 x, float a2, bool y_real, EvalCount &n)
@@ -231,25 +257,28 @@ __device__ __forceinline__ void fad_pair_in(float2 x, const Geo<float> &g, float
     const float m = pair_min_abs(x);
     if (!warp_all(m > g.tmid, g.vmask)) fad_int2(x, g.a, q, wx, wy, qi);
     else if (!warp_all(m > g.text, g.vmask)) fad_cf2<5>(x, g.a, g.a2, qs, wx, wy, qi);
-    else fad_ext2(x, g.a, g.a2, qs, wx, wy, qi);
+    else if (!warp_all(m > g.t80, g.vmask)) fad_ext2(x, g.a, g.a2, qs, wx, wy, qi);
+    else fad_even2(x, g.a, g.a2, qs, wx, wy, qi);
 }
 
-// One component at a known level: 2 = every lane's pair is in the far
-// field, 1 = beyond the continued-fraction threshold (the 3rd convergent,
-// accurate there, also where a component is already far: cheaper than
-// testing each component), 0 = anywhere.
+// One component at a known level: 3 = every lane's pair is in the far
+// field, 2 = beyond the outer shell's threshold (the even convergent, accurate
+// there, also where a component is already far), 1 = beyond the
+// continued-fraction threshold (the 3rd convergent, likewise), 0 = anywhere
+// (cheaper than testing each component).
 template <int LEVEL>
 __device__ __forceinline__ void fad_level(float2 x, const Geo<float> &g, float2 q, float2 qs, float2 &wx,
                                           float2 &wy, float2 &qi)
 {
-    if (LEVEL == 2) fad_far2(x, g.a, g.a2, qs, wx, wy, qi);
+    if (LEVEL == 3) fad_far2(x, g.a, g.a2, qs, wx, wy, qi);
+    else if (LEVEL == 2) fad_even2(x, g.a, g.a2, qs, wx, wy, qi);
     else if (LEVEL == 1) fad_ext2(x, g.a, g.a2, qs, wx, wy, qi);
     else fad_pair_in(x, g, q, qs, wx, wy, qi);
 }
 
 // One effective triplet's contribution to a pair's profile sums, each
-// component added as soon as it is evaluated (EXT: every lane's triplet is
-// exterior, 2 when it is in the far field as a whole).
+// component added as soon as it is evaluated (EXT: the level of fad_level
+// that every lane's triplet reaches as a whole).
 template <int EXT, bool FILL>
 __device__ __forceinline__ void triplet_acc(float2 xb, float2 v, float2 xr, const Geo<float> &g, float2 q,
                                             float2 &P, float2 &Pim, float2 &Sg, float2 &Sgi, float2 &Dd,
@@ -274,14 +303,16 @@ __device__ __forceinline__ void triplet_acc(float2 xb, float2 v, float2 xr, cons
 }
 
 // The branch level of an effective triplet for a pair, voted across the warp
-// from its pi arguments v (the sigma arguments are v +- v_B): 2 when every
-// lane's triplet is wholly in the far field (|v| > t_far + |v_B|), 1 when
-// wholly beyond the continued-fraction threshold, 0 near a line core.
+// from its pi arguments v (the sigma arguments are v +- v_B): 3 when every
+// lane's triplet is wholly in the far field (|v| > t_far + |v_B|), 2 when
+// wholly beyond the outer shell's threshold, 1 when wholly beyond the
+// continued-fraction threshold, 0 near a line core.
 __device__ __forceinline__ int triplet_level(float2 v, const Geo<float> &g, int l)
 {
     const float mv = pair_min_abs(v);
-    if (warp_all(mv > g.t3[l], g.vmask)) return warp_all(mv > g.t3far[l], g.vmask) ? 2 : 1;
-    return 0;
+    if (!warp_all(mv > g.t3[l], g.vmask)) return 0;
+    if (warp_all(mv > g.t3far[l], g.vmask)) return 3;
+    return warp_all(mv > g.t3e2[l], g.vmask) ? 2 : 1;
 }
 
 // Residuals o - Stokes at two wavelength points (the synthesis of Section
@@ -330,7 +361,9 @@ __device__ __forceinline__ Stokes4x2 resid_x2(const Geo<float> &g, const float2 
             }
             const float2 q = f2(half_eta[l]);
             const int lev = triplet_level(v, g, l);
-            if (lev == 2)
+            if (lev == 3)
+                triplet_acc<3, FILL>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
+            else if (lev == 2)
                 triplet_acc<2, FILL>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
             else if (lev == 1)
                 triplet_acc<1, FILL>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);

@@ -29,7 +29,7 @@ WZ_ABS = 1.5e-7              # branch budget of the pair path's convergents and 
 WZ_REL = 1.0e-6              # FP32 rounding floor of Weideman's series, relative to |w|
 U32 = 2.0 ** -24
 FULL_6301 = (gi.FE6301[0], 1.667, gi.eta_ratio_6301(), 2, 11 / 6, 2, 1.5)
-THRESHOLDS = (21.0, 36.0, 360.0)   # |z|^2 of the middle shell, continued fraction, far field
+THRESHOLDS = (21.0, 36.0, 80.0, 360.0)   # |z|^2 of the middle shell, 3rd convergent, outer shell, far field
 
 
 # ------------------------------------------------------------------ w(z)
@@ -121,11 +121,12 @@ def test_wz_triplet_level_matches_oracle(gpu, orc):
     vb[: 32 * 8] = 0.0                               # field-free triplets
     vb[32 * 8: 32 * 12] = rng.uniform(0, 0.05, 128)  # tiny splitting
     v = rng.uniform(-80, 80, (n, 2))
-    # warps whose triplets all sit just beyond t_ext + |v_B| or t_far + |v_B|
-    for w, r2 in [(20, 36.0), (21, 360.0), (22, 36.0), (23, 360.0)]:
+    # warps whose triplets all sit just beyond (or just inside) t_ext, t_80 or
+    # t_far + |v_B|
+    for w, r2 in [(20, 36.0), (21, 360.0), (24, 80.0), (22, 36.0), (23, 360.0), (25, 80.0)]:
         s = slice(32 * w, 32 * w + 32)
         t = np.sqrt(np.maximum(r2 - a[s].astype(np.float64) ** 2, 0)) + vb[s]
-        side = 1.0 if w < 22 else 0.995
+        side = 1.0 if w in (20, 21, 24) else 0.995
         v[s] = (t * side)[:, None] * rng.uniform(1.0, 1.02, (32, 2)) * rng.choice([-1, 1], (32, 2))
     vb = vb.astype(np.float32)
     v = v.astype(np.float32)

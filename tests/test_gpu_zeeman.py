@@ -74,8 +74,9 @@ def test_full_pattern_ga_fp32_and_polish(gpu, orc):
     counts = gpu.ga_count_evaluations(pb, ob[:32].contiguous(), gi.PRIOR_LO, gi.PRIOR_HI,
                                       gpu.GaSettings(npop=64, ngen=4, seed=3))
     # 12 components for 6301.5 + 3 for 6302.5 per wavelength point
-    assert counts["weideman"] + counts["mid"] + counts["cf"] + counts["far"] == counts["points"] * 15
-    assert min(counts["weideman"], counts["mid"], counts["cf"], counts["far"]) > 0
+    assert (counts["weideman"] + counts["mid"] + counts["cf"] + counts["even2"] + counts["far"] ==
+            counts["points"] * 15)
+    assert min(counts["weideman"], counts["mid"], counts["cf"], counts["even2"], counts["far"]) > 0
     # syntheses: the initial population, every child of every generation and
     # the restarted half at each generation t < ngen with t % nsamp == 0
     # (nsamp = ngen // 4 = 1 here, so t = 1, 2, 3)

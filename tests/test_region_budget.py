@@ -3,9 +3,10 @@
 The region thresholds are read from the CUDA headers, each branch formula is
 evaluated in float32 (numpy, without fused multiply-adds, so a little
 pessimistic) beyond its threshold, and compared with scipy's wofz: the far
-field, the 3rd convergent and the 5th convergent of the Laplace continued
-fraction w = (i/sqrt(pi)) / (z - (1/2) / (z - 1 / (z - (3/2) / ...))) must stay
-within 1.5e-7 absolute (1.3e-7 with the kernel's FMAs).  Moving a threshold
+field, the even (three-node) convergent of the outer shell, the 3rd
+convergent and the 5th convergent of the Laplace continued fraction
+w = (i/sqrt(pi)) / (z - (1/2) / (z - 1 / (z - (3/2) / ...))) must stay within
+1.5e-7 absolute (1.3e-7 with the kernel's FMAs).  Moving a threshold
 inward past the budget fails here.  Weideman's series, the branch a mixed
 warp may take anywhere, is checked the same way in the pair path's
 algebraic form (coefficients from their defining integral, N and L read
@@ -33,6 +34,7 @@ def _constant(path, pattern):
 
 def thresholds():
     return {"far": _constant("me_pair.cuh", r"constexpr float kFarR2 = ([0-9.]+)f;"),
+            "even2": _constant("me_pair.cuh", r"constexpr float kEven2R2 = ([0-9.]+)f;"),
             "mid": _constant("me_pair.cuh", r"constexpr float kMidR2 = ([0-9.]+)f;"),
             "ext": _constant("me_device.cuh", r"static constexpr float R2 = ([0-9.]+)f;"),
             "K": _constant("me_device.cuh", r"static constexpr int K = ([0-9]+);")}
@@ -74,6 +76,18 @@ def far32(x, y):
     return ((x * uy - y * dx) * inv).astype(float) + 1j * ((x * dx + y * uy) * inv).astype(float)
 
 
+def even2_32(x, y):
+    """The outer shell's even convergent (i/sqrt(pi)) (z^2 - 1) / (z (z^2 - 3/2))
+    in float32, in the pair path's algebraic form."""
+    x, y = x.astype(f32), f32(y)
+    a2 = y * y
+    nx, ny = x * x + f32(-a2 - 1.0), x * (f32(2) * y)
+    dx = x * (x * x + f32(-3 * a2 - 1.5))
+    dy = (x * (f32(3) * y)) * x + f32(y * (-a2 - 1.5))
+    qi = f32(0.56418958354775628695) * (f32(1) / (dx * dx + dy * dy))
+    return (qi * (nx * dy - ny * dx)).astype(float) + 1j * (qi * (nx * dx + ny * dy)).astype(float)
+
+
 def worst_beyond(fn, r2):
     worst = 0.0
     for y in np.concatenate([[0.0], np.geomspace(1e-4, 1.0, 30)]):
@@ -85,8 +99,17 @@ def worst_beyond(fn, r2):
 
 def test_threshold_order():
     t = thresholds()
-    assert 0 < t["mid"] < t["ext"] < t["far"]
+    assert 0 < t["mid"] < t["ext"] < t["even2"] < t["far"]
     assert t["K"] == 3
+
+
+def test_even_convergent_within_budget():
+    assert worst_beyond(even2_32, thresholds()["even2"]) < BUDGET
+
+
+def test_even_convergent_budget_has_teeth():
+    """Moved a little inward, the outer shell's formula exceeds the budget."""
+    assert worst_beyond(even2_32, 0.8 * thresholds()["even2"]) > BUDGET
 
 
 def test_far_field_within_budget():
