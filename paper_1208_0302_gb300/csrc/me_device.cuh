@@ -252,13 +252,10 @@ template <class R> struct Geo {
     R kUV, kQV;         // kU kV, kQ kV
     R S0, muS1;
     R eta0, alpha;          // line strength; fill fraction (1 without one)
-    // FP32 pair path: |x| thresholds of the far, continued-fraction and middle
-    // regions (|x| > t <=> x^2 + a^2 > R^2; -1 when a^2 >= R^2) and, per line,
-    // the all-exterior test of a triplet |v| > t_ext + |v_B|
+    // FP32 pair path: |x| thresholds of the far, outer-shell, continued-
+    // fraction and middle regions (|x| > t <=> x^2 + a^2 > R^2; -1 when
+    // a^2 >= R^2); a triplet is wholly beyond one when |v| - |v_B| is
     R tfar, t80, text, tmid;
-    R t3[ME_MAX_LINES];
-    R t3far[ME_MAX_LINES];  // pair path: the all-far test of a triplet |v| > t_far + |v_B|
-    R t3e2[ME_MAX_LINES];   // pair path: the all-beyond-80 test of a triplet |v| > t_80 + |v_B|
     unsigned vmask;     // pair path: the lanes that evaluate together (votes)
     R shift[ME_MAX_LINES];  // lambda0 v_LOS / c [A]
     R invD[ME_MAX_LINES];   // 1 / Doppler width [1/A]

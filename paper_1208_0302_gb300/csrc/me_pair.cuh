@@ -156,21 +156,12 @@ __device__ __forceinline__ void fad_int2(float2 x, float y, float2 q, float2 &wx
 // |x| threshold of a region x^2 + a^2 > R2 (once per individual).
 __device__ __forceinline__ float region_threshold(float R2, float a2) { return a2 >= R2 ? -1.0f : sqrtf(R2 - a2); }
 // Fill the pair path's thresholds of a geometry (once per individual).
-__device__ __forceinline__ void pair_thresholds(Geo<float> &g, int nlines)
+__device__ __forceinline__ void pair_thresholds(Geo<float> &g, int)
 {
     g.tfar = region_threshold(kFarR2, g.a2);
     g.t80 = region_threshold(kEven2R2, g.a2);
     g.text = region_threshold(FadCfg<float>::R2, g.a2);
     g.tmid = region_threshold(kMidR2, g.a2);
-#pragma unroll
-    for (int l = 0; l < ME_MAX_LINES; ++l)
-        g.t3[l] = (l < nlines && g.text >= 0.0f) ? g.text + fabsf(g.vB[l]) : -1.0f;
-#pragma unroll
-    for (int l = 0; l < ME_MAX_LINES; ++l)
-        g.t3far[l] = (l < nlines && g.tfar >= 0.0f) ? g.tfar + fabsf(g.vB[l]) : -1.0f;
-#pragma unroll
-    for (int l = 0; l < ME_MAX_LINES; ++l)
-        g.t3e2[l] = (l < nlines && g.t80 >= 0.0f) ? g.t80 + fabsf(g.vB[l]) : -1.0f;
 }
 // Nearer |x| of a pair: the pair is beyond a threshold t when this is.
 __device__ __forceinline__ float pair_min_abs(float2 x) { return fminf(fabsf(x.x), fabsf(x.y)); }
@@ -309,10 +300,11 @@ __device__ __forceinline__ void triplet_acc(float2 xb, float2 v, float2 xr, cons
 // continued-fraction threshold, 0 near a line core.
 __device__ __forceinline__ int triplet_level(float2 v, const Geo<float> &g, int l)
 {
-    const float mv = pair_min_abs(v);
-    if (!warp_all(mv > g.t3[l], g.vmask)) return 0;
-    if (warp_all(mv > g.t3far[l], g.vmask)) return 3;
-    return warp_all(mv > g.t3e2[l], g.vmask) ? 2 : 1;
+    // the nearest component's |x| is at least |v| - |v_B|
+    const float m = pair_min_abs(v) - fabsf(g.vB[l]);
+    if (!warp_all(m > g.text, g.vmask)) return 0;
+    if (warp_all(m > g.tfar, g.vmask)) return 3;
+    return warp_all(m > g.t80, g.vmask) ? 2 : 1;
 }
 
 // Residuals o - Stokes at two wavelength points (the synthesis of Section
