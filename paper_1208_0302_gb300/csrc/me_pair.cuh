@@ -96,15 +96,15 @@ constexpr float kEven2R2 = 80.0f;
 __device__ __forceinline__ void fad_even2(float2 x, float y, float a2, float2 qs, float2 &wx, float2 &wy,
                                           float2 &qi)
 {
-    // N = z^2 - 1, D = z^3 - (3/2) z = x (x^2 - 3y^2 - 3/2) + i y (3x^2 - y^2 - 3/2)
-    const float2 Nx = fma2(x, x, f2(-a2 - 1.0f));
-    const float2 Ny = mul2(x, f2(2.0f * y));
-    const float2 Dx = mul2(x, fma2(x, x, f2(-3.0f * a2 - 1.5f)));
-    const float2 Dy = fma2(mul2(x, f2(3.0f * y)), x, f2(y * (-a2 - 1.5f)));
-    qi = mul2(qs, rcp2(fma2(Dx, Dx, mul2(Dy, Dy))));
-    // w = (i/sqrt(pi)) N conj(D) / |D|^2
-    wx = fma2(Nx, Dy, neg2(mul2(Ny, Dx)));
-    wy = fma2(Nx, Dx, mul2(Ny, Dy));
+    // With N = z^2 - 1, D = z (z^2 - 3/2), z = x + i y and s = |z|^2 = x^2 + y^2
+    // (x real, y the damping): i N conj(D) = y (s^2 - 1.5 s + 4 y^2 + 1.5)
+    // + i x (s^2 - 2.5 s + 4 y^2 + 1.5) and |D|^2 = s (s^2 - 3 s + 6 y^2 + 9/4).
+    const float2 s = fma2(x, x, f2(a2));
+    const float2 pr = fma2(s, s, fma2(f2(-1.5f), s, f2(4.0f * a2 + 1.5f)));
+    const float2 u = fma2(s, s, fma2(f2(-3.0f), s, f2(6.0f * a2 + 2.25f)));
+    qi = mul2(qs, rcp2(mul2(s, u)));
+    wx = mul2(f2(y), pr);
+    wy = mul2(x, sub2(pr, s));
 }
 
 // Far field (|z|^2 > kFarR2): the first non-trivial convergent of the Laplace
@@ -115,11 +115,12 @@ constexpr float kFarR2 = 360.0f;
 __device__ __forceinline__ void fad_far2(float2 x, float y, float a2, float2 qs, float2 &wx, float2 &wy,
                                          float2 &qi)
 {
-    const float2 dx = fma2(x, x, f2(-a2 - 0.5f));  // Re(z^2 - 1/2)
-    const float2 uy = mul2(x, f2(2.0f * y));       // Im(z^2)
-    qi = mul2(qs, rcp2(fma2(dx, dx, mul2(uy, uy))));
-    wx = fma2(x, uy, neg2(mul2(f2(y), dx)));
-    wy = fma2(x, dx, mul2(f2(y), uy));
+    // With z = x + i y and s = |z|^2 (x real): i z conj(z^2 - 1/2) =
+    // y (s + 1/2) + i x (s - 1/2) and |z^2 - 1/2|^2 = s^2 - x^2 + y^2 + 1/4.
+    const float2 s = fma2(x, x, f2(a2));
+    qi = mul2(qs, rcp2(fma2(s, s, fma2(neg2(x), x, f2(a2 + 0.25f)))));
+    wx = fma2(f2(y), s, f2(0.5f * y));
+    wy = mul2(x, add2(s, f2(-0.5f)));
 }
 
 // Interior branch (Weideman N = 16, real-quadratic synthetic division) for a

@@ -69,23 +69,27 @@ def cf32(x, y, k):
 
 
 def far32(x, y):
+    """The far-field approximant (i/sqrt(pi)) z / (z^2 - 1/2) in float32, in the
+    pair path's algebraic form: y (s + 1/2) + i x (s - 1/2) over
+    s^2 - x^2 + y^2 + 1/4, s = x^2 + y^2."""
     x, y = x.astype(f32), f32(y)
-    ux, uy = x * x - f32(y * y), x * (f32(2) * y)
-    dx = ux - f32(0.5)
-    inv = (f32(1) / (dx * dx + uy * uy)) * f32(0.56418958354775628695)
-    return ((x * uy - y * dx) * inv).astype(float) + 1j * ((x * dx + y * uy) * inv).astype(float)
+    a2 = y * y
+    s = x * x + a2
+    qi = f32(0.56418958354775628695) * (f32(1) / (s * s + (-(x * x) + f32(a2 + 0.25))))
+    return (qi * (y * s + f32(0.5) * y)).astype(float) + 1j * (qi * (x * (s + f32(-0.5)))).astype(float)
 
 
 def even2_32(x, y):
     """The outer shell's even convergent (i/sqrt(pi)) (z^2 - 1) / (z (z^2 - 3/2))
-    in float32, in the pair path's algebraic form."""
+    in float32, in the pair path's algebraic form: y P + i x (P - s) over
+    s (s^2 - 3 s + 6 y^2 + 9/4), P = s^2 - 1.5 s + 4 y^2 + 1.5."""
     x, y = x.astype(f32), f32(y)
     a2 = y * y
-    nx, ny = x * x + f32(-a2 - 1.0), x * (f32(2) * y)
-    dx = x * (x * x + f32(-3 * a2 - 1.5))
-    dy = (x * (f32(3) * y)) * x + f32(y * (-a2 - 1.5))
-    qi = f32(0.56418958354775628695) * (f32(1) / (dx * dx + dy * dy))
-    return (qi * (nx * dy - ny * dx)).astype(float) + 1j * (qi * (nx * dx + ny * dy)).astype(float)
+    s = x * x + a2
+    pr = s * s + (f32(-1.5) * s + f32(4 * a2 + 1.5))
+    u = s * s + (f32(-3.0) * s + f32(6 * a2 + 2.25))
+    qi = f32(0.56418958354775628695) * (f32(1) / (s * u))
+    return (qi * (y * pr)).astype(float) + 1j * (qi * (x * (pr - s))).astype(float)
 
 
 def worst_beyond(fn, r2):
