@@ -145,7 +145,7 @@ def flop_model(nlines):
     per-individual invariants such as 2a or (L + a)^2), per unit: an
     evaluation of w(z) in the interior (Weideman N = 16 by real-quadratic
     synthetic division, 91), in the middle shell (5th convergent, 43), in the
-    continued-fraction region (3rd convergent, 29), in the outer shell (the
+    continued-fraction region (3rd convergent in s = |z|^2, 23), in the outer shell (the
     even convergent, 16) and in the far field (two-node approximant, 12), the
     rational branches leaving their
     normalisation to the accumulation weight; and per wavelength
@@ -156,7 +156,7 @@ def flop_model(nlines):
     summed by FMA and 4 for the Kahan-compensated running sum.  Each point's
     evaluations are classified by its own region; branch tests, votes and work
     a pair or warp does beyond that are not counted."""
-    return {"weideman": 91.0, "mid": 43.0, "cf": 29.0, "even2": 16.0, "far": 12.0, "point": 23.0 * nlines + 67.0}
+    return {"weideman": 91.0, "mid": 43.0, "cf": 23.0, "even2": 16.0, "far": 12.0, "point": 23.0 * nlines + 67.0}
 
 
 def run_ours(args):

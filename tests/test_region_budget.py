@@ -4,7 +4,7 @@ The region thresholds are read from the CUDA headers, each branch formula is
 evaluated in float32 (numpy, without fused multiply-adds, so a little
 pessimistic) beyond its threshold, and compared with scipy's wofz: the far
 field, the even (three-node) convergent of the outer shell, the 3rd
-convergent and the 5th convergent of the Laplace continued fraction
+convergent (in its s-form, FMAs kept) and the 5th convergent of the Laplace continued fraction
 w = (i/sqrt(pi)) / (z - (1/2) / (z - 1 / (z - (3/2) / ...))) must stay within
 1.5e-7 absolute (1.3e-7 with the kernel's FMAs).  Moving a threshold
 inward past the budget fails here.  Weideman's series, the branch a mixed
@@ -92,6 +92,29 @@ def even2_32(x, y):
     return (qi * (y * pr)).astype(float) + 1j * (qi * (x * (pr - s))).astype(float)
 
 
+def fma32(a, b, c):
+    """A float32 fused multiply-add: the float64 product of two float32 values
+    is exact, so one rounding of the float64 sum stands for the kernel's."""
+    return (np.float64(a) * np.float64(b) + np.float64(c)).astype(f32)
+
+
+def cf3_s32(x, y):
+    """The 3rd convergent (i/sqrt(pi)) z (z^2 - 5/2) / (z^4 - 3 z^2 + 3/4) in
+    float32 in the pair path's s-form (s = x^2 + y^2, the kernel's FMAs kept):
+    y (s^3 - 4.5 s^2 + c1 s + c0) + i x (s^3 - 5.5 s^2 + (c1 + 3) s - c0) over
+    s^4 - 6 s^3 + d2 s^2 + (6 - d2) s + d0."""
+    x, y = x.astype(f32), f32(y)
+    a2 = f32(y * y)
+    c1, c0 = fma32(10.0, a2, 5.25), fma32(3.0, a2, 1.875)
+    d2, d0 = fma32(12.0, a2, 10.5), fma32(fma32(12.0, a2, 9.0), a2, 0.5625)
+    s = fma32(x, x, a2)
+    pr = fma32(fma32(s, s + f32(-4.5), c1), s, c0)
+    pi = fma32(fma32(s, s + f32(-5.5), c1 + f32(3)), s, -c0)
+    den = fma32(fma32(fma32(s + f32(-6), s, d2), s, f32(6) - d2), s, d0)
+    qi = f32(0.56418958354775628695) * (f32(1) / den)
+    return (qi * (y * pr)).astype(float) + 1j * (qi * (x * pi)).astype(float)
+
+
 def worst_beyond(fn, r2):
     worst = 0.0
     for y in np.concatenate([[0.0], np.geomspace(1e-4, 1.0, 30)]):
@@ -121,7 +144,30 @@ def test_far_field_within_budget():
 
 
 def test_third_convergent_within_budget():
-    assert worst_beyond(lambda x, y: cf32(x, y, 3), thresholds()["ext"]) < BUDGET
+    assert worst_beyond(cf3_s32, thresholds()["ext"]) < BUDGET
+
+
+def test_third_convergent_s_form_is_the_convergent():
+    """The s-form is the same rational function as the complex polynomials of
+    the continued fraction (checked in float64, away from rounding)."""
+    x = np.linspace(0.0, 40.0, 401)
+    for y in (0.0, 0.05, 0.7):
+        z = x + 1j * y
+        ref = 1j / np.sqrt(np.pi) * z * (z * z - 2.5) / (z ** 4 - 3 * z * z + 0.75)
+        a, b = convergent_polys(3)
+        u = z * z
+        poly = 1j / np.sqrt(np.pi) * z * np.polyval(b[::-1], u) / np.polyval(a[::-1], u)
+        assert np.allclose(ref, poly, rtol=1e-13, atol=0)
+        s = x * x + y * y
+        c1, c0, d2, d0 = 5.25 + 10 * y * y, 1.875 + 3 * y * y, 10.5 + 12 * y * y, 12 * y ** 4 + 9 * y * y + 0.5625
+        w = (y * (s ** 3 - 4.5 * s * s + c1 * s + c0) + 1j * x * (s ** 3 - 5.5 * s * s + (c1 + 3) * s - c0)) \
+            / (s ** 4 - 6 * s ** 3 + d2 * s * s + (6 - d2) * s + d0) / np.sqrt(np.pi)
+        assert np.allclose(w, ref, rtol=1e-12, atol=1e-300)
+
+
+def test_third_convergent_budget_has_teeth():
+    """Moved a little inward, the 3rd convergent exceeds the budget."""
+    assert worst_beyond(cf3_s32, 0.9 * thresholds()["ext"]) > BUDGET
 
 
 def test_fifth_convergent_within_budget():
