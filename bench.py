@@ -34,17 +34,23 @@ import numpy as np  # noqa: E402
 import genesis_inputs as gi  # noqa: E402
 
 METRIC = "pixels inverted/s at fixed median chi2 vs plain FP64 GA"
-WORKLOAD = ("two-line Fe I 6301.5+6302.5 ME inversion, 512x512 px, 128 lambda, float32 cube, npop 128, 200 gen, "
-            "FP32 GA + 10 L-M (analytic adjoint, FP64 Cholesky)")
+
+
+def workload(side):
+    return (f"two-line Fe I 6301.5+6302.5 ME inversion, {side}x{side} px, 128 lambda, float32 cube, npop 128, "
+            "200 gen, FP32 GA + 10 L-M (analytic adjoint, FP64 Cholesky)")
+
+
+L2_BYTES = 129e6
 E2E_STEPS_MAX = 5   # the end-to-end leg repeats at most this many steps
 NPOP, NGEN, LM_ITERS = 128, 200, 10
 KERNELS_PER_STEP = 4  # GA evolve, FP64 chi2, L-M, FP64 chi2
 # DRAM bytes (read + write) per pixel of one GA launch, from an ncu capture of
-# k_ga_evolve on the 4096-pixel two-line case (dram__bytes_read.sum 8511744 +
+# k_ga_evolve on the 4096-pixel two-line case (dram__bytes_read.sum 8738816 +
 # dram__bytes_write.sum 0, divided by 4096; traffic grows in proportion to
 # pixels: each block reads its pixel's cube row once).  Set to None whenever
 # the kernel changes, until it is captured again.
-GA_DRAM_BYTES_PER_PIXEL = None
+GA_DRAM_BYTES_PER_PIXEL = 2133.5
 
 
 def parse():
@@ -306,6 +312,7 @@ def run_ours(args):
                  counts["even2"] * fm["even2"] + counts["far"] * fm["far"] + counts["points"] * fm["point"])
         props = torch.cuda.get_device_properties(dev)
         sms = props.multi_processor_count
+        cube_bytes = obs.numel() * obs.element_size()
         max_mhz = clk.get("sm_max_mhz") or 2070.0
         peak_derived = sms * 128 * 2 * max_mhz * 1e6 / 1e12      # FP32 FMA lanes x 2 flops x clock
         ga_kernel_ms = ga_avg - chi_ms
@@ -317,10 +324,10 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded truth from the priors, GPU ME synthesis + 1e-3 Ic Gaussian noise)",
-            "config": {"workload": WORKLOAD, "pixels_per_gpu": npix, "side": side, "n_lambda": spec.n_lambda,
+            "config": {"workload": workload(side), "pixels_per_gpu": npix, "side": side, "n_lambda": spec.n_lambda,
                        "npop": NPOP, "ngen": NGEN, "lm_iters": LM_ITERS,
-                       "l2": f"inputs larger than L2 ({obs.numel() * obs.element_size() / 1e6:.0f} MB float32 "
-                             "cube); compute bound"},
+                       "l2": (f"inputs {'larger' if cube_bytes > L2_BYTES else 'smaller'} than L2 "
+                              f"({cube_bytes / 1e6:.0f} MB float32 cube, L2 129 MB, no flush); compute bound")},
             "median_chi2": chi2_med,
             "syntheses_per_s": syntheses / (ga_kernel_ms / 1e3),
             "recovery": recovery,
@@ -693,7 +700,7 @@ def run_reference(args):
     return {"impl": "reference", "metric": METRIC, "value": val, "unit": "pixels/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD + " (oracle on a pixel sample)"},
+            "data": "synthetic", "config": {"workload": workload(args.side) + " (oracle on a pixel sample)"},
             "cpu_baseline": {"value": val, "unit": "pixels/s", "cores": nth, "kind": "oracle",
                              "sample": f"{n} pixels per step"},
             "e2e": {"value": val, "unit": "pixels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
