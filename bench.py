@@ -150,19 +150,20 @@ def flop_model(nlines):
     counted from the source of the GA's fitness path (per call, without the
     per-individual invariants such as 2a or (L + a)^2), per unit: an
     evaluation of w(z) in the interior (Weideman N = 16 by real-quadratic
-    synthetic division, 91), in the middle shell (5th convergent, 43), in the
+    synthetic division, 85), in the middle shell (5th convergent, 43), in the
     continued-fraction region (3rd convergent in s = |z|^2, 23), in the outer shell (the
     even convergent, 16) and in the far field (two-node approximant, 12), the
     rational branches leaving their
     normalisation to the accumulation weight; and per wavelength
-    point 23 per line for the component arguments, the weight q / sqrt(pi)
-    and the profile sums, 35 for K
+    point 19 per line for the component arguments, the weight q / sqrt(pi)
+    and the blue, pi and red profile sums, 4 for the sums and differences of
+    the sigma profiles, 35 for K
     and its closed-form inverse, 21 for the four Stokes values formed into
     their weighted residuals (w_I by one multiply), 7 for the four squares
     summed by FMA and 4 for the Kahan-compensated running sum.  Each point's
     evaluations are classified by its own region; branch tests, votes and work
     a pair or warp does beyond that are not counted."""
-    return {"weideman": 91.0, "mid": 43.0, "cf": 23.0, "even2": 16.0, "far": 12.0, "point": 23.0 * nlines + 67.0}
+    return {"weideman": 85.0, "mid": 43.0, "cf": 23.0, "even2": 16.0, "far": 12.0, "point": 19.0 * nlines + 71.0}
 
 
 def run_ours(args):

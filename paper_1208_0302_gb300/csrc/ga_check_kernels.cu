@@ -35,6 +35,7 @@ k_ga_fitness(const __grid_constant__ KProblem pb, int weight_mode, const R *__re
     R *s_doff = (R *)(smem + L.doff);
     R *s_w2 = (R *)(smem + L.w2);
     R *s_he = (R *)(smem + L.he);
+    float4 *s_kc = (float4 *)(smem + L.kc);
     const R inv_nu = R(1) / R(4 * nl - M);
     stage_offsets_ga<R>(pb, nlines, nl, k, s_doff, s_he);
     stage_obs<R>(obs + (size_t)pix * 4 * nl, nl, k, s_obs);
@@ -56,7 +57,7 @@ k_ga_fitness(const __grid_constant__ KProblem pb, int weight_mode, const R *__re
         for (int d = 0; d < M; ++d) p[d] = R(params[ind * M + d]);
         WorkCount wc{};
         const R f = fitness<R, NL, false, PAT, FILL, true>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu,
-                                                           wc, res ? res + ind * 4 * nl : nullptr);
+                                                           wc, s_kc, res ? res + ind * 4 * nl : nullptr);
         fit[ind] = double(f);
     }
 }
@@ -98,17 +99,18 @@ __global__ void k_fad_probe(const float2 *__restrict__ x, const float *__restric
     if (mode == 2) {
         const float2 xb = add2(v, f2(g.vB[0])), xr = sub2(v, f2(g.vB[0]));
         const float2 q = f2(1.0f);
-        float2 P = f2(0.f), Pim = f2(0.f), Sg = f2(0.f), Sgi = f2(0.f), Dd = f2(0.f), Di = f2(0.f), P0 = f2(0.f);
+        float2 P = f2(0.f), Pim = f2(0.f), Sb = f2(0.f), Sbi = f2(0.f), Sr = f2(0.f), Sri = f2(0.f), P0 = f2(0.f);
         const int lev = triplet_level(v, g, 0);
         if (lev == 3)
-            triplet_acc<3, false>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
+            triplet_acc<3, false>(xb, v, xr, g, q, mul2(q, f2(kInvSqrtPi)), P, Pim, Sb, Sbi, Sr, Sri, P0);
         else if (lev == 2)
-            triplet_acc<2, false>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
+            triplet_acc<2, false>(xb, v, xr, g, q, mul2(q, f2(kInvSqrtPi)), P, Pim, Sb, Sbi, Sr, Sri, P0);
         else if (lev == 1)
-            triplet_acc<1, false>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
+            triplet_acc<1, false>(xb, v, xr, g, q, mul2(q, f2(kInvSqrtPi)), P, Pim, Sb, Sbi, Sr, Sri, P0);
         else
-            triplet_acc<0, false>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
-        const float2 o[6] = {P, Pim, Sg, Sgi, Dd, Di};
+            triplet_acc<0, false>(xb, v, xr, g, q, mul2(q, f2(kInvSqrtPi)), P, Pim, Sb, Sbi, Sr, Sri, P0);
+        // the sums and differences of the sigma profiles, as the fitness forms them
+        const float2 o[6] = {P, Pim, add2(Sb, Sr), add2(Sbi, Sri), sub2(Sr, Sb), sub2(Sri, Sbi)};
         float *r = out + (size_t)i * 12;
 #pragma unroll
         for (int c = 0; c < 6; ++c) {

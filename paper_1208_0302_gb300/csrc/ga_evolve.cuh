@@ -132,11 +132,16 @@ __device__ __forceinline__ R fitness_rows(const KProblem &pb, int nlines, int nl
 // lane with Kahan's compensation, so the sum's relative error stays at a few
 // units of 2^-24 whatever the number of wavelengths.  The fitness only ranks
 // individuals; the best individual's chi2 is re-evaluated in FP64.
+// s_kc: the calling thread's shared-memory slots, three float4 at s_kc[k],
+// s_kc[k + blockDim], s_kc[k + 2 blockDim] (k = threadIdx.x), which hold the
+// individual's closed-form constants and w_I for the length of the call:
+// they are read once per pair instead of holding registers through the
+// profile evaluations.
 template <int NL, bool COUNT, bool PAT, bool FILL, bool STORE = false>
 __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, int nl, const float *p,
                                                float mu, const float *s_obs, const float *s_doff,
                                                const float *he, const float *s_w2, float inv_nu,
-                                               WorkCount &wc, float *res = nullptr)
+                                               WorkCount &wc, float4 *s_kc, float *res = nullptr)
 {
     Geo<float> geo = make_geo<float, NL, FILL>(pb, nlines, p, mu);
     pair_thresholds(geo, nlines);
@@ -147,12 +152,15 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
     geo.kU *= sw[2];
     geo.kQV *= sw[2];
     geo.kV *= sw[3];
-    const float2 wI = f2(sw[0]);
+    const int kt = threadIdx.x, nt = blockDim.x;
+    s_kc[kt] = make_float4(geo.kIs, geo.kIp, geo.kIp2, geo.kV2);
+    s_kc[nt + kt] = make_float4(geo.muS1, geo.S0, geo.kQ, geo.kUV);
+    s_kc[2 * nt + kt] = make_float4(geo.kU, geo.kQV, geo.kV, sw[0]);
+    const float4 *kc = s_kc + kt;
     float2 sum = f2(0.f), comp = f2(0.f);
     const int npair = (nl + 1) >> 1;
     EvalCount cnt{0u, 0u, 0u, 0u};
     for (int q = 0; q < npair; ++q) {
-        const float4 o0 = *(const float4 *)(s_obs + 8 * q), o1 = *(const float4 *)(s_obs + 8 * q + 4);
         const float4 d0 = *(const float4 *)(s_doff + 8 * q);
         float2 doff2[ME_MAX_LINES];
         doff2[0] = make_float2(d0.x, d0.y);
@@ -163,10 +171,10 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
             doff2[3] = make_float2(d1.z, d1.w);
         }
         const bool y_real = 2 * q + 1 < nl;
-        const Stokes4x2 ob = {make_float2(o0.x, o0.y), make_float2(o0.z, o0.w), make_float2(o1.x, o1.y),
-                              make_float2(o1.z, o1.w)};
-        const Stokes4x2 rr = resid_x2<NL, COUNT, PAT, FILL>(geo, doff2, ob, he, nlines, y_real, cnt, pb.line);
-        float2 rI = mul2(rr.I, wI), rQ = rr.Q, rU = rr.U, rV = rr.V;
+        float wIs;
+        const Stokes4x2 rr = resid_x2<NL, COUNT, PAT, FILL>(geo, doff2, s_obs + 8 * q, he, nlines, y_real, cnt, pb.line, kc, nt,
+                                                            wIs);
+        float2 rI = mul2(rr.I, f2(wIs)), rQ = rr.Q, rU = rr.U, rV = rr.V;
         if (!y_real) rI.y = rQ.y = rU.y = rV.y = 0.f;  // padded partner
         if (STORE && res) {
             const int j = 2 * q;
@@ -201,11 +209,11 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
 template <class R, int NL, bool COUNT, bool PAT, bool FILL, bool STORE = false>
 __device__ __forceinline__ R fitness(const KProblem &pb, int nlines, int nl, const R *p, R mu,
                                      const R *s_obs, const R *s_doff, const R *he,
-                                     const R *s_w2, R inv_nu, WorkCount &wc, R *res = nullptr)
+                                     const R *s_w2, R inv_nu, WorkCount &wc, float4 *s_kc, R *res = nullptr)
 {
     if constexpr (std::is_same<R, float>::value)
         return fitness_pairs<NL, COUNT, PAT, FILL, STORE>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2,
-                                                          inv_nu, wc, res);
+                                                          inv_nu, wc, s_kc, res);
     else
         return fitness_rows<R, NL, COUNT, PAT, FILL, STORE>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2,
                                                             inv_nu, wc, res);
@@ -333,7 +341,7 @@ __device__ __forceinline__ void breed_one(const KGa &ga, uint64_t pid, int t, in
 
 struct GaSmem {
     // byte offsets into dynamic shared memory
-    int obs, doff, fit, wmin, widx, w2, he, dom, genes, total;
+    int obs, doff, fit, wmin, widx, w2, he, dom, genes, kc, total;
 };
 
 template <class R>
@@ -357,6 +365,7 @@ __host__ __device__ __forceinline__ GaSmem ga_smem_layout(int nl, int nlines, in
     L.he = take(4 * (int)sizeof(R), 16);
     L.dom = take((int)sizeof(DecodeDomain), 16);  // the pixel's decode domain
     L.genes = take(2 * npop * npar * 2, 16);
+    L.kc = take(sizeof(R) == 4 ? 3 * npop * 16 : 0, 16);  // FP32: 3 float4 of closed-form constants per thread
     L.total = (o + 15) / 16 * 16;
     return L;
 }
@@ -517,6 +526,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
     R *s_he = (R *)(smem + L.he);
     DecodeDomain &D = *(DecodeDomain *)(smem + L.dom);
     uint16_t *s_genes = (uint16_t *)(smem + L.genes);
+    float4 *s_kc = (float4 *)(smem + L.kc);
 
     // per-launch constants
     const R inv_nu = R(1) / R(4 * nl - M);
@@ -569,7 +579,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
         int cur = 0;
 #pragma unroll
         for (int d = 0; d < M; ++d) s_genes[k * M + d] = g[d];
-        s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, wc));
+        s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, wc, s_kc));
         if (COUNT) ++nfit;
         uint64_t sobol_next = (uint64_t)npop + 1;
 
@@ -586,7 +596,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
                 p[d] = GaDecode<R>::get(D, d, g[d]);
             }
             cur ^= 1;
-            s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, wc));
+            s_fit[k] = clean_fit(fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, wc, s_kc));
             if (COUNT) ++nfit;
             // a13: worst-half Sobol restart.  The individual of rank npop/2 + i
             // takes Sobol point sobol_next + i; thread i evaluates it, so the
@@ -609,7 +619,7 @@ k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
                         p[d] = GaDecode<R>::get(D, d, g[d]);
                     }
                     s_fit[kr] = clean_fit(
-                        fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, wc));
+                        fitness<R, NL, COUNT, PAT, FILL>(pb, nlines, nl, p, mu, s_obs, s_doff, he, s_w2, inv_nu, wc, s_kc));
                     if (COUNT) ++nfit;
                 }
                 sobol_next += (uint64_t)(npop / 2);

@@ -30,6 +30,7 @@ struct KLine {
     double cstr[3][ME_MAX_COMP];    // component strengths (sum 1 per group)
     float cshift32[3][ME_MAX_COMP];
     float cstr32[3][ME_MAX_COMP];
+    float2 q2, qs2;    // FP32 pair path: (half_eta, half_eta) and the same / sqrt(pi)
 };
 
 template <class R> __device__ __forceinline__ R comp_shift(const KLine &ln, int g, int i);

@@ -36,6 +36,15 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
 __device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(fast_rcp(a.x), fast_rcp(a.y)); }
+// A shared-memory vector load the compiler keeps where it is written (not
+// hoisted out of the loop that contains it).
+__device__ __forceinline__ float4 lds4(const float4 *p)
+{
+    float4 v;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
 
 // Every branch returns a weighted profile value q w(z) as qi (nx + i ny): the
 // caller adds qi nx and qi ny into its sums with one FMA each.  The rational
@@ -164,10 +173,11 @@ __device__ __forceinline__ void fad_int2(float2 x, float y, float2 q, float2 &wx
         b1 = b0;
     }
     const float2 px = fma2(sq, b2, fma2(b1, Zx, c_fad.w32x2[1])), py = mul2(b1, Zy);
-    const float2 r2x = fma2(rx, rx, neg2(mul2(ry, ry))), r2y = mul2(add2(rx, rx), ry);
-    const float2 s = f2(0.56418958354775628695f);
-    wx = fma2(px, r2x, fma2(neg2(py), r2y, mul2(rx, s)));
-    wy = fma2(px, r2y, fma2(py, r2x, mul2(ry, s)));
+    // w = (2 p(Z) r + 1/sqrt(pi)) r with r = 1/(L - i z) = rx + i ry
+    const float2 ux = fma2(px, rx, fma2(neg2(py), ry, f2(0.56418958354775628695f)));
+    const float2 uy = fma2(px, ry, mul2(py, rx));
+    wx = fma2(ux, rx, neg2(mul2(uy, ry)));
+    wy = fma2(ux, ry, mul2(uy, rx));
 }
 
 
@@ -287,28 +297,25 @@ __device__ __forceinline__ void fad_level(float2 x, const Geo<float> &g, float2 
 
 // One effective triplet's contribution to a pair's profile sums, each
 // component added as soon as it is evaluated (EXT: the level of fad_level
-// that every lane's triplet reaches as a whole).
+// that every lane's triplet reaches as a whole).  The sigma components go
+// into sums of their own (Sb, Sbi blue, Sr, Sri red), two FMAs each; their
+// sum and difference are formed once per point after the last line.
 template <int EXT, bool FILL>
 __device__ __forceinline__ void triplet_acc(float2 xb, float2 v, float2 xr, const Geo<float> &g, float2 q,
-                                            float2 &P, float2 &Pim, float2 &Sg, float2 &Sgi, float2 &Dd,
-                                            float2 &Di, float2 &P0)
+                                            float2 qs, float2 &P, float2 &Pim, float2 &Sb, float2 &Sbi, float2 &Sr,
+                                            float2 &Sri, float2 &P0)
 {
-    const float2 qs = mul2(q, f2(kInvSqrtPi));
     float2 wx, wy, qi;
     fad_level<EXT>(xb, g, q, qs, wx, wy, qi);
-    Sg = fma2(qi, wx, Sg);
-    Sgi = fma2(qi, wy, Sgi);
-    Dd = fma2(neg2(qi), wx, Dd);
-    Di = fma2(neg2(qi), wy, Di);
+    Sb = fma2(qi, wx, Sb);
+    Sbi = fma2(qi, wy, Sbi);
     fad_level<EXT>(v, g, q, qs, wx, wy, qi);
     if (FILL) P0 = fma2(qi, wx, P0);  // the pi profile is unshifted
     P = fma2(qi, wx, P);
     Pim = fma2(qi, wy, Pim);
     fad_level<EXT>(xr, g, q, qs, wx, wy, qi);
-    Sg = fma2(qi, wx, Sg);
-    Sgi = fma2(qi, wy, Sgi);
-    Dd = fma2(qi, wx, Dd);
-    Di = fma2(qi, wy, Di);
+    Sr = fma2(qi, wx, Sr);
+    Sri = fma2(qi, wy, Sri);
 }
 
 // The branch level of an effective triplet for a pair, voted across the warp
@@ -328,16 +335,21 @@ __device__ __forceinline__ int triplet_level(float2 v, const Geo<float> &g, int 
 // Residuals o - Stokes at two wavelength points (the synthesis of Section
 // 5 and the difference of Eq. chisq).  doff2[l] holds (lambda_j -
 // lambda0_l, lambda_{j+1} - lambda0_l).  FILL mixes in the field-free
-// profile with the fill fraction (Section 5.2, see fill_mix).
+// profile with the fill fraction (Section 5.2, see fill_mix).  kc points at
+// the individual's shared-memory slots (stride nt float4): (kIs, kIp, kIp2,
+// kV2), (muS1, S0, kQ, kUV), (kU, kQV, kV, w_I), the last three weighted as
+// fitness_pairs stores them; wI receives w_I.
 template <int NL, bool COUNT, bool PAT, bool FILL = false>
-__device__ __forceinline__ Stokes4x2 resid_x2(const Geo<float> &g, const float2 *doff2, const Stokes4x2 &o,
+__device__ __forceinline__ Stokes4x2 resid_x2(const Geo<float> &g, const float2 *doff2, const float *op,
                                               const float *half_eta, int nlines, bool y_real,
-                                              EvalCount &ncount, const KLine *lines)
+                                              EvalCount &ncount, const KLine *lines, const float4 *kc, int nt,
+                                              float &wI)
 {
-    // per-line profile sums: P, Pi = sum q phi_p, q psi_p; Sg, Sgi = sum q (phi_b
-    // + phi_r), q (psi_b + psi_r); Dd, Di = sum q (phi_r - phi_b), q (psi_r - psi_b);
-    // T = P - Sg/2 and Ti = Pi - Sgi/2 follow once per point
-    float2 P = f2(0.f), Sg = f2(0.f), Pim = f2(0.f), Sgi = f2(0.f), Dd = f2(0.f), Di = f2(0.f);
+    // profile sums over the lines: P, Pim = sum q phi_p, q psi_p; Sb, Sbi =
+    // sum q phi_b, q psi_b; Sr, Sri = sum q phi_r, q psi_r.  Once per point:
+    // Sg, Sgi = Sb + Sr, Sbi + Sri; Dd, Di = Sr - Sb, Sri - Sbi; T = P - Sg/2
+    // and Ti = Pim - Sgi/2
+    float2 P = f2(0.f), Pim = f2(0.f), Sb = f2(0.f), Sbi = f2(0.f), Sr = f2(0.f), Sri = f2(0.f);
     float2 P0 = f2(0.f);
     const int nl = NL > 0 ? NL : nlines;
 #pragma unroll
@@ -355,10 +367,10 @@ __device__ __forceinline__ Stokes4x2 resid_x2(const Geo<float> &g, const float2 
             const float2 q = f2(half_eta[l]);
             P = fma2(q, w[2], P);
             Pim = fma2(q, w[3], Pim);
-            Sg = fma2(q, add2(w[0], w[4]), Sg);
-            Sgi = fma2(q, add2(w[1], w[5]), Sgi);
-            Dd = fma2(q, sub2(w[4], w[0]), Dd);
-            Di = fma2(q, sub2(w[5], w[1]), Di);
+            Sb = fma2(q, w[0], Sb);
+            Sbi = fma2(q, w[1], Sbi);
+            Sr = fma2(q, w[4], Sr);
+            Sri = fma2(q, w[5], Sri);
         } else if (l < nl) {
             const float2 id = f2(g.invD[l]);
             const float2 v = fma2(doff2[l], id, f2(g.cp[l]));
@@ -369,31 +381,40 @@ __device__ __forceinline__ Stokes4x2 resid_x2(const Geo<float> &g, const float2 
                 count_pair(v, g.a2, y_real, ncount);
                 count_pair(xr, g.a2, y_real, ncount);
             }
-            const float2 q = f2(half_eta[l]);
+            const float2 q = lines[l].q2, qs = lines[l].qs2;
             const int lev = triplet_level(v, g, l);
             if (lev == 3)
-                triplet_acc<3, FILL>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
+                triplet_acc<3, FILL>(xb, v, xr, g, q, qs, P, Pim, Sb, Sbi, Sr, Sri, P0);
             else if (lev == 2)
-                triplet_acc<2, FILL>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
+                triplet_acc<2, FILL>(xb, v, xr, g, q, qs, P, Pim, Sb, Sbi, Sr, Sri, P0);
             else if (lev == 1)
-                triplet_acc<1, FILL>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
+                triplet_acc<1, FILL>(xb, v, xr, g, q, qs, P, Pim, Sb, Sbi, Sr, Sri, P0);
             else
-                triplet_acc<0, FILL>(xb, v, xr, g, q, P, Pim, Sg, Sgi, Dd, Di, P0);
+                triplet_acc<0, FILL>(xb, v, xr, g, q, qs, P, Pim, Sb, Sbi, Sr, Sri, P0);
         }
     }
+    // the sigma sums and differences, once per point
+    const float2 Sg = add2(Sb, Sr), Sgi = add2(Sbi, Sri), Dd = sub2(Sr, Sb), Di = sub2(Sri, Sbi);
     // closed form of K^-1 e (see me_point), with G = eI^2 + rho^2 shared by
-    // Delta = eI^2 (G - E2) - Pi^2 and I = S0 + f eI G
+    // Delta = eI^2 (G - E2) - Pi^2 and I = S0 + f eI G.  The individual's
+    // constants are read from its shared-memory slot here, once per pair, so
+    // that they hold no registers across the profile evaluations.
+    const float4 k0 = lds4(kc), k1 = lds4(kc + nt), k2 = lds4(kc + 2 * nt);
+    const float kIs = k0.x, kIp = k0.y, kIp2 = k0.z, kV2 = k0.w;
+    const float muS1 = k1.x, S0 = k1.y, kQ = k1.z, kUV = k1.w;
+    const float kU = k2.x, kQV = k2.y, kV = k2.z;
+    wI = k2.w;
     const float2 T = fma2(f2(-0.5f), Sg, P), Ti = fma2(f2(-0.5f), Sgi, Pim);
-    const float2 eI = fma2(f2(g.kIs), Sg, fma2(f2(g.kIp), P, f2(1.0f)));
-    const float2 pT = mul2(f2(g.kIp2), T), pTi = mul2(f2(g.kIp2), Ti);
-    const float2 vD = mul2(f2(g.kV2), Dd), vDi = mul2(f2(g.kV2), Di);
+    const float2 eI = fma2(f2(kIs), Sg, fma2(f2(kIp), P, f2(1.0f)));
+    const float2 pT = mul2(f2(kIp2), T), pTi = mul2(f2(kIp2), Ti);
+    const float2 vD = mul2(f2(kV2), Dd), vDi = mul2(f2(kV2), Di);
     const float2 E2 = fma2(pT, T, mul2(vD, Dd));
     const float2 rho2 = fma2(pTi, Ti, mul2(vDi, Di));
     const float2 Pi = fma2(pT, Ti, mul2(vD, Di));
     const float2 eI2 = mul2(eI, eI);
     const float2 G = add2(eI2, rho2);
     const float2 Delta = fma2(eI2, sub2(G, E2), neg2(mul2(Pi, Pi)));
-    const float2 f = mul2(f2(g.muS1), rcp2(Delta));
+    const float2 f = mul2(f2(muS1), rcp2(Delta));
     const float2 A = fma2(eI2, T, mul2(Ti, Pi));
     const float2 C = fma2(Dd, Ti, neg2(mul2(T, Di)));
     // Q, U, V = -f X: the residual o - (-f X) is formed by FMAs on o, with f
@@ -402,17 +423,21 @@ __device__ __forceinline__ Stokes4x2 resid_x2(const Geo<float> &g, const float2 
     const float2 fq = FILL ? mul2(f, f2(g.alpha)) : f;
     const float2 fqeI = mul2(fq, eI);
     const float2 fA = mul2(fq, A), fC = mul2(fqeI, C);
+    // the observed pair, read here rather than held through the evaluations
+    const float4 o0 = lds4((const float4 *)op), o1 = lds4((const float4 *)(op + 4));
+    const Stokes4x2 o = {make_float2(o0.x, o0.y), make_float2(o0.z, o0.w), make_float2(o1.x, o1.y),
+                         make_float2(o1.z, o1.w)};
     Stokes4x2 r;
     if (FILL) {
-        const float2 inm = mul2(f2(g.muS1), rcp2(fma2(f2(2.0f * g.eta0), P0, f2(1.0f))));
-        const float2 base = fma2(f2(1.0f - g.alpha), inm, f2(g.S0));
+        const float2 inm = mul2(f2(muS1), rcp2(fma2(f2(2.0f * g.eta0), P0, f2(1.0f))));
+        const float2 base = fma2(f2(1.0f - g.alpha), inm, f2(S0));
         r.I = sub2(o.I, fma2(fqeI, G, base));
     } else {
-        r.I = sub2(o.I, fma2(fqeI, G, f2(g.S0)));
+        r.I = sub2(o.I, fma2(fqeI, G, f2(S0)));
     }
-    r.Q = fma2(f2(g.kQ), fA, fma2(f2(g.kUV), fC, o.Q));
-    r.U = fma2(f2(g.kU), fA, fma2(f2(-g.kQV), fC, o.U));
-    r.V = fma2(mul2(fq, f2(g.kV)), fma2(eI2, Dd, mul2(Di, Pi)), o.V);
+    r.Q = fma2(f2(kQ), fA, fma2(f2(kUV), fC, o.Q));
+    r.U = fma2(f2(kU), fA, fma2(f2(-kQV), fC, o.U));
+    r.V = fma2(mul2(fq, f2(kV)), fma2(eI2, Dd, mul2(Di, Pi)), o.V);
     return r;
 }
 

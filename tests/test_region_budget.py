@@ -197,25 +197,26 @@ def _weideman_setup():
 def weideman32(x, y, L, n, a):
     """The pair path's interior branch in float32: Z = ((L^2 - y^2 - x^2) + 2iLx)
     / ((L+y)^2 + x^2), p(Z) by real-quadratic synthetic division with the
-    doubled coefficients, w = p (r^2) + r / sqrt(pi), r = 1/(L - iz)."""
+    doubled coefficients, w = (p r + 1/sqrt(pi)) r, r = 1/(L - iz) (the
+    kernel's FMAs kept)."""
     x, y = x.astype(f32), f32(y)
     Lf = f32(L)
     dx = Lf + y
-    inv = f32(1) / (x * x + dx * dx)
+    inv = f32(1) / fma32(x, x, dx * dx)
     rx, ry = dx * inv, x * inv
-    zx = (-(x * x) + (Lf - y) * dx) * inv
+    zx = fma32(-x, x, (Lf - y) * dx) * inv
     zy = ry * (f32(2) * Lf)
     w = [f32(2 * c) for c in a]
-    r, sq = zx + zx, -(zx * zx + zy * zy)
+    r, sq = zx + zx, -fma32(zx, zx, zy * zy)
     b2 = np.full_like(x, w[n])
-    b1 = r * b2 + w[n - 1]
+    b1 = fma32(r, b2, w[n - 1])
     for j in range(n - 3, 0, -1):
-        b2, b1 = b1, r * b1 + (sq * b2 + w[j + 1])
-    px, py = sq * b2 + (b1 * zx + w[1]), b1 * zy
-    r2x, r2y = rx * rx - ry * ry, (rx + rx) * ry
-    s = f32(0.56418958354775628695)
-    wx = px * r2x + (-py * r2y + rx * s)
-    wy = px * r2y + (py * r2x + ry * s)
+        b2, b1 = b1, fma32(r, b1, fma32(sq, b2, w[j + 1]))
+    px, py = fma32(sq, b2, fma32(b1, zx, w[1])), b1 * zy
+    ux = fma32(px, rx, fma32(-py, ry, f32(0.56418958354775628695)))
+    uy = fma32(px, ry, py * rx)
+    wx = fma32(ux, rx, -(uy * ry))
+    wy = fma32(ux, ry, uy * rx)
     return wx.astype(float) + 1j * wy.astype(float)
 
 
