@@ -157,7 +157,7 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
     s_kc[nt + kt] = make_float4(geo.muS1, geo.S0, geo.kQ, geo.kUV);
     s_kc[2 * nt + kt] = make_float4(geo.kU, geo.kQV, geo.kV, sw[0]);
     const float4 *kc = s_kc + kt;
-    float2 sum = f2(0.f), comp = f2(0.f);
+    float sum = 0.f, comp = 0.f;
     const int npair = (nl + 1) >> 1;
     EvalCount cnt{0u, 0u, 0u, 0u};
     for (int q = 0; q < npair; ++q) {
@@ -192,9 +192,9 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
         float2 t2 = fma2(rQ, rQ, mul2(rI, rI));
         t2 = fma2(rU, rU, t2);
         t2 = fma2(rV, rV, t2);
-        const float2 y = sub2(t2, comp);  // Kahan: comp holds the lost low part, negated
-        const float2 t = add2(sum, y);
-        comp = sub2(sub2(t, sum), y);
+        const float y = (t2.x + t2.y) - comp;  // Kahan: comp holds the lost low part, negated
+        const float t = sum + y;
+        comp = (t - sum) - y;
         sum = t;
     }
     if (COUNT) {
@@ -203,7 +203,7 @@ __device__ __forceinline__ float fitness_pairs(const KProblem &pb, int nlines, i
         wc.even2 += cnt.even2;
         wc.far += cnt.far;
     }
-    return ((sum.x - comp.x) + (sum.y - comp.y)) * inv_nu;
+    return (sum - comp) * inv_nu;
 }
 
 template <class R, int NL, bool COUNT, bool PAT, bool FILL, bool STORE = false>
