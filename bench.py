@@ -439,7 +439,9 @@ def serving(api, torch, pb, device, seconds, loads=(0.7,), polish=LM_ITERS):
                           pixel_id0=pid0, polish_iters=polish, polish_w=w)
 
     out = {"polish_iters": polish}
-    with api.Server(pb, arena_bytes=2 << 30, max_inflight=16, max_queue=100000, small_pixels=256) as srv:
+    # every request on a stream of equal priority (small_pixels = 0): the fair
+    # share that keeps the large requests' tail shortest on this mix
+    with api.Server(pb, arena_bytes=2 << 30, max_inflight=16, max_queue=100000, small_pixels=0) as srv:
         # capacity: a burst of 24 requests submitted at once
         nb = 24
         for i in range(nb):
