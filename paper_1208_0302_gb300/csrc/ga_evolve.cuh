@@ -127,10 +127,11 @@ __device__ __forceinline__ R fitness_rows(const KProblem &pb, int nlines, int nl
 // step, packed FP32x2 arithmetic), as a Kahan-compensated sum.  The residuals
 // come out weighted: the staged Q, U, V rows carry the pixel's weights
 // (weight_obs_rows) and so do the individual's Q, U, V output constants, and
-// the I residual takes w_I with one multiply.  Each pair's four squared
-// weighted residuals are summed by FMA and added into one running total per
-// lane with Kahan's compensation, so the sum's relative error stays at a few
-// units of 2^-24 whatever the number of wavelengths.  The fitness only ranks
+// the I residual takes w_I with one multiply.  Each pair's eight squared
+// weighted residuals are summed by packed FMAs, its two lanes added, and the
+// result taken into one scalar running total with Kahan's compensation, so
+// the sum's relative error stays at a few units of 2^-24 whatever the number
+// of wavelengths.  The fitness only ranks
 // individuals; the best individual's chi2 is re-evaluated in FP64.
 // s_kc: the calling thread's shared-memory slots, three float4 at s_kc[k],
 // s_kc[k + blockDim], s_kc[k + 2 blockDim] (k = threadIdx.x), which hold the

@@ -177,6 +177,24 @@ def test_ga_fp32_partial_warp_restarts(gpu, orc):
     assert torch.equal(gpu.me_chi2(pb, ob, best), chi2)
 
 
+def test_ga_fp32_largest_population(gpu, orc):
+    """FP32, npop 1024 (the 1024-thread instantiation, whose per-thread
+    shared-memory slots take 48 KB of the block): results in bounds, finite,
+    consistent with me_chi2 and independent of the batch."""
+    spec = gi.two_line_spec()
+    truth, obs = make_obs(orc, spec, 12, seed=14)
+    pb = gpu.Problem.from_spec(spec, "f32")
+    ob = torch.tensor(obs, device="cuda", dtype=torch.float32)
+    ga = gpu.GaSettings(npop=1024, ngen=6, seed=8)   # restarts at t = 1..5 (nsamp = ngen / 4 -> 1)
+    best, chi2 = gpu.ga_invert_batch(pb, ob, gi.PRIOR_LO, gi.PRIOR_HI, ga, pixel_id0=7)
+    b2, c2 = gpu.ga_invert_batch(pb, ob[5:9].contiguous(), gi.PRIOR_LO, gi.PRIOR_HI, ga, pixel_id0=12)
+    assert torch.equal(best[5:9], b2) and torch.equal(chi2[5:9], c2)
+    bn = best.cpu().numpy()
+    assert np.all(np.isfinite(chi2.cpu().numpy()))
+    assert np.all(bn >= gi.PRIOR_LO) and np.all(bn <= gi.PRIOR_HI)
+    assert torch.equal(gpu.me_chi2(pb, ob, best), chi2)
+
+
 def test_ga_batch_invariance_and_consistency(gpu, orc):
     """A pixel's result depends only on (obs, pixel id, seed), not on the batch."""
     spec = gi.two_line_spec()
