@@ -46,11 +46,11 @@ E2E_STEPS_MAX = 5   # the end-to-end leg repeats at most this many steps
 NPOP, NGEN, LM_ITERS = 128, 200, 10
 KERNELS_PER_STEP = 4  # GA evolve, FP64 chi2, L-M, FP64 chi2
 # DRAM bytes (read + write) per pixel of one GA launch, from an ncu capture of
-# k_ga_evolve on the 4096-pixel two-line case (dram__bytes_read.sum 8514560 +
+# k_ga_evolve on the 4096-pixel two-line case (dram__bytes_read.sum 8512768 +
 # dram__bytes_write.sum 0, divided by 4096; traffic grows in proportion to
 # pixels: each block reads its pixel's cube row once).  Set to None whenever
 # the kernel changes, until it is captured again.
-GA_DRAM_BYTES_PER_PIXEL = 2078.75
+GA_DRAM_BYTES_PER_PIXEL = 2078.31
 
 
 def parse():
@@ -150,20 +150,22 @@ def flop_model(nlines):
     counted from the source of the GA's fitness path (per call, without the
     per-individual invariants such as 2a or (L + a)^2), per unit: an
     evaluation of w(z) in the interior (Weideman N = 16 by real-quadratic
-    synthetic division, 85), in the middle shell (5th convergent, 43), in the
-    continued-fraction region (3rd convergent in s = |z|^2, 23), in the outer shell (the
-    even convergent, 16) and in the far field (two-node approximant, 12), the
-    rational branches leaving their
-    normalisation to the accumulation weight; and per wavelength
-    point 19 per line for the component arguments, the weight q / sqrt(pi)
-    and the blue, pi and red profile sums, 4 for the sums and differences of
-    the sigma profiles, 35 for K
+    synthetic division, its last product added straight into the profile
+    sums, 83 besides the two accumulating FMAs counted per point), in the
+    middle shell (5th convergent, 43), in the continued-fraction region (3rd
+    convergent in s = |z|^2, 23), in the outer shell (the even convergent in
+    m = s - 3/2, 14) and in the far field (two-node approximant in
+    u = s - 1/2, 9), the rational branches leaving their normalisation to
+    the accumulation weight; and per wavelength point 16 per line for the
+    component arguments (the pi argument by FMA, the sigma ones by adding
+    and subtracting v_B) and the blue, pi and red profile sums (two FMAs
+    each), 4 for the sums and differences of the sigma profiles, 35 for K
     and its closed-form inverse, 21 for the four Stokes values formed into
     their weighted residuals (w_I by one multiply), 7 for the four squares
     summed by FMA and 4 for the Kahan-compensated running sum.  Each point's
     evaluations are classified by its own region; branch tests, votes and work
     a pair or warp does beyond that are not counted."""
-    return {"weideman": 85.0, "mid": 43.0, "cf": 23.0, "even2": 16.0, "far": 12.0, "point": 19.0 * nlines + 71.0}
+    return {"weideman": 83.0, "mid": 43.0, "cf": 23.0, "even2": 14.0, "far": 9.0, "point": 16.0 * nlines + 71.0}
 
 
 def run_ours(args):

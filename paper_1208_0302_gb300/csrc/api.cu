@@ -175,6 +175,13 @@ int make_problem(const me_problem *pb, KProblem &k)
         k.line[l].q2 = make_float2((float)k.line[l].half_eta, (float)k.line[l].half_eta);
         k.line[l].qs2 = make_float2((float)(k.line[l].half_eta * 0.56418958354775628695),
                                     (float)(k.line[l].half_eta * 0.56418958354775628695));
+        {
+            const HostTables &ht = host_tables();
+            for (int n = 0; n <= 16; ++n) {
+                const float c = (float)(2.0 * (double)ht.fad.w32[n] * k.line[l].half_eta);
+                k.line[l].wq2[n] = make_float2(c, c);
+            }
+        }
         k.line[l].zfacL = kZeeman * ln.lambda0_A * ln.lambda0_A;
         if (ln.pattern) {
             int rc = zeeman_pattern(ln.j_lower, ln.g_lower, ln.j_upper, ln.g_upper, k.line[l].ncomp,

@@ -98,17 +98,18 @@ __global__ void k_fad_probe(const float2 *__restrict__ x, const float *__restric
     const float2 v = x[i];
     if (mode == 2) {
         const float2 xb = add2(v, f2(g.vB[0])), xr = sub2(v, f2(g.vB[0]));
-        const float2 q = f2(1.0f);
+        // unit strength: the series' doubled coefficients as they are
+        const float2 *wq = c_fad.w32x2, qs = f2(kInvSqrtPi);
         float2 P = f2(0.f), Pim = f2(0.f), Sb = f2(0.f), Sbi = f2(0.f), Sr = f2(0.f), Sri = f2(0.f), P0 = f2(0.f);
         const int lev = triplet_level(v, g, 0);
         if (lev == 3)
-            triplet_acc<3, false>(xb, v, xr, g, q, mul2(q, f2(kInvSqrtPi)), P, Pim, Sb, Sbi, Sr, Sri, P0);
+            triplet_acc<3, false>(xb, v, xr, g, wq, qs, P, Pim, Sb, Sbi, Sr, Sri, P0);
         else if (lev == 2)
-            triplet_acc<2, false>(xb, v, xr, g, q, mul2(q, f2(kInvSqrtPi)), P, Pim, Sb, Sbi, Sr, Sri, P0);
+            triplet_acc<2, false>(xb, v, xr, g, wq, qs, P, Pim, Sb, Sbi, Sr, Sri, P0);
         else if (lev == 1)
-            triplet_acc<1, false>(xb, v, xr, g, q, mul2(q, f2(kInvSqrtPi)), P, Pim, Sb, Sbi, Sr, Sri, P0);
+            triplet_acc<1, false>(xb, v, xr, g, wq, qs, P, Pim, Sb, Sbi, Sr, Sri, P0);
         else
-            triplet_acc<0, false>(xb, v, xr, g, q, mul2(q, f2(kInvSqrtPi)), P, Pim, Sb, Sbi, Sr, Sri, P0);
+            triplet_acc<0, false>(xb, v, xr, g, wq, qs, P, Pim, Sb, Sbi, Sr, Sri, P0);
         // the sums and differences of the sigma profiles, as the fitness forms them
         const float2 o[6] = {P, Pim, add2(Sb, Sr), add2(Sbi, Sri), sub2(Sr, Sb), sub2(Sri, Sbi)};
         float *r = out + (size_t)i * 12;

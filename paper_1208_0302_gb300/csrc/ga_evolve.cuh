@@ -268,7 +268,8 @@ __device__ __forceinline__ void breed_one(const KGa &ga, uint64_t pid, int t, in
 {
     const U4 u = ga_random_rk(ga.rk, pid, t, (uint32_t)k, kPurposeSelect);
     const int i = (int)(((uint64_t)u.x * (uint64_t)npop) >> 32);
-    const int j = (i + 1 + (int)(((uint64_t)u.y * (uint64_t)(npop - 1)) >> 32)) % npop;
+    int j = i + 1 + (int)(((uint64_t)u.y * (uint64_t)(npop - 1)) >> 32);  // at most 2 npop - 2
+    if (j >= npop) j -= npop;
     const R fi = s_fit[i], fj = s_fit[j];
     const int win = (fj < fi || (fj == fi && j < i)) ? j : i;
 #pragma unroll

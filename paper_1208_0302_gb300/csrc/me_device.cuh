@@ -31,6 +31,7 @@ struct KLine {
     float cshift32[3][ME_MAX_COMP];
     float cstr32[3][ME_MAX_COMP];
     float2 q2, qs2;    // FP32 pair path: (half_eta, half_eta) and the same / sqrt(pi)
+    float2 wq2[17];    // FP32 pair path: Weideman coefficients 2 a_n times half_eta, in both lanes
 };
 
 template <class R> __device__ __forceinline__ R comp_shift(const KLine &ln, int g, int i);

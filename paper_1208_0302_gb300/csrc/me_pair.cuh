@@ -50,7 +50,9 @@ __device__ __forceinline__ float4 lds4(const float4 *p)
 // caller adds qi nx and qi ny into its sums with one FMA each.  The rational
 // branches leave their numerator unnormalised and put q / (sqrt(pi) |A|^2)
 // into qi (qs = q / sqrt(pi) is passed in), which saves the two multiplies of
-// a normalised w; the series returns w itself with qi = q.
+// a normalised w; the series returns w itself with qi = q.  For an effective
+// triplet the series instead adds q w into the sums itself (fad_int2_acc,
+// with the line's coefficients scaled by q on the host).
 
 // Continued-fraction branch (K-th convergent, monic a(u), b(u)) for a pair of
 // real arguments x and a common damping y (a2 = y^2).
@@ -123,11 +125,14 @@ __device__ __forceinline__ void fad_even2(float2 x, float y, float a2, float2 qs
                                           float2 &qi)
 {
     // With N = z^2 - 1, D = z (z^2 - 3/2), z = x + i y and s = |z|^2 = x^2 + y^2
-    // (x real, y the damping): i N conj(D) = y (s^2 - 1.5 s + 4 y^2 + 1.5)
-    // + i x (s^2 - 2.5 s + 4 y^2 + 1.5) and |D|^2 = s (s^2 - 3 s + 6 y^2 + 9/4).
+    // (x real, y the damping): i N conj(D) = y P + i x (P - s) with
+    // P = s^2 - 1.5 s + 4 y^2 + 1.5, and |D|^2 = s (s^2 - 3 s + 6 y^2 + 9/4).
+    // In m = s - 3/2 (one FMA from x, like s): P = m s + 4 y^2 + 1.5 and
+    // s^2 - 3 s + 6 y^2 + 9/4 = m^2 + 6 y^2, nine packed operations in all.
     const float2 s = fma2(x, x, f2(a2));
-    const float2 pr = fma2(s, s, fma2(f2(-1.5f), s, f2(4.0f * a2 + 1.5f)));
-    const float2 u = fma2(s, s, fma2(f2(-3.0f), s, f2(6.0f * a2 + 2.25f)));
+    const float2 m = fma2(x, x, f2(a2 - 1.5f));
+    const float2 pr = fma2(m, s, f2(4.0f * a2 + 1.5f));
+    const float2 u = fma2(m, m, f2(6.0f * a2));
     qi = mul2(qs, rcp2(mul2(s, u)));
     wx = mul2(f2(y), pr);
     wy = mul2(x, sub2(pr, s));
@@ -142,11 +147,12 @@ __device__ __forceinline__ void fad_far2(float2 x, float y, float a2, float2 qs,
                                          float2 &qi)
 {
     // With z = x + i y and s = |z|^2 (x real): i z conj(z^2 - 1/2) =
-    // y (s + 1/2) + i x (s - 1/2) and |z^2 - 1/2|^2 = s^2 - x^2 + y^2 + 1/4.
-    const float2 s = fma2(x, x, f2(a2));
-    qi = mul2(qs, rcp2(fma2(s, s, fma2(neg2(x), x, f2(a2 + 0.25f)))));
-    wx = fma2(f2(y), s, f2(0.5f * y));
-    wy = mul2(x, add2(s, f2(-0.5f)));
+    // y (s + 1/2) + i x (s - 1/2) and |z^2 - 1/2|^2 = (s - 1/2)^2 + 2 y^2, all
+    // three in u = s - 1/2 (one FMA from x): five packed operations.
+    const float2 u = fma2(x, x, f2(a2 - 0.5f));
+    qi = mul2(qs, rcp2(fma2(u, u, f2(2.0f * a2))));
+    wx = fma2(f2(y), u, f2(y));
+    wy = mul2(x, u);
 }
 
 // Interior branch (Weideman N = 16, real-quadratic synthetic division) for a
@@ -180,6 +186,36 @@ __device__ __forceinline__ void fad_int2(float2 x, float y, float2 q, float2 &wx
     wy = fma2(ux, ry, mul2(uy, rx));
 }
 
+
+// Weideman's series for an effective triplet's component, added into the
+// caller's sums: the line's coefficients arrive scaled by its strength q
+// (wq = q 2 a_n) and qs = q / sqrt(pi), so (p r + qs) r is q w itself and its
+// product with r goes straight into the sums (Ax, Ay) += q w.
+__device__ __forceinline__ void fad_int2_acc(float2 x, float y, const float2 *wq, float2 qs, float2 &Ax,
+                                             float2 &Ay)
+{
+    constexpr int N = FadCfg<float>::N;
+    const float L = c_fad.L32;
+    const float dx = L + y;
+    const float2 inv = rcp2(fma2(x, x, f2(dx * dx)));
+    const float2 rx = mul2(f2(dx), inv), ry = mul2(x, inv);
+    const float2 Zx = mul2(fma2(neg2(x), x, f2((L - y) * dx)), inv);
+    const float2 Zy = mul2(ry, f2(2.0f * L));
+    const float2 r = add2(Zx, Zx), sq = neg2(fma2(Zx, Zx, mul2(Zy, Zy)));
+    float2 b2 = wq[N];
+    float2 b1 = fma2(r, b2, wq[N - 1]);
+#pragma unroll
+    for (int j = N - 3; j >= 1; --j) {
+        const float2 b0 = fma2(r, b1, fma2(sq, b2, wq[j + 1]));
+        b2 = b1;
+        b1 = b0;
+    }
+    const float2 px = fma2(sq, b2, fma2(b1, Zx, wq[1])), py = mul2(b1, Zy);
+    const float2 ux = fma2(px, rx, fma2(neg2(py), ry, qs));
+    const float2 uy = fma2(px, ry, mul2(py, rx));
+    Ax = fma2(ux, rx, fma2(neg2(uy), ry, Ax));
+    Ay = fma2(ux, ry, fma2(uy, rx, Ay));
+}
 
 // |x| threshold of a region x^2 + a^2 > R2 (once per individual).
 __device__ __forceinline__ float region_threshold(float R2, float a2) { return a2 >= R2 ? -1.0f : sqrtf(R2 - a2); }
@@ -280,42 +316,71 @@ __device__ __forceinline__ void fad_pair_in(float2 x, const Geo<float> &g, float
     else fad_even2(x, g.a, g.a2, qs, wx, wy, qi);
 }
 
-// One component at a known level: 3 = every lane's pair is in the far
-// field, 2 = beyond the outer shell's threshold (the even convergent, accurate
-// there, also where a component is already far), 1 = beyond the
-// continued-fraction threshold (the 3rd convergent, likewise), 0 = anywhere
-// (cheaper than testing each component).
-template <int LEVEL>
-__device__ __forceinline__ void fad_level(float2 x, const Geo<float> &g, float2 q, float2 qs, float2 &wx,
-                                          float2 &wy, float2 &qi)
+// Adds qi (wx + i wy) into (Ax, Ay).
+__device__ __forceinline__ void acc_w(float2 qi, float2 wx, float2 wy, float2 &Ax, float2 &Ay)
 {
+    Ax = fma2(qi, wx, Ax);
+    Ay = fma2(qi, wy, Ay);
+}
+
+// One effective-triplet component near a line core, added into (Ax, Ay):
+// the branches of fad_pair_in, the series with the line's scaled coefficients.
+__device__ __forceinline__ void fad_pair_in_acc(float2 x, const Geo<float> &g, const float2 *wq, float2 qs,
+                                                float2 &Ax, float2 &Ay)
+{
+    const float m = pair_min_abs(x);
+    if (!warp_all(m > g.tmid, g.vmask)) {
+        fad_int2_acc(x, g.a, wq, qs, Ax, Ay);
+        return;
+    }
+    float2 wx, wy, qi;
+    if (!warp_all(m > g.text, g.vmask)) fad_cf2<5>(x, g.a, g.a2, qs, wx, wy, qi);
+    else if (!warp_all(m > g.t80, g.vmask)) fad_ext2(x, g.a, g.a2, qs, wx, wy, qi);
+    else fad_even2(x, g.a, g.a2, qs, wx, wy, qi);
+    acc_w(qi, wx, wy, Ax, Ay);
+}
+
+// One component at a known level, added into (Ax, Ay): 3 = every lane's pair
+// is in the far field, 2 = beyond the outer shell's threshold (the even
+// convergent, accurate there, also where a component is already far), 1 =
+// beyond the continued-fraction threshold (the 3rd convergent, likewise), 0 =
+// anywhere (cheaper than testing each component).
+template <int LEVEL>
+__device__ __forceinline__ void fad_level_acc(float2 x, const Geo<float> &g, const float2 *wq, float2 qs,
+                                              float2 &Ax, float2 &Ay)
+{
+    if (LEVEL == 0) {
+        fad_pair_in_acc(x, g, wq, qs, Ax, Ay);
+        return;
+    }
+    float2 wx, wy, qi;
     if (LEVEL == 3) fad_far2(x, g.a, g.a2, qs, wx, wy, qi);
     else if (LEVEL == 2) fad_even2(x, g.a, g.a2, qs, wx, wy, qi);
-    else if (LEVEL == 1) fad_ext2(x, g.a, g.a2, qs, wx, wy, qi);
-    else fad_pair_in(x, g, q, qs, wx, wy, qi);
+    else fad_ext2(x, g.a, g.a2, qs, wx, wy, qi);
+    acc_w(qi, wx, wy, Ax, Ay);
 }
 
 // One effective triplet's contribution to a pair's profile sums, each
-// component added as soon as it is evaluated (EXT: the level of fad_level
+// component added as soon as it is evaluated (EXT: the level of fad_level_acc
 // that every lane's triplet reaches as a whole).  The sigma components go
-// into sums of their own (Sb, Sbi blue, Sr, Sri red), two FMAs each; their
-// sum and difference are formed once per point after the last line.
+// into sums of their own (Sb, Sbi blue, Sr, Sri red); their sum and
+// difference are formed once per point after the last line.
 template <int EXT, bool FILL>
-__device__ __forceinline__ void triplet_acc(float2 xb, float2 v, float2 xr, const Geo<float> &g, float2 q,
-                                            float2 qs, float2 &P, float2 &Pim, float2 &Sb, float2 &Sbi, float2 &Sr,
-                                            float2 &Sri, float2 &P0)
+__device__ __forceinline__ void triplet_acc(float2 xb, float2 v, float2 xr, const Geo<float> &g,
+                                            const float2 *wq, float2 qs, float2 &P, float2 &Pim, float2 &Sb,
+                                            float2 &Sbi, float2 &Sr, float2 &Sri, float2 &P0)
 {
-    float2 wx, wy, qi;
-    fad_level<EXT>(xb, g, q, qs, wx, wy, qi);
-    Sb = fma2(qi, wx, Sb);
-    Sbi = fma2(qi, wy, Sbi);
-    fad_level<EXT>(v, g, q, qs, wx, wy, qi);
-    if (FILL) P0 = fma2(qi, wx, P0);  // the pi profile is unshifted
-    P = fma2(qi, wx, P);
-    Pim = fma2(qi, wy, Pim);
-    fad_level<EXT>(xr, g, q, qs, wx, wy, qi);
-    Sr = fma2(qi, wx, Sr);
-    Sri = fma2(qi, wy, Sri);
+    fad_level_acc<EXT>(xb, g, wq, qs, Sb, Sbi);
+    if (FILL) {  // the pi profile is unshifted: its real part also feeds P0
+        float2 tx = f2(0.f), ty = f2(0.f);
+        fad_level_acc<EXT>(v, g, wq, qs, tx, ty);
+        P = add2(P, tx);
+        Pim = add2(Pim, ty);
+        P0 = add2(P0, tx);
+    } else {
+        fad_level_acc<EXT>(v, g, wq, qs, P, Pim);
+    }
+    fad_level_acc<EXT>(xr, g, wq, qs, Sr, Sri);
 }
 
 // The branch level of an effective triplet for a pair, voted across the warp
@@ -378,23 +443,24 @@ __device__ __forceinline__ Stokes4x2 resid_x2(const Geo<float> &g, const float2 
         } else if (l < nl) {
             const float2 id = f2(g.invD[l]);
             const float2 v = fma2(doff2[l], id, f2(g.cp[l]));
-            const float2 xb = fma2(doff2[l], id, f2(g.cp[l] + g.vB[l]));
-            const float2 xr = fma2(doff2[l], id, f2(g.cp[l] - g.vB[l]));
+            const float2 xb = add2(v, f2(g.vB[l]));
+            const float2 xr = sub2(v, f2(g.vB[l]));
             if (COUNT) {
                 count_pair(xb, g.a2, y_real, ncount);
                 count_pair(v, g.a2, y_real, ncount);
                 count_pair(xr, g.a2, y_real, ncount);
             }
-            const float2 q = lines[l].q2, qs = lines[l].qs2;
+            const float2 *wq = lines[l].wq2;
+            const float2 qs = lines[l].qs2;
             const int lev = triplet_level(v, g, l);
             if (lev == 3)
-                triplet_acc<3, FILL>(xb, v, xr, g, q, qs, P, Pim, Sb, Sbi, Sr, Sri, P0);
+                triplet_acc<3, FILL>(xb, v, xr, g, wq, qs, P, Pim, Sb, Sbi, Sr, Sri, P0);
             else if (lev == 2)
-                triplet_acc<2, FILL>(xb, v, xr, g, q, qs, P, Pim, Sb, Sbi, Sr, Sri, P0);
+                triplet_acc<2, FILL>(xb, v, xr, g, wq, qs, P, Pim, Sb, Sbi, Sr, Sri, P0);
             else if (lev == 1)
-                triplet_acc<1, FILL>(xb, v, xr, g, q, qs, P, Pim, Sb, Sbi, Sr, Sri, P0);
+                triplet_acc<1, FILL>(xb, v, xr, g, wq, qs, P, Pim, Sb, Sbi, Sr, Sri, P0);
             else
-                triplet_acc<0, FILL>(xb, v, xr, g, q, qs, P, Pim, Sb, Sbi, Sr, Sri, P0);
+                triplet_acc<0, FILL>(xb, v, xr, g, wq, qs, P, Pim, Sb, Sbi, Sr, Sri, P0);
         }
     }
     // the sigma sums and differences, once per point

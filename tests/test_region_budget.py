@@ -1,10 +1,11 @@
 """The FP32 pair path's w(z) regions keep their error budget.
 
 The region thresholds are read from the CUDA headers, each branch formula is
-evaluated in float32 (numpy, without fused multiply-adds, so a little
-pessimistic) beyond its threshold, and compared with scipy's wofz: the far
-field, the even (three-node) convergent of the outer shell, the 3rd
-convergent (in its s-form, FMAs kept) and the 5th convergent of the Laplace continued fraction
+evaluated in float32 (numpy; the far field, the even (three-node) convergent
+of the outer shell and the 3rd convergent in the pair path's s-forms with its
+fused multiply-adds kept, the others without them, which is a little
+pessimistic) beyond its threshold, and compared with scipy's wofz: those three
+and the 5th convergent of the Laplace continued fraction
 w = (i/sqrt(pi)) / (z - (1/2) / (z - 1 / (z - (3/2) / ...))) must stay within
 1.5e-7 absolute (1.3e-7 with the kernel's FMAs).  Moving a threshold
 inward past the budget fails here.  Weideman's series, the branch a mixed
@@ -68,34 +69,35 @@ def cf32(x, y, k):
     return ((nx * ay - ny * ax) * inv).astype(float) + 1j * ((nx * ax + ny * ay) * inv).astype(float)
 
 
-def far32(x, y):
-    """The far-field approximant (i/sqrt(pi)) z / (z^2 - 1/2) in float32, in the
-    pair path's algebraic form: y (s + 1/2) + i x (s - 1/2) over
-    s^2 - x^2 + y^2 + 1/4, s = x^2 + y^2."""
-    x, y = x.astype(f32), f32(y)
-    a2 = y * y
-    s = x * x + a2
-    qi = f32(0.56418958354775628695) * (f32(1) / (s * s + (-(x * x) + f32(a2 + 0.25))))
-    return (qi * (y * s + f32(0.5) * y)).astype(float) + 1j * (qi * (x * (s + f32(-0.5)))).astype(float)
-
-
-def even2_32(x, y):
-    """The outer shell's even convergent (i/sqrt(pi)) (z^2 - 1) / (z (z^2 - 3/2))
-    in float32, in the pair path's algebraic form: y P + i x (P - s) over
-    s (s^2 - 3 s + 6 y^2 + 9/4), P = s^2 - 1.5 s + 4 y^2 + 1.5."""
-    x, y = x.astype(f32), f32(y)
-    a2 = y * y
-    s = x * x + a2
-    pr = s * s + (f32(-1.5) * s + f32(4 * a2 + 1.5))
-    u = s * s + (f32(-3.0) * s + f32(6 * a2 + 2.25))
-    qi = f32(0.56418958354775628695) * (f32(1) / (s * u))
-    return (qi * (y * pr)).astype(float) + 1j * (qi * (x * (pr - s))).astype(float)
-
-
 def fma32(a, b, c):
     """A float32 fused multiply-add: the float64 product of two float32 values
     is exact, so one rounding of the float64 sum stands for the kernel's."""
     return (np.float64(a) * np.float64(b) + np.float64(c)).astype(f32)
+
+
+def far32(x, y):
+    """The far-field approximant (i/sqrt(pi)) z / (z^2 - 1/2) in float32, in the
+    pair path's algebraic form (FMAs kept): y (s + 1/2) + i x (s - 1/2) over
+    (s - 1/2)^2 + 2 y^2, s = x^2 + y^2, all in u = s - 1/2."""
+    x, y = x.astype(f32), f32(y)
+    a2 = f32(y * y)
+    u = fma32(x, x, a2 - f32(0.5))
+    qi = f32(0.56418958354775628695) * (f32(1) / fma32(u, u, f32(2) * a2))
+    return (qi * fma32(y, u, y)).astype(float) + 1j * (qi * (x * u)).astype(float)
+
+
+def even2_32(x, y):
+    """The outer shell's even convergent (i/sqrt(pi)) (z^2 - 1) / (z (z^2 - 3/2))
+    in float32, in the pair path's algebraic form (FMAs kept): y P + i x (P - s)
+    over s (m^2 + 6 y^2), P = m s + 4 y^2 + 1.5, m = s - 3/2."""
+    x, y = x.astype(f32), f32(y)
+    a2 = f32(y * y)
+    s = fma32(x, x, a2)
+    m = fma32(x, x, a2 - f32(1.5))
+    pr = fma32(m, s, f32(4) * a2 + f32(1.5))
+    u = fma32(m, m, f32(6) * a2)
+    qi = f32(0.56418958354775628695) * (f32(1) / (s * u))
+    return (qi * (y * pr)).astype(float) + 1j * (qi * (x * (pr - s))).astype(float)
 
 
 def cf3_s32(x, y):
