@@ -20,7 +20,7 @@ namespace {
 // evaluate inside a divergent branch, as the GA's restarts do, so the pair
 // path's votes run over exactly those lanes.
 template <class R, int NL, int MAXT, bool PAT, int M>
-__global__ void GENESIS_GA_BOUNDS(MAXT, R)
+__global__ void GENESIS_GA_BOUNDS(MAXT, R, NL, PAT)
 k_ga_fitness(const __grid_constant__ KProblem pb, int weight_mode, const R *__restrict__ obs,
              const double *__restrict__ w_user, const double *__restrict__ mu_px, int nactive,
              const double *__restrict__ params, double *__restrict__ fit, R *__restrict__ res)

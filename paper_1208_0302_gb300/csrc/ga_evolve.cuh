@@ -487,23 +487,29 @@ __device__ __forceinline__ void weight_obs_rows(R *s_obs, int nl, int k, const R
     }
 }
 
-// Register budget of the FP32 npop <= 256 instantiations: MAXT * GENESIS_GA_MINB
-// threads must fit an SM's 64K registers, which caps registers per thread
-// (more resident warps hide the FP32 pipe latency).  FP64 instantiations are
-// bound by the FP64 units and keep the compiler's register choice.
-#ifndef GENESIS_GA_MINB
-#define GENESIS_GA_MINB 3
+// Register budget per thread.  FP32 instantiations for npop <= 256 with one
+// or two effective-triplet lines: GENESIS_GA_NREG32 = 72, so that seven
+// 128-thread blocks fit an SM's 64K registers (more resident warps hide the
+// FP32 pipe's latency; a few bytes spill in the two-line form, whose launch
+// is still 0.5 % faster than six blocks at 80 registers).  The other FP32
+// ones for npop <= 256 (any line count, full patterns) keep 80, where they
+// spill less.  1024-thread instantiations: 64, so that a whole block fits.
+// FP64 ones are bound by the FP64 units and may use up to 255.
+#ifndef GENESIS_GA_NREG32
+#define GENESIS_GA_NREG32 72
 #endif
 // Build option: GENESIS_GA_MAXNREG=N caps every instantiation at N registers
-// per thread instead (for tuning the cap; the two qualifiers exclude each other).
+// per thread instead (for tuning the cap).
 #ifdef GENESIS_GA_MAXNREG
-#define GENESIS_GA_BOUNDS(MAXT, R) __maxnreg__(GENESIS_GA_MAXNREG)
+#define GENESIS_GA_BOUNDS(MAXT, R, NL, PAT) __maxnreg__(GENESIS_GA_MAXNREG)
 #else
-#define GENESIS_GA_BOUNDS(MAXT, R) __launch_bounds__(MAXT, ((MAXT) <= 256 && sizeof(R) == 4) ? GENESIS_GA_MINB : 1)
+#define GENESIS_GA_BOUNDS(MAXT, R, NL, PAT)                                                         \
+    __maxnreg__((MAXT) > 256 ? 65536 / (MAXT)                                                     \
+                             : (sizeof(R) == 4 ? ((NL) > 0 && !(PAT) ? GENESIS_GA_NREG32 : 80) : 255))
 #endif
 
 template <class R, int NL, int MAXT, bool COUNT, bool PAT, int M>
-__global__ void GENESIS_GA_BOUNDS(MAXT, R)
+__global__ void GENESIS_GA_BOUNDS(MAXT, R, NL, PAT)
 k_ga_evolve(const __grid_constant__ KProblem pb, const __grid_constant__ KGa ga,
             const R *__restrict__ obs, const double *__restrict__ w_user,
             const double *__restrict__ mu_px, int npix, double *__restrict__ best,
