@@ -161,7 +161,11 @@ k_vjp(const __grid_constant__ KProblem pb, const double *__restrict__ params,
 // FP64 chi-square (Eq. chisq) of given parameters, one block per pixel,
 // threads over wavelengths.  Inverse-max weights (Section 5.4) are formed in
 // FP64 from the observed values when w is NULL.
-template <class RO, bool FILL = false>
+// NL > 0 with PAT = false: problems with NL effective-triplet lines (the
+// loops over lines unrolled, the full-pattern code compiled out; the same
+// arithmetic in the same order as the generic form, 4.6 % faster on the
+// two-line map, where the pass is bound by the FP64 pipe).
+template <class RO, bool FILL = false, int NL = 0, bool PAT = true>
 __global__ void __launch_bounds__(kSynthBlock)
 k_chi2_f64(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
            const double *__restrict__ w_user, const double *__restrict__ mu_px, int npix,
@@ -218,7 +222,7 @@ k_chi2_f64(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
 #pragma unroll
         for (int d = 0; d < M; ++d) p[d] = params[(size_t)pix * M + d];
         const double mu = mu_px ? mu_px[pix] : pb.mu;
-        s_geo = make_geo<double, 0, FILL>(pb, nlines, p, mu);
+        s_geo = make_geo<double, NL, FILL>(pb, nlines, p, mu);
     }
     __syncthreads();
     const Geo<double> &g = s_geo;
@@ -230,7 +234,7 @@ k_chi2_f64(const __grid_constant__ KProblem pb, const RO *__restrict__ obs,
         double doff[ME_MAX_LINES];
 #pragma unroll
         for (int l = 0; l < ME_MAX_LINES; ++l) doff[l] = l < nlines ? pb.lam[j] - pb.line[l].lam0 : 0.0;
-        const Stokes4<double> s = me_point<double, 0, true, FILL>(g, doff, he, nlines, pb.line);
+        const Stokes4<double> s = me_point<double, NL, PAT, FILL>(g, doff, he, nlines, pb.line);
         const double r0 = (double)o[j] - s.I, r1 = (double)o[nl + j] - s.Q;
         const double r2 = (double)o[2 * nl + j] - s.U, r3 = (double)o[3 * nl + j] - s.V;
         ss[0] += r0 * r0;
@@ -413,6 +417,12 @@ cudaError_t launch_chi2_f64(const KProblem &pb, int dtype, const void *obs, cons
     if (dtype == ME_F32 && pb.fill)
         k_chi2_f64<float, true><<<npix, kSynthBlock, 0, st>>>(pb, (const float *)obs, w, mu_px, npix, params,
                                                               chi2, sub);
+    else if (dtype == ME_F32 && !has_pattern(pb) && pb.n_lines == 2)
+        k_chi2_f64<float, false, 2, false><<<npix, kSynthBlock, 0, st>>>(pb, (const float *)obs, w, mu_px, npix,
+                                                                        params, chi2, sub);
+    else if (dtype == ME_F32 && !has_pattern(pb) && pb.n_lines == 1)
+        k_chi2_f64<float, false, 1, false><<<npix, kSynthBlock, 0, st>>>(pb, (const float *)obs, w, mu_px, npix,
+                                                                        params, chi2, sub);
     else if (dtype == ME_F32)
         k_chi2_f64<float><<<npix, kSynthBlock, 0, st>>>(pb, (const float *)obs, w, mu_px, npix, params, chi2,
                                                         sub);
