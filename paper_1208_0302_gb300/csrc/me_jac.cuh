@@ -64,6 +64,47 @@ template <class R> struct Sums {
     R dP[4], dSg[4], dT[4], dTi[4], dDd[4], dDi[4];
 };
 
+// Near a line core the sigma-minus-pi combinations of a weakly split
+// effective triplet, T = w(v) - (w(v + d) + w(v - d)) / 2 and its
+// derivatives, lose their relative precision to cancellation in FP32 (about
+// 1e-7 / d^2 at d = v_B).  There they are formed instead from Taylor series
+// in d about the pi point z = v + i a:
+//   h  = (w(v+d) + w(v-d)) / 2 - w(v)    = sum_k d^2k / (2k)! w^(2k)(z),
+//   hp = (w'(v+d) + w'(v-d)) / 2 - w'(v) = sum_k d^2k / (2k)! w^(2k+1)(z),
+//   g1 = (w'(v+d) - w'(v-d)) / 2         = sum_k d^(2k-1) / (2k-1)! w^(2k)(z),
+// k = 1..5, with the derivatives of w from w^(n+1) = -2 z w^(n) - 2 n w^(n-1)
+// (the derivative of w' = -2 z w + 2i/sqrt(pi)).  The caller takes this form
+// for |d| <= 0.25 and |z|^2 <= 16, and for |d| <= 0.1 and |z|^2 <= 36: there the
+// recurrence loses at most a factor 2 |z|^2 / (n + 1) per step, which the
+// factors d^m / m! absorb (w'' itself to about 6e-8 (2/3) |z|^4 relative), and
+// the first omitted term is below 1e-8 of the sums.  w1 = w'(z).
+template <class R>
+__device__ __forceinline__ void split_series(R v, R a, R d, C2<R> w0, C2<R> w1, C2<R> &h, C2<R> &hp,
+                                             C2<R> &g1)
+{
+    C2<R> wm = w0, wc = w1;  // w^(n-1), w^(n)
+    R c = d;                 // d^n / n!
+    h = hp = g1 = C2<R>{R(0), R(0)};
+#pragma unroll
+    for (int n = 1; n <= 10; ++n) {
+        const C2<R> wn = {R(-2) * (v * wc.x - a * wc.y) - R(2 * n) * wm.x,
+                          R(-2) * (v * wc.y + a * wc.x) - R(2 * n) * wm.y};  // w^(n+1)
+        const R cn = c * d * R(1.0 / (n + 1));                                // d^(n+1) / (n+1)!
+        if ((n + 1) % 2 == 0) {
+            h.x += cn * wn.x;
+            h.y += cn * wn.y;
+            g1.x += c * wn.x;
+            g1.y += c * wn.y;
+        } else {
+            hp.x += c * wn.x;
+            hp.y += c * wn.y;
+        }
+        wm = wc;
+        wc = wn;
+        c = cn;
+    }
+}
+
 // Stokes vector and J[s][k] = d Stokes_s / d p_k at one wavelength.
 // FILL: Section 5.2 fill fraction, p[9] = alpha, J has a 10th column.
 template <class R, int NL, bool FILL = false>
@@ -87,6 +128,9 @@ __device__ __forceinline__ void me_point_jac(const GeoJ<R> &G, const R *doff, co
             const R q = half_eta[l];
             C2<R> w[3], wd[3][4];
             const R sv = -G.kv[l];
+            // T + i Ti of this line and its derivatives, when the series form applies
+            C2<R> tc{R(0), R(0)}, dtc[4];
+            bool series = false;
             if (lines[l].ncomp[0] == 0) {
                 const R xs[3] = {doff[l] * g.invD[l] + (g.cp[l] + g.vB[l]),  // blue
                                  doff[l] * g.invD[l] + g.cp[l],              // pi
@@ -103,6 +147,23 @@ __device__ __forceinline__ void me_point_jac(const GeoJ<R> &G, const R *doff, co
                     wd[c][1] = {dx * sv, dy * sv};   // d/dv_LOS
                     wd[c][2] = {dx * sD, dy * sD};   // d/dD
                     wd[c][3] = {-dy, dx};            // d/da = i w'
+                }
+                if constexpr (sizeof(R) == 4) {
+                    // a weakly split triplet near its core: T and its
+                    // derivatives without the cancellation of the three
+                    // profiles (split_series)
+                    const R v = xs[1], d = g.vB[l], ad = fabs(d), r2 = v * v + g.a2;
+                    if ((ad <= R(0.25) && r2 <= R(16)) || (ad <= R(0.1) && r2 <= FadCfg<R>::R2)) {
+                        C2<R> h, hp, g1;
+                        split_series<R>(v, g.a, d, w[1], C2<R>{wd[1][3].y, -wd[1][3].x}, h, hp, g1);
+                        tc = C2<R>{-h.x, -h.y};
+                        dtc[0] = C2<R>{-G.kB[l] * g1.x, -G.kB[l] * g1.y};               // d/dB
+                        dtc[1] = C2<R>{-sv * hp.x, -sv * hp.y};                         // d/dv_LOS
+                        dtc[2] = C2<R>{G.invDpar * (v * hp.x + d * g1.x),
+                                       G.invDpar * (v * hp.y + d * g1.y)};              // d/dD
+                        dtc[3] = C2<R>{hp.y, -hp.x};                                    // d/da
+                        series = true;
+                    }
                 }
                 if (FILL) {  // the pi component is unshifted
                     P0 += q * w[1].x;
@@ -149,8 +210,8 @@ __device__ __forceinline__ void me_point_jac(const GeoJ<R> &G, const R *doff, co
             const R sx = w[0].x + w[2].x, sy = w[0].y + w[2].y;
             S.P += q * w[1].x;
             S.Sg += q * sx;
-            S.T += q * (w[1].x - R(0.5) * sx);
-            S.Ti += q * (w[1].y - R(0.5) * sy);
+            S.T += q * (series ? tc.x : w[1].x - R(0.5) * sx);
+            S.Ti += q * (series ? tc.y : w[1].y - R(0.5) * sy);
             S.Dd += q * (w[2].x - w[0].x);
             S.Di += q * (w[2].y - w[0].y);
 #pragma unroll
@@ -158,8 +219,8 @@ __device__ __forceinline__ void me_point_jac(const GeoJ<R> &G, const R *doff, co
                 const R bx = wd[0][d].x + wd[2][d].x, by = wd[0][d].y + wd[2][d].y;
                 S.dP[d] += q * wd[1][d].x;
                 S.dSg[d] += q * bx;
-                S.dT[d] += q * (wd[1][d].x - R(0.5) * bx);
-                S.dTi[d] += q * (wd[1][d].y - R(0.5) * by);
+                S.dT[d] += q * (series ? dtc[d].x : wd[1][d].x - R(0.5) * bx);
+                S.dTi[d] += q * (series ? dtc[d].y : wd[1][d].y - R(0.5) * by);
                 S.dDd[d] += q * (wd[2][d].x - wd[0][d].x);
                 S.dDi[d] += q * (wd[2][d].y - wd[0][d].y);
             }

@@ -33,12 +33,16 @@ def test_adjoint_against_central_differences_1000_vectors(gpu, orc):
     * The differences are a sound reference: they agree with the oracle's
       Richardson-extrapolated Jacobian to 1e-5 of the floored scale.
     * FP32: within 2e-4 for every vector with B >= 100 G.  Below 100 G the
-      linear polarization scales as B^2 and its FP32 value, formed from
-      T = P - (phi_b + phi_r) / 2 where the three profiles nearly cancel,
-      keeps a relative precision of about 1e-7 / v_B^2; the azimuth column
-      (d(Q, U)/dchi = 2 pi / 180 (-U, Q)) inherits it, so those vectors are held
-      to 1e-3 (measured: 1.95e-4 at B >= 100 G, 8.9e-4 below; the median
-      over vectors of their worst column is 5.2e-5).
+      linear polarization scales as B^2 and the azimuth column,
+      d(Q, U)/dchi = (pi / 90) (-U, Q), falls below the floor; 2e-4 of the
+      floor would ask for Q and U to about 3e-8 I_c, under the FP32
+      resolution of I_c itself (the FP32 Q and U in the line wings differ
+      from the oracle's by about 1e-7 I_c).  Near the line cores the
+      Jacobian forms T = P - (phi_b + phi_r) / 2 from a Taylor series in v_B
+      rather than from the nearly cancelling profiles, so those vectors are
+      held to 8e-4 (measured: 1.95e-4 at B >= 100 G, 6.2e-4 below, 8.9e-4
+      before the series form; the median over vectors of their worst column
+      is 5.1e-5).
     * FP64: within 2e-7 against the Richardson Jacobian (measured 6.9e-8)."""
     spec = gi.two_line_spec()
     P = gi.draw_params_uniform(1000, seed=3)
@@ -65,7 +69,7 @@ def test_adjoint_against_central_differences_1000_vectors(gpu, orc):
     e32 = err(jac, fd)
     strong = P[:, 0] >= 100.0
     assert e32[strong].max() < 2e-4, (float(e32[strong].max()), int(np.argmax(np.where(strong, e32, 0))))
-    assert e32.max() < 1e-3, float(e32.max())
+    assert e32.max() < 8e-4, float(e32.max())
     assert np.median(e32) < 1e-4
     assert err(jac64, rich).max() < 2e-7
 
