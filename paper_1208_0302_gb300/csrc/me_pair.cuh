@@ -401,9 +401,9 @@ __device__ __forceinline__ int triplet_level(float2 v, const Geo<float> &g, int 
 // 5 and the difference of Eq. chisq).  doff2[l] holds (lambda_j -
 // lambda0_l, lambda_{j+1} - lambda0_l); op points at the pair's staged
 // observed values (I, I', Q, Q', U, U', V, V' in shared memory), read only
-// where the residuals are formed.  An effective triplet's strength q and
-// q / sqrt(pi) come from the kernel parameters (lines[l].q2, qs2), so they
-// are constant-bank operands.  FILL mixes in the field-free
+// where the residuals are formed.  An effective triplet's q / sqrt(pi) and
+// its series coefficients scaled by q come from the kernel parameters
+// (lines[l].qs2, wq2), so they are constant-bank operands.  FILL mixes in the field-free
 // profile with the fill fraction (Section 5.2, see fill_mix).  kc points at
 // the individual's shared-memory slots (stride nt float4): (kIs, kIp, kIp2,
 // kV2), (muS1, S0, kQ, kUV), (kU, kQV, kV, w_I), the last three weighted as
