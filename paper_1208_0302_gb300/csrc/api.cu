@@ -172,7 +172,6 @@ int make_problem(const me_problem *pb, KProblem &k)
         k.line[l].dscale = 1e-3 * ln.lambda0_A / pb->lambda_dop_A;
         k.line[l].zfac = kZeeman * ln.g_eff * ln.lambda0_A * ln.lambda0_A;
         k.line[l].half_eta = 0.5 * ln.eta_ratio;
-        k.line[l].q2 = make_float2((float)k.line[l].half_eta, (float)k.line[l].half_eta);
         k.line[l].qs2 = make_float2((float)(k.line[l].half_eta * 0.56418958354775628695),
                                     (float)(k.line[l].half_eta * 0.56418958354775628695));
         {

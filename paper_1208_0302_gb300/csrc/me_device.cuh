@@ -30,7 +30,7 @@ struct KLine {
     double cstr[3][ME_MAX_COMP];    // component strengths (sum 1 per group)
     float cshift32[3][ME_MAX_COMP];
     float cstr32[3][ME_MAX_COMP];
-    float2 q2, qs2;    // FP32 pair path: (half_eta, half_eta) and the same / sqrt(pi)
+    float2 qs2;        // FP32 pair path: half_eta / sqrt(pi) in both lanes
     float2 wq2[17];    // FP32 pair path: Weideman coefficients 2 a_n times half_eta, in both lanes
 };
 
