@@ -46,11 +46,11 @@ E2E_STEPS_MAX = 5   # the end-to-end leg repeats at most this many steps
 NPOP, NGEN, LM_ITERS = 128, 200, 10
 KERNELS_PER_STEP = 4  # GA evolve, FP64 chi2, L-M, FP64 chi2
 # DRAM bytes (read + write) per pixel of one GA launch, from an ncu capture of
-# k_ga_evolve on the 4096-pixel two-line case (dram__bytes_read.sum 8533504 +
+# k_ga_evolve on the 4096-pixel two-line case (dram__bytes_read.sum 8580608 +
 # dram__bytes_write.sum 0, divided by 4096; traffic grows in proportion to
 # pixels: each block reads its pixel's cube row once).  Set to None whenever
 # the kernel changes, until it is captured again.
-GA_DRAM_BYTES_PER_PIXEL = 2083.38
+GA_DRAM_BYTES_PER_PIXEL = 2094.88
 
 
 def parse():
