@@ -21,9 +21,12 @@
  * quadrature, the a->0 closed forms and scipy.special.wofz; the closed-form ME
  * solution against a direct 4x4 solve; physics invariants (B=0, theta=0/90,
  * azimuth flips, weak-field limit); Philox against triton's independent
- * implementation; Sobol dimensions 0-1 against scipy and the (0,m,1)-net
- * property of every dimension; the GA operators on hand-built bit patterns and
- * a brute-force search; the L-M polish on noiseless truth.
+ * implementation; Sobol dimensions 0-1 against scipy, the (0,m,1)-net
+ * property of every dimension, and each dimension's direction numbers against
+ * the recurrence of its primitive polynomial (the primitive polynomials over
+ * GF(2) in degree-then-encoding order, checked by their order); the GA
+ * operators on hand-built bit patterns and a brute-force search; the L-M
+ * polish on noiseless truth.
  */
 #ifndef GENESIS_ORACLE_H
 #define GENESIS_ORACLE_H
