@@ -96,6 +96,21 @@ def one_line_spec(n_lambda=64, lo=6302.0, hi=6303.0) -> ProblemSpec:
                        lambda_grid=np.linspace(lo, hi, n_lambda))
 
 
+# Table 1's lines with their levels for the full Zeeman pattern: (lambda0,
+# g_eff, eta_ratio, J_lower, g_lower, J_upper, g_upper); Fe I 6301.5 is
+# 5P2 - 5D2 (LS Lande factors 11/6 and 3/2), Fe I 6302.5 5P1 - 5D0.
+def fe6301_full_line():
+    return (FE6301[0], FE6301[1], eta_ratio_6301(), 2, 11.0 / 6.0, 2, 1.5)
+
+
+def two_line_pattern_spec(n_lambda=128, lo=6301.0, hi=6303.0) -> ProblemSpec:
+    """The two-line grid with Fe I 6301.5 as its full Zeeman pattern (four
+    components per sigma_b, pi, sigma_r group) and 6302.5 as its normal
+    triplet."""
+    return ProblemSpec(lines=[fe6301_full_line(), (FE6302[0], FE6302[1], 1.0)],
+                       lambda_grid=np.linspace(lo, hi, n_lambda))
+
+
 def two_line_spec(n_lambda=128, lo=6301.0, hi=6303.0) -> ProblemSpec:
     return ProblemSpec(lines=[(FE6301[0], FE6301[1], eta_ratio_6301()),
                               (FE6302[0], FE6302[1], 1.0)],
