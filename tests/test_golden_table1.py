@@ -70,3 +70,17 @@ def test_inputs_use_the_printed_table():
     for const in (gi.FE6301, gi.FE6302):
         lam, _, _, geff, chi, loggf = rows[const[0]]
         assert (const[1], const[2], const[3]) == (geff, chi, loggf)
+
+
+def test_full_pattern_input_uses_the_printed_terms():
+    """The full-pattern input line of 6301.5 carries the levels of Table 1's
+    printed transition (J and the LS Lande factors formed from the term
+    symbols above), its printed g_eff and wavelength."""
+    rows = {r[0]: r for r in _rows()}
+    lam, lo, up, geff, _, _ = rows[6301.5091]
+    jl, gl = _term(lo)
+    ju, gu = _term(up)
+    line = gi.two_line_pattern_spec().lines[0]
+    assert line[0] == lam and line[1] == geff and line[2] == gi.eta_ratio_6301()
+    assert line[3] == jl and line[5] == ju
+    assert abs(line[4] - gl) < 1e-15 and abs(line[6] - gu) < 1e-15
